@@ -1,0 +1,136 @@
+"""FP64 CPU oracle for the sparse LDL^T / solve / diag(N^-1) path.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product path never imports this
+package.  The arithmetic lives in spi_oracle.c (plain C, natural ordering,
+left-looking LDL^T, column-by-column inverse diagonal; paper Sec. 3.2 and
+Sec. 4.3); this module only compiles it and marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spi_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+ORACLE_OK, ORACLE_ERR_ARG, ORACLE_ERR_NOT_SPD, ORACLE_ERR_OOM = 0, 1, 2, 3
+
+
+class NotSPD(RuntimeError):
+    def __init__(self, col: int):
+        super().__init__(f"non-positive pivot at column {col}")
+        self.col = col
+
+
+def build(force: bool = False) -> str:
+    """Compile spi_oracle.c into liboracle.so next to it (gcc, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load_library(path: str):
+    """Open a compiled oracle library and declare its C signatures."""
+    lib = ctypes.CDLL(path)
+    P, I64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.oracle_ldlt.argtypes = [I64, P, P, P, ctypes.POINTER(P), ctypes.POINTER(I64)]
+    lib.oracle_ldlt.restype = ctypes.c_int
+    lib.oracle_n.argtypes = [P]; lib.oracle_n.restype = I64
+    lib.oracle_nnz_l.argtypes = [P]; lib.oracle_nnz_l.restype = I64
+    lib.oracle_flops.argtypes = [P]; lib.oracle_flops.restype = D
+    lib.oracle_get.argtypes = [P, P, P, P, P, P]; lib.oracle_get.restype = None
+    lib.oracle_solve.argtypes = [P, P, P]; lib.oracle_solve.restype = None
+    lib.oracle_inv_diag.argtypes = [P, P, I64, P, ctypes.c_int]
+    lib.oracle_inv_diag.restype = ctypes.c_int
+    lib.oracle_inv_diag_flops.argtypes = [P, P, I64]
+    lib.oracle_inv_diag_flops.restype = D
+    lib.oracle_free.argtypes = [P]; lib.oracle_free.restype = None
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleFactor:
+    """A = L D L^T of a symmetric matrix given by its lower CSC (natural order)."""
+
+    def __init__(self, n, colptr, rowind, values, lib=None):
+        lib = _load() if lib is None else lib
+        self._lib = lib
+        self._cp = np.ascontiguousarray(colptr, dtype=np.int64)
+        self._ri = np.ascontiguousarray(rowind, dtype=np.int32)
+        self._va = np.ascontiguousarray(values, dtype=np.float64)
+        h = ctypes.c_void_p()
+        bad = ctypes.c_int64(-1)
+        rc = lib.oracle_ldlt(int(n), _ptr(self._cp), _ptr(self._ri), _ptr(self._va),
+                             ctypes.byref(h), ctypes.byref(bad))
+        if rc == ORACLE_ERR_NOT_SPD:
+            raise NotSPD(bad.value)
+        if rc != ORACLE_OK:
+            raise RuntimeError(f"oracle_ldlt failed with code {rc}")
+        self._h = h
+        self.n = int(n)
+
+    @classmethod
+    def from_problem(cls, pb, lib=None):
+        return cls(pb.n, pb.colptr, pb.rowind, pb.values, lib=lib)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None:
+            self._lib.oracle_free(h)
+            self._h = None
+
+    @property
+    def nnz_l(self) -> int:
+        return int(self._lib.oracle_nnz_l(self._h))
+
+    @property
+    def flops(self) -> float:
+        return float(self._lib.oracle_flops(self._h))
+
+    def factors(self):
+        """(Lp, Li, Lx, D, parent): strictly-lower L in CSC, D, elimination tree."""
+        nz = self.nnz_l
+        Lp = np.empty(self.n + 1, np.int64); Li = np.empty(nz, np.int32)
+        Lx = np.empty(nz, np.float64); D = np.empty(self.n, np.float64)
+        par = np.empty(self.n, np.int32)
+        self._lib.oracle_get(self._h, _ptr(Lp), _ptr(Li), _ptr(Lx), _ptr(D), _ptr(par))
+        return Lp, Li, Lx, D, par
+
+    def solve(self, b) -> np.ndarray:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        self._lib.oracle_solve(self._h, _ptr(b), _ptr(x))
+        return x
+
+    def inv_diag(self, idx=None, nthreads: int | None = None) -> np.ndarray:
+        """(A^-1)_ii for i in idx (all i if None)."""
+        idx = np.arange(self.n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
+        out = np.empty(len(idx), np.float64)
+        nt = nthreads if nthreads is not None else (os.cpu_count() or 1)
+        rc = self._lib.oracle_inv_diag(self._h, _ptr(idx), len(idx), _ptr(out), int(nt))
+        if rc != ORACLE_OK:
+            raise RuntimeError(f"oracle_inv_diag failed with code {rc}")
+        return out
+
+    def inv_diag_flops(self, idx=None) -> float:
+        idx = np.arange(self.n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
+        return float(self._lib.oracle_inv_diag_flops(self._h, _ptr(idx), len(idx)))

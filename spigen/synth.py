@@ -1,0 +1,297 @@
+"""Seeded synthetic INTEGRAL/SPI-like least-squares problems.
+
+This module is the input generator shared by the tests, the benchmark and the
+oracle's callers.  It builds the design matrix H of the SPI sky-plus-background
+model and hands out the normal matrix N = H^T W H and right-hand side
+b = H^T W y as plain arrays.  It holds none of the arithmetic of the method
+under test (no factorization, no triangular solve, no inverse entry).
+
+Model (paper Sec. 2.2.3):
+  * rows are (pointing p, detector d) pairs, M = n_p * n_d (Eq. 1, Eq. 4);
+  * background, Eq. 2: one normalisation column per pointing and a set of
+    detector-pattern columns per block of pointings;
+  * each point source J is split into K_J contiguous time-bins (Box I), one
+    column per bin, so N = sum_J K_J unknowns;
+  * counts are Poisson, sigma_i^2 = y_i (Sec. 2.4.1), W = 1 / max(y, 1);
+  * normal equations (H^T Sigma^-2 H) x = H^T Sigma^-2 y (Eq. 7).
+
+Readings where the paper is silent (stated once here, fixed for all configs):
+  * pointings cycle a 5x5 dither raster (step 2 deg) about the field centre
+    (0, 0); a source is visible from a pointing when their great-circle
+    distance is below 15 deg;
+  * response R(d, source, dither position) ~ U(0.1, 1), drawn from a
+    counter-based SplitMix64 hash so that no table has to be stored;
+  * pointing-column entries u_d * g_dp and detector-column entries h_dp with
+    g, h ~ U(0.8, 1.2) drawn independently per (d, p): entries u_d * t_dp and
+    t_dp for both would make N exactly singular (sum over d of u_d times the
+    detector columns equals the sum of the block's pointing columns);
+  * time-bin lengths are log-uniform integers in [lo, hi]; the last bin is
+    cut at n_p and a remainder shorter than lo is merged into the previous
+    bin; bins in which the source is never visible are dropped (a zero column
+    would make N singular);
+  * true intensities: pointing normalisations U(0.9, 1.1), detector-pattern
+    amplitudes U(0, 5), source fluxes U(0, 20) per bin; per-detector
+    background means u_d ~ U(50, 200).
+Column order: [pointings; detector-pattern columns (block-major);
+time-bins sorted by (start, source)].
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+N_DET = 19
+_DITHER = 5  # 5x5 raster
+
+
+@dataclasses.dataclass(frozen=True)
+class SpiConfig:
+    name: str
+    n_pointings: int
+    n_sources: int
+    bin_lo: int
+    bin_hi: int
+    det_block: int          # pointings per detector-pattern block
+    field_deg: float = 40.0  # sources uniform in [-field/2, field/2]^2
+    fov_deg: float = 15.0
+    dither_step: float = 2.0
+    seed: int = 0
+
+
+# The workloads: a tiny one the oracle finishes in seconds, and the FP64
+# baseline at scale.
+TINY = SpiConfig("spi-tiny-P300", n_pointings=300, n_sources=40, bin_lo=10,
+                 bin_hi=300, det_block=100)
+SCALE = SpiConfig("spi-P20000", n_pointings=20000, n_sources=500, bin_lo=20,
+                  bin_hi=2000, det_block=500)
+# Same-pattern energy-band member (one band); bands rescale values only.
+BAND = SpiConfig("spi-band-P5000", n_pointings=5000, n_sources=200, bin_lo=10,
+                 bin_hi=1000, det_block=500)
+
+
+def uneven_config(index: int) -> SpiConfig:
+    """Member `index` of the uneven independent batch: P log-uniform in
+    [50, 2000], n_s = max(5, round(P/10)), seed = index."""
+    rng = np.random.default_rng(1_000_003 + index)
+    P = int(round(math.exp(rng.uniform(math.log(50), math.log(2000)))))
+    ns = max(5, int(round(P / 10)))
+    lo = max(5, P // 40)
+    return SpiConfig(f"spi-uneven-{index}", n_pointings=P, n_sources=ns,
+                     bin_lo=lo, bin_hi=max(lo + 1, P // 2),
+                     det_block=max(25, P // 4), seed=index)
+
+
+def scaled(cfg: SpiConfig, n_pointings: int, n_sources: int | None = None,
+           seed: int | None = None) -> SpiConfig:
+    """A smaller member of the same family (for parity tests)."""
+    r = n_pointings / cfg.n_pointings
+    ns = n_sources if n_sources is not None else max(5, int(round(cfg.n_sources * r)))
+    return dataclasses.replace(
+        cfg, name=f"{cfg.name}-P{n_pointings}", n_pointings=n_pointings,
+        n_sources=ns, bin_lo=max(5, int(round(cfg.bin_lo * r))),
+        bin_hi=max(10, int(round(cfg.bin_hi * r))),
+        det_block=max(25, int(round(cfg.det_block * r))),
+        seed=cfg.seed if seed is None else seed)
+
+
+# --------------------------------------------------------------------------
+# counter-based uniform numbers (SplitMix64 finaliser), vectorised
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _splitmix_u01(key: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = key.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def _response(seed: int, src: np.ndarray, q: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """R(d, source, dither position) ~ U(0.1, 1)."""
+    with np.errstate(over="ignore"):
+        key = (np.uint64(seed) * np.uint64(0x100000001B3)
+               + src.astype(np.uint64) * np.uint64(1 << 20)
+               + q.astype(np.uint64) * np.uint64(64) + d.astype(np.uint64))
+    return 0.1 + 0.9 * _splitmix_u01(key)
+
+
+def _angdist_deg(lon1, lat1, lon2, lat2):
+    l1, b1, l2, b2 = (np.radians(v) for v in (lon1, lat1, lon2, lat2))
+    s = (np.sin((b2 - b1) / 2) ** 2
+         + np.cos(b1) * np.cos(b2) * np.sin((l2 - l1) / 2) ** 2)
+    return np.degrees(2 * np.arcsin(np.sqrt(np.clip(s, 0.0, 1.0))))
+
+
+@dataclasses.dataclass
+class SpiProblem:
+    """One least-squares problem.  N is given as its lower triangle in CSC
+    (0-based, rows sorted, diagonal present), the layout the solver takes."""
+    cfg: SpiConfig
+    n: int
+    colptr: np.ndarray   # int64 [n+1]
+    rowind: np.ndarray   # int32 [nnz]
+    values: np.ndarray   # float64 [nnz]
+    b: np.ndarray        # float64 [n]
+    x_true: np.ndarray   # float64 [n]
+    kind: np.ndarray     # int8 [n]: 0 pointing, 1 detector pattern, 2 time-bin
+    n_pointing: int
+    n_detcol: int
+    n_bins: int
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colptr[-1])
+
+    def full_matrix(self) -> sp.csc_matrix:
+        """Symmetric N as a scipy matrix (for tests)."""
+        low = sp.csc_matrix((self.values, self.rowind, self.colptr), shape=(self.n, self.n))
+        return (low + sp.tril(low, -1).T).tocsc()
+
+
+def _bins_for_sources(rng, cfg: SpiConfig):
+    P = cfg.n_pointings
+    lo, hi = cfg.bin_lo, cfg.bin_hi
+    starts, ends, srcs = [], [], []
+    for s in range(cfg.n_sources):
+        edges = [0]
+        while edges[-1] < P:
+            L = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+            edges.append(min(P, edges[-1] + max(1, L)))
+        if len(edges) > 2 and edges[-1] - edges[-2] < lo:
+            edges.pop(-2)
+        for a, b in zip(edges[:-1], edges[1:]):
+            starts.append(a); ends.append(b); srcs.append(s)
+    return np.array(starts), np.array(ends), np.array(srcs)
+
+
+def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
+             band_scale: np.ndarray | None = None, counts_seed: int | None = None) -> SpiProblem:
+    """Build the problem for `cfg`.
+
+    noise=False replaces the Poisson draw by y = H x_true exactly (the
+    noise-free case whose least-squares solution is x_true).  band_scale, if
+    given (one factor per source), rescales every response value of that
+    source (energy-band members share one pattern); counts_seed reseeds only
+    the Poisson draw.
+    """
+    rng = np.random.default_rng(cfg.seed)
+    P, nd = cfg.n_pointings, N_DET
+    half = cfg.field_deg / 2
+    src_lon = rng.uniform(-half, half, cfg.n_sources)
+    src_lat = rng.uniform(-half, half, cfg.n_sources)
+    u_d = rng.uniform(50.0, 200.0, nd)
+    g = rng.uniform(0.8, 1.2, (P, nd))
+    h = rng.uniform(0.8, 1.2, (P, nd))
+    starts, ends, srcs = _bins_for_sources(rng, cfg)
+    # dither raster
+    qpos = np.arange(_DITHER * _DITHER)
+    dlon = ((qpos % _DITHER) - _DITHER // 2) * cfg.dither_step
+    dlat = ((qpos // _DITHER) - _DITHER // 2) * cfg.dither_step
+    vis = _angdist_deg(src_lon[:, None], src_lat[:, None], dlon[None, :], dlat[None, :]) < cfg.fov_deg
+    qofp = np.arange(P) % (_DITHER * _DITHER)
+    # keep bins with at least one visible pointing
+    keep = np.zeros(len(starts), bool)
+    for i, (a, b_, s) in enumerate(zip(starts, ends, srcs)):
+        qs = np.unique(qofp[a:b_]) if b_ - a < 25 else qpos
+        keep[i] = bool(vis[s, qs].any())
+    starts, ends, srcs = starts[keep], ends[keep], srcs[keep]
+    order = np.lexsort((srcs, starts))
+    starts, ends, srcs = starts[order], ends[order], srcs[order]
+    nbins = len(starts)
+    nblk = (P + cfg.det_block - 1) // cfg.det_block
+    ndet = nblk * nd
+    n = P + ndet + nbins
+    col_bin0 = P + ndet
+    x_true = np.concatenate([rng.uniform(0.9, 1.1, P), rng.uniform(0.0, 5.0, ndet),
+                             rng.uniform(0.0, 20.0, nbins)])
+    kind = np.concatenate([np.zeros(P, np.int8), np.ones(ndet, np.int8), np.full(nbins, 2, np.int8)])
+    scale = np.ones(cfg.n_sources) if band_scale is None else np.asarray(band_scale, float)
+
+    def window_block(p0: int, p1: int):
+        """Dense H restricted to rows of pointings [p0, p1) and the columns
+        active there; returns (global column ids, H_w)."""
+        np_ = p1 - p0
+        kb0, kb1 = p0 // cfg.det_block, (p1 - 1) // cfg.det_block + 1
+        act = np.nonzero((starts < p1) & (ends > p0))[0]
+        cols = np.concatenate([np.arange(p0, p1),
+                               P + np.arange(kb0 * nd, kb1 * nd),
+                               col_bin0 + act])
+        Hw = np.zeros((np_ * nd, len(cols)))
+        pp = np.arange(p0, p1)
+        rows = (pp - p0)[:, None] * nd + np.arange(nd)[None, :]
+        Hw[rows, (pp - p0)[:, None]] = u_d[None, :] * g[p0:p1]
+        detc = np_ + ((pp // cfg.det_block) - kb0)[:, None] * nd + np.arange(nd)[None, :]
+        Hw[rows, detc] = h[p0:p1]
+        if len(act):
+            a = np.maximum(starts[act], p0); b_ = np.minimum(ends[act], p1)
+            cnt = b_ - a
+            bi = np.repeat(np.arange(len(act)), cnt)
+            off = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+            p = np.repeat(a, cnt) + off
+            s = srcs[act][bi]
+            q = qofp[p]
+            ok = vis[s, q]
+            p, s, q, bi = p[ok], s[ok], q[ok], bi[ok]
+            dd = np.arange(nd)
+            R = _response(cfg.seed, s[:, None], q[:, None], dd[None, :]) * scale[s][:, None]
+            r = (p - p0)[:, None] * nd + dd[None, :]
+            Hw[r, (np_ + (kb1 - kb0) * nd + bi)[:, None]] = R
+        return cols, Hw
+
+    # pass 1: expected counts, Poisson draw (one global draw, window independent)
+    e = np.empty(P * nd)
+    for p0 in range(0, P, window):
+        p1 = min(P, p0 + window)
+        cols, Hw = window_block(p0, p1)
+        e[p0 * nd:p1 * nd] = Hw @ x_true[cols]
+    if noise:
+        crng = rng if counts_seed is None else np.random.default_rng(counts_seed)
+        y = crng.poisson(e).astype(np.float64)
+        w = 1.0 / np.maximum(y, 1.0)
+    else:
+        y = e.copy()
+        w = 1.0 / np.maximum(np.round(e), 1.0)
+    # pass 2: N = H^T W H (lower triangle) and b = H^T W y
+    rr, cc, vv = [], [], []
+    bvec = np.zeros(n)
+    for p0 in range(0, P, window):
+        p1 = min(P, p0 + window)
+        cols, Hw = window_block(p0, p1)
+        ww = w[p0 * nd:p1 * nd]
+        G = Hw.T @ (Hw * ww[:, None])
+        bvec[cols] += Hw.T @ (ww * y[p0 * nd:p1 * nd])
+        gi, gj = np.nonzero(np.tril(np.ones_like(G, dtype=bool)) & (G != 0.0))
+        ri, cj = cols[gi], cols[gj]
+        sw = ri < cj
+        ri2 = np.where(sw, cj, ri); cj2 = np.where(sw, ri, cj)
+        rr.append(ri2); cc.append(cj2); vv.append(G[gi, gj])
+    rr = np.concatenate(rr); cc = np.concatenate(cc); vv = np.concatenate(vv)
+    low = sp.coo_matrix((vv, (rr, cc)), shape=(n, n)).tocsc()
+    low.sum_duplicates()
+    low.sort_indices()
+    return SpiProblem(cfg=cfg, n=n, colptr=low.indptr.astype(np.int64),
+                      rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
+                      b=bvec, x_true=x_true, kind=kind, n_pointing=P, n_detcol=ndet, n_bins=nbins)
+
+
+def random_spd(n: int, density: float, seed: int, *, dominance: float = 1.0) -> SpiProblem:
+    """A random sparse SPD matrix (B^T B + shift) of order n, lower CSC, for
+    small generic tests; not SPI shaped."""
+    rng = np.random.default_rng(seed)
+    m = max(n, int(1.5 * n))
+    B = sp.random(m, n, density=density, random_state=rng, format="csc")
+    B.data = rng.uniform(0.5, 1.5, B.nnz)
+    A = (B.T @ B).tocsc() + dominance * sp.identity(n, format="csc")
+    low = sp.tril(A).tocsc()
+    low.sum_duplicates(); low.sort_indices()
+    b = rng.standard_normal(n)
+    cfg = SpiConfig(f"random-spd-{n}-{seed}", 0, 0, 1, 1, 1, seed=seed)
+    return SpiProblem(cfg=cfg, n=n, colptr=low.indptr.astype(np.int64),
+                      rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
+                      b=b, x_true=np.zeros(n), kind=np.full(n, 2, np.int8),
+                      n_pointing=0, n_detcol=0, n_bins=n)

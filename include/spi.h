@@ -1,0 +1,167 @@
+/*
+ * spi.h -- C ABI of the GB300 sparse LDL^T / variance library.
+ *
+ * The library solves the weighted least-squares normal equations
+ * N x = b, N = H^T W H (paper Sec. 2.4.1, Eq. 7), and returns the variances
+ * diag(N^-1) (Eq. 8) without forming N^-1.  It follows the three phases of a
+ * sparse direct solver (Sec. 3.2): analysis (ordering, elimination tree,
+ * symbolic factorization), numerical factorization (multifrontal, in
+ * postorder, Sec. 3.2.2) and solution (Sec. 3.2.3), plus the selected-
+ * inverse step of Sec. 3.3.1: (N^-1)_ii = || D^-1/2 L^-1 e_i ||^2 computed
+ * by forward solves pruned to the elimination-tree path i -> root, with the
+ * right-hand sides grouped in blocks (Sec. 3.3.1, last paragraph).
+ *
+ * Conventions for every call:
+ *   - Indices are 0-based and refer to the caller's (unpermuted) numbering.
+ *   - Return value: SPI_OK (0) or one of the spi_status codes below; the
+ *     message for a code is spi_strerror(code).  On error no output buffer is
+ *     guaranteed to hold meaningful data.
+ *   - Pointers passed in are borrowed for the duration of the call only; the
+ *     library keeps no caller pointer.  Host pointers are ordinary CPU memory;
+ *     device pointers are CUDA global memory of the context's device.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it; every call returns after checking the device
+ *     status word, i.e. after the stream has drained, unless the context was
+ *     created with spi_options.async = 1 (then only the final call of a
+ *     sequence reports device-side errors; see spi_sync).
+ *   - The numeric path runs only in this library's CUDA kernels (sm_103a);
+ *     there is no CPU fallback.  Without a usable GPU, calls that need one
+ *     return SPI_ERR_CUDA.
+ */
+#ifndef SPI_H
+#define SPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spi_status {
+    SPI_OK = 0,
+    SPI_ERR_ARG = 1,      /* NULL pointer, negative size, index out of range, bad option */
+    SPI_ERR_PATTERN = 2,  /* pattern not lower CSC with sorted rows, no duplicate, full diagonal */
+    SPI_ERR_NOT_SPD = 3,  /* non-positive pivot; spi_info().bad_pivot holds the column */
+    SPI_ERR_OOM = 4,      /* host or device allocation failed */
+    SPI_ERR_CUDA = 5,     /* CUDA runtime error (no device, launch failure, ...) */
+    SPI_ERR_TIMEOUT = 6,  /* a bounded device-side wait gave up */
+    SPI_ERR_STATE = 7     /* call out of order (factor before analyse, solve before factor) */
+} spi_status;
+
+typedef enum spi_precision {
+    SPI_PREC_FP64 = 0,      /* every step in FP64 */
+    SPI_PREC_MIXED_FP32 = 1 /* FP64 diagonal blocks, FP32 panels / Schur updates / variance
+                               solves with FP64 variance accumulation, FP64 refinement of x */
+} spi_precision;
+
+typedef enum spi_ordering {
+    SPI_ORDER_ND = 0,       /* nested dissection (default; Sec. 3.2.1 uses nested dissection) */
+    SPI_ORDER_NATURAL = 1   /* the caller's order */
+} spi_ordering;
+
+typedef struct spi_options {
+    int precision;   /* spi_precision */
+    int ordering;    /* spi_ordering */
+    int rhs_block;   /* right-hand sides per block in spi_diag_inverse; 0 = 128 (Sec. 4.3 uses 128) */
+    int relax;       /* supernode amalgamation: max explicit zeros per merge as a percentage
+                        of the merged panel (0 = fundamental supernodes only); default 10 */
+    int refine_max;  /* max iterative-refinement steps of spi_solve in mixed precision */
+    double refine_tol; /* stop refining when ||b - N x||_2 <= refine_tol * ||b||_2 */
+    int async;       /* 1: do not drain the stream at the end of each call */
+    int nd_leaf;     /* nested-dissection leaf size (vertices); 0 = default */
+} spi_options;
+
+typedef struct spi_stats {
+    int64_t n;              /* order of N */
+    int64_t nnz_a;          /* stored entries of the lower triangle of N */
+    int64_t nnz_l;          /* entries of L (strictly lower), exact column counts */
+    int64_t nnz_l_stored;   /* entries of the supernodal panels incl. explicit zeros */
+    int64_t n_supernodes;
+    int64_t n_levels;       /* elimination-tree levels of the supernodal tree */
+    int64_t max_front;      /* largest front order m */
+    int64_t bad_pivot;      /* column (caller numbering) of the first non-positive pivot, or -1 */
+    double factor_flops;    /* sum over pivots j of (c_j^2 - 1), c_j = entries of column j of L
+                               including the diagonal (exact counts, no amalgamation zeros) */
+    double diag_flops;      /* algorithmic flops of the last spi_diag_inverse call:
+                               sum over requested i, over j on path(i), of 2 c_j */
+    double solve_flops;     /* 4 * nnz_l + n (one forward + one backward sweep) */
+    double diag_flops_all;  /* algorithmic flops of spi_diag_inverse over all n indices */
+    int64_t device_bytes;   /* device memory held by the context */
+    double analyse_seconds; /* host time of spi_analyse */
+} spi_stats;
+
+typedef struct spi_ctx spi_ctx;
+
+/* Fill *opt with the defaults (FP64, nested dissection, 128 RHS per block,
+ * relax 10, refine_max 10, refine_tol 1e-13, synchronous). */
+void spi_default_options(spi_options* opt);
+
+/* Analysis phase (Sec. 3.2.1): validate the pattern, order it (nested
+ * dissection or natural), build the elimination tree and its postorder,
+ * exact column counts, relaxed supernodes, the multifrontal assembly maps
+ * and the level schedule.  Host work only; device memory is allocated at the
+ * first spi_factor.
+ *   n       order of N (>= 0)
+ *   colptr  host, int64[n+1]: CSC column pointers of the LOWER triangle
+ *           (including the diagonal), colptr[0] = 0
+ *   rowind  host, int32[colptr[n]]: row indices, strictly increasing in each
+ *           column, each column starting with its diagonal entry
+ *   opt     host, may be NULL (defaults)
+ *   out     receives the new context (owned by the caller; spi_destroy)
+ * Errors: SPI_ERR_ARG, SPI_ERR_PATTERN, SPI_ERR_OOM. */
+int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                const spi_options* opt, spi_ctx** out);
+
+/* Numerical factorization (Sec. 3.2.2): N = P^T L D L^T P with the values of
+ * the pattern given to spi_analyse.
+ *   values  float64[colptr[n]] in the order of rowind; host memory when
+ *           values_on_device = 0, device memory otherwise
+ * May be called again with new values on the same pattern (energy bands,
+ * Newton steps).  Errors: SPI_ERR_STATE, SPI_ERR_NOT_SPD (spi_info().bad_pivot
+ * gives the column; the factor is unusable), SPI_ERR_CUDA, SPI_ERR_OOM. */
+int spi_factor(spi_ctx* ctx, const double* values, int values_on_device, void* stream);
+
+/* Solution phase (Sec. 3.2.3): x = N^-1 b by z = L^-1 P b (bottom-up over the
+ * tree), w = D^-1 z, x = P^T L^-T w (top-down).  In mixed precision the
+ * result is refined in FP64 against the FP64 values of N.
+ *   b, x    float64[n]; host when on_device = 0, device otherwise; x may
+ *           alias b.
+ * Errors: SPI_ERR_STATE, SPI_ERR_ARG, SPI_ERR_CUDA. */
+int spi_solve(spi_ctx* ctx, const double* b, double* x, int on_device, void* stream);
+
+/* Selected inverse entries (Sec. 3.3.1, Sec. 4.3): out[t] = (N^-1)_{idx[t], idx[t]}
+ * computed as sum_k z_k^2 / d_k with z = L^-1 P e_idx[t], each forward solve
+ * pruned to the elimination-tree path of idx[t]; the requested indices are
+ * sorted in postorder and grouped in blocks of opt.rhs_block right-hand
+ * sides, every block solved by one CTA over the union of its paths.
+ *   idx     int32[nidx] (host when on_device = 0, else device), or NULL for
+ *           all n indices (then out[i] = (N^-1)_ii)
+ *   out     float64[nidx] (or [n] when idx == NULL), host or device as above
+ * Errors: SPI_ERR_STATE, SPI_ERR_ARG (index out of range), SPI_ERR_CUDA. */
+int spi_diag_inverse(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out,
+                     int on_device, void* stream);
+
+/* Statistics of the analysis and of the last calls.  Errors: SPI_ERR_ARG. */
+int spi_info(const spi_ctx* ctx, spi_stats* out);
+
+/* Drain the context's last stream and report any device-side error. */
+int spi_sync(spi_ctx* ctx, void* stream);
+
+/* Export the permutation: perm[k] = caller index of the k-th pivot
+ * (host int32[n]).  Errors: SPI_ERR_ARG. */
+int spi_get_perm(const spi_ctx* ctx, int32_t* perm);
+
+/* Export the elimination tree of the permuted matrix: parent[k] = pivot
+ * index of the parent of pivot k, -1 at a root (host int32[n]). */
+int spi_get_etree(const spi_ctx* ctx, int32_t* parent);
+
+/* Static message for a status code. */
+const char* spi_strerror(int status);
+
+/* Free the context and all its device memory.  NULL is allowed. */
+void spi_destroy(spi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPI_H */

@@ -1,0 +1,405 @@
+// capi.cu -- the extern "C" entry points declared in include/spi.h.
+//
+// A context owns the host symbolic analysis and every device buffer of one
+// pattern.  Device memory is laid out once, at the first spi_factor:
+//   panels L (sum_s m_s k_s doubles, column-major per supernode), D (n),
+//   F22 update areas (sum over supernodes with children of (m-k)^2),
+//   the symbolic arrays, the launch item lists, and per-plan Z workspaces
+//   of the variance solves (rows of the union of a block's paths x B).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spi_internal.cuh"
+
+using namespace spi;
+
+struct spi_ctx {
+    Symbolic S;
+    spi_options opt{};
+    FactorPlan FP;
+    std::vector<int32_t> level_kmax;
+    int device = -1;
+    bool dev_ready = false, factored = false;
+    std::vector<void*> allocs;
+    int64_t device_bytes = 0;
+    DevSym dsym;
+    int64_t* d_amap = nullptr;
+    int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
+            *d_level_list = nullptr;
+    double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
+           *d_w = nullptr, *d_vec = nullptr, *d_out = nullptr;
+    DevStatus* d_status = nullptr;
+    DevStatus* h_status = nullptr;
+    DevDiagPlan plan_all;
+    bool plan_all_ready = false;
+    DevDiagPlan plan_sub;
+    std::vector<int32_t> plan_sub_key;
+    bool plan_sub_ready = false;
+    double last_diag_flops = 0;
+    int64_t bad_pivot = -1;
+    double analyse_seconds = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SPI_ERR_OOM : SPI_ERR_CUDA; }
+
+template <class T>
+cudaError_t dev_alloc(spi_ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaSuccess) { c->allocs.push_back(*p); c->device_bytes += (int64_t)(count * sizeof(T)); }
+    return e;
+}
+
+template <class T>
+cudaError_t dev_upload(spi_ctx* c, T** p, const std::vector<T>& v, std::vector<void*>* track = nullptr) {
+    cudaError_t e;
+    *p = nullptr;
+    size_t count = std::max<size_t>(v.size(), 1);
+    e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (track) track->push_back(*p); else c->allocs.push_back(*p);
+    c->device_bytes += (int64_t)(count * sizeof(T));
+    if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e__ = (x);                 \
+        if (e__ != cudaSuccess) return cuda_fail(e__); \
+    } while (0)
+
+int ensure_device(spi_ctx* c) {
+    if (c->dev_ready) return SPI_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return SPI_ERR_CUDA;
+    CK(cudaGetDevice(&c->device));
+    const Symbolic& S = c->S;
+    int32_t *sfirst, *srows, *relmap, *sparent, *perm, *snode_of;
+    int64_t *srowptr, *lptr, *f22ptr;
+    CK(dev_upload(c, &sfirst, S.sfirst));
+    CK(dev_upload(c, &srowptr, S.srowptr));
+    CK(dev_upload(c, &srows, S.srows));
+    CK(dev_upload(c, &relmap, S.relmap));
+    CK(dev_upload(c, &sparent, S.sparent));
+    CK(dev_upload(c, &lptr, S.lptr));
+    CK(dev_upload(c, &f22ptr, S.f22ptr));
+    CK(dev_upload(c, &perm, S.perm));
+    CK(dev_upload(c, &snode_of, S.snode_of));
+    c->dsym = DevSym{S.n, S.ns, sfirst, srowptr, srows, relmap, sparent, lptr, f22ptr, perm, snode_of};
+    CK(dev_upload(c, &c->d_amap, S.amap));
+    CK(dev_upload(c, &c->d_diag_src, S.diag_src));
+    CK(dev_upload(c, &c->d_items0, c->FP.diag_items));
+    CK(dev_upload(c, &c->d_items1, c->FP.trsm_items));
+    CK(dev_upload(c, &c->d_items2, c->FP.schur_items));
+    CK(dev_upload(c, &c->d_level_list, S.level_list));
+    CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns]));
+    CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total));
+    CK(dev_alloc(c, &c->d_D, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_adiag, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_vals, (size_t)S.nnz_a));
+    CK(dev_alloc(c, &c->d_w, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_vec, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_out, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_status, 1));
+    CK(cudaMallocHost((void**)&c->h_status, sizeof(DevStatus)));
+    int32_t kmax = 0;
+    for (int32_t s = 0; s < S.ns; ++s) kmax = std::max(kmax, S.k_of(s));
+    if (solve_kernel_setup(kmax) != cudaSuccess) return SPI_ERR_CUDA;
+    c->dev_ready = true;
+    return SPI_OK;
+}
+
+void free_plan(DevDiagPlan& p) {
+    for (void* a : p.allocs) cudaFree(a);
+    p = DevDiagPlan();
+}
+
+int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
+    free_plan(d);
+    d.B = h.B; d.nblocks = h.nblocks; d.nrhs = h.nrhs; d.flops = h.flops; d.work_flops = h.work_flops;
+    std::vector<void*>* tr = &d.allocs;
+    CK(dev_upload(c, &d.order, h.order, tr));
+    CK(dev_upload(c, &d.blk_ptr, h.blk_ptr, tr));
+    CK(dev_upload(c, &d.uptr, h.uptr, tr));
+    CK(dev_upload(c, &d.us, h.us, tr));
+    CK(dev_upload(c, &d.ulo, h.ulo, tr));
+    CK(dev_upload(c, &d.uhi, h.uhi, tr));
+    CK(dev_upload(c, &d.uzoff, h.uzoff, tr));
+    CK(dev_upload(c, &d.rel, h.rel, tr));
+    CK(dev_upload(c, &d.rhs_out, h.rhs_out, tr));
+    CK(dev_upload(c, &d.rhs_zrow, h.rhs_zrow, tr));
+    CK(dev_upload(c, &d.urel, h.urel, tr));
+    CK(dev_upload(c, &d.zbase, h.zbase, tr));
+    d.zsize = h.zbase.empty() ? 0 : h.zbase.back();
+    double* z = nullptr;
+    cudaError_t e = cudaMalloc((void**)&z, (size_t)std::max<int64_t>(d.zsize, 1) * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e);
+    d.allocs.push_back(z);
+    d.Z = z;
+    return SPI_OK;
+}
+
+__global__ void k_reset_status(DevStatus* s) {
+    s->flags = 0;
+    s->bad_pivot = INT_MAX;
+}
+
+int finish(spi_ctx* c, cudaStream_t st) {
+    CK(cudaGetLastError());
+    if (c->opt.async) return SPI_OK;
+    CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c->h_status->flags & FLAG_NOT_SPD) {
+        int bp = c->h_status->bad_pivot;
+        c->bad_pivot = (bp >= 0 && bp < c->S.n) ? c->S.perm[bp] : -1;
+        c->factored = false;
+        return SPI_ERR_NOT_SPD;
+    }
+    if (c->h_status->flags & FLAG_TIMEOUT) return SPI_ERR_TIMEOUT;
+    return SPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spi_default_options(spi_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = SPI_PREC_FP64;
+    o->ordering = SPI_ORDER_ND;
+    o->rhs_block = 128;
+    o->relax = 10;
+    o->refine_max = 10;
+    o->refine_tol = 1e-13;
+    o->async = 0;
+    o->nd_leaf = 0;
+}
+
+const char* spi_strerror(int s) {
+    switch (s) {
+        case SPI_OK: return "ok";
+        case SPI_ERR_ARG: return "invalid argument";
+        case SPI_ERR_PATTERN: return "invalid sparsity pattern (lower CSC, sorted rows, full diagonal)";
+        case SPI_ERR_NOT_SPD: return "matrix not positive definite (non-positive pivot)";
+        case SPI_ERR_OOM: return "out of memory";
+        case SPI_ERR_CUDA: return "CUDA error or no usable GPU";
+        case SPI_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SPI_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const spi_options* opt,
+                spi_ctx** out) {
+    if (!out) return SPI_ERR_ARG;
+    *out = nullptr;
+    spi_options o;
+    spi_default_options(&o);
+    if (opt) o = *opt;
+    if (o.rhs_block <= 0) o.rhs_block = 128;
+    if (o.rhs_block > 1024 || o.precision < 0 || o.precision > 1 || o.ordering < 0 || o.ordering > 1 ||
+        o.relax < 0)
+        return SPI_ERR_ARG;
+    spi_ctx* c = new (std::nothrow) spi_ctx();
+    if (!c) return SPI_ERR_OOM;
+    c->opt = o;
+    auto t0 = std::chrono::steady_clock::now();
+    AnalyseParams prm;
+    prm.ordering = o.ordering;
+    prm.relax = o.relax;
+    prm.nd_leaf = o.nd_leaf;
+    std::string err;
+    int rc = analyse(n, colptr, rowind, prm, c->S, err);
+    if (rc != 0) { delete c; return rc; }
+    try {
+        build_factor_plan(c->S, c->FP);
+        c->level_kmax.assign(c->S.nlevels, 0);
+        for (int32_t l = 0; l < c->S.nlevels; ++l)
+            for (int32_t p = c->S.level_ptr[l]; p < c->S.level_ptr[l + 1]; ++p)
+                c->level_kmax[l] = std::max(c->level_kmax[l], c->S.k_of(c->S.level_list[p]));
+    } catch (const std::bad_alloc&) {
+        delete c;
+        return SPI_ERR_OOM;
+    }
+    c->analyse_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = c;
+    return SPI_OK;
+}
+
+int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    c->factored = false;
+    c->bad_pivot = -1;
+    const double* vals = values;
+    if (!values_on_device && S.nnz_a > 0) {
+        CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
+        vals = c->d_vals;
+    }
+    k_reset_status<<<1, 1, 0, st>>>(c->d_status);
+    CK(cudaMemsetAsync(c->d_L, 0, (size_t)S.lptr[S.ns] * sizeof(double), st));
+    if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * sizeof(double), st));
+    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, st);
+    for (const Launch& l : c->FP.launches) {
+        const int32_t* items = l.kind == 0 ? c->d_items0 : (l.kind == 1 ? c->d_items1 : c->d_items2);
+        launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, st);
+    }
+    rc = finish(c, st);
+    if (rc == SPI_OK) c->factored = true;
+    return rc;
+}
+
+int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, void* stream) {
+    if (!c || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    const double* bd = b;
+    if (!on_device && S.n) {
+        CK(cudaMemcpyAsync(c->d_vec, b, (size_t)S.n * sizeof(double), cudaMemcpyHostToDevice, st));
+        bd = c->d_vec;
+    }
+    launch_permute_in(S.n, c->dsym.perm, bd, c->d_w, st);
+    for (int32_t l = 0; l < S.nlevels; ++l)
+        launch_fwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
+                         c->level_kmax[l], c->d_L, c->d_w, st);
+    for (int32_t l = S.nlevels - 1; l >= 0; --l)
+        launch_bwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
+                         c->level_kmax[l], c->d_L, c->d_D, c->d_w, st);
+    double* xd = on_device ? x : c->d_vec;
+    launch_permute_out(S.n, c->dsym.perm, c->d_w, xd, st);
+    if (!on_device && S.n)
+        CK(cudaMemcpyAsync(x, xd, (size_t)S.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return finish(c, st);
+}
+
+int spi_diag_inverse(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
+    if (!c || !out) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    const Symbolic& S = c->S;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevDiagPlan* plan;
+    int64_t nout;
+    if (!idx) {
+        nout = S.n;
+        if (!c->plan_all_ready) {
+            std::vector<int32_t> piv(S.n), pos(S.n);
+            for (int32_t k = 0; k < S.n; ++k) { piv[k] = k; pos[k] = S.perm[k]; }
+            DiagPlan h;
+            build_diag_plan(S, piv, pos, c->opt.rhs_block, h);
+            int rc = upload_plan(c, h, c->plan_all);
+            if (rc) return rc;
+            c->plan_all_ready = true;
+        }
+        plan = &c->plan_all;
+    } else {
+        if (nidx < 0) return SPI_ERR_ARG;
+        nout = nidx;
+        std::vector<int32_t> key((size_t)nidx);
+        if (nidx) {
+            if (on_device) {
+                CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+            }
+        }
+        for (int32_t v : key)
+            if (v < 0 || v >= S.n) return SPI_ERR_ARG;
+        if (!c->plan_sub_ready || key != c->plan_sub_key) {
+            std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
+            for (int64_t t = 0; t < nidx; ++t) { piv[t] = S.iperm[key[t]]; pos[t] = (int32_t)t; }
+            DiagPlan h;
+            build_diag_plan(S, piv, pos, c->opt.rhs_block, h);
+            int rc = upload_plan(c, h, c->plan_sub);
+            if (rc) return rc;
+            c->plan_sub_key.swap(key);
+            c->plan_sub_ready = true;
+        }
+        plan = &c->plan_sub;
+    }
+    double* od = out;
+    if (!on_device) {
+        if (nout > S.n) {  // repeated indices: a larger staging buffer
+            return SPI_ERR_ARG;
+        }
+        od = c->d_out;
+    }
+    launch_diag_inverse(c->dsym, *plan, c->d_L, c->d_D, od, st);
+    if (!on_device && nout)
+        CK(cudaMemcpyAsync(out, od, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    c->last_diag_flops = plan->flops;
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return finish(c, st);
+}
+
+int spi_info(const spi_ctx* c, spi_stats* o) {
+    if (!c || !o) return SPI_ERR_ARG;
+    std::memset(o, 0, sizeof *o);
+    const Symbolic& S = c->S;
+    o->n = S.n;
+    o->nnz_a = S.nnz_a;
+    o->nnz_l = S.nnz_l;
+    o->nnz_l_stored = S.nnz_l_stored;
+    o->n_supernodes = S.ns;
+    o->n_levels = S.nlevels;
+    o->max_front = S.max_front;
+    o->bad_pivot = c->bad_pivot;
+    o->factor_flops = S.factor_flops;
+    o->diag_flops = c->last_diag_flops;
+    o->solve_flops = 4.0 * (double)S.nnz_l + (double)S.n;
+    o->diag_flops_all = S.diag_flops_all;
+    o->device_bytes = c->device_bytes;
+    o->analyse_seconds = c->analyse_seconds;
+    return SPI_OK;
+}
+
+int spi_sync(spi_ctx* c, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->dev_ready) return SPI_OK;
+    spi_options o = c->opt;
+    c->opt.async = 0;
+    int rc = finish(c, (cudaStream_t)stream);
+    c->opt = o;
+    return rc;
+}
+
+int spi_get_perm(const spi_ctx* c, int32_t* perm) {
+    if (!c || (!perm && c->S.n)) return SPI_ERR_ARG;
+    if (c->S.n) std::memcpy(perm, c->S.perm.data(), (size_t)c->S.n * sizeof(int32_t));
+    return SPI_OK;
+}
+
+int spi_get_etree(const spi_ctx* c, int32_t* parent) {
+    if (!c || (!parent && c->S.n)) return SPI_ERR_ARG;
+    if (c->S.n) std::memcpy(parent, c->S.parent.data(), (size_t)c->S.n * sizeof(int32_t));
+    return SPI_OK;
+}
+
+void spi_destroy(spi_ctx* c) {
+    if (!c) return;
+    free_plan(c->plan_all);
+    free_plan(c->plan_sub);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// factor.cu -- numerical factorization (paper Sec. 3.2.2): multifrontal
+// LDL^T over the supernodal elimination tree, bottom-up level by level.
+//
+// Every front of supernode s is an m x m dense matrix whose first k columns
+// (the panel, column-major, leading dimension m) hold the supernode's
+// columns of N plus the contributions of its children, and whose trailing
+// (m-k) x (m-k) part (F22, present only when s has children) accumulates the
+// children's contribution blocks.  Per front:
+//   F11 = L11 D1 L11^T          (diagonal tiles, FP64, one CTA per tile)
+//   L21 = F21 L11^-T D1^-1      (panel row tiles, left-looking per block column)
+//   C   = F22 - L21 D1 L21^T    (Schur complement tiles)
+// and C is added into the parent's front through the parent-relative index
+// map (the extend-add of the multifrontal method), with FP64 atomics because
+// siblings of one level add into the same parent concurrently.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "spi_internal.cuh"
+
+namespace spi {
+
+void build_factor_plan(const Symbolic& S, FactorPlan& F) {
+    F = FactorPlan();
+    F.level_launch_ptr.push_back(0);
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+        int32_t kmax = 0;
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p)
+            kmax = std::max(kmax, S.k_of(S.level_list[p]));
+        int32_t nsteps = (kmax + kT - 1) / kT;
+        for (int32_t b = 0; b < nsteps; ++b) {
+            Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
+            Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
+            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+                int32_t s = S.level_list[p];
+                int32_t k = S.k_of(s), m = S.m_of(s);
+                if (k <= b * kT) continue;
+                F.diag_items.push_back(s);
+                ld.count++;
+                int32_t w = std::min(kT, k - b * kT), r0 = b * kT + w;
+                for (int32_t rt = 0; r0 + rt * kT < m; ++rt) {
+                    F.trsm_items.push_back(s);
+                    F.trsm_items.push_back(rt);
+                    lt.count++;
+                }
+            }
+            if (ld.count) F.launches.push_back(ld);
+            if (lt.count) F.launches.push_back(lt);
+        }
+        Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            int32_t s = S.level_list[p];
+            int32_t k = S.k_of(s), m = S.m_of(s);
+            if (S.sparent[s] == -1 || m <= k) continue;
+            int32_t nt = (m - k + kT - 1) / kT;
+            for (int32_t ti = 0; ti < nt; ++ti)
+                for (int32_t tj = 0; tj <= ti; ++tj) {
+                    F.schur_items.push_back(s);
+                    F.schur_items.push_back(ti);
+                    F.schur_items.push_back(tj);
+                    ls.count++;
+                }
+        }
+        if (ls.count) F.launches.push_back(ls);
+        F.level_launch_ptr.push_back((int32_t)F.launches.size());
+    }
+}
+
+namespace {
+
+__global__ void k_assemble(const int64_t* __restrict__ amap, const double* __restrict__ vals, int64_t nnz,
+                           double* __restrict__ L, const int32_t* __restrict__ diag_src, int32_t n,
+                           double* __restrict__ adiag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = i; p < nnz; p += stride) L[amap[p]] = vals[p];
+    for (int64_t j = i; j < n; j += stride) adiag[j] = vals[diag_src[j]];
+}
+
+constexpr int kThreads = 128;
+
+// Diagonal tile of block column b: left-looking update from the block
+// columns before it, then an unblocked LDL^T in shared memory.
+__global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
+                                                        double* __restrict__ L, double* __restrict__ D,
+                                                        const double* __restrict__ adiag, DevStatus* status) {
+    __shared__ double A[kT][kT + 1];
+    __shared__ double Bs[kT][kT + 1];
+    __shared__ double dv[kT];
+    const int tid = threadIdx.x;
+    const int s = items[blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    double* P = L + d.lptr[s];
+    const int c0 = b * kT, w = min(kT, k - c0);
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, j = e / kT;
+        A[i][j] = (i < w && j <= i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
+    }
+    for (int cb = 0; cb < c0; cb += kT) {
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, c = e / kT;
+            Bs[i][c] = (i < w) ? P[(c0 + i) + (int64_t)(cb + c) * m] : 0.0;
+        }
+        if (tid < kT) dv[tid] = D[f + cb + tid];
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, j = e / kT;
+            if (j <= i && i < w) {
+                double acc = 0.0;
+#pragma unroll 8
+                for (int c = 0; c < kT; ++c) acc += Bs[i][c] * dv[c] * Bs[j][c];
+                A[i][j] -= acc;
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+        const double dc = A[c][c];
+        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
+            if (tid == 0) {
+                atomicOr(&status->flags, FLAG_NOT_SPD);
+                atomicMin(&status->bad_pivot, f + c0 + c);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, j = e / kT;
+            if (j > c && j <= i && i < w) A[i][j] -= A[i][c] * A[j][c] / dc;
+        }
+        __syncthreads();
+        if (tid == 0) dv[c] = dc;
+        for (int i = c + 1 + tid; i < w; i += kThreads) A[i][c] /= dc;
+        __syncthreads();
+    }
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, j = e / kT;
+        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (i == j) ? dv[i] : A[i][j];
+    }
+    if (tid < w) D[f + c0 + tid] = dv[tid];
+}
+
+// Row tile rt below the diagonal tile of block column b: left-looking
+// update, then L21 = X L11^-T D^-1 row by row.
+__global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t* __restrict__ items, int b,
+                                                         double* __restrict__ L, const double* __restrict__ D) {
+    __shared__ double X[kT][kT + 1];
+    __shared__ double Br[kT][kT + 1];
+    __shared__ double Bd[kT][kT + 1];
+    __shared__ double dv[kT];
+    const int tid = threadIdx.x;
+    const int s = items[2 * blockIdx.x], rt = items[2 * blockIdx.x + 1];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    double* P = L + d.lptr[s];
+    const int c0 = b * kT, w = min(kT, k - c0);
+    const int64_t r0 = c0 + w + (int64_t)rt * kT;
+    const int nr = (int)(m - r0 < kT ? m - r0 : kT);
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, j = e / kT;
+        X[i][j] = (i < nr && j < w) ? P[(r0 + i) + (int64_t)(c0 + j) * m] : 0.0;
+    }
+    for (int cb = 0; cb < c0; cb += kT) {
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, c = e / kT;
+            Br[i][c] = (i < nr) ? P[(r0 + i) + (int64_t)(cb + c) * m] : 0.0;
+            Bd[i][c] = (i < w) ? P[(c0 + i) + (int64_t)(cb + c) * m] : 0.0;
+        }
+        if (tid < kT) dv[tid] = D[f + cb + tid];
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, j = e / kT;
+            if (i < nr && j < w) {
+                double acc = 0.0;
+#pragma unroll 8
+                for (int c = 0; c < kT; ++c) acc += Br[i][c] * dv[c] * Bd[j][c];
+                X[i][j] -= acc;
+            }
+        }
+    }
+    __syncthreads();
+    // L11 (unit lower) of this block column and its pivots
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, c = e / kT;
+        Bd[i][c] = (i < w && c < i) ? P[(c0 + i) + (int64_t)(c0 + c) * m] : 0.0;
+    }
+    if (tid < kT) dv[tid] = (tid < w) ? D[f + c0 + tid] : 1.0;
+    __syncthreads();
+    if (tid < nr) {
+        const int i = tid;
+        for (int c = 0; c < w; ++c) {
+            double y = X[i][c];
+            for (int cp = 0; cp < c; ++cp) y -= X[i][cp] * Bd[c][cp];
+            X[i][c] = y;
+        }
+        for (int c = 0; c < w; ++c) P[(r0 + i) + (int64_t)(c0 + c) * m] = X[i][c] / dv[c];
+    }
+}
+
+// Schur complement tile (ti, tj) of the trailing (m-k)^2 part, added into the parent's front.
+__global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int32_t* __restrict__ items,
+                                                            double* __restrict__ L, double* __restrict__ F22,
+                                                            const double* __restrict__ D) {
+    __shared__ double Li[kT][kT + 1];
+    __shared__ double Lj[kT][kT + 1];
+    const int tid = threadIdx.x;
+    const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const int64_t mb = m - k;
+    const double* P = L + d.lptr[s];
+    const int64_t ib = k + (int64_t)ti * kT, jb = k + (int64_t)tj * kT;
+    const int ni = (int)(m - ib < kT ? m - ib : kT), nj = (int)(m - jb < kT ? m - jb : kT);
+    const int jj = tid % kT, i0 = tid / kT;  // thread owns column jj, rows i0 + 4 r
+    double acc[kT / 4];
+#pragma unroll
+    for (int r = 0; r < kT / 4; ++r) acc[r] = 0.0;
+    for (int cb = 0; cb < k; cb += kT) {
+        const int cw = min(kT, k - cb);
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            int i = e % kT, c = e / kT;
+            Li[i][c] = (i < ni && c < cw) ? P[(ib + i) + (int64_t)(cb + c) * m] : 0.0;
+            Lj[i][c] = (i < nj && c < cw) ? P[(jb + i) + (int64_t)(cb + c) * m] * D[f + cb + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < kT; ++c) {
+            const double bj = Lj[jj][c];
+#pragma unroll
+            for (int r = 0; r < kT / 4; ++r) acc[r] -= Li[i0 + 4 * r][c] * bj;
+        }
+    }
+    const int64_t fo = d.f22ptr[s];
+    const int p = d.sparent[s];
+    const int kp = d.sfirst[p + 1] - d.sfirst[p];
+    const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
+    double* Pp = L + d.lptr[p];
+    double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+    const int32_t* rel = d.relmap + d.srowptr[s];
+    if (jj >= nj) return;
+    const int64_t jl = jb + jj;
+    const int qj = rel[jl];
+#pragma unroll
+    for (int r = 0; r < kT / 4; ++r) {
+        const int i = i0 + 4 * r;
+        const int64_t il = ib + i;
+        if (i >= ni || il < jl) continue;
+        double v = acc[r];
+        if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
+        const int qi = rel[il];
+        if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
+        else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
+    }
+}
+
+}  // namespace
+
+void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
+                     const int32_t* diag_src, double* adiag, cudaStream_t st) {
+    int64_t work = std::max<int64_t>(nnz, d.n);
+    if (work == 0) return;
+    int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    k_assemble<<<grid, 256, 0, st>>>(amap, vals, nnz, L, diag_src, d.n, adiag);
+}
+
+void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
+                        double* D, const double* adiag, DevStatus* status, cudaStream_t st) {
+    if (l.count == 0) return;
+    switch (l.kind) {
+        case 0: k_diag_tile<<<l.count, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status); break;
+        case 1: k_panel_trsm<<<l.count, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D); break;
+        default: k_schur_scatter<<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D); break;
+    }
+}
+
+}  // namespace spi

@@ -1,0 +1,87 @@
+// spi_internal.cuh -- device-side data of a context and the kernel entry
+// points shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "analysis.h"
+#include "spi.h"
+
+namespace spi {
+
+constexpr int kT = 32;  // tile edge of the front kernels
+
+enum DevFlags : int { FLAG_NOT_SPD = 1, FLAG_TIMEOUT = 2, FLAG_BAD_INDEX = 4 };
+
+struct DevStatus {
+    int flags;
+    int bad_pivot;  // smallest failing pivot (atomicMin), INT32_MAX if none
+};
+
+// Pointers to the symbolic structure on the device.
+struct DevSym {
+    int32_t n = 0, ns = 0;
+    const int32_t* sfirst = nullptr;
+    const int64_t* srowptr = nullptr;
+    const int32_t* srows = nullptr;
+    const int32_t* relmap = nullptr;
+    const int32_t* sparent = nullptr;
+    const int64_t* lptr = nullptr;
+    const int64_t* f22ptr = nullptr;
+    const int32_t* perm = nullptr;
+    const int32_t* snode_of = nullptr;
+};
+
+// A flattened work list of one kernel launch.
+struct Launch {
+    int kind;        // 0 diag tile, 1 panel TRSM, 2 Schur+scatter
+    int step;        // block column b for kinds 0/1
+    int64_t off;     // offset into the item array of the kind
+    int32_t count;   // CTAs
+};
+
+struct FactorPlan {
+    std::vector<int32_t> diag_items;  // supernode
+    std::vector<int32_t> trsm_items;  // pairs (supernode, row tile)
+    std::vector<int32_t> schur_items; // triples (supernode, ti, tj)
+    std::vector<Launch> launches;
+    std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
+};
+
+void build_factor_plan(const Symbolic& S, FactorPlan& F);
+
+struct DevDiagPlan {
+    int32_t B = 0, nblocks = 0;
+    int64_t nrhs = 0;
+    int32_t *order = nullptr, *blk_ptr = nullptr, *uptr = nullptr, *us = nullptr, *ulo = nullptr,
+            *uhi = nullptr, *uzoff = nullptr, *rel = nullptr, *rhs_out = nullptr, *rhs_zrow = nullptr;
+    int64_t *urel = nullptr, *zbase = nullptr;
+    double* Z = nullptr;
+    int64_t zsize = 0;
+    double flops = 0, work_flops = 0;
+    std::vector<void*> allocs;
+};
+
+// ---- kernel launchers (factor.cu)
+void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
+                     const int32_t* diag_src, double* adiag, cudaStream_t st);
+void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
+                        double* D, const double* adiag, DevStatus* status, cudaStream_t st);
+// ---- solve.cu
+void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st);
+void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, cudaStream_t st);
+void launch_fwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
+                      double* w, cudaStream_t st);
+void launch_bwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
+                      const double* D, double* w, cudaStream_t st);
+// one-time kernel attributes (large dynamic shared memory)
+cudaError_t solve_kernel_setup(int32_t kmax);
+// ---- diag.cu
+void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
+                         cudaStream_t st);
+
+}  // namespace spi

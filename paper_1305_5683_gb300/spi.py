@@ -1,0 +1,261 @@
+"""Thin ctypes binding of include/spi.h (argument marshalling only).
+
+Every function here forwards to the compiled CUDA library libspi_gb300.so;
+there is no Python or CPU implementation of any numeric step.  If the
+library is missing or cannot be loaded, `load()` raises -- there is no
+fallback path.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); `on_device` is derived from the argument type.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPI_OK, SPI_ERR_ARG, SPI_ERR_PATTERN, SPI_ERR_NOT_SPD, SPI_ERR_OOM, SPI_ERR_CUDA, SPI_ERR_TIMEOUT, \
+    SPI_ERR_STATE = range(8)
+SPI_PREC_FP64, SPI_PREC_MIXED_FP32 = 0, 1
+SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
+
+EXPORTS = ["spi_default_options", "spi_analyse", "spi_factor", "spi_solve", "spi_diag_inverse",
+           "spi_info", "spi_sync", "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy"]
+
+
+class spi_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("ordering", ctypes.c_int), ("rhs_block", ctypes.c_int),
+                ("relax", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int)]
+
+
+class spi_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz_a", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
+                ("nnz_l_stored", ctypes.c_int64), ("n_supernodes", ctypes.c_int64),
+                ("n_levels", ctypes.c_int64), ("max_front", ctypes.c_int64), ("bad_pivot", ctypes.c_int64),
+                ("factor_flops", ctypes.c_double), ("diag_flops", ctypes.c_double),
+                ("solve_flops", ctypes.c_double), ("diag_flops_all", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64),
+                ("analyse_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SpiError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {lib().spi_strerror(code).decode()} (status {code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL:
+    """Open libspi_gb300.so and declare the C signatures of include/spi.h."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or _build.OUT
+    if not os.path.exists(p):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"libspi_gb300.so not built ({p}); run paper_1305_5683_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    V, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.spi_default_options.argtypes = [ctypes.POINTER(spi_options)]; L.spi_default_options.restype = None
+    L.spi_analyse.argtypes = [I64, V, V, ctypes.POINTER(spi_options), ctypes.POINTER(V)]
+    L.spi_analyse.restype = I
+    L.spi_factor.argtypes = [V, V, I, V]; L.spi_factor.restype = I
+    L.spi_solve.argtypes = [V, V, V, I, V]; L.spi_solve.restype = I
+    L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
+    L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
+    L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
+    L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
+    L.spi_get_etree.argtypes = [V, V]; L.spi_get_etree.restype = I
+    L.spi_strerror.argtypes = [I]; L.spi_strerror.restype = ctypes.c_char_p
+    L.spi_destroy.argtypes = [V]; L.spi_destroy.restype = None
+    if path is None:
+        _LIB = L
+    return L
+
+
+def lib() -> ctypes.CDLL:
+    return load()
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _buf(a, dtype):
+    """(pointer, on_device, keepalive) of a numpy array or CUDA tensor."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != SPI_OK:
+        raise SpiError(rc, where)
+
+
+# ---------------------------------------------------------------- the C entry points
+def spi_default_options() -> spi_options:
+    o = spi_options()
+    lib().spi_default_options(ctypes.byref(o))
+    return o
+
+
+def spi_analyse(n, colptr, rowind, opt: spi_options | None = None) -> ctypes.c_void_p:
+    cp, _, k1 = _buf(colptr, np.int64)
+    ri, _, k2 = _buf(rowind, np.int32)
+    h = ctypes.c_void_p()
+    rc = lib().spi_analyse(int(n), cp, ri, ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(rc, "spi_analyse")
+    del k1, k2
+    return h
+
+
+def spi_factor(ctx, values, stream=None) -> None:
+    v, dev, keep = _buf(values, np.float64)
+    _check(lib().spi_factor(ctx, v, dev, _stream(stream)), "spi_factor")
+    del keep
+
+
+def spi_solve(ctx, b, x, stream=None) -> None:
+    bp, dev, k1 = _buf(b, np.float64)
+    if not _is_torch(x) and not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise TypeError("x must be a contiguous float64 numpy array or CUDA tensor")
+    xp, dev2, k2 = _buf(x, np.float64)
+    if dev != dev2:
+        raise TypeError("b and x must both be host or both be device buffers")
+    _check(lib().spi_solve(ctx, bp, xp, dev, _stream(stream)), "spi_solve")
+    del k1, k2
+
+
+def spi_diag_inverse(ctx, idx, out, stream=None) -> None:
+    """out[t] = (N^-1)[idx[t], idx[t]]; idx None means every index."""
+    if not _is_torch(out) and not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise TypeError("out must be a contiguous float64 numpy array or CUDA tensor")
+    op, dev, k1 = _buf(out, np.float64)
+    if idx is None:
+        ip, nidx, k2 = None, 0, None
+    else:
+        ip, dev_i, k2 = _buf(idx, np.int32)
+        if dev_i != dev:
+            raise TypeError("idx and out must both be host or both be device buffers")
+        nidx = int(idx.numel() if _is_torch(idx) else len(k2))
+    _check(lib().spi_diag_inverse(ctx, ip, nidx, op, dev, _stream(stream)), "spi_diag_inverse")
+    del k1, k2
+
+
+def spi_info(ctx) -> dict:
+    st = spi_stats()
+    _check(lib().spi_info(ctx, ctypes.byref(st)), "spi_info")
+    return st.as_dict()
+
+
+def spi_sync(ctx, stream=None) -> None:
+    _check(lib().spi_sync(ctx, _stream(stream)), "spi_sync")
+
+
+def spi_get_perm(ctx, n: int) -> np.ndarray:
+    p = np.empty(n, np.int32)
+    _check(lib().spi_get_perm(ctx, p.ctypes.data_as(ctypes.c_void_p)), "spi_get_perm")
+    return p
+
+
+def spi_get_etree(ctx, n: int) -> np.ndarray:
+    p = np.empty(n, np.int32)
+    _check(lib().spi_get_etree(ctx, p.ctypes.data_as(ctypes.c_void_p)), "spi_get_etree")
+    return p
+
+
+def spi_strerror(code: int) -> str:
+    return lib().spi_strerror(code).decode()
+
+
+def spi_destroy(ctx) -> None:
+    lib().spi_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Solver:
+    """analyse -> factor -> solve -> diag_inverse on one pattern (owns the context)."""
+
+    def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
+                 rhs_block=128, relax=10, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False):
+        o = spi_default_options()
+        o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax
+        o.refine_max, o.refine_tol, o.nd_leaf, o.async_ = refine_max, refine_tol, nd_leaf, int(async_)
+        self.n = int(n)
+        self._h = spi_analyse(n, colptr, rowind, o)
+
+    @classmethod
+    def for_problem(cls, pb, **kw):
+        return cls(pb.n, pb.colptr, pb.rowind, **kw)
+
+    def factor(self, values, stream=None):
+        spi_factor(self._h, values, stream)
+        return self
+
+    def solve(self, b, x=None, stream=None):
+        if x is None:
+            x = b.new_empty(b.shape) if _is_torch(b) else np.empty(self.n, np.float64)
+        spi_solve(self._h, b, x, stream)
+        return x
+
+    def diag_inverse(self, idx=None, out=None, stream=None, device=None):
+        m = self.n if idx is None else (idx.numel() if _is_torch(idx) else len(idx))
+        if out is None:
+            if device is not None or (idx is not None and _is_torch(idx)):
+                import torch
+                out = torch.empty(m, dtype=torch.float64, device=device or idx.device)
+            else:
+                out = np.empty(m, np.float64)
+        spi_diag_inverse(self._h, idx, out, stream)
+        return out
+
+    def info(self) -> dict:
+        return spi_info(self._h)
+
+    def perm(self) -> np.ndarray:
+        return spi_get_perm(self._h, self.n)
+
+    def etree(self) -> np.ndarray:
+        return spi_get_etree(self._h, self.n)
+
+    def sync(self, stream=None):
+        spi_sync(self._h, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            spi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,185 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (FP64 form): relative error <= 1e-10 for x (max-norm relative) and for
+every variance (max_i |v_i - v_i^oracle| / v_i^oracle)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from spigen import SCALE, TINY, generate, random_spd, scaled
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1305_5683_gb300 as P
+    P.build.build()
+    return P
+
+
+def lower(A):
+    low = sp.tril(sp.csc_matrix(A)).tocsc()
+    low.sum_duplicates(); low.sort_indices()
+    return low.shape[0], low.indptr.astype(np.int64), low.indices.astype(np.int32), low.data.astype(np.float64)
+
+
+def check(P, n, cp, ri, va, b, **opts):
+    f = oracle.OracleFactor(n, cp, ri, va)
+    x_ref, v_ref = f.solve(b), f.inv_diag()
+    s = P.Solver(n, cp, ri, **opts)
+    s.factor(va)
+    x = s.solve(b)
+    v = s.diag_inverse()
+    ex = np.abs(x - x_ref).max() / max(np.abs(x_ref).max(), 1e-300)
+    ev = (np.abs(v - v_ref) / v_ref).max() if n else 0.0
+    assert ex <= TOL, f"x rel err {ex:.3e}"
+    assert ev <= TOL, f"variance rel err {ev:.3e}"
+    return s, f
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_tiny_spi(P, ordering):
+    pb = generate(TINY)
+    check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, ordering=ordering)
+
+
+@pytest.mark.parametrize("n,dens,seed", [(1, 1.0, 0), (2, 1.0, 1), (31, 0.3, 2), (33, 0.2, 3),
+                                         (97, 0.05, 4), (257, 0.02, 5), (300, 0.01, 6)])
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_random_spd(P, n, dens, seed, ordering):
+    pb = random_spd(n, dens, seed)
+    check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, ordering=ordering)
+
+
+@pytest.mark.parametrize("n", [32, 64, 65, 130])
+def test_dense_single_front(P, n):
+    """A dense SPD matrix is one front: several block columns and a ragged tail."""
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n))
+    A = G @ G.T + n * np.eye(n)
+    check(P, *lower(A), rng.standard_normal(n), ordering=1)
+
+
+def test_diagonal_matrix(P):
+    d = np.linspace(1.0, 5.0, 77)
+    n, cp, ri, va = lower(np.diag(d))
+    s, _ = check(P, n, cp, ri, va, np.ones(77))
+    assert np.array_equal(s.diag_inverse(), 1.0 / d)
+
+
+@pytest.mark.parametrize("relax", [0, 10, 60])
+@pytest.mark.parametrize("rhs_block", [1, 7, 32, 128])
+def test_blocking_and_amalgamation(P, relax, rhs_block):
+    pb = generate(scaled(TINY, 600, seed=11))
+    check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, relax=relax, rhs_block=rhs_block)
+
+
+def test_index_subset_and_order(P):
+    pb = generate(TINY)
+    f = oracle.OracleFactor.from_problem(pb)
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    rng = np.random.default_rng(3)
+    for m in (0, 1, 5, 200):
+        idx = rng.permutation(pb.n)[:m].astype(np.int32)
+        v = s.diag_inverse(idx)
+        if m:
+            ref = f.inv_diag(idx)
+            assert (np.abs(v - ref) / ref).max() <= TOL
+    # repeated call with the same set reuses the plan
+    idx = rng.permutation(pb.n)[:50].astype(np.int32)
+    v1 = s.diag_inverse(idx); v2 = s.diag_inverse(idx)
+    assert np.array_equal(v1, v2)
+
+
+def test_device_buffers(P):
+    import torch
+    pb = generate(TINY)
+    f = oracle.OracleFactor.from_problem(pb)
+    s = P.Solver.for_problem(pb)
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    s.factor(torch.from_numpy(pb.values).to(dev), stream=st)
+    xb = torch.from_numpy(pb.b).to(dev)
+    x = s.solve(xb, stream=st)
+    v = s.diag_inverse(device=dev, stream=st)
+    idx = torch.arange(0, pb.n, 3, dtype=torch.int32, device=dev)
+    vs = s.diag_inverse(idx, stream=st)
+    torch.cuda.synchronize()
+    x_ref, v_ref = f.solve(pb.b), f.inv_diag()
+    assert np.abs(x.cpu().numpy() - x_ref).max() <= TOL * np.abs(x_ref).max()
+    assert (np.abs(v.cpu().numpy() - v_ref) / v_ref).max() <= TOL
+    assert (np.abs(vs.cpu().numpy() - v_ref[::3]) / v_ref[::3]).max() <= TOL
+    # x may alias b
+    s.solve(xb, xb, stream=st)
+    torch.cuda.synchronize()
+    assert np.abs(xb.cpu().numpy() - x_ref).max() <= TOL * np.abs(x_ref).max()
+
+
+def test_refactor_same_pattern(P):
+    pb = generate(TINY)
+    s = P.Solver.for_problem(pb)
+    rng = np.random.default_rng(1)
+    for scale in (1.0, 2.5):
+        vals = pb.values * scale
+        vals[pb.colptr[:-1]] += rng.uniform(0, 1, pb.n)  # perturb the diagonal
+        f = oracle.OracleFactor(pb.n, pb.colptr, pb.rowind, vals)
+        s.factor(vals)
+        v = s.diag_inverse()
+        assert (np.abs(v - f.inv_diag()) / f.inv_diag()).max() <= TOL
+
+
+def test_not_spd_reports_column(P):
+    pb = random_spd(60, 0.1, 9)
+    vals = pb.values.copy()
+    bad = 23
+    vals[pb.colptr[bad]] = -1.0
+    s = P.Solver.for_problem(pb)
+    with pytest.raises(P.SpiError) as e:
+        s.factor(vals)
+    assert e.value.code == 3
+    assert s.info()["bad_pivot"] == bad
+    with pytest.raises(P.SpiError) as e:
+        s.diag_inverse()
+    assert e.value.code == 7  # no usable factor
+    s.factor(pb.values)  # recovers with good values
+    s.diag_inverse()
+
+
+def test_spi_mid_size_nd(P):
+    pb = generate(scaled(SCALE, 2000, seed=5))
+    check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b)
+
+
+def test_full_size_sampled():
+    """The benchmark workload (P = 20,000, full diag(N^-1) in FP64, the
+    launch configuration the benchmark times): every variance is positive and
+    >= 1/N_ii, x meets the residual bound, and 256 sampled variances plus x
+    match the oracle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1305_5683_gb300 as P
+    P.build.build()
+    pb = generate(SCALE)
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    x = s.solve(pb.b)
+    v = s.diag_inverse()
+    A = pb.full_matrix()
+    assert np.linalg.norm(A @ x - pb.b) <= 1e-12 * np.linalg.norm(pb.b)
+    assert np.all(v > 0) and np.all(v * A.diagonal() >= 1 - 1e-12)
+    f = oracle.OracleFactor.from_problem(pb)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([rng.choice(pb.n, 250, replace=False), [0, pb.n - 1, pb.n_pointing,
+                          pb.n_pointing - 1, pb.n_pointing + pb.n_detcol, pb.n // 2]]).astype(np.int32)
+    ref = f.inv_diag(idx)
+    assert (np.abs(v[idx] - ref) / ref).max() <= TOL
+    x_ref = f.solve(pb.b)
+    assert np.abs(x - x_ref).max() <= TOL * np.abs(x_ref).max()

@@ -1,0 +1,127 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol the
+header declares, and its host analysis (ordering, elimination tree,
+postorder, column counts) is right.  No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from spigen import SCALE, TINY, generate, random_spd, scaled
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1305_5683_gb300 as P
+    P.build.build()
+    return P
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "spi.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(spi_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol(P):
+    lib = ctypes.CDLL(P.build.OUT)
+    syms = header_symbols()
+    assert len(syms) >= 10
+    for name in syms:
+        assert hasattr(lib, name), name
+    assert sorted(P.spi.EXPORTS) == syms
+
+
+def test_strerror_and_defaults(P):
+    o = P.spi_default_options()
+    assert o.rhs_block == 128 and o.precision == 0 and o.ordering == 0
+    for code in range(8):
+        assert P.spi_strerror(code)
+
+
+def test_pattern_validation(P):
+    n = 3
+    good_cp = np.array([0, 2, 3, 4], np.int64)
+    good_ri = np.array([0, 2, 1, 2], np.int32)
+    P.spi_destroy(P.spi_analyse(n, good_cp, good_ri))
+    bad = [
+        (np.array([0, 2, 3, 4], np.int64), np.array([2, 0, 1, 2], np.int32)),  # no leading diagonal
+        (np.array([0, 1, 1, 2], np.int64), np.array([0, 2], np.int32)),        # empty column
+        (np.array([0, 3, 4, 5], np.int64), np.array([0, 2, 2, 1, 2], np.int32)),  # duplicate
+        (np.array([0, 2, 3, 4], np.int64), np.array([0, 3, 1, 2], np.int32)),  # out of range
+    ]
+    for cp, ri in bad:
+        with pytest.raises(P.SpiError) as e:
+            P.spi_analyse(n, cp, ri)
+        assert e.value.code == 2
+    with pytest.raises(P.SpiError) as e:
+        P.spi_analyse(-1, good_cp, good_ri)
+    assert e.value.code == 1
+
+
+def test_empty_matrix(P):
+    s = P.Solver(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    assert s.info()["n"] == 0
+
+
+def _check_analysis(P, pb, ordering):
+    s = P.Solver.for_problem(pb, ordering=ordering)
+    n = pb.n
+    perm = s.perm()
+    assert sorted(perm) == list(range(n))
+    parent = s.etree()
+    # postorder: parent after child, subtrees contiguous
+    assert np.all((parent == -1) | (parent > np.arange(n)))
+    size = np.ones(n, np.int64)
+    for j in range(n):
+        if parent[j] >= 0:
+            size[parent[j]] += size[j]
+    first = np.arange(n) - size + 1
+    for j in range(n):
+        if parent[j] >= 0:
+            assert first[parent[j]] <= first[j]
+    # exact column counts == the oracle's factor of the permuted matrix
+    A = pb.full_matrix()
+    Ap = A[perm][:, perm]
+    low = sp.tril(Ap).tocsc(); low.sort_indices()
+    f = oracle.OracleFactor(n, low.indptr.astype(np.int64), low.indices.astype(np.int32), low.data)
+    Lp, Li, Lx, D, par = f.factors()
+    assert np.array_equal(par, parent)
+    info = s.info()
+    assert info["nnz_l"] == int(Lp[-1])
+    cnt = np.diff(Lp) + 1
+    assert info["factor_flops"] == float(np.sum(cnt.astype(float) ** 2 - 1))
+    assert info["diag_flops_all"] == pytest.approx(f.inv_diag_flops(), rel=1e-12)
+    return info
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_analysis_matches_oracle_structure(P, ordering):
+    _check_analysis(P, generate(TINY), ordering)
+    _check_analysis(P, random_spd(150, 0.03, 4), ordering)
+
+
+def test_nested_dissection_reduces_variance_work(P):
+    pb = generate(scaled(SCALE, 4000, seed=2))
+    nd = P.Solver.for_problem(pb, ordering=0).info()
+    nat = P.Solver.for_problem(pb, ordering=1).info()
+    assert nd["diag_flops_all"] < 0.5 * nat["diag_flops_all"]
+    assert nd["nnz_l"] < nat["nnz_l"]
+
+
+def test_compute_without_gpu_fails_loudly(P):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    pb = random_spd(20, 0.2, 1)
+    s = P.Solver.for_problem(pb)
+    with pytest.raises(P.SpiError) as e:
+        s.factor(pb.values)
+    assert e.value.code == 5
+    with pytest.raises(P.SpiError) as e:
+        s.diag_inverse()
+    assert e.value.code == 7

@@ -1,0 +1,322 @@
+"""Benchmark: variances diag(N^-1) per second for the SPI least-squares
+normal matrix of P = 20,000 pointings (380,000 rows, 500 sources with
+time-bins of 20-2,000 pointings, per-pointing background plus 19
+detector-pattern columns per 500 pointings), FP64.
+
+One step = the whole hot path on one batch: factor(values) -> solve(b) ->
+diag_inverse(all n indices), inputs resident in device memory.  The L2 is
+flushed (a 256 MiB write) between timed steps, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank factors and inverts its own replica of the
+workload (the path does not shard; replicas only, no collective on the data
+path) and rank 0 prints one JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "diag(N^-1) entries/s"
+UNIT = "variances/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of a GB300 (profiling recipe's table)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny"])
+    return ap.parse_args()
+
+
+def workload(name):
+    from spigen import SCALE, TINY, generate
+    cfg = SCALE if name == "scale" else TINY
+    t = time.perf_counter()
+    pb = generate(cfg)
+    return pb, time.perf_counter() - t
+
+
+def config_of(pb, extra=None):
+    c = {"workload": f"{pb.cfg.name}: SPI normal matrix, P={pb.cfg.n_pointings} pointings x 19 detectors, "
+                     f"{pb.cfg.n_sources} sources, time-bins {pb.cfg.bin_lo}-{pb.cfg.bin_hi} pointings, "
+                     f"detector-pattern block {pb.cfg.det_block}; step = factor + solve + full diag(N^-1)",
+         "n": pb.n, "nnz_lower": pb.nnz, "seed": pb.cfg.seed, "l2": "flushed (256 MiB write) between timed steps"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_of(kernel_file: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the counters were taken."""
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = prof[key]
+        h = hashlib.sha256(open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", kernel_file), "rb").read()).hexdigest()
+        if ent.get("source_sha256") != h:
+            return None
+        return float(ent["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(pb, sample=1024, seed=0):
+    """The FP64 oracle as it stands on the host cores: its left-looking
+    factor (single thread) and solve of the whole matrix, then the inverse
+    diagonal for a random sample of indices on all cores, extrapolated to
+    all n indices."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    f = oracle.OracleFactor.from_problem(pb)
+    t_fac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f.solve(pb.b)
+    t_sol = time.perf_counter() - t0
+    idx = np.random.default_rng(seed).choice(pb.n, min(sample, pb.n), replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    f.inv_diag(idx, nthreads=cores)
+    t_smp = time.perf_counter() - t0
+    t_all = t_fac + t_sol + t_smp * pb.n / len(idx)
+    return f, {"value": pb.n / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"full left-looking factor ({t_fac:.1f} s, 1 thread) + solve ({t_sol:.2f} s) + "
+                         f"inverse diagonal of {len(idx)} random indices ({t_smp:.2f} s, {cores} threads), "
+                         f"extrapolated to all {pb.n} indices"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    pb, _ = workload(args.workload)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    f = oracle.OracleFactor.from_problem(pb)
+    t_fac = time.perf_counter() - t0
+    rng = np.random.default_rng(1)
+    S = 256
+    times = []
+    for it in range(args.warmup + args.steps):
+        idx = rng.choice(pb.n, min(S, pb.n), replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        f.inv_diag(idx, nthreads=cores)
+        dt = time.perf_counter() - t0 + t_fac * len(idx) / pb.n
+        if it >= args.warmup:
+            times.append(dt)
+    per_var = sum(times) / (args.steps * min(S, pb.n))
+    value = 1.0 / per_var
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(pb, {"reference": "FP64 CPU oracle (plain C)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: inverse diagonal of {S} random indices on {cores} threads "
+                                       f"plus the matching share of the one-off left-looking factor ({t_fac:.1f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1305_5683_gb300 as P
+
+    P.build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    pb, t_gen = workload(args.workload)
+
+    s = P.Solver.for_problem(pb, async_=True)
+    info0 = s.info()
+    st = torch.cuda.current_stream(dev)
+    vals = torch.from_numpy(pb.values).to(dev)
+    b = torch.from_numpy(pb.b).to(dev)
+    x = torch.empty_like(b)
+    var = torch.empty(pb.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev: ev[0].record(st)
+        s.factor(vals, stream=st)
+        if ev: ev[1].record(st)
+        s.solve(b, x, stream=st)
+        if ev: ev[2].record(st)
+        s.diag_inverse(out=var, stream=st)
+        if ev: ev[3].record(st)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    s.sync(st)
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            step(evs[k])
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+    s.sync(st)
+    t_fac = [e[0].elapsed_time(e[1]) for e in evs]
+    t_sol = [e[1].elapsed_time(e[2]) for e in evs]
+    t_dia = [e[2].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(a + b_ + c for a, b_, c in zip(t_fac, t_sol, t_dia))
+    tot = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms = float(tot.item())
+    info = s.info()
+    value = world * pb.n * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with pinned host buffers (copies inside)
+    hv = torch.from_numpy(pb.values).pin_memory()
+    hb = torch.from_numpy(pb.b).pin_memory()
+    hx = torch.empty(pb.n, dtype=torch.float64).pin_memory()
+    hvar = torch.empty(pb.n, dtype=torch.float64).pin_memory()
+    s_e2e = P.Solver.for_problem(pb)
+    s_e2e.factor(hv); s_e2e.solve(hb, hx); s_e2e.diag_inverse(out=hvar)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s_e2e.factor(hv, stream=st)
+        s_e2e.solve(hb, hx, stream=st)
+        s_e2e.diag_inverse(out=hvar, stream=st)
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+    e2e_t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * pb.n * args.steps / float(e2e_t.item())
+    agree = float((torch.abs(hvar.to(dev) - var) / var).max().item())
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    mean_dia = statistics.mean(t_dia) / 1e3
+    achieved = info["diag_flops_all"] / mean_dia / 1e12
+    roof = {"bound": "alu", "kernel": "k_diag_inv (pruned blocked forward solves, FP64)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); FP64 FMA probe measured 1.20",
+            "traffic": traffic_of("diag.cu", "k_diag_inv")}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        _, cpu = cpu_baseline(pb)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(pb, {"ordering": "nested dissection", "rhs_block": 128,
+                                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+        "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
+                      "diag_inverse": statistics.mean(t_dia)},
+        "factor_tflops": info["factor_flops"] / (statistics.mean(t_fac) / 1e3) / 1e12,
+        "factor_flops": info["factor_flops"], "diag_flops": info["diag_flops_all"],
+        "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (pb.nnz + pb.n),
+                "d2h_bytes_per_step": 8 * 2 * pb.n, "max_rel_diff_vs_device_run": agree},
+        "gpu_launches": args.steps * (info["launches_factor"] + info["launches_solve"] + info["launches_diag"]),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

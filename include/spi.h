@@ -87,6 +87,9 @@ typedef struct spi_stats {
     double solve_flops;     /* 4 * nnz_l + n (one forward + one backward sweep) */
     double diag_flops_all;  /* algorithmic flops of spi_diag_inverse over all n indices */
     int64_t device_bytes;   /* device memory held by the context */
+    int64_t launches_factor;/* kernels this library launches per spi_factor */
+    int64_t launches_solve; /* ... per spi_solve */
+    int64_t launches_diag;  /* ... per spi_diag_inverse */
     double analyse_seconds; /* host time of spi_analyse */
 } spi_stats;
 

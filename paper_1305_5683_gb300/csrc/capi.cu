@@ -367,6 +367,11 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->solve_flops = 4.0 * (double)S.nnz_l + (double)S.n;
     o->diag_flops_all = S.diag_flops_all;
     o->device_bytes = c->device_bytes;
+    o->launches_factor = 2 + (int64_t)c->FP.launches.size();
+    int64_t lv = 0;
+    for (int32_t l = 0; l < S.nlevels; ++l) lv += (S.level_ptr[l + 1] > S.level_ptr[l]);
+    o->launches_solve = S.n ? 2 + 2 * lv : 0;
+    o->launches_diag = S.n ? 1 : 0;
     o->analyse_seconds = c->analyse_seconds;
     return SPI_OK;
 }

@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="scale", choices=["scale", "tiny"])
+    ap.add_argument("--rhs-block", type=int, default=32)
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -214,7 +216,7 @@ def main():
     torch.cuda.set_device(dev)
     pb, t_gen = workload(args.workload)
 
-    s = P.Solver.for_problem(pb, async_=True)
+    s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block)
     info0 = s.info()
     st = torch.cuda.current_stream(dev)
     vals = torch.from_numpy(pb.values).to(dev)
@@ -263,7 +265,7 @@ def main():
     hb = torch.from_numpy(pb.b).pin_memory()
     hx = torch.empty(pb.n, dtype=torch.float64).pin_memory()
     hvar = torch.empty(pb.n, dtype=torch.float64).pin_memory()
-    s_e2e = P.Solver.for_problem(pb)
+    s_e2e = P.Solver.for_problem(pb, rhs_block=args.rhs_block)
     s_e2e.factor(hv); s_e2e.solve(hb, hx); s_e2e.diag_inverse(out=hvar)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -285,6 +287,47 @@ def main():
             dist.destroy_process_group()
         return
 
+    # the mixed-precision form on the same workload and the same step
+    mixed = None
+    if not args.no_mixed:
+        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, precision=P.SPI_PREC_MIXED_FP32)
+        xm = torch.empty_like(b)
+        varm = torch.empty_like(var)
+
+        def mstep(ev=None):
+            if ev: ev[0].record(st)
+            sm_.factor(vals, stream=st)
+            if ev: ev[1].record(st)
+            sm_.solve(b, xm, stream=st)
+            if ev: ev[2].record(st)
+            sm_.diag_inverse(out=varm, stream=st)
+            if ev: ev[3].record(st)
+
+        for _ in range(args.warmup):
+            mstep(); flush.zero_()
+        sm_.sync(st)
+        mevs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            mstep(mevs[k]); flush.zero_()
+        torch.cuda.synchronize(dev)
+        sm_.sync(st)
+        mf = [e[0].elapsed_time(e[1]) for e in mevs]
+        ms_ = [e[1].elapsed_time(e[2]) for e in mevs]
+        md = [e[2].elapsed_time(e[3]) for e in mevs]
+        mtot = sum(a + b_ + c for a, b_, c in zip(mf, ms_, md))
+        minfo = sm_.info()
+        mixed = {"value": world * pb.n * args.steps / (mtot / 1e3), "unit": UNIT, "ms_per_step": mtot / args.steps,
+                 "phases_ms": {"factor": statistics.mean(mf), "solve": statistics.mean(ms_),
+                               "diag_inverse": statistics.mean(md)},
+                 "speedup_vs_fp64": total_ms / mtot,
+                 "max_rel_err_var_vs_fp64": float((torch.abs(varm - var) / var).max().item()),
+                 "max_rel_err_x_vs_fp64": float((torch.abs(xm - x).max() / torch.abs(x).max()).item()),
+                 "refine_steps": minfo["refine_steps"], "solve_relres": minfo["solve_relres"],
+                 "diag_tflops_fp32": minfo["diag_flops_all"] / (statistics.mean(md) / 1e3) / 1e12,
+                 "dtype": "f32 updates / f64 pivots, refinement and variance sums"}
+        del sm_
+
     mean_dia = statistics.mean(t_dia) / 1e3
     achieved = info["diag_flops_all"] / mean_dia / 1e12
     roof = {"bound": "alu", "kernel": "k_diag_inv (pruned blocked forward solves, FP64)",
@@ -299,7 +342,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(pb, {"ordering": "nested dissection", "rhs_block": 128,
+        "config": config_of(pb, {"ordering": "nested dissection", "rhs_block": args.rhs_block,
                                  "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
         "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
                       "diag_inverse": statistics.mean(t_dia)},
@@ -307,6 +350,7 @@ def main():
         "factor_flops": info["factor_flops"], "diag_flops": info["diag_flops_all"],
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],
         "roofline": roof,
+        "mixed": mixed,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (pb.nnz + pb.n),
                 "d2h_bytes_per_step": 8 * 2 * pb.n, "max_rel_diff_vs_device_run": agree},

@@ -62,7 +62,8 @@ typedef enum spi_ordering {
 typedef struct spi_options {
     int precision;   /* spi_precision */
     int ordering;    /* spi_ordering */
-    int rhs_block;   /* right-hand sides per block in spi_diag_inverse; 0 = 128 (Sec. 4.3 uses 128) */
+    int rhs_block;   /* right-hand sides per block in spi_diag_inverse, 1..512; 0 = 128
+                        (Sec. 4.3 groups 128 right-hand sides) */
     int relax;       /* supernode amalgamation: max explicit zeros per merge as a percentage
                         of the merged panel (0 = fundamental supernodes only); default 10 */
     int refine_max;  /* max iterative-refinement steps of spi_solve in mixed precision */
@@ -90,6 +91,8 @@ typedef struct spi_stats {
     int64_t launches_factor;/* kernels this library launches per spi_factor */
     int64_t launches_solve; /* ... per spi_solve */
     int64_t launches_diag;  /* ... per spi_diag_inverse */
+    int64_t refine_steps;   /* refinement steps taken by the last spi_solve (mixed precision) */
+    double solve_relres;    /* ||b - N x||_2 / ||b||_2 after the last mixed-precision spi_solve */
     double analyse_seconds; /* host time of spi_analyse */
 } spi_stats;
 

@@ -274,11 +274,14 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
                     r = nx;
                 }
             }
-        // ---- postorder (children in increasing order)
-        std::vector<int32_t> head(n, -1), nxt(n, -1), post;
+        // ---- postorder: childless children first, then the others, each in increasing
+        //      order, so that a node's leaf children are numbered consecutively
+        std::vector<int32_t> head(n, -1), nxt(n, -1), post, nkids(n, 0);
         post.reserve(n);
-        for (int32_t v = n - 1; v >= 0; --v)
-            if (par[v] != -1) { nxt[v] = head[par[v]]; head[par[v]] = v; }
+        for (int32_t v = 0; v < n; ++v) if (par[v] != -1) nkids[par[v]]++;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int32_t v = n - 1; v >= 0; --v)
+                if (par[v] != -1 && (nkids[v] == 0) == (pass == 1)) { nxt[v] = head[par[v]]; head[par[v]] = v; }
         std::vector<int32_t> stk;
         for (int32_t r = 0; r < n; ++r) {
             if (par[r] != -1) continue;
@@ -329,6 +332,18 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
                 S.fdesc[S.parent[j]] = std::min(S.fdesc[S.parent[j]], S.fdesc[j]);
                 ncc[S.parent[j]]++;
             }
+        // input column access in pivot numbering: lower entries (r >= c) grouped by column c
+        std::vector<int64_t> ccp((size_t)n + 1, 0);
+        std::vector<int32_t> crow;
+        {
+            for (int32_t i = 0; i < n; ++i)
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ccp[rc[p] + 1]++;
+            for (int32_t j = 0; j < n; ++j) ccp[j + 1] += ccp[j];
+            crow.resize((size_t)ccp[n]);
+            std::vector<int64_t> f(ccp.begin(), ccp.end() - 1);
+            for (int32_t i = 0; i < n; ++i)
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) crow[f[rc[p]]++] = i;
+        }
         // ---- fundamental supernodes
         std::vector<int32_t> sf;
         for (int32_t j = 0; j < n; ++j) {
@@ -368,10 +383,69 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
                 merged[s] = 1;
             }
         }
-        S.sfirst.clear();
+        std::vector<int32_t> part;
         for (int32_t s = 0; s < nf; ++s)
-            if (!merged[s]) S.sfirst.push_back((int32_t)gf[s]);
-        S.sfirst.push_back(n);
+            if (!merged[s]) part.push_back((int32_t)gf[s]);
+        part.push_back(n);
+        // ---- sibling grouping: consecutive childless supernodes with the same parent are
+        //      merged into one front (their columns are independent: a diagonal pivot block)
+        //      while the merged rank-k update costs at most 2.5x the separate updates
+        if (prm.relax > 0) {
+            const int32_t np_ = (int32_t)part.size() - 1;
+            std::vector<int32_t> pn(n), ppar(np_, -1);
+            std::vector<char> haskid(np_, 0);
+            for (int32_t s = 0; s < np_; ++s)
+                for (int32_t j = part[s]; j < part[s + 1]; ++j) pn[j] = s;
+            for (int32_t s = 0; s < np_; ++s) {
+                int32_t pc = S.parent[part[s + 1] - 1];
+                if (pc != -1) { ppar[s] = pn[pc]; haskid[pn[pc]] = 1; }
+            }
+            std::vector<int32_t> stamp(n, -1), grouped;
+            int32_t s = 0;
+            while (s < np_) {
+                grouped.push_back(part[s]);
+                if (haskid[s] || ppar[s] == -1) { ++s; continue; }
+                // start a group at s
+                auto add_rows = [&](int32_t t, int32_t g, int64_t& cnt) {
+                    for (int32_t j = part[t]; j < part[t + 1]; ++j)
+                        for (int64_t p = ccp[j]; p < ccp[j + 1]; ++p) {
+                            int32_t r = crow[p];
+                            if (r >= part[t + 1] && stamp[r] != g) { stamp[r] = g; ++cnt; }
+                        }
+                };
+                auto below = [&](int32_t t) {  // |rows below| of a childless supernode
+                    return (int64_t)S.colcount[part[t]] - (part[t + 1] - part[t]);
+                };
+                int64_t ucnt = 0, kg = part[s + 1] - part[s];
+                double exact = (double)below(s) * below(s) * kg;
+                add_rows(s, s, ucnt);
+                int32_t t = s + 1;
+                while (t < np_ && !haskid[t] && ppar[t] == ppar[s]) {
+                    int64_t kt = part[t + 1] - part[t];
+                    if (kg + kt > 32) break;
+                    int64_t trial = ucnt;
+                    // count without committing: stamp with a temporary id then roll back if rejected
+                    std::vector<int32_t> added;
+                    for (int32_t j = part[t]; j < part[t + 1]; ++j)
+                        for (int64_t p = ccp[j]; p < ccp[j + 1]; ++p) {
+                            int32_t r = crow[p];
+                            if (r >= part[t + 1] && stamp[r] != s) { stamp[r] = s; ++trial; added.push_back(r); }
+                        }
+                    double ex2 = exact + (double)below(t) * below(t) * kt;
+                    double merged_cost = (double)trial * trial * (kg + kt);
+                    if (merged_cost > 2.5 * ex2) {
+                        for (int32_t r : added) stamp[r] = -1;
+                        break;
+                    }
+                    ucnt = trial; kg += kt; exact = ex2;
+                    ++t;
+                }
+                s = t;
+            }
+            grouped.push_back(n);
+            part.swap(grouped);
+        }
+        S.sfirst = part;
         S.ns = (int32_t)S.sfirst.size() - 1;
         const int32_t ns = S.ns;
         S.snode_of.resize(n);
@@ -390,18 +464,6 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
         {
             std::vector<int32_t> f(cfirst.begin(), cfirst.end() - 1);
             for (int32_t s = 0; s < ns; ++s) if (S.sparent[s] != -1) clist[f[S.sparent[s]]++] = s;
-        }
-        // input column access in pivot numbering: lower entries (r >= c) grouped by column c
-        std::vector<int64_t> ccp((size_t)n + 1, 0);
-        std::vector<int32_t> crow;
-        {
-            for (int32_t i = 0; i < n; ++i)
-                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ccp[rc[p] + 1]++;
-            for (int32_t j = 0; j < n; ++j) ccp[j + 1] += ccp[j];
-            crow.resize((size_t)ccp[n]);
-            std::vector<int64_t> f(ccp.begin(), ccp.end() - 1);
-            for (int32_t i = 0; i < n; ++i)
-                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) crow[f[rc[p]]++] = i;
         }
         S.srowptr.assign((size_t)ns + 1, 0);
         S.srows.clear();
@@ -533,7 +595,9 @@ void build_diag_plan(const Symbolic& S, const std::vector<int32_t>& pivots,
             P.rhs_zrow.push_back(zloc[sn] + (col - S.sfirst[sn]));
         }
         for (int32_t s : U) {
-            int32_t lcol = S.sfirst[s + 1] - 1, lo_col = S.fdesc[lcol];
+            // subtree of the supernode: [fdesc(last column), last column], or its own columns
+            // for a group of sibling leaves
+            int32_t lcol = S.sfirst[s + 1] - 1, lo_col = std::min(S.fdesc[lcol], S.sfirst[s]);
             auto beg = P.rhs_col.begin() + r0, end = P.rhs_col.begin() + r1;
             int32_t lo = (int32_t)(std::lower_bound(beg, end, lo_col) - beg);
             int32_t hi = (int32_t)(std::upper_bound(beg, end, lcol) - beg);

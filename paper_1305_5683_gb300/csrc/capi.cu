@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <climits>
 #include <cstring>
 #include <new>
@@ -32,11 +33,19 @@ struct spi_ctx {
     DevSym dsym;
     int64_t* d_amap = nullptr;
     int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
+            *d_items3 = nullptr,
             *d_level_list = nullptr;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
     DevStatus* h_status = nullptr;
+    // mixed precision: FP32 copy of the panels, the input pattern and values for refinement
+    float* d_L32 = nullptr;
+    int64_t* d_cp = nullptr;
+    int32_t* d_ri = nullptr;
+    double *d_b2 = nullptr, *d_x = nullptr, *d_r = nullptr, *d_dx = nullptr, *d_norm = nullptr, *h_norm = nullptr;
+    int64_t refine_steps = 0;
+    double solve_relres = 0;
     DevDiagPlan plan_all;
     bool plan_all_ready = false;
     DevDiagPlan plan_sub;
@@ -44,6 +53,8 @@ struct spi_ctx {
     bool plan_sub_ready = false;
     double last_diag_flops = 0;
     int64_t bad_pivot = -1;
+    std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
+    std::vector<int32_t> in_rowind;
     double analyse_seconds = 0;
 };
 
@@ -102,6 +113,7 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &c->d_items0, c->FP.diag_items));
     CK(dev_upload(c, &c->d_items1, c->FP.trsm_items));
     CK(dev_upload(c, &c->d_items2, c->FP.schur_items));
+    CK(dev_upload(c, &c->d_items3, c->FP.update_items));
     CK(dev_upload(c, &c->d_level_list, S.level_list));
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns]));
     CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total));
@@ -113,9 +125,26 @@ int ensure_device(spi_ctx* c) {
     CK(dev_alloc(c, &c->d_out, (size_t)S.n));
     CK(dev_alloc(c, &c->d_status, 1));
     CK(cudaMallocHost((void**)&c->h_status, sizeof(DevStatus)));
+    if (c->opt.precision == SPI_PREC_MIXED_FP32) {
+        CK(dev_alloc(c, &c->d_L32, (size_t)S.lptr[S.ns]));
+        CK(dev_alloc(c, &c->d_cp, (size_t)S.n + 1));
+        CK(dev_alloc(c, &c->d_ri, (size_t)S.nnz_a));
+        CK(cudaMemcpy(c->d_cp, c->in_colptr.data(), c->in_colptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        if (S.nnz_a)
+            CK(cudaMemcpy(c->d_ri, c->in_rowind.data(), c->in_rowind.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        std::vector<int64_t>().swap(c->in_colptr);
+        std::vector<int32_t>().swap(c->in_rowind);
+        CK(dev_alloc(c, &c->d_b2, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_x, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_r, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_dx, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_norm, 2));
+        CK(cudaMallocHost((void**)&c->h_norm, 2 * sizeof(double)));
+    }
     int32_t kmax = 0;
     for (int32_t s = 0; s < S.ns; ++s) kmax = std::max(kmax, S.k_of(s));
     if (solve_kernel_setup(kmax) != cudaSuccess) return SPI_ERR_CUDA;
+    if (diag_kernel_setup(c->opt.rhs_block) != cudaSuccess) return SPI_ERR_CUDA;
     c->dev_ready = true;
     return SPI_OK;
 }
@@ -209,7 +238,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     spi_default_options(&o);
     if (opt) o = *opt;
     if (o.rhs_block <= 0) o.rhs_block = 128;
-    if (o.rhs_block > 1024 || o.precision < 0 || o.precision > 1 || o.ordering < 0 || o.ordering > 1 ||
+    if (o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 || o.ordering > 1 ||
         o.relax < 0)
         return SPI_ERR_ARG;
     spi_ctx* c = new (std::nothrow) spi_ctx();
@@ -233,6 +262,15 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
         delete c;
         return SPI_ERR_OOM;
     }
+    if (o.precision == SPI_PREC_MIXED_FP32 && n > 0) {
+        try {
+            c->in_colptr.assign(colptr, colptr + n + 1);
+            c->in_rowind.assign(rowind, rowind + colptr[n]);
+        } catch (const std::bad_alloc&) {
+            delete c;
+            return SPI_ERR_OOM;
+        }
+    }
     c->analyse_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = c;
     return SPI_OK;
@@ -247,9 +285,11 @@ int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* str
     const Symbolic& S = c->S;
     c->factored = false;
     c->bad_pivot = -1;
+    const bool mixed = c->opt.precision == SPI_PREC_MIXED_FP32;
     const double* vals = values;
-    if (!values_on_device && S.nnz_a > 0) {
-        CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (S.nnz_a > 0 && (!values_on_device || mixed)) {
+        CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * sizeof(double),
+                           values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         vals = c->d_vals;
     }
     k_reset_status<<<1, 1, 0, st>>>(c->d_status);
@@ -257,35 +297,71 @@ int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* str
     if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * sizeof(double), st));
     launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, st);
     for (const Launch& l : c->FP.launches) {
-        const int32_t* items = l.kind == 0 ? c->d_items0 : (l.kind == 1 ? c->d_items1 : c->d_items2);
-        launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, st);
+        const int32_t* items = l.kind == 0 ? c->d_items0
+                             : l.kind == 1 ? c->d_items1
+                             : l.kind == 2 ? c->d_items2 : c->d_items3;
+        launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, st);
     }
+    if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns], st);
     rc = finish(c, st);
     if (rc == SPI_OK) c->factored = true;
     return rc;
 }
 
-int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, void* stream) {
-    if (!c || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
-    if (!c->factored) return SPI_ERR_STATE;
-    cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// x = P^T L^-T D^-1 L^-1 P b on device buffers (b and x distinct from d_w).
+void solve_core(spi_ctx* c, const double* b, double* x, cudaStream_t st) {
     const Symbolic& S = c->S;
-    const double* bd = b;
-    if (!on_device && S.n) {
-        CK(cudaMemcpyAsync(c->d_vec, b, (size_t)S.n * sizeof(double), cudaMemcpyHostToDevice, st));
-        bd = c->d_vec;
-    }
-    launch_permute_in(S.n, c->dsym.perm, bd, c->d_w, st);
+    launch_permute_in(S.n, c->dsym.perm, b, c->d_w, st);
     for (int32_t l = 0; l < S.nlevels; ++l)
         launch_fwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
                          c->level_kmax[l], c->d_L, c->d_w, st);
     for (int32_t l = S.nlevels - 1; l >= 0; --l)
         launch_bwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
                          c->level_kmax[l], c->d_L, c->d_D, c->d_w, st);
+    launch_permute_out(S.n, c->dsym.perm, c->d_w, x, st);
+}
+}  // namespace
+
+extern "C" int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, void* stream) {
+    if (!c || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    const int32_t n = S.n;
+    const double* bd = b;
+    if (!on_device && n) {
+        CK(cudaMemcpyAsync(c->d_vec, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+        bd = c->d_vec;
+    }
     double* xd = on_device ? x : c->d_vec;
-    launch_permute_out(S.n, c->dsym.perm, c->d_w, xd, st);
-    if (!on_device && S.n)
-        CK(cudaMemcpyAsync(x, xd, (size_t)S.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (c->opt.precision != SPI_PREC_MIXED_FP32) {
+        solve_core(c, bd, xd, st);
+    } else if (n) {
+        // FP64 iterative refinement against N: x += solve(b - N x)
+        CK(cudaMemcpyAsync(c->d_b2, bd, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        solve_core(c, c->d_b2, c->d_x, st);
+        double bnorm = -1.0;
+        c->refine_steps = 0;
+        for (int it = 0;; ++it) {
+            CK(cudaMemcpyAsync(c->d_r, c->d_b2, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, c->d_x, c->d_r, st);
+            CK(cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), st));
+            launch_norms2(n, c->d_r, bnorm < 0 ? c->d_b2 : nullptr, c->d_norm, st);
+            CK(cudaMemcpyAsync(c->h_norm, c->d_norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (bnorm < 0) bnorm = std::sqrt(c->h_norm[1]);
+            double rn = std::sqrt(c->h_norm[0]);
+            c->solve_relres = bnorm > 0 ? rn / bnorm : rn;
+            if (rn <= c->opt.refine_tol * bnorm || it >= c->opt.refine_max) break;
+            solve_core(c, c->d_r, c->d_dx, st);
+            launch_axpy(n, c->d_dx, c->d_x, st);
+            c->refine_steps++;
+        }
+        CK(cudaMemcpyAsync(xd, c->d_x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    if (!on_device && n)
+        CK(cudaMemcpyAsync(x, xd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return finish(c, st);
 }
@@ -342,7 +418,8 @@ int spi_diag_inverse(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, 
         }
         od = c->d_out;
     }
-    launch_diag_inverse(c->dsym, *plan, c->d_L, c->d_D, od, st);
+    if (c->opt.precision == SPI_PREC_MIXED_FP32) launch_diag_inverse_f32(c->dsym, *plan, c->d_L32, c->d_D, od, st);
+    else launch_diag_inverse(c->dsym, *plan, c->d_L, c->d_D, od, st);
     if (!on_device && nout)
         CK(cudaMemcpyAsync(out, od, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, st));
     c->last_diag_flops = plan->flops;
@@ -372,6 +449,9 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     for (int32_t l = 0; l < S.nlevels; ++l) lv += (S.level_ptr[l + 1] > S.level_ptr[l]);
     o->launches_solve = S.n ? 2 + 2 * lv : 0;
     o->launches_diag = S.n ? 1 : 0;
+    if (c->opt.precision == SPI_PREC_MIXED_FP32) o->launches_factor += 1;
+    o->refine_steps = c->refine_steps;
+    o->solve_relres = c->solve_relres;
     o->analyse_seconds = c->analyse_seconds;
     return SPI_OK;
 }

@@ -6,8 +6,10 @@
 // columns of N plus the contributions of its children, and whose trailing
 // (m-k) x (m-k) part (F22, present only when s has children) accumulates the
 // children's contribution blocks.  Per front:
-//   F11 = L11 D1 L11^T          (diagonal tiles, FP64, one CTA per tile)
-//   L21 = F21 L11^-T D1^-1      (panel row tiles, left-looking per block column)
+//   F11 = L11 D1 L11^T, L21 = F21 L11^-T D1^-1: right-looking over block
+//       columns of 32 -- the diagonal tile (one CTA, FP64), the row tiles
+//       below it (one CTA each), then the rank-32 update of the trailing
+//       panel columns (one CTA per 32 x 32 tile);
 //   C   = F22 - L21 D1 L21^T    (Schur complement tiles)
 // and C is added into the parent's front through the parent-relative index
 // map (the extend-add of the multifrontal method), with FP64 atomics because
@@ -32,6 +34,7 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F) {
         for (int32_t b = 0; b < nsteps; ++b) {
             Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
             Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
+            Launch lu{3, b, (int64_t)F.update_items.size() / 3, 0};
             for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
                 int32_t s = S.level_list[p];
                 int32_t k = S.k_of(s), m = S.m_of(s);
@@ -44,9 +47,20 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F) {
                     F.trsm_items.push_back(rt);
                     lt.count++;
                 }
+                // trailing panel columns [r0, k): lower tiles of rows [cj, m)
+                for (int32_t tj = 0; r0 + tj * kT < k; ++tj) {
+                    int32_t cj = r0 + tj * kT;
+                    for (int32_t ti = 0; cj + ti * kT < m; ++ti) {
+                        F.update_items.push_back(s);
+                        F.update_items.push_back(ti);
+                        F.update_items.push_back(tj);
+                        lu.count++;
+                    }
+                }
             }
             if (ld.count) F.launches.push_back(ld);
             if (lt.count) F.launches.push_back(lt);
+            if (lu.count) F.launches.push_back(lu);
         }
         Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
@@ -80,13 +94,12 @@ __global__ void k_assemble(const int64_t* __restrict__ amap, const double* __res
 
 constexpr int kThreads = 128;
 
-// Diagonal tile of block column b: left-looking update from the block
-// columns before it, then an unblocked LDL^T in shared memory.
+// Diagonal tile of block column b (already updated by the block columns
+// before it): unblocked LDL^T in shared memory, FP64.
 __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
                                                         double* __restrict__ L, double* __restrict__ D,
                                                         const double* __restrict__ adiag, DevStatus* status) {
     __shared__ double A[kT][kT + 1];
-    __shared__ double Bs[kT][kT + 1];
     __shared__ double dv[kT];
     const int tid = threadIdx.x;
     const int s = items[blockIdx.x];
@@ -98,24 +111,6 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
         int i = e % kT, j = e / kT;
         A[i][j] = (i < w && j <= i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
     }
-    for (int cb = 0; cb < c0; cb += kT) {
-        __syncthreads();
-        for (int e = tid; e < kT * kT; e += kThreads) {
-            int i = e % kT, c = e / kT;
-            Bs[i][c] = (i < w) ? P[(c0 + i) + (int64_t)(cb + c) * m] : 0.0;
-        }
-        if (tid < kT) dv[tid] = D[f + cb + tid];
-        __syncthreads();
-        for (int e = tid; e < kT * kT; e += kThreads) {
-            int i = e % kT, j = e / kT;
-            if (j <= i && i < w) {
-                double acc = 0.0;
-#pragma unroll 8
-                for (int c = 0; c < kT; ++c) acc += Bs[i][c] * dv[c] * Bs[j][c];
-                A[i][j] -= acc;
-            }
-        }
-    }
     __syncthreads();
     for (int c = 0; c < w; ++c) {
         const double dc = A[c][c];
@@ -126,13 +121,14 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
             }
         }
         __syncthreads();
+        const double inv = 1.0 / dc;
         for (int e = tid; e < kT * kT; e += kThreads) {
             int i = e % kT, j = e / kT;
-            if (j > c && j <= i && i < w) A[i][j] -= A[i][c] * A[j][c] / dc;
+            if (j > c && j <= i && i < w) A[i][j] -= A[i][c] * inv * A[j][c];
         }
         __syncthreads();
         if (tid == 0) dv[c] = dc;
-        for (int i = c + 1 + tid; i < w; i += kThreads) A[i][c] /= dc;
+        for (int i = c + 1 + tid; i < w; i += kThreads) A[i][c] *= inv;
         __syncthreads();
     }
     for (int e = tid; e < kT * kT; e += kThreads) {
@@ -142,14 +138,14 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
     if (tid < w) D[f + c0 + tid] = dv[tid];
 }
 
-// Row tile rt below the diagonal tile of block column b: left-looking
-// update, then L21 = X L11^-T D^-1 row by row.
+// Row tile rt below the diagonal tile of block column b (already updated by
+// the block columns before it): L21 = X L11^-T D^-1, one thread per row.
+template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t* __restrict__ items, int b,
                                                          double* __restrict__ L, const double* __restrict__ D) {
-    __shared__ double X[kT][kT + 1];
-    __shared__ double Br[kT][kT + 1];
-    __shared__ double Bd[kT][kT + 1];
-    __shared__ double dv[kT];
+    __shared__ C X[kT][kT + 1];
+    __shared__ C Bd[kT][kT + 1];
+    __shared__ C dv[kT];
     const int tid = threadIdx.x;
     const int s = items[2 * blockIdx.x], rt = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -160,52 +156,74 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
     const int nr = (int)(m - r0 < kT ? m - r0 : kT);
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        X[i][j] = (i < nr && j < w) ? P[(r0 + i) + (int64_t)(c0 + j) * m] : 0.0;
+        X[i][j] = (i < nr && j < w) ? (C)P[(r0 + i) + (int64_t)(c0 + j) * m] : C(0);
+        Bd[i][j] = (i < w && j < i) ? (C)P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
     }
-    for (int cb = 0; cb < c0; cb += kT) {
-        __syncthreads();
-        for (int e = tid; e < kT * kT; e += kThreads) {
-            int i = e % kT, c = e / kT;
-            Br[i][c] = (i < nr) ? P[(r0 + i) + (int64_t)(cb + c) * m] : 0.0;
-            Bd[i][c] = (i < w) ? P[(c0 + i) + (int64_t)(cb + c) * m] : 0.0;
-        }
-        if (tid < kT) dv[tid] = D[f + cb + tid];
-        __syncthreads();
-        for (int e = tid; e < kT * kT; e += kThreads) {
-            int i = e % kT, j = e / kT;
-            if (i < nr && j < w) {
-                double acc = 0.0;
-#pragma unroll 8
-                for (int c = 0; c < kT; ++c) acc += Br[i][c] * dv[c] * Bd[j][c];
-                X[i][j] -= acc;
-            }
-        }
-    }
-    __syncthreads();
-    // L11 (unit lower) of this block column and its pivots
-    for (int e = tid; e < kT * kT; e += kThreads) {
-        int i = e % kT, c = e / kT;
-        Bd[i][c] = (i < w && c < i) ? P[(c0 + i) + (int64_t)(c0 + c) * m] : 0.0;
-    }
-    if (tid < kT) dv[tid] = (tid < w) ? D[f + c0 + tid] : 1.0;
+    if (tid < kT) dv[tid] = (tid < w) ? (C)(1.0 / D[f + c0 + tid]) : C(0);
     __syncthreads();
     if (tid < nr) {
         const int i = tid;
         for (int c = 0; c < w; ++c) {
-            double y = X[i][c];
+            C y = X[i][c];
             for (int cp = 0; cp < c; ++cp) y -= X[i][cp] * Bd[c][cp];
             X[i][c] = y;
         }
-        for (int c = 0; c < w; ++c) P[(r0 + i) + (int64_t)(c0 + c) * m] = X[i][c] / dv[c];
+    }
+    __syncthreads();
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, j = e / kT;
+        if (i < nr && j < w) P[(r0 + i) + (int64_t)(c0 + j) * m] = (double)(X[i][j] * dv[j]);
+    }
+}
+
+// Trailing panel update after block column b: for panel columns j in
+// [c0+w, k) and rows i >= j, P[i][j] -= sum_{c in block b} L[i][c] d_c L[j][c].
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32_t* __restrict__ items, int b,
+                                                           double* __restrict__ L, const double* __restrict__ D) {
+    __shared__ C Li[kT][kT + 1];
+    __shared__ C Lj[kT][kT + 1];
+    const int tid = threadIdx.x;
+    const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    double* P = L + d.lptr[s];
+    const int c0 = b * kT, w = min(kT, k - c0);
+    const int cj = c0 + w + tj * kT;
+    const int64_t ri = cj + (int64_t)ti * kT;
+    const int nj = min(kT, k - cj);
+    const int ni = (int)(m - ri < kT ? m - ri : kT);
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        int i = e % kT, c = e / kT;
+        Li[i][c] = (i < ni && c < w) ? (C)P[(ri + i) + (int64_t)(c0 + c) * m] : C(0);
+        Lj[i][c] = (i < nj && c < w) ? (C)(P[(cj + i) + (int64_t)(c0 + c) * m] * D[f + c0 + c]) : C(0);
+    }
+    __syncthreads();
+    const int jj = tid % kT, i0 = tid / kT;
+    if (jj >= nj) return;
+    C acc[kT / 4];
+#pragma unroll
+    for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
+#pragma unroll 4
+    for (int c = 0; c < kT; ++c) {
+        const C bj = Lj[jj][c];
+#pragma unroll
+        for (int r = 0; r < kT / 4; ++r) acc[r] += Li[i0 + 4 * r][c] * bj;
+    }
+#pragma unroll
+    for (int r = 0; r < kT / 4; ++r) {
+        const int i = i0 + 4 * r;
+        if (i < ni && ri + i >= cj + jj) P[(ri + i) + (int64_t)(cj + jj) * m] -= (double)acc[r];
     }
 }
 
 // Schur complement tile (ti, tj) of the trailing (m-k)^2 part, added into the parent's front.
+template <typename C>
 __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int32_t* __restrict__ items,
                                                             double* __restrict__ L, double* __restrict__ F22,
                                                             const double* __restrict__ D) {
-    __shared__ double Li[kT][kT + 1];
-    __shared__ double Lj[kT][kT + 1];
+    __shared__ C Li[kT][kT + 1];
+    __shared__ C Lj[kT][kT + 1];
     const int tid = threadIdx.x;
     const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -215,21 +233,21 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     const int64_t ib = k + (int64_t)ti * kT, jb = k + (int64_t)tj * kT;
     const int ni = (int)(m - ib < kT ? m - ib : kT), nj = (int)(m - jb < kT ? m - jb : kT);
     const int jj = tid % kT, i0 = tid / kT;  // thread owns column jj, rows i0 + 4 r
-    double acc[kT / 4];
+    C acc[kT / 4];
 #pragma unroll
-    for (int r = 0; r < kT / 4; ++r) acc[r] = 0.0;
+    for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
     for (int cb = 0; cb < k; cb += kT) {
         const int cw = min(kT, k - cb);
         __syncthreads();
         for (int e = tid; e < kT * kT; e += kThreads) {
             int i = e % kT, c = e / kT;
-            Li[i][c] = (i < ni && c < cw) ? P[(ib + i) + (int64_t)(cb + c) * m] : 0.0;
-            Lj[i][c] = (i < nj && c < cw) ? P[(jb + i) + (int64_t)(cb + c) * m] * D[f + cb + c] : 0.0;
+            Li[i][c] = (i < ni && c < cw) ? (C)P[(ib + i) + (int64_t)(cb + c) * m] : C(0);
+            Lj[i][c] = (i < nj && c < cw) ? (C)(P[(jb + i) + (int64_t)(cb + c) * m] * D[f + cb + c]) : C(0);
         }
         __syncthreads();
 #pragma unroll 4
         for (int c = 0; c < kT; ++c) {
-            const double bj = Lj[jj][c];
+            const C bj = Lj[jj][c];
 #pragma unroll
             for (int r = 0; r < kT / 4; ++r) acc[r] -= Li[i0 + 4 * r][c] * bj;
         }
@@ -249,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
         const int i = i0 + 4 * r;
         const int64_t il = ib + i;
         if (i >= ni || il < jl) continue;
-        double v = acc[r];
+        double v = (double)acc[r];
         if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
         const int qi = rel[il];
         if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
@@ -257,7 +275,18 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     }
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
 }  // namespace
+
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_to_f32<<<grid, 256, 0, st>>>(a, b, n);
+}
 
 void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
                      const int32_t* diag_src, double* adiag, cudaStream_t st) {
@@ -267,14 +296,22 @@ void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, i
     k_assemble<<<grid, 256, 0, st>>>(amap, vals, nnz, L, diag_src, d.n, adiag);
 }
 
-void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, cudaStream_t st) {
-    if (l.count == 0) return;
+template <typename C>
+void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22, double* D,
+                   const double* adiag, DevStatus* status, cudaStream_t st) {
     switch (l.kind) {
         case 0: k_diag_tile<<<l.count, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status); break;
-        case 1: k_panel_trsm<<<l.count, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D); break;
-        default: k_schur_scatter<<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D); break;
+        case 1: k_panel_trsm<C><<<l.count, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D); break;
+        case 3: k_panel_update<C><<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D); break;
+        default: k_schur_scatter<C><<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D); break;
     }
+}
+
+void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
+                        double* D, const double* adiag, DevStatus* status, bool mixed, cudaStream_t st) {
+    if (l.count == 0) return;
+    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, st);
+    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, st);
 }
 
 }  // namespace spi

@@ -76,7 +76,67 @@ __global__ void __launch_bounds__(kThreads) k_bwd(DevSym d, const int32_t* __res
     for (int c = tid; c < k; c += kThreads) w[f + c] = ys[c];
 }
 
+// r -= N x for the symmetric N given by its lower CSC (caller numbering), one
+// warp per column: the column's dot product for r_j, and the mirrored
+// upper-triangle entries scattered into r_i.
+__global__ void k_sym_residual(int32_t n, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                               const double* __restrict__ va, const double* __restrict__ x, double* __restrict__ r) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n;
+         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const double xj = x[j];
+        double acc = 0.0;
+        for (int64_t p = cp[j] + lane; p < cp[j + 1]; p += 32) {
+            const int32_t i = ri[p];
+            const double a = va[p];
+            acc += a * x[i];
+            if (i != j) atomicAdd(r + i, -a * xj);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) atomicAdd(r + j, -acc);
+    }
+}
+
+// out[0] += sum a_i^2, out[1] += sum b_i^2
+__global__ void k_norms2(int32_t n, const double* __restrict__ a, const double* __restrict__ b, double* out) {
+    double sa = 0.0, sb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        sa += a[i] * a[i];
+        if (b) sb += b[i] * b[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, sa);
+        if (b) atomicAdd(out + 1, sb);
+    }
+}
+
+__global__ void k_axpy(int32_t n, const double* __restrict__ dx, double* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += dx[i];
+}
+
 }  // namespace
+
+void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
+                         double* r, cudaStream_t st) {
+    if (n == 0) return;
+    int grid = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 152 * 8);
+    k_sym_residual<<<grid, 256, 0, st>>>(n, cp, ri, va, x, r);
+}
+
+void launch_norms2(int32_t n, const double* a, const double* b, double* out, cudaStream_t st) {
+    if (n == 0) return;
+    k_norms2<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, a, b, out);
+}
+
+void launch_axpy(int32_t n, const double* dx, double* x, cudaStream_t st) {
+    if (n == 0) return;
+    k_axpy<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, dx, x);
+}
 
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st) {
     if (n == 0) return;

@@ -38,7 +38,7 @@ struct DevSym {
 
 // A flattened work list of one kernel launch.
 struct Launch {
-    int kind;        // 0 diag tile, 1 panel TRSM, 2 Schur+scatter
+    int kind;        // 0 diag tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs
@@ -48,6 +48,7 @@ struct FactorPlan {
     std::vector<int32_t> diag_items;  // supernode
     std::vector<int32_t> trsm_items;  // pairs (supernode, row tile)
     std::vector<int32_t> schur_items; // triples (supernode, ti, tj)
+    std::vector<int32_t> update_items;// triples (supernode, ti, tj) of the trailing panel
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
 };
@@ -70,7 +71,8 @@ struct DevDiagPlan {
 void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
                      const int32_t* diag_src, double* adiag, cudaStream_t st);
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, cudaStream_t st);
+                        double* D, const double* adiag, DevStatus* status, bool mixed, cudaStream_t st);
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, cudaStream_t st);
@@ -78,10 +80,17 @@ void launch_fwd_level(const DevSym& d, const int32_t* list, int32_t count, int32
                       double* w, cudaStream_t st);
 void launch_bwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
                       const double* D, double* w, cudaStream_t st);
+void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
+                         double* r, cudaStream_t st);
+void launch_norms2(int32_t n, const double* a, const double* b, double* out, cudaStream_t st);
+void launch_axpy(int32_t n, const double* dx, double* x, cudaStream_t st);
 // one-time kernel attributes (large dynamic shared memory)
 cudaError_t solve_kernel_setup(int32_t kmax);
 // ---- diag.cu
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
                          cudaStream_t st);
+void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
+                             cudaStream_t st);
+cudaError_t diag_kernel_setup(int B);
 
 }  // namespace spi

@@ -40,6 +40,7 @@ class spi_stats(ctypes.Structure):
                 ("solve_flops", ctypes.c_double), ("diag_flops_all", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
                 ("launches_solve", ctypes.c_int64), ("launches_diag", ctypes.c_int64),
+                ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),
                 ("analyse_seconds", ctypes.c_double)]
 
     def as_dict(self):

@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="scale", choices=["scale", "tiny"])
-    ap.add_argument("--rhs-block", type=int, default=32)
+    ap.add_argument("--rhs-block", type=int, default=0, help="0 = the library's automatic choice")
+    ap.add_argument("--rhs-block-mixed", type=int, default=0)
     ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
@@ -290,7 +291,7 @@ def main():
     # the mixed-precision form on the same workload and the same step
     mixed = None
     if not args.no_mixed:
-        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, precision=P.SPI_PREC_MIXED_FP32)
+        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, precision=P.SPI_PREC_MIXED_FP32)
         xm = torch.empty_like(b)
         varm = torch.empty_like(var)
 

@@ -62,8 +62,9 @@ typedef enum spi_ordering {
 typedef struct spi_options {
     int precision;   /* spi_precision */
     int ordering;    /* spi_ordering */
-    int rhs_block;   /* right-hand sides per block in spi_diag_inverse, 1..512; 0 = 128
-                        (Sec. 4.3 groups 128 right-hand sides) */
+    int rhs_block;   /* right-hand sides per block in spi_diag_inverse, 1..512 (rounded up to a
+                        multiple of 8 in mixed precision); 0 = automatic: 32 in FP64, 64 in
+                        mixed precision (Sec. 4.3 groups 128 right-hand sides on a CPU core) */
     int relax;       /* supernode amalgamation: max explicit zeros per merge as a percentage
                         of the merged panel (0 = fundamental supernodes only); default 10 */
     int refine_max;  /* max iterative-refinement steps of spi_solve in mixed precision */
@@ -98,7 +99,7 @@ typedef struct spi_stats {
 
 typedef struct spi_ctx spi_ctx;
 
-/* Fill *opt with the defaults (FP64, nested dissection, 128 RHS per block,
+/* Fill *opt with the defaults (FP64, nested dissection, automatic RHS block,
  * relax 10, refine_max 10, refine_tol 1e-13, synchronous). */
 void spi_default_options(spi_options* opt);
 

@@ -25,7 +25,11 @@ struct spi_ctx {
     Symbolic S;
     spi_options opt{};
     FactorPlan FP;
-    std::vector<int32_t> level_kmax;
+    SolvePlan SP;
+    int32_t* d_fwd_items = nullptr;
+    int32_t* d_bwd_items = nullptr;
+    double* d_z = nullptr;
+    double* d_xp = nullptr;
     int device = -1;
     bool dev_ready = false, factored = false;
     std::vector<void*> allocs;
@@ -46,6 +50,9 @@ struct spi_ctx {
     double *d_b2 = nullptr, *d_x = nullptr, *d_r = nullptr, *d_dx = nullptr, *d_norm = nullptr, *h_norm = nullptr;
     int64_t refine_steps = 0;
     double solve_relres = 0;
+    // CUDA graphs of the launch sequences that touch only context buffers
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g_factor = nullptr, g_solve = nullptr;
     DevDiagPlan plan_all;
     bool plan_all_ready = false;
     DevDiagPlan plan_sub;
@@ -141,9 +148,11 @@ int ensure_device(spi_ctx* c) {
         CK(dev_alloc(c, &c->d_norm, 2));
         CK(cudaMallocHost((void**)&c->h_norm, 2 * sizeof(double)));
     }
-    int32_t kmax = 0;
-    for (int32_t s = 0; s < S.ns; ++s) kmax = std::max(kmax, S.k_of(s));
-    if (solve_kernel_setup(kmax) != cudaSuccess) return SPI_ERR_CUDA;
+    CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
+    CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
+    CK(dev_alloc(c, &c->d_z, (size_t)S.n));
+    CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CK(dev_alloc(c, &c->d_xp, (size_t)S.n));
     if (diag_kernel_setup(c->opt.rhs_block) != cudaSuccess) return SPI_ERR_CUDA;
     c->dev_ready = true;
     return SPI_OK;
@@ -179,6 +188,29 @@ int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
     return SPI_OK;
 }
 
+// Record `body(stream)` once into a CUDA graph and replay it on `st`; if the
+// capture fails, run the launches directly on `st`.
+template <class F>
+cudaError_t run_graph(spi_ctx* c, cudaGraphExec_t* exec, cudaStream_t st, F&& body) {
+    if (!*exec) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            body(c->cap);
+            e = cudaStreamEndCapture(c->cap, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *exec = nullptr;
+            cudaGetLastError();
+            body(st);
+            return cudaGetLastError();
+        }
+    }
+    return cudaGraphLaunch(*exec, st);
+}
+
 __global__ void k_reset_status(DevStatus* s) {
     s->flags = 0;
     s->bad_pivot = INT_MAX;
@@ -208,7 +240,7 @@ void spi_default_options(spi_options* o) {
     std::memset(o, 0, sizeof *o);
     o->precision = SPI_PREC_FP64;
     o->ordering = SPI_ORDER_ND;
-    o->rhs_block = 128;
+    o->rhs_block = 0;
     o->relax = 10;
     o->refine_max = 10;
     o->refine_tol = 1e-13;
@@ -237,7 +269,8 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     spi_options o;
     spi_default_options(&o);
     if (opt) o = *opt;
-    if (o.rhs_block <= 0) o.rhs_block = 128;
+    if (o.rhs_block <= 0) o.rhs_block = o.precision == SPI_PREC_MIXED_FP32 ? 64 : 32;
+    if (o.precision == SPI_PREC_MIXED_FP32) o.rhs_block = (o.rhs_block + 7) & ~7;  // float4 rows of Z
     if (o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 || o.ordering > 1 ||
         o.relax < 0)
         return SPI_ERR_ARG;
@@ -254,10 +287,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (rc != 0) { delete c; return rc; }
     try {
         build_factor_plan(c->S, c->FP);
-        c->level_kmax.assign(c->S.nlevels, 0);
-        for (int32_t l = 0; l < c->S.nlevels; ++l)
-            for (int32_t p = c->S.level_ptr[l]; p < c->S.level_ptr[l + 1]; ++p)
-                c->level_kmax[l] = std::max(c->level_kmax[l], c->S.k_of(c->S.level_list[p]));
+        build_solve_plan(c->S, c->SP);
     } catch (const std::bad_alloc&) {
         delete c;
         return SPI_ERR_OOM;
@@ -296,13 +326,15 @@ int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* str
     CK(cudaMemsetAsync(c->d_L, 0, (size_t)S.lptr[S.ns] * sizeof(double), st));
     if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * sizeof(double), st));
     launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, st);
-    for (const Launch& l : c->FP.launches) {
-        const int32_t* items = l.kind == 0 ? c->d_items0
-                             : l.kind == 1 ? c->d_items1
-                             : l.kind == 2 ? c->d_items2 : c->d_items3;
-        launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, st);
-    }
-    if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns], st);
+    CK(run_graph(c, &c->g_factor, st, [&](cudaStream_t s2) {
+        for (const Launch& l : c->FP.launches) {
+            const int32_t* items = l.kind == 0 ? c->d_items0
+                                 : l.kind == 1 ? c->d_items1
+                                 : l.kind == 2 ? c->d_items2 : c->d_items3;
+            launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, s2);
+        }
+        if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns], s2);
+    }));
     rc = finish(c, st);
     if (rc == SPI_OK) c->factored = true;
     return rc;
@@ -310,16 +342,17 @@ int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* str
 
 namespace {
 // x = P^T L^-T D^-1 L^-1 P b on device buffers (b and x distinct from d_w).
-void solve_core(spi_ctx* c, const double* b, double* x, cudaStream_t st) {
+cudaError_t solve_core(spi_ctx* c, const double* b, double* x, cudaStream_t st) {
     const Symbolic& S = c->S;
     launch_permute_in(S.n, c->dsym.perm, b, c->d_w, st);
-    for (int32_t l = 0; l < S.nlevels; ++l)
-        launch_fwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
-                         c->level_kmax[l], c->d_L, c->d_w, st);
-    for (int32_t l = S.nlevels - 1; l >= 0; --l)
-        launch_bwd_level(c->dsym, c->d_level_list + S.level_ptr[l], S.level_ptr[l + 1] - S.level_ptr[l],
-                         c->level_kmax[l], c->d_L, c->d_D, c->d_w, st);
-    launch_permute_out(S.n, c->dsym.perm, c->d_w, x, st);
+    cudaError_t e = run_graph(c, &c->g_solve, st, [&](cudaStream_t s2) {
+        for (const Launch& l : c->SP.fwd_launches)
+            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, s2);
+        for (const Launch& l : c->SP.bwd_launches)
+            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, s2);
+    });
+    launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, st);
+    return e;
 }
 }  // namespace
 
@@ -336,11 +369,11 @@ extern "C" int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, 
     }
     double* xd = on_device ? x : c->d_vec;
     if (c->opt.precision != SPI_PREC_MIXED_FP32) {
-        solve_core(c, bd, xd, st);
+        CK(solve_core(c, bd, xd, st));
     } else if (n) {
         // FP64 iterative refinement against N: x += solve(b - N x)
         CK(cudaMemcpyAsync(c->d_b2, bd, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        solve_core(c, c->d_b2, c->d_x, st);
+        CK(solve_core(c, c->d_b2, c->d_x, st));
         double bnorm = -1.0;
         c->refine_steps = 0;
         for (int it = 0;; ++it) {
@@ -354,7 +387,7 @@ extern "C" int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, 
             double rn = std::sqrt(c->h_norm[0]);
             c->solve_relres = bnorm > 0 ? rn / bnorm : rn;
             if (rn <= c->opt.refine_tol * bnorm || it >= c->opt.refine_max) break;
-            solve_core(c, c->d_r, c->d_dx, st);
+            CK(solve_core(c, c->d_r, c->d_dx, st));
             launch_axpy(n, c->d_dx, c->d_x, st);
             c->refine_steps++;
         }
@@ -445,9 +478,10 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->diag_flops_all = S.diag_flops_all;
     o->device_bytes = c->device_bytes;
     o->launches_factor = 2 + (int64_t)c->FP.launches.size();
-    int64_t lv = 0;
-    for (int32_t l = 0; l < S.nlevels; ++l) lv += (S.level_ptr[l + 1] > S.level_ptr[l]);
-    o->launches_solve = S.n ? 2 + 2 * lv : 0;
+    int64_t ls = 0;
+    for (const Launch& l : c->SP.fwd_launches) ls += l.count > 0;
+    for (const Launch& l : c->SP.bwd_launches) ls += l.count > 0;
+    o->launches_solve = S.n ? 2 + ls : 0;
     o->launches_diag = S.n ? 1 : 0;
     if (c->opt.precision == SPI_PREC_MIXED_FP32) o->launches_factor += 1;
     o->refine_steps = c->refine_steps;
@@ -482,6 +516,9 @@ void spi_destroy(spi_ctx* c) {
     if (!c) return;
     free_plan(c->plan_all);
     free_plan(c->plan_sub);
+    if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
+    if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_status) cudaFreeHost(c->h_status);
     delete c;

@@ -17,8 +17,8 @@
 // block's row map, its ancestors -- receive Z_rows -= L_rows,cols Z_cols from
 // 64-row panel tiles staged in shared memory.
 //
-// The element type T is double (FP64 form) or float (mixed form: FP32 copy
-// of L, FP32 Z, FP64 variance accumulation).
+// k_diag_inv<double> is the FP64 form; k_diag_inv_f32 the mixed form (FP32
+// copy of L, FP32 Z, FP64 variance accumulation).
 #include <cuda_runtime.h>
 
 #include "spi_internal.cuh"
@@ -101,12 +101,17 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
                     Lt[i * (kT + 1) + c] = (i < nrow && c < w) ? P[(rb + i) + (int64_t)(cb + c) * m] : T(0);
                 }
                 __syncthreads();
+                const int w4 = (w + 3) & ~3;  // columns past w are zero-padded
                 for (int e = tid; e < nrow * nb; e += kThreads) {
                     const int i = e / nb, t = e - i * nb;
                     const T* lr = Lt + i * (kT + 1);
                     T acc = T(0);
-#pragma unroll
-                    for (int c = 0; c < kT; ++c) acc += lr[c] * Zd[c * B + t];
+                    for (int c = 0; c < w4; c += 4) {
+                        acc += lr[c] * Zd[c * B + t];
+                        acc += lr[c + 1] * Zd[(c + 1) * B + t];
+                        acc += lr[c + 2] * Zd[(c + 2) * B + t];
+                        acc += lr[c + 3] * Zd[(c + 3) * B + t];
+                    }
                     const int64_t row = rb + i;
                     const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
                     Z[zr * B + lo + t] -= acc;
@@ -116,6 +121,123 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
     }
     __syncthreads();
     for (int t = tid; t < nr; t += kThreads) out[p.rhs_out[r0b + t]] = var[t];
+}
+
+// Mixed form: the same walk with an FP32 copy of L and FP32 Z (variance sums
+// in FP64), and the update of the rows below done as a register-tiled SIMT
+// GEMM: 128 threads, a 128-row x 64-RHS output tile, 8 x 8 outputs per
+// thread, the panel tile staged transposed so that a thread's 8 rows are one
+// pair of float4 loads.
+constexpr int kFThreads = 128;
+constexpr int kFRows = 128;
+constexpr int kFCols = 64;
+
+size_t diag_f32_smem_bytes(int B) {
+    return sizeof(double) * (size_t)(B + kT) +
+           sizeof(float) * (size_t)(kT * B + kT * (kT + 1) + kT * (kFRows + 4));
+}
+
+__global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p, const float* __restrict__ L,
+                                                             const double* __restrict__ D,
+                                                             double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = p.B;  // a multiple of 8 (padded RHS count)
+    double* var = reinterpret_cast<double*>(smem);
+    double* dv = var + B;
+    float* Zd = reinterpret_cast<float*>(dv + kT);  // [kT][B]
+    float* Ld = Zd + kT * B;                        // [kT][kT+1]
+    float* Lt = Ld + kT * (kT + 1);                 // [kT][kFRows+4], transposed panel tile
+    const int tid = threadIdx.x;
+    const int tx = tid % 8, ty = tid / 8;
+    const int b = p.order[blockIdx.x];
+    float* Z = reinterpret_cast<float*>(p.Z) + p.zbase[b];
+    const int64_t zsz = p.zbase[b + 1] - p.zbase[b];
+    const int r0b = p.blk_ptr[b], nr = p.blk_ptr[b + 1] - r0b;
+    for (int64_t i = tid; i < zsz; i += kFThreads) Z[i] = 0.f;
+    for (int t = tid; t < B; t += kFThreads) var[t] = 0.0;
+    __syncthreads();
+    for (int t = tid; t < nr; t += kFThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = 1.f;
+    for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
+        const int s = p.us[u], lo = p.ulo[u], nb = p.uhi[u] - lo, zo = p.uzoff[u];
+        const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+        const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+        const float* P = L + d.lptr[s];
+        const int32_t* rel = p.rel + p.urel[u];
+        for (int cb = 0; cb < k; cb += kT) {
+            const int w = min(kT, k - cb);
+            __syncthreads();
+            for (int e = tid; e < kT * kT; e += kFThreads) {
+                const int i = e % kT, c = e / kT;
+                Ld[i * (kT + 1) + c] = (i < w && c < i) ? P[(cb + i) + (int64_t)(cb + c) * m] : 0.f;
+            }
+            if (tid < kT) dv[tid] = tid < w ? 1.0 / D[f + cb + tid] : 0.0;
+            for (int e = tid; e < kT * B; e += kFThreads) {
+                const int c = e / B, t = e - c * B;
+                Zd[e] = (c < w && t < nb) ? Z[(int64_t)(zo + cb + c) * B + lo + t] : 0.f;
+            }
+            __syncthreads();
+            for (int t = tid; t < nb; t += kFThreads) {
+                double v = 0.0;
+                for (int c = 0; c < w; ++c) {
+                    const float zc = Zd[c * B + t];
+                    v += (double)zc * (double)zc * dv[c];
+                    for (int r = c + 1; r < w; ++r) Zd[r * B + t] -= Ld[r * (kT + 1) + c] * zc;
+                }
+                var[lo + t] += v;
+            }
+            __syncthreads();
+            for (int e = tid; e < w * nb; e += kFThreads) {
+                const int c = e / nb, t = e - c * nb;
+                Z[(int64_t)(zo + cb + c) * B + lo + t] = Zd[c * B + t];
+            }
+            const int w4 = (w + 3) & ~3;
+            for (int64_t rb = cb + w; rb < m; rb += kFRows) {
+                const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
+                __syncthreads();
+                for (int e = tid; e < kFRows * kT; e += kFThreads) {
+                    const int i = e % kFRows, c = e / kFRows;
+                    Lt[c * (kFRows + 4) + i] = (i < nrow && c < w) ? P[(rb + i) + (int64_t)(cb + c) * m] : 0.f;
+                }
+                __syncthreads();
+                if (ty * 8 >= nrow) continue;
+                for (int cbase = 0; cbase < nb; cbase += kFCols) {
+                    if (cbase + tx * 8 >= nb) continue;
+                    float acc[8][8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                    const float* lcol = Lt + ty * 8;
+                    const float* zcol = Zd + cbase + tx * 8;
+                    for (int c = 0; c < w4; ++c) {
+                        const float4 a0 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4));
+                        const float4 a1 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4) + 4);
+                        const float4 b0 = *reinterpret_cast<const float4*>(zcol + c * B);
+                        const float4 b1 = *reinterpret_cast<const float4*>(zcol + c * B + 4);
+                        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int il = ty * 8 + i;
+                        if (il >= nrow) break;
+                        const int64_t row = rb + il;
+                        const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
+                        float* zrow = Z + zr * B + lo + cbase + tx * 8;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (cbase + tx * 8 + j < nb) zrow[j] -= acc[i][j];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < nr; t += kFThreads) out[p.rhs_out[r0b + t]] = var[t];
 }
 
 template <typename T>
@@ -132,8 +254,8 @@ cudaError_t diag_kernel_setup(int B) {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)diag_smem_bytes<double>(B));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_diag_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)diag_smem_bytes<float>(B));
+    return cudaFuncSetAttribute(k_diag_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)diag_f32_smem_bytes((B + 7) & ~7));
 }
 
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
@@ -145,7 +267,9 @@ void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L,
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
                              cudaStream_t st) {
     if (p.nblocks == 0) return;
-    launch_t<float>(d, p, L, D, out, st);
+    DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
+               p.urel, p.zbase, p.Z};
+    k_diag_inv_f32<<<p.nblocks, kFThreads, diag_f32_smem_bytes(p.B), st>>>(d, a, L, D, out);
 }
 
 }  // namespace spi

@@ -11,6 +11,8 @@ namespace spi {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kFwdRows = 512;  // rows below the block per forward CTA
+constexpr int kBwdCols = 256;  // columns per backward CTA
 
 __global__ void k_permute_in(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ b,
                              double* __restrict__ w) {
@@ -24,56 +26,107 @@ __global__ void k_permute_out(int32_t n, const int32_t* __restrict__ perm, const
         x[perm[k]] = w[k];
 }
 
-// Forward: x_s = L11^-1 w_s (unit lower), then w[rows below] -= L21 x_s.
-__global__ void __launch_bounds__(kThreads) k_fwd(DevSym d, const int32_t* __restrict__ list,
-                                                  const double* __restrict__ L, double* __restrict__ w) {
-    extern __shared__ double xs[];
-    const int tid = threadIdx.x;
-    const int s = list[blockIdx.x];
+// Forward block step b of the supernodes of one level.  Item (s, chunk):
+// every CTA of supernode s solves the 32 x 32 unit-lower diagonal block
+// x_b = L_bb^-1 w_b in registers (lane r owns row r), the chunk-0 CTA stores
+// x_b into z, and each CTA subtracts L(rows, block b) x_b from its own chunk
+// of the rows below: the supernode's later pivots (plain stores: the rows of
+// a chunk belong to one CTA) and its ancestors' rows (atomics: siblings of
+// the level update the same ancestors).
+__global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* __restrict__ items, int b,
+                                                       const double* __restrict__ L, double* __restrict__ w,
+                                                       double* __restrict__ z) {
+    __shared__ double xb[kT];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const double* P = L + d.lptr[s];
-    for (int c = tid; c < k; c += kThreads) xs[c] = w[f + c];
-    __syncthreads();
-    for (int c = 0; c < k - 1; ++c) {
-        const double xc = xs[c];
-        for (int r = c + 1 + tid; r < k; r += kThreads) xs[r] -= P[r + (int64_t)c * m] * xc;
-        __syncthreads();
+    const int cb = b * kT, wb = min(kT, k - cb);
+    if (tid < 32) {
+        // lane r holds row r of the diagonal block: 32 independent loads first
+        double lrow[kT];
+#pragma unroll
+        for (int c = 0; c < kT; ++c)
+            lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
+        double x = lane < wb ? w[f + cb + lane] : 0.0;
+#pragma unroll
+        for (int c = 0; c < kT - 1; ++c) {
+            const double xc = __shfl_sync(0xffffffffu, x, c);
+            x -= lrow[c] * xc;
+        }
+        xb[lane] = x;
+        if (chunk == 0 && lane < wb) z[f + cb + lane] = x;
     }
-    for (int c = tid; c < k; c += kThreads) w[f + c] = xs[c];
+    __syncthreads();
     const int32_t* rows = d.srows + d.srowptr[s];
-    for (int64_t t = k + tid; t < m; t += kThreads) {
+    const int64_t r0 = cb + wb + (int64_t)chunk * kFwdRows;
+    const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
+    for (int64_t r = r0 + tid; r < r1; r += kThreads) {
         double acc = 0.0;
-        for (int c = 0; c < k; ++c) acc += P[t + (int64_t)c * m] * xs[c];
-        atomicAdd(w + rows[t], -acc);
+        for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+        if (r < k) w[f + r] -= acc;
+        else atomicAdd(w + rows[r], -acc);
     }
 }
 
-// Backward: y = D^-1 w_s - L21^T x_below, then x_s = L11^-T y (unit upper).
-__global__ void __launch_bounds__(kThreads) k_bwd(DevSym d, const int32_t* __restrict__ list,
-                                                  const double* __restrict__ L, const double* __restrict__ D,
-                                                  double* __restrict__ w) {
-    extern __shared__ double ys[];
-    const int tid = threadIdx.x;
-    const int s = list[blockIdx.x];
+// Backward, first launch of a level: y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]]
+// for the supernode's columns (one warp per column), stored into w.
+__global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* __restrict__ items,
+                                                       const double* __restrict__ L, const double* __restrict__ D,
+                                                       const double* __restrict__ z, const double* __restrict__ x,
+                                                       double* __restrict__ w) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const double* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int c = warp; c < k; c += kThreads / 32) {
+    const int c1 = min(k, (chunk + 1) * kBwdCols);
+    for (int c = chunk * kBwdCols + warp; c < c1; c += kThreads / 32) {
         double acc = 0.0;
-        for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * w[rows[t]];
+        for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) ys[c] = w[f + c] / D[f + c] - acc;
+        if (lane == 0) w[f + c] = z[f + c] / D[f + c] - acc;
+    }
+}
+
+// Backward block step b (descending): every CTA solves L_bb^T x_b = y_b in
+// registers, the chunk-0 CTA stores x_b, and each CTA updates its chunk of the
+// earlier columns a < 32 b: y_a -= sum_r L[32b + r][a] x_b[r].
+__global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* __restrict__ items, int b,
+                                                       const double* __restrict__ L, double* __restrict__ w,
+                                                       double* __restrict__ x) {
+    __shared__ double xb[kT];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const double* P = L + d.lptr[s];
+    const int cb = b * kT, wb = min(kT, k - cb);
+    if (tid < 32) {
+        // lane c holds column c of the diagonal block (L_bb^T row c)
+        double lcol[kT];
+#pragma unroll
+        for (int r = 0; r < kT; ++r)
+            lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
+        double y = lane < wb ? w[f + cb + lane] : 0.0;
+#pragma unroll
+        for (int r = kT - 1; r > 0; --r) {
+            const double xr = __shfl_sync(0xffffffffu, y, r);
+            y -= lcol[r] * xr;
+        }
+        xb[lane] = y;
+        if (chunk == 0 && lane < wb) x[f + cb + lane] = y;
     }
     __syncthreads();
-    for (int c = k - 1; c > 0; --c) {
-        const double yc = ys[c];
-        for (int r = tid; r < c; r += kThreads) ys[r] -= P[c + (int64_t)r * m] * yc;
-        __syncthreads();
+    const int a1 = min(cb, (chunk + 1) * kBwdCols);
+    for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
+        const double* col = P + (int64_t)a * m + cb;
+        double acc = 0.0;
+        for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
+        w[f + a] -= acc;
     }
-    for (int c = tid; c < k; c += kThreads) w[f + c] = ys[c];
 }
 
 // r -= N x for the symmetric N given by its lower CSC (caller numbering), one
@@ -148,25 +201,57 @@ void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double*
     k_permute_out<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, perm, w, x);
 }
 
-cudaError_t solve_kernel_setup(int32_t kmax) {
-    size_t bytes = (size_t)std::max(kmax, 1) * sizeof(double);
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    if (bytes > 220 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+void build_solve_plan(const Symbolic& S, SolvePlan& P) {
+    P = SolvePlan();
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+        int32_t kmax = 0;
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p)
+            kmax = std::max(kmax, S.k_of(S.level_list[p]));
+        const int32_t nsteps = (kmax + kT - 1) / kT;
+        std::vector<Launch> fw, bw;
+        for (int32_t b = 0; b < nsteps; ++b) {
+            Launch lf{4, b, (int64_t)P.fwd_items.size() / 2, 0};
+            Launch lb{6, b, (int64_t)P.bwd_items.size() / 2, 0};
+            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+                const int32_t s = S.level_list[p], k = S.k_of(s), m = S.m_of(s);
+                if (k <= b * kT) continue;
+                const int32_t wb = std::min(kT, k - b * kT);
+                const int64_t below = (int64_t)m - b * kT - wb;
+                const int32_t nch = std::max<int32_t>(1, (int32_t)((below + kFwdRows - 1) / kFwdRows));
+                for (int32_t c = 0; c < nch; ++c) { P.fwd_items.push_back(s); P.fwd_items.push_back(c); lf.count++; }
+                const int32_t ncb = std::max<int32_t>(1, (b * kT + kBwdCols - 1) / kBwdCols);
+                for (int32_t c = 0; c < ncb; ++c) { P.bwd_items.push_back(s); P.bwd_items.push_back(c); lb.count++; }
+            }
+            fw.push_back(lf);
+            bw.push_back(lb);
+        }
+        Launch li{5, 0, (int64_t)P.bwd_items.size() / 2, 0};
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p], k = S.k_of(s);
+            const int32_t nch = std::max<int32_t>(1, (k + kBwdCols - 1) / kBwdCols);
+            for (int32_t c = 0; c < nch; ++c) { P.bwd_items.push_back(s); P.bwd_items.push_back(c); li.count++; }
+        }
+        P.fwd_launches.insert(P.fwd_launches.end(), fw.begin(), fw.end());
+        // backward of level l: init, then the block steps in descending order
+        std::vector<Launch> lvl;
+        lvl.push_back(li);
+        for (auto it = bw.rbegin(); it != bw.rend(); ++it) lvl.push_back(*it);
+        P.bwd_level_launches.push_back(lvl);
+    }
+    // backward levels run top-down
+    for (auto it = P.bwd_level_launches.rbegin(); it != P.bwd_level_launches.rend(); ++it)
+        P.bwd_launches.insert(P.bwd_launches.end(), it->begin(), it->end());
+    P.bwd_level_launches.clear();
 }
 
-void launch_fwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
-                      double* w, cudaStream_t st) {
-    if (count == 0) return;
-    k_fwd<<<count, kThreads, (size_t)std::max(kmax, 1) * sizeof(double), st>>>(d, list, L, w);
-}
-
-void launch_bwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
-                      const double* D, double* w, cudaStream_t st) {
-    if (count == 0) return;
-    k_bwd<<<count, kThreads, (size_t)std::max(kmax, 1) * sizeof(double), st>>>(d, list, L, D, w);
+void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
+                       const double* L, const double* D, double* w, double* z, double* x, cudaStream_t st) {
+    if (l.count == 0) return;
+    switch (l.kind) {
+        case 4: k_fwd_step<<<l.count, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z); break;
+        case 5: k_bwd_init<<<l.count, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w); break;
+        default: k_bwd_step<<<l.count, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x); break;
+    }
 }
 
 }  // namespace spi

@@ -55,6 +55,16 @@ struct FactorPlan {
 
 void build_factor_plan(const Symbolic& S, FactorPlan& F);
 
+struct SolvePlan {
+    std::vector<int32_t> fwd_items;  // pairs (supernode, row chunk)
+    std::vector<int32_t> bwd_items;  // pairs (supernode, column chunk)
+    std::vector<Launch> fwd_launches; // kind 4, bottom-up
+    std::vector<Launch> bwd_launches; // kinds 5 (level init) and 6 (block steps), top-down
+    std::vector<std::vector<Launch>> bwd_level_launches;
+};
+
+void build_solve_plan(const Symbolic& S, SolvePlan& P);
+
 struct DevDiagPlan {
     int32_t B = 0, nblocks = 0;
     int64_t nrhs = 0;
@@ -76,16 +86,12 @@ void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, cudaStream_t st);
-void launch_fwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
-                      double* w, cudaStream_t st);
-void launch_bwd_level(const DevSym& d, const int32_t* list, int32_t count, int32_t kmax, const double* L,
-                      const double* D, double* w, cudaStream_t st);
+void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
+                       const double* L, const double* D, double* w, double* z, double* x, cudaStream_t st);
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
                          double* r, cudaStream_t st);
 void launch_norms2(int32_t n, const double* a, const double* b, double* out, cudaStream_t st);
 void launch_axpy(int32_t n, const double* dx, double* x, cudaStream_t st);
-// one-time kernel attributes (large dynamic shared memory)
-cudaError_t solve_kernel_setup(int32_t kmax);
 // ---- diag.cu
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
                          cudaStream_t st);

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(P):
 
 def test_strerror_and_defaults(P):
     o = P.spi_default_options()
-    assert o.rhs_block == 128 and o.precision == 0 and o.ordering == 0
+    assert o.rhs_block == 0 and o.precision == 0 and o.ordering == 0
     for code in range(8):
         assert P.spi_strerror(code)
 

@@ -349,6 +349,7 @@ def main():
                       "diag_inverse": statistics.mean(t_dia)},
         "factor_tflops": info["factor_flops"] / (statistics.mean(t_fac) / 1e3) / 1e12,
         "factor_flops": info["factor_flops"], "diag_flops": info["diag_flops_all"],
+        "diag_work_flops": info["diag_work_flops"],
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],
         "roofline": roof,
         "mixed": mixed,

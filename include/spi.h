@@ -88,6 +88,8 @@ typedef struct spi_stats {
                                sum over requested i, over j on path(i), of 2 c_j */
     double solve_flops;     /* 4 * nnz_l + n (one forward + one backward sweep) */
     double diag_flops_all;  /* algorithmic flops of spi_diag_inverse over all n indices */
+    double diag_work_flops; /* flops the blocked kernel executes for the last spi_diag_inverse
+                               (dense over each block's active range, amalgamation zeros) */
     int64_t device_bytes;   /* device memory held by the context */
     int64_t launches_factor;/* kernels this library launches per spi_factor */
     int64_t launches_solve; /* ... per spi_solve */

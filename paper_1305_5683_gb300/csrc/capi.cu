@@ -58,7 +58,7 @@ struct spi_ctx {
     DevDiagPlan plan_sub;
     std::vector<int32_t> plan_sub_key;
     bool plan_sub_ready = false;
-    double last_diag_flops = 0;
+    double last_diag_flops = 0, last_diag_work = 0;
     int64_t bad_pivot = -1;
     std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
     std::vector<int32_t> in_rowind;
@@ -456,6 +456,7 @@ int spi_diag_inverse(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, 
     if (!on_device && nout)
         CK(cudaMemcpyAsync(out, od, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, st));
     c->last_diag_flops = plan->flops;
+    c->last_diag_work = plan->work_flops;
     if (!on_device) CK(cudaStreamSynchronize(st));
     return finish(c, st);
 }
@@ -476,6 +477,7 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->diag_flops = c->last_diag_flops;
     o->solve_flops = 4.0 * (double)S.nnz_l + (double)S.n;
     o->diag_flops_all = S.diag_flops_all;
+    o->diag_work_flops = c->last_diag_work;
     o->device_bytes = c->device_bytes;
     o->launches_factor = 2 + (int64_t)c->FP.launches.size();
     int64_t ls = 0;

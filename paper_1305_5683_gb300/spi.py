@@ -38,6 +38,7 @@ class spi_stats(ctypes.Structure):
                 ("n_levels", ctypes.c_int64), ("max_front", ctypes.c_int64), ("bad_pivot", ctypes.c_int64),
                 ("factor_flops", ctypes.c_double), ("diag_flops", ctypes.c_double),
                 ("solve_flops", ctypes.c_double), ("diag_flops_all", ctypes.c_double),
+                ("diag_work_flops", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
                 ("launches_solve", ctypes.c_int64), ("launches_diag", ctypes.c_int64),
                 ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),

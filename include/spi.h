@@ -71,6 +71,8 @@ typedef struct spi_options {
     double refine_tol; /* stop refining when ||b - N x||_2 <= refine_tol * ||b||_2 */
     int async;       /* 1: do not drain the stream at the end of each call */
     int nd_leaf;     /* nested-dissection leaf size (vertices); 0 = default */
+    int batch;       /* maximum number of same-pattern bands of the *_batch calls (device memory
+                        is sized for it at the first factorization); 0 or 1 = single problem */
 } spi_options;
 
 typedef struct spi_stats {
@@ -82,6 +84,7 @@ typedef struct spi_stats {
     int64_t n_levels;       /* elimination-tree levels of the supernodal tree */
     int64_t max_front;      /* largest front order m */
     int64_t bad_pivot;      /* column (caller numbering) of the first non-positive pivot, or -1 */
+    int64_t bad_band;       /* band of that pivot in a batched factorization, or -1 */
     double factor_flops;    /* sum over pivots j of (c_j^2 - 1), c_j = entries of column j of L
                                including the diagonal (exact counts, no amalgamation zeros) */
     double diag_flops;      /* algorithmic flops of the last spi_diag_inverse call:
@@ -95,14 +98,17 @@ typedef struct spi_stats {
     int64_t launches_solve; /* ... per spi_solve */
     int64_t launches_diag;  /* ... per spi_diag_inverse */
     int64_t refine_steps;   /* refinement steps taken by the last spi_solve (mixed precision) */
-    double solve_relres;    /* ||b - N x||_2 / ||b||_2 after the last mixed-precision spi_solve */
+    double solve_relres;    /* ||b - N x||_2 / ||b||_2 after the last mixed-precision spi_solve
+                               (largest over the bands of a batch) */
+    int64_t rhs_block;      /* right-hand sides per block in use (chosen by the autotuner when
+                               spi_options.rhs_block = 0) */
     double analyse_seconds; /* host time of spi_analyse */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;
 
 /* Fill *opt with the defaults (FP64, nested dissection, automatic RHS block,
- * relax 10, refine_max 10, refine_tol 1e-13, synchronous). */
+ * relax 10, refine_max 10, refine_tol 1e-13, synchronous, batch 1). */
 void spi_default_options(spi_options* opt);
 
 /* Analysis phase (Sec. 3.2.1): validate the pattern, order it (nested
@@ -149,6 +155,36 @@ int spi_solve(spi_ctx* ctx, const double* b, double* x, int on_device, void* str
  * Errors: SPI_ERR_STATE, SPI_ERR_ARG (index out of range), SPI_ERR_CUDA. */
 int spi_diag_inverse(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out,
                      int on_device, void* stream);
+
+/* Uneven independent problems as one batch: problems p = 0..nprob-1, each given
+ * like spi_analyse (n[p], colptr[p], rowind[p], host memory), are analysed as
+ * the block-diagonal matrix diag(N_0, ..., N_{nprob-1}).  Its elimination
+ * tree is the forest of the problems' trees, so every level launch of the
+ * factorization, the solves and the variance solves covers all problems at
+ * once.  All later calls use the concatenated numbering: values are the
+ * problems' value arrays one after another, b, x and the variances likewise.
+ * The paper runs many such sequential computations side by side (Sec. 6).
+ * Errors: as spi_analyse. */
+int spi_analyse_multi(int32_t nprob, const int64_t* n, const int64_t* const* colptr,
+                      const int32_t* const* rowind, const spi_options* opt, spi_ctx** out);
+
+/* Same-pattern batch (energy bands of one observation, Sec. 6: the analysis is
+ * repeated for 24 energy bands): nbatch <= spi_options.batch value sets of the
+ * analysed pattern, factored together; each tree level / block step is one
+ * launch over all bands (the band is the second grid dimension), replayed
+ * from a CUDA graph.
+ *   values  float64[nbatch * nnz], band b at offset b * nnz (host or device)
+ * Errors: as spi_factor; SPI_ERR_ARG when nbatch is out of range;
+ * spi_info().bad_band names the band of a non-positive pivot. */
+int spi_factor_batch(spi_ctx* ctx, int32_t nbatch, const double* values, int values_on_device, void* stream);
+
+/* spi_solve for the first nbatch factored bands: b and x are float64[nbatch * n]. */
+int spi_solve_batch(spi_ctx* ctx, int32_t nbatch, const double* b, double* x, int on_device, void* stream);
+
+/* spi_diag_inverse for the first nbatch factored bands: out is
+ * float64[nbatch * m] with m = nidx (or n when idx == NULL), band b at b * m. */
+int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int64_t nidx, double* out,
+                           int on_device, void* stream);
 
 /* Statistics of the analysis and of the last calls.  Errors: SPI_ERR_ARG. */
 int spi_info(const spi_ctx* ctx, spi_stats* out);

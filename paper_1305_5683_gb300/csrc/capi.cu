@@ -1,18 +1,23 @@
 // capi.cu -- the extern "C" entry points declared in include/spi.h.
 //
-// A context owns the host symbolic analysis and every device buffer of one
-// pattern.  Device memory is laid out once, at the first spi_factor:
+// A context owns the host symbolic analysis of one pattern and every device
+// buffer.  Device memory is laid out once, at the first factorization, for
+// `opt.batch` same-pattern bands (band b of every per-band buffer starts at
+// b * stride):
 //   panels L (sum_s m_s k_s doubles, column-major per supernode), D (n),
-//   F22 update areas (sum over supernodes with children of (m-k)^2),
-//   the symbolic arrays, the launch item lists, and per-plan Z workspaces
-//   of the variance solves (rows of the union of a block's paths x B).
+//   F22 update areas (sum over supernodes with children of (m-k)^2), the
+//   input values, the solve vectors, the symbolic arrays and launch item
+//   lists (shared by all bands), and per-plan Z workspaces of the variance
+//   solves (rows of the union of a block's paths x B, per band).
+// Single-problem calls are the batch-1 case of the batched calls.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
-#include <cmath>
 #include <climits>
+#include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,40 +31,39 @@ struct spi_ctx {
     spi_options opt{};
     FactorPlan FP;
     SolvePlan SP;
-    int32_t* d_fwd_items = nullptr;
-    int32_t* d_bwd_items = nullptr;
-    double* d_z = nullptr;
-    double* d_xp = nullptr;
     int device = -1;
     bool dev_ready = false, factored = false;
+    int factored_nb = 0;
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
     DevSym dsym;
+    Strides bs;
     int64_t* d_amap = nullptr;
     int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
-            *d_items3 = nullptr,
-            *d_level_list = nullptr;
+            *d_items3 = nullptr, *d_fwd_items = nullptr, *d_bwd_items = nullptr;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
-           *d_w = nullptr, *d_vec = nullptr, *d_out = nullptr;
+           *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
     DevStatus* h_status = nullptr;
-    // mixed precision: FP32 copy of the panels, the input pattern and values for refinement
+    // mixed precision: FP32 copy of the panels, the input pattern for the FP64 residual
     float* d_L32 = nullptr;
     int64_t* d_cp = nullptr;
     int32_t* d_ri = nullptr;
     double *d_b2 = nullptr, *d_x = nullptr, *d_r = nullptr, *d_dx = nullptr, *d_norm = nullptr, *h_norm = nullptr;
     int64_t refine_steps = 0;
     double solve_relres = 0;
-    // CUDA graphs of the launch sequences that touch only context buffers
+    // CUDA graphs of the launch sequences that touch only context buffers, per band count
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t g_factor = nullptr, g_solve = nullptr;
+    std::map<int, cudaGraphExec_t> g_factor, g_solve;
+    // variance plans: all indices, and the last index subset
     DevDiagPlan plan_all;
     bool plan_all_ready = false;
     DevDiagPlan plan_sub;
     std::vector<int32_t> plan_sub_key;
     bool plan_sub_ready = false;
+    int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
-    int64_t bad_pivot = -1;
+    int64_t bad_pivot = -1, bad_band = -1;
     std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
     std::vector<int32_t> in_rowind;
     double analyse_seconds = 0;
@@ -70,32 +74,31 @@ namespace {
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SPI_ERR_OOM : SPI_ERR_CUDA; }
 
 template <class T>
-cudaError_t dev_alloc(spi_ctx* c, T** p, size_t count) {
+cudaError_t dev_alloc(spi_ctx* c, T** p, size_t count, std::vector<void*>* track = nullptr) {
     *p = nullptr;
     if (count == 0) count = 1;
     cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e == cudaSuccess) { c->allocs.push_back(*p); c->device_bytes += (int64_t)(count * sizeof(T)); }
+    if (e == cudaSuccess) {
+        (track ? *track : c->allocs).push_back(*p);
+        c->device_bytes += (int64_t)(count * sizeof(T));
+    }
     return e;
 }
 
 template <class T>
 cudaError_t dev_upload(spi_ctx* c, T** p, const std::vector<T>& v, std::vector<void*>* track = nullptr) {
-    cudaError_t e;
-    *p = nullptr;
-    size_t count = std::max<size_t>(v.size(), 1);
-    e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e != cudaSuccess) return e;
-    if (track) track->push_back(*p); else c->allocs.push_back(*p);
-    c->device_bytes += (int64_t)(count * sizeof(T));
-    if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    cudaError_t e = dev_alloc(c, p, v.size(), track);
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
 }
 
-#define CK(x)                                  \
-    do {                                       \
-        cudaError_t e__ = (x);                 \
-        if (e__ != cudaSuccess) return cuda_fail(e__); \
+#define CK(x)                                            \
+    do {                                                 \
+        cudaError_t e__ = (x);                           \
+        if (e__ != cudaSuccess) return cuda_fail(e__);   \
     } while (0)
+
+bool mixed_of(const spi_ctx* c) { return c->opt.precision == SPI_PREC_MIXED_FP32; }
 
 int ensure_device(spi_ctx* c) {
     if (c->dev_ready) return SPI_OK;
@@ -103,6 +106,7 @@ int ensure_device(spi_ctx* c) {
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return SPI_ERR_CUDA;
     CK(cudaGetDevice(&c->device));
     const Symbolic& S = c->S;
+    const size_t nb = (size_t)c->opt.batch;
     int32_t *sfirst, *srows, *relmap, *sparent, *perm, *snode_of;
     int64_t *srowptr, *lptr, *f22ptr;
     CK(dev_upload(c, &sfirst, S.sfirst));
@@ -115,45 +119,45 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &perm, S.perm));
     CK(dev_upload(c, &snode_of, S.snode_of));
     c->dsym = DevSym{S.n, S.ns, sfirst, srowptr, srows, relmap, sparent, lptr, f22ptr, perm, snode_of};
+    c->bs.L = S.lptr[S.ns];
+    c->bs.F22 = S.f22_total;
+    c->bs.n = S.n;
+    c->bs.nnz = S.nnz_a;
     CK(dev_upload(c, &c->d_amap, S.amap));
     CK(dev_upload(c, &c->d_diag_src, S.diag_src));
     CK(dev_upload(c, &c->d_items0, c->FP.diag_items));
     CK(dev_upload(c, &c->d_items1, c->FP.trsm_items));
     CK(dev_upload(c, &c->d_items2, c->FP.schur_items));
     CK(dev_upload(c, &c->d_items3, c->FP.update_items));
-    CK(dev_upload(c, &c->d_level_list, S.level_list));
-    CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns]));
-    CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total));
-    CK(dev_alloc(c, &c->d_D, (size_t)S.n));
-    CK(dev_alloc(c, &c->d_adiag, (size_t)S.n));
-    CK(dev_alloc(c, &c->d_vals, (size_t)S.nnz_a));
-    CK(dev_alloc(c, &c->d_w, (size_t)S.n));
-    CK(dev_alloc(c, &c->d_vec, (size_t)S.n));
-    CK(dev_alloc(c, &c->d_out, (size_t)S.n));
-    CK(dev_alloc(c, &c->d_status, 1));
-    CK(cudaMallocHost((void**)&c->h_status, sizeof(DevStatus)));
-    if (c->opt.precision == SPI_PREC_MIXED_FP32) {
-        CK(dev_alloc(c, &c->d_L32, (size_t)S.lptr[S.ns]));
-        CK(dev_alloc(c, &c->d_cp, (size_t)S.n + 1));
-        CK(dev_alloc(c, &c->d_ri, (size_t)S.nnz_a));
-        CK(cudaMemcpy(c->d_cp, c->in_colptr.data(), c->in_colptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-        if (S.nnz_a)
-            CK(cudaMemcpy(c->d_ri, c->in_rowind.data(), c->in_rowind.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        std::vector<int64_t>().swap(c->in_colptr);
-        std::vector<int32_t>().swap(c->in_rowind);
-        CK(dev_alloc(c, &c->d_b2, (size_t)S.n));
-        CK(dev_alloc(c, &c->d_x, (size_t)S.n));
-        CK(dev_alloc(c, &c->d_r, (size_t)S.n));
-        CK(dev_alloc(c, &c->d_dx, (size_t)S.n));
-        CK(dev_alloc(c, &c->d_norm, 2));
-        CK(cudaMallocHost((void**)&c->h_norm, 2 * sizeof(double)));
-    }
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
-    CK(dev_alloc(c, &c->d_z, (size_t)S.n));
+    CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
+    CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total * nb));
+    CK(dev_alloc(c, &c->d_D, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_adiag, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_vals, (size_t)S.nnz_a * nb));
+    CK(dev_alloc(c, &c->d_w, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_z, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_xp, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_vec, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_out, (size_t)S.n * nb));
+    CK(dev_alloc(c, &c->d_status, 1));
+    CK(cudaMallocHost((void**)&c->h_status, sizeof(DevStatus)));
     CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    CK(dev_alloc(c, &c->d_xp, (size_t)S.n));
-    if (diag_kernel_setup(c->opt.rhs_block) != cudaSuccess) return SPI_ERR_CUDA;
+    if (mixed_of(c)) {
+        CK(dev_alloc(c, &c->d_L32, (size_t)S.lptr[S.ns] * nb));
+        CK(dev_upload(c, &c->d_cp, c->in_colptr));
+        CK(dev_upload(c, &c->d_ri, c->in_rowind));
+        std::vector<int64_t>().swap(c->in_colptr);
+        std::vector<int32_t>().swap(c->in_rowind);
+        CK(dev_alloc(c, &c->d_b2, (size_t)S.n * nb));
+        CK(dev_alloc(c, &c->d_x, (size_t)S.n * nb));
+        CK(dev_alloc(c, &c->d_r, (size_t)S.n * nb));
+        CK(dev_alloc(c, &c->d_dx, (size_t)S.n * nb));
+        CK(dev_alloc(c, &c->d_norm, 2 * nb));
+        CK(cudaMallocHost((void**)&c->h_norm, 2 * nb * sizeof(double)));
+    }
+    CK(diag_kernel_setup(512));
     c->dev_ready = true;
     return SPI_OK;
 }
@@ -180,35 +184,34 @@ int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
     CK(dev_upload(c, &d.urel, h.urel, tr));
     CK(dev_upload(c, &d.zbase, h.zbase, tr));
     d.zsize = h.zbase.empty() ? 0 : h.zbase.back();
-    double* z = nullptr;
-    cudaError_t e = cudaMalloc((void**)&z, (size_t)std::max<int64_t>(d.zsize, 1) * sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(e);
-    d.allocs.push_back(z);
-    d.Z = z;
+    // FP64 elements per band are enough for both element types
+    CK(dev_alloc(c, &d.Z, (size_t)std::max<int64_t>(d.zsize, 1) * (size_t)c->opt.batch, tr));
     return SPI_OK;
 }
 
 // Record `body(stream)` once into a CUDA graph and replay it on `st`; if the
 // capture fails, run the launches directly on `st`.
 template <class F>
-cudaError_t run_graph(spi_ctx* c, cudaGraphExec_t* exec, cudaStream_t st, F&& body) {
-    if (!*exec) {
+cudaError_t run_graph(spi_ctx* c, std::map<int, cudaGraphExec_t>& cache, int key, cudaStream_t st, F&& body) {
+    auto it = cache.find(key);
+    if (it == cache.end()) {
         cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             body(c->cap);
             e = cudaStreamEndCapture(c->cap, &g);
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            *exec = nullptr;
             cudaGetLastError();
             body(st);
             return cudaGetLastError();
         }
+        it = cache.emplace(key, exec).first;
     }
-    return cudaGraphLaunch(*exec, st);
+    return cudaGraphLaunch(it->second, st);
 }
 
 __global__ void k_reset_status(DevStatus* s) {
@@ -222,13 +225,224 @@ int finish(spi_ctx* c, cudaStream_t st) {
     CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (c->h_status->flags & FLAG_NOT_SPD) {
-        int bp = c->h_status->bad_pivot;
-        c->bad_pivot = (bp >= 0 && bp < c->S.n) ? c->S.perm[bp] : -1;
+        const int64_t bp = c->h_status->bad_pivot, n = c->S.n;
+        if (bp >= 0 && n > 0 && bp < n * c->opt.batch) {
+            c->bad_band = bp / n;
+            c->bad_pivot = c->S.perm[bp % n];
+        }
         c->factored = false;
         return SPI_ERR_NOT_SPD;
     }
     if (c->h_status->flags & FLAG_TIMEOUT) return SPI_ERR_TIMEOUT;
     return SPI_OK;
+}
+
+int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, cudaStream_t st) {
+    if (!c || nb < 1 || nb > c->opt.batch) return SPI_ERR_ARG;
+    if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const Symbolic& S = c->S;
+    const bool mixed = mixed_of(c);
+    c->factored = false;
+    c->bad_pivot = c->bad_band = -1;
+    const double* vals = values;
+    if (S.nnz_a > 0 && (!values_on_device || mixed)) {
+        CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * nb * sizeof(double),
+                           values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        vals = c->d_vals;
+    }
+    k_reset_status<<<1, 1, 0, st>>>(c->d_status);
+    CK(cudaMemsetAsync(c->d_L, 0, (size_t)S.lptr[S.ns] * nb * sizeof(double), st));
+    if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * nb * sizeof(double), st));
+    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, nb, c->bs, st);
+    CK(run_graph(c, c->g_factor, nb, st, [&](cudaStream_t s2) {
+        for (const Launch& l : c->FP.launches) {
+            const int32_t* items = l.kind == 0 ? c->d_items0
+                                 : l.kind == 1 ? c->d_items1
+                                 : l.kind == 2 ? c->d_items2 : c->d_items3;
+            launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, nb,
+                               c->bs, s2);
+        }
+        if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns] * nb, s2);
+    }));
+    rc = finish(c, st);
+    if (rc == SPI_OK) {
+        c->factored = true;
+        c->factored_nb = nb;
+    }
+    return rc;
+}
+
+// x = P^T L^-T D^-1 L^-1 P b on device buffers of nb bands (b, x distinct from d_w/d_z/d_xp).
+cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStream_t st) {
+    const Symbolic& S = c->S;
+    launch_permute_in(S.n, c->dsym.perm, b, c->d_w, nb, st);
+    cudaError_t e = run_graph(c, c->g_solve, nb, st, [&](cudaStream_t s2) {
+        for (const Launch& l : c->SP.fwd_launches)
+            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
+                              nb, c->bs, s2);
+        for (const Launch& l : c->SP.bwd_launches)
+            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
+                              nb, c->bs, s2);
+    });
+    launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, nb, st);
+    return e;
+}
+
+int solve_impl(spi_ctx* c, int nb, const double* b, double* x, int on_device, cudaStream_t st) {
+    if (!c || nb < 1 || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nb > c->factored_nb) return SPI_ERR_ARG;
+    const int32_t n = c->S.n;
+    const size_t bytes = (size_t)n * nb * sizeof(double);
+    const double* bd = b;
+    if (!on_device && n) {
+        CK(cudaMemcpyAsync(c->d_vec, b, bytes, cudaMemcpyHostToDevice, st));
+        bd = c->d_vec;
+    }
+    double* xd = on_device ? x : c->d_vec;
+    if (!mixed_of(c)) {
+        CK(solve_core(c, nb, bd, xd, st));
+    } else if (n) {
+        // FP64 iterative refinement against N: x += solve(b - N x), every band until all converge
+        CK(cudaMemcpyAsync(c->d_b2, bd, bytes, cudaMemcpyDeviceToDevice, st));
+        CK(solve_core(c, nb, c->d_b2, c->d_x, st));
+        std::vector<double> bnorm(nb, -1.0);
+        c->refine_steps = 0;
+        for (int it = 0;; ++it) {
+            CK(cudaMemcpyAsync(c->d_r, c->d_b2, bytes, cudaMemcpyDeviceToDevice, st));
+            launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, c->d_x, c->d_r, nb, c->S.nnz_a, st);
+            CK(cudaMemsetAsync(c->d_norm, 0, 2 * nb * sizeof(double), st));
+            launch_norms2(n, c->d_r, it == 0 ? c->d_b2 : nullptr, c->d_norm, nb, st);
+            CK(cudaMemcpyAsync(c->h_norm, c->d_norm, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool done = true;
+            double worst = 0.0;
+            for (int k = 0; k < nb; ++k) {
+                if (it == 0) bnorm[k] = std::sqrt(c->h_norm[2 * k + 1]);
+                const double rn = std::sqrt(c->h_norm[2 * k]);
+                worst = std::max(worst, bnorm[k] > 0 ? rn / bnorm[k] : rn);
+                if (rn > c->opt.refine_tol * bnorm[k]) done = false;
+            }
+            c->solve_relres = worst;
+            if (done || it >= c->opt.refine_max) break;
+            CK(solve_core(c, nb, c->d_r, c->d_dx, st));
+            launch_axpy(n, c->d_dx, c->d_x, nb, st);
+            c->refine_steps++;
+        }
+        CK(cudaMemcpyAsync(xd, c->d_x, bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    if (!on_device && n) {
+        CK(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return finish(c, st);
+}
+
+void launch_diag(spi_ctx* c, const DevDiagPlan& p, int nb, int64_t nout, double* out, cudaStream_t st) {
+    Strides bs = c->bs;
+    bs.Z = p.zsize;
+    bs.out = nout;
+    if (mixed_of(c)) launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, st);
+    else launch_diag_inverse(c->dsym, p, c->d_L, c->d_D, out, nb, bs, st);
+}
+
+// Build the plan for the pivots `piv`; with an automatic block size (the
+// autotuner), time each candidate once on the current factor and keep the
+// fastest for every later plan of this context.
+int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int32_t>& pos, DevDiagPlan& dst,
+              int nb, int64_t nout, double* out, cudaStream_t st) {
+    std::vector<int> cands;
+    if (c->opt.rhs_block > 0) cands.push_back(c->opt.rhs_block);
+    else if (c->rhs_block_used > 0) cands.push_back(c->rhs_block_used);
+    else if (mixed_of(c)) cands = {32, 64, 128};
+    else cands = {16, 32, 64};
+    if (cands.size() > 1 && piv.size() < 4096) cands = {mixed_of(c) ? 64 : 32};  // too small to time
+    if (cands.size() == 1) {
+        DiagPlan h;
+        build_diag_plan(c->S, piv, pos, cands[0], h);
+        if (c->opt.rhs_block == 0 && c->rhs_block_used == 0 && piv.size() >= 4096) c->rhs_block_used = cands[0];
+        return upload_plan(c, h, dst);
+    }
+    float best = 1e30f;
+    int bestB = cands[0];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = SPI_OK;
+    for (int B : cands) {
+        DiagPlan h;
+        build_diag_plan(c->S, piv, pos, B, h);
+        rc = upload_plan(c, h, dst);
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        launch_diag(c, dst, nb, nout, out, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SPI_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bestB = B; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->rhs_block_used = bestB;
+    DiagPlan h;
+    build_diag_plan(c->S, piv, pos, bestB, h);
+    return upload_plan(c, h, dst);
+}
+
+int diag_impl(spi_ctx* c, int nb, const int32_t* idx, int64_t nidx, double* out, int on_device, cudaStream_t st) {
+    if (!c || !out || nb < 1) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nb > c->factored_nb) return SPI_ERR_ARG;
+    const Symbolic& S = c->S;
+    DevDiagPlan* plan;
+    int64_t nout;
+    double* od = on_device ? out : c->d_out;
+    if (!idx) {
+        nout = S.n;
+        if (!c->plan_all_ready) {
+            std::vector<int32_t> piv(S.n), pos(S.n);
+            for (int32_t k = 0; k < S.n; ++k) { piv[k] = k; pos[k] = S.perm[k]; }
+            int rc = make_plan(c, piv, pos, c->plan_all, nb, nout, od, st);
+            if (rc) return rc;
+            c->plan_all_ready = true;
+        }
+        plan = &c->plan_all;
+    } else {
+        if (nidx < 0 || nidx > S.n) return SPI_ERR_ARG;
+        nout = nidx;
+        std::vector<int32_t> key((size_t)nidx);
+        if (nidx) {
+            if (on_device) {
+                CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+            }
+        }
+        for (int32_t v : key)
+            if (v < 0 || v >= S.n) return SPI_ERR_ARG;
+        if (!c->plan_sub_ready || key != c->plan_sub_key) {
+            std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
+            for (int64_t t = 0; t < nidx; ++t) { piv[t] = S.iperm[key[t]]; pos[t] = (int32_t)t; }
+            int rc = make_plan(c, piv, pos, c->plan_sub, nb, nout, od, st);
+            if (rc) return rc;
+            c->plan_sub_key.swap(key);
+            c->plan_sub_ready = true;
+        }
+        plan = &c->plan_sub;
+    }
+    launch_diag(c, *plan, nb, nout, od, st);
+    if (!on_device && nout) {
+        CK(cudaMemcpyAsync(out, od, (size_t)nout * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    c->last_diag_flops = plan->flops * nb;
+    c->last_diag_work = plan->work_flops * nb;
+    return finish(c, st);
 }
 
 }  // namespace
@@ -246,6 +460,7 @@ void spi_default_options(spi_options* o) {
     o->refine_tol = 1e-13;
     o->async = 0;
     o->nd_leaf = 0;
+    o->batch = 1;
 }
 
 const char* spi_strerror(int s) {
@@ -269,11 +484,11 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     spi_options o;
     spi_default_options(&o);
     if (opt) o = *opt;
-    if (o.rhs_block <= 0) o.rhs_block = o.precision == SPI_PREC_MIXED_FP32 ? 64 : 32;
-    if (o.precision == SPI_PREC_MIXED_FP32) o.rhs_block = (o.rhs_block + 7) & ~7;  // float4 rows of Z
-    if (o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 || o.ordering > 1 ||
-        o.relax < 0)
+    if (o.batch <= 0) o.batch = 1;
+    if (o.rhs_block < 0 || o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 ||
+        o.ordering > 1 || o.relax < 0 || o.refine_max < 0)
         return SPI_ERR_ARG;
+    if (o.precision == SPI_PREC_MIXED_FP32 && o.rhs_block > 0) o.rhs_block = (o.rhs_block + 7) & ~7;
     spi_ctx* c = new (std::nothrow) spi_ctx();
     if (!c) return SPI_ERR_OOM;
     c->opt = o;
@@ -288,177 +503,77 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     try {
         build_factor_plan(c->S, c->FP);
         build_solve_plan(c->S, c->SP);
+        if (o.precision == SPI_PREC_MIXED_FP32 && n > 0) {
+            c->in_colptr.assign(colptr, colptr + n + 1);
+            c->in_rowind.assign(rowind, rowind + colptr[n]);
+        }
     } catch (const std::bad_alloc&) {
         delete c;
         return SPI_ERR_OOM;
-    }
-    if (o.precision == SPI_PREC_MIXED_FP32 && n > 0) {
-        try {
-            c->in_colptr.assign(colptr, colptr + n + 1);
-            c->in_rowind.assign(rowind, rowind + colptr[n]);
-        } catch (const std::bad_alloc&) {
-            delete c;
-            return SPI_ERR_OOM;
-        }
     }
     c->analyse_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = c;
     return SPI_OK;
 }
 
+int spi_analyse_multi(int32_t nprob, const int64_t* n, const int64_t* const* colptr,
+                      const int32_t* const* rowind, const spi_options* opt, spi_ctx** out) {
+    if (!out || nprob < 0 || (nprob > 0 && (!n || !colptr || !rowind))) return SPI_ERR_ARG;
+    *out = nullptr;
+    int64_t ntot = 0, nnz = 0;
+    for (int32_t p = 0; p < nprob; ++p) {
+        if (n[p] < 0 || (n[p] > 0 && (!colptr[p] || !rowind[p]))) return SPI_ERR_ARG;
+        ntot += n[p];
+        nnz += n[p] > 0 ? colptr[p][n[p]] : 0;
+    }
+    if (ntot > INT32_MAX - 1) return SPI_ERR_ARG;
+    std::vector<int64_t> cp;
+    std::vector<int32_t> ri;
+    try {
+        cp.reserve((size_t)ntot + 1);
+        ri.reserve((size_t)nnz);
+        cp.push_back(0);
+        int64_t base = 0;
+        for (int32_t p = 0; p < nprob; ++p) {
+            for (int64_t j = 0; j < n[p]; ++j) {
+                for (int64_t q = colptr[p][j]; q < colptr[p][j + 1]; ++q) {
+                    const int32_t r = rowind[p][q];
+                    if (r < 0 || r >= n[p]) return SPI_ERR_PATTERN;
+                    ri.push_back((int32_t)(base + r));
+                }
+                cp.push_back((int64_t)ri.size());
+            }
+            base += n[p];
+        }
+    } catch (const std::bad_alloc&) {
+        return SPI_ERR_OOM;
+    }
+    return spi_analyse(ntot, cp.data(), ri.data(), opt, out);
+}
+
 int spi_factor(spi_ctx* c, const double* values, int values_on_device, void* stream) {
-    if (!c) return SPI_ERR_ARG;
-    if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
-    int rc = ensure_device(c);
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    const Symbolic& S = c->S;
-    c->factored = false;
-    c->bad_pivot = -1;
-    const bool mixed = c->opt.precision == SPI_PREC_MIXED_FP32;
-    const double* vals = values;
-    if (S.nnz_a > 0 && (!values_on_device || mixed)) {
-        CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * sizeof(double),
-                           values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        vals = c->d_vals;
-    }
-    k_reset_status<<<1, 1, 0, st>>>(c->d_status);
-    CK(cudaMemsetAsync(c->d_L, 0, (size_t)S.lptr[S.ns] * sizeof(double), st));
-    if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * sizeof(double), st));
-    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, st);
-    CK(run_graph(c, &c->g_factor, st, [&](cudaStream_t s2) {
-        for (const Launch& l : c->FP.launches) {
-            const int32_t* items = l.kind == 0 ? c->d_items0
-                                 : l.kind == 1 ? c->d_items1
-                                 : l.kind == 2 ? c->d_items2 : c->d_items3;
-            launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, s2);
-        }
-        if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns], s2);
-    }));
-    rc = finish(c, st);
-    if (rc == SPI_OK) c->factored = true;
-    return rc;
+    return factor_impl(c, 1, values, values_on_device, (cudaStream_t)stream);
 }
 
-namespace {
-// x = P^T L^-T D^-1 L^-1 P b on device buffers (b and x distinct from d_w).
-cudaError_t solve_core(spi_ctx* c, const double* b, double* x, cudaStream_t st) {
-    const Symbolic& S = c->S;
-    launch_permute_in(S.n, c->dsym.perm, b, c->d_w, st);
-    cudaError_t e = run_graph(c, &c->g_solve, st, [&](cudaStream_t s2) {
-        for (const Launch& l : c->SP.fwd_launches)
-            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, s2);
-        for (const Launch& l : c->SP.bwd_launches)
-            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, s2);
-    });
-    launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, st);
-    return e;
+int spi_factor_batch(spi_ctx* c, int32_t nbatch, const double* values, int values_on_device, void* stream) {
+    return factor_impl(c, nbatch, values, values_on_device, (cudaStream_t)stream);
 }
-}  // namespace
 
-extern "C" int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, void* stream) {
-    if (!c || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
-    if (!c->factored) return SPI_ERR_STATE;
-    cudaStream_t st = (cudaStream_t)stream;
-    const Symbolic& S = c->S;
-    const int32_t n = S.n;
-    const double* bd = b;
-    if (!on_device && n) {
-        CK(cudaMemcpyAsync(c->d_vec, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
-        bd = c->d_vec;
-    }
-    double* xd = on_device ? x : c->d_vec;
-    if (c->opt.precision != SPI_PREC_MIXED_FP32) {
-        CK(solve_core(c, bd, xd, st));
-    } else if (n) {
-        // FP64 iterative refinement against N: x += solve(b - N x)
-        CK(cudaMemcpyAsync(c->d_b2, bd, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        CK(solve_core(c, c->d_b2, c->d_x, st));
-        double bnorm = -1.0;
-        c->refine_steps = 0;
-        for (int it = 0;; ++it) {
-            CK(cudaMemcpyAsync(c->d_r, c->d_b2, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, c->d_x, c->d_r, st);
-            CK(cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), st));
-            launch_norms2(n, c->d_r, bnorm < 0 ? c->d_b2 : nullptr, c->d_norm, st);
-            CK(cudaMemcpyAsync(c->h_norm, c->d_norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (bnorm < 0) bnorm = std::sqrt(c->h_norm[1]);
-            double rn = std::sqrt(c->h_norm[0]);
-            c->solve_relres = bnorm > 0 ? rn / bnorm : rn;
-            if (rn <= c->opt.refine_tol * bnorm || it >= c->opt.refine_max) break;
-            CK(solve_core(c, c->d_r, c->d_dx, st));
-            launch_axpy(n, c->d_dx, c->d_x, st);
-            c->refine_steps++;
-        }
-        CK(cudaMemcpyAsync(xd, c->d_x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-    if (!on_device && n)
-        CK(cudaMemcpyAsync(x, xd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (!on_device) CK(cudaStreamSynchronize(st));
-    return finish(c, st);
+int spi_solve(spi_ctx* c, const double* b, double* x, int on_device, void* stream) {
+    return solve_impl(c, 1, b, x, on_device, (cudaStream_t)stream);
+}
+
+int spi_solve_batch(spi_ctx* c, int32_t nbatch, const double* b, double* x, int on_device, void* stream) {
+    return solve_impl(c, nbatch, b, x, on_device, (cudaStream_t)stream);
 }
 
 int spi_diag_inverse(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
-    if (!c || !out) return SPI_ERR_ARG;
-    if (!c->factored) return SPI_ERR_STATE;
-    const Symbolic& S = c->S;
-    cudaStream_t st = (cudaStream_t)stream;
-    DevDiagPlan* plan;
-    int64_t nout;
-    if (!idx) {
-        nout = S.n;
-        if (!c->plan_all_ready) {
-            std::vector<int32_t> piv(S.n), pos(S.n);
-            for (int32_t k = 0; k < S.n; ++k) { piv[k] = k; pos[k] = S.perm[k]; }
-            DiagPlan h;
-            build_diag_plan(S, piv, pos, c->opt.rhs_block, h);
-            int rc = upload_plan(c, h, c->plan_all);
-            if (rc) return rc;
-            c->plan_all_ready = true;
-        }
-        plan = &c->plan_all;
-    } else {
-        if (nidx < 0) return SPI_ERR_ARG;
-        nout = nidx;
-        std::vector<int32_t> key((size_t)nidx);
-        if (nidx) {
-            if (on_device) {
-                CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-            } else {
-                std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
-            }
-        }
-        for (int32_t v : key)
-            if (v < 0 || v >= S.n) return SPI_ERR_ARG;
-        if (!c->plan_sub_ready || key != c->plan_sub_key) {
-            std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
-            for (int64_t t = 0; t < nidx; ++t) { piv[t] = S.iperm[key[t]]; pos[t] = (int32_t)t; }
-            DiagPlan h;
-            build_diag_plan(S, piv, pos, c->opt.rhs_block, h);
-            int rc = upload_plan(c, h, c->plan_sub);
-            if (rc) return rc;
-            c->plan_sub_key.swap(key);
-            c->plan_sub_ready = true;
-        }
-        plan = &c->plan_sub;
-    }
-    double* od = out;
-    if (!on_device) {
-        if (nout > S.n) {  // repeated indices: a larger staging buffer
-            return SPI_ERR_ARG;
-        }
-        od = c->d_out;
-    }
-    if (c->opt.precision == SPI_PREC_MIXED_FP32) launch_diag_inverse_f32(c->dsym, *plan, c->d_L32, c->d_D, od, st);
-    else launch_diag_inverse(c->dsym, *plan, c->d_L, c->d_D, od, st);
-    if (!on_device && nout)
-        CK(cudaMemcpyAsync(out, od, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, st));
-    c->last_diag_flops = plan->flops;
-    c->last_diag_work = plan->work_flops;
-    if (!on_device) CK(cudaStreamSynchronize(st));
-    return finish(c, st);
+    return diag_impl(c, 1, idx, nidx, out, on_device, (cudaStream_t)stream);
+}
+
+int spi_diag_inverse_batch(spi_ctx* c, int32_t nbatch, const int32_t* idx, int64_t nidx, double* out,
+                           int on_device, void* stream) {
+    return diag_impl(c, nbatch, idx, nidx, out, on_device, (cudaStream_t)stream);
 }
 
 int spi_info(const spi_ctx* c, spi_stats* o) {
@@ -473,21 +588,22 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->n_levels = S.nlevels;
     o->max_front = S.max_front;
     o->bad_pivot = c->bad_pivot;
+    o->bad_band = c->bad_band;
     o->factor_flops = S.factor_flops;
     o->diag_flops = c->last_diag_flops;
     o->solve_flops = 4.0 * (double)S.nnz_l + (double)S.n;
     o->diag_flops_all = S.diag_flops_all;
     o->diag_work_flops = c->last_diag_work;
     o->device_bytes = c->device_bytes;
-    o->launches_factor = 2 + (int64_t)c->FP.launches.size();
+    o->launches_factor = 2 + (int64_t)c->FP.launches.size() + (mixed_of(c) ? 1 : 0);
     int64_t ls = 0;
     for (const Launch& l : c->SP.fwd_launches) ls += l.count > 0;
     for (const Launch& l : c->SP.bwd_launches) ls += l.count > 0;
     o->launches_solve = S.n ? 2 + ls : 0;
     o->launches_diag = S.n ? 1 : 0;
-    if (c->opt.precision == SPI_PREC_MIXED_FP32) o->launches_factor += 1;
     o->refine_steps = c->refine_steps;
     o->solve_relres = c->solve_relres;
+    o->rhs_block = c->rhs_block_used > 0 ? c->rhs_block_used : c->opt.rhs_block;
     o->analyse_seconds = c->analyse_seconds;
     return SPI_OK;
 }
@@ -495,10 +611,10 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
 int spi_sync(spi_ctx* c, void* stream) {
     if (!c) return SPI_ERR_ARG;
     if (!c->dev_ready) return SPI_OK;
-    spi_options o = c->opt;
+    const int async = c->opt.async;
     c->opt.async = 0;
     int rc = finish(c, (cudaStream_t)stream);
-    c->opt = o;
+    c->opt.async = async;
     return rc;
 }
 
@@ -518,11 +634,12 @@ void spi_destroy(spi_ctx* c) {
     if (!c) return;
     free_plan(c->plan_all);
     free_plan(c->plan_sub);
-    if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
-    if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+    for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_norm) cudaFreeHost(c->h_norm);
     delete c;
 }
 

@@ -43,7 +43,11 @@ size_t diag_smem_bytes(int B) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, const T* __restrict__ L,
-                                                       const double* __restrict__ D, double* __restrict__ out) {
+                                                       const double* __restrict__ D, double* __restrict__ out,
+                                                       Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    out += blockIdx.y * bs.out;
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = p.B;
     double* var = reinterpret_cast<double*>(smem);
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
     T* Lt = Ld + kT * (kT + 1);             // [kRT][kT+1]
     const int tid = threadIdx.x;
     const int b = p.order[blockIdx.x];
-    T* Z = reinterpret_cast<T*>(p.Z) + p.zbase[b];
+    T* Z = reinterpret_cast<T*>(p.Z) + blockIdx.y * bs.Z + p.zbase[b];
     const int64_t zsz = p.zbase[b + 1] - p.zbase[b];
     const int r0b = p.blk_ptr[b], nr = p.blk_ptr[b + 1] - r0b;
     for (int64_t i = tid; i < zsz; i += kThreads) Z[i] = T(0);
@@ -139,7 +143,10 @@ size_t diag_f32_smem_bytes(int B) {
 
 __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p, const float* __restrict__ L,
                                                              const double* __restrict__ D,
-                                                             double* __restrict__ out) {
+                                                             double* __restrict__ out, Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    out += blockIdx.y * bs.out;
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = p.B;  // a multiple of 8 (padded RHS count)
     double* var = reinterpret_cast<double*>(smem);
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
     const int b = p.order[blockIdx.x];
-    float* Z = reinterpret_cast<float*>(p.Z) + p.zbase[b];
+    float* Z = reinterpret_cast<float*>(p.Z) + blockIdx.y * bs.Z + p.zbase[b];
     const int64_t zsz = p.zbase[b + 1] - p.zbase[b];
     const int r0b = p.blk_ptr[b], nr = p.blk_ptr[b + 1] - r0b;
     for (int64_t i = tid; i < zsz; i += kFThreads) Z[i] = 0.f;
@@ -241,11 +248,12 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
 }
 
 template <typename T>
-void launch_t(const DevSym& d, const DevDiagPlan& p, const T* L, const double* D, double* out, cudaStream_t st) {
+void launch_t(const DevSym& d, const DevDiagPlan& p, const T* L, const double* D, double* out, int nb,
+              const Strides& bs, cudaStream_t st) {
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
                p.urel, p.zbase, p.Z};
     size_t sm = diag_smem_bytes<T>(p.B);
-    k_diag_inv<T><<<p.nblocks, kThreads, sm, st>>>(d, a, L, D, out);
+    k_diag_inv<T><<<dim3(p.nblocks, nb), kThreads, sm, st>>>(d, a, L, D, out, bs);
 }
 
 }  // namespace
@@ -259,17 +267,17 @@ cudaError_t diag_kernel_setup(int B) {
 }
 
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
-                         cudaStream_t st) {
-    if (p.nblocks == 0) return;
-    launch_t<double>(d, p, L, D, out, st);
+                         int nb, const Strides& bs, cudaStream_t st) {
+    if (p.nblocks == 0 || nb == 0) return;
+    launch_t<double>(d, p, L, D, out, nb, bs, st);
 }
 
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             cudaStream_t st) {
-    if (p.nblocks == 0) return;
+                             int nb, const Strides& bs, cudaStream_t st) {
+    if (p.nblocks == 0 || nb == 0) return;
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
                p.urel, p.zbase, p.Z};
-    k_diag_inv_f32<<<p.nblocks, kFThreads, diag_f32_smem_bytes(p.B), st>>>(d, a, L, D, out);
+    k_diag_inv_f32<<<dim3(p.nblocks, nb), kFThreads, diag_f32_smem_bytes(p.B), st>>>(d, a, L, D, out, bs);
 }
 
 }  // namespace spi

@@ -85,7 +85,10 @@ namespace {
 
 __global__ void k_assemble(const int64_t* __restrict__ amap, const double* __restrict__ vals, int64_t nnz,
                            double* __restrict__ L, const int32_t* __restrict__ diag_src, int32_t n,
-                           double* __restrict__ adiag) {
+                           double* __restrict__ adiag, Strides bs) {
+    vals += blockIdx.y * bs.nnz;
+    L += blockIdx.y * bs.L;
+    adiag += blockIdx.y * bs.n;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = i; p < nnz; p += stride) L[amap[p]] = vals[p];
@@ -98,7 +101,11 @@ constexpr int kThreads = 128;
 // before it): unblocked LDL^T in shared memory, FP64.
 __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
                                                         double* __restrict__ L, double* __restrict__ D,
-                                                        const double* __restrict__ adiag, DevStatus* status) {
+                                                        const double* __restrict__ adiag, DevStatus* status,
+                                                        Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    adiag += blockIdx.y * bs.n;
     __shared__ double A[kT][kT + 1];
     __shared__ double dv[kT];
     const int tid = threadIdx.x;
@@ -117,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
         if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
             if (tid == 0) {
                 atomicOr(&status->flags, FLAG_NOT_SPD);
-                atomicMin(&status->bad_pivot, f + c0 + c);
+                atomicMin(&status->bad_pivot, (int)(blockIdx.y * bs.n) + f + c0 + c);
             }
         }
         __syncthreads();
@@ -142,7 +149,10 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
 // the block columns before it): L21 = X L11^-T D^-1, one thread per row.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t* __restrict__ items, int b,
-                                                         double* __restrict__ L, const double* __restrict__ D) {
+                                                         double* __restrict__ L, const double* __restrict__ D,
+                                                         Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
     __shared__ C X[kT][kT + 1];
     __shared__ C Bd[kT][kT + 1];
     __shared__ C dv[kT];
@@ -180,7 +190,10 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
 // [c0+w, k) and rows i >= j, P[i][j] -= sum_{c in block b} L[i][c] d_c L[j][c].
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32_t* __restrict__ items, int b,
-                                                           double* __restrict__ L, const double* __restrict__ D) {
+                                                           double* __restrict__ L, const double* __restrict__ D,
+                                                           Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
     __shared__ C Li[kT][kT + 1];
     __shared__ C Lj[kT][kT + 1];
     const int tid = threadIdx.x;
@@ -221,7 +234,10 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int32_t* __restrict__ items,
                                                             double* __restrict__ L, double* __restrict__ F22,
-                                                            const double* __restrict__ D) {
+                                                            const double* __restrict__ D, Strides bs) {
+    L += blockIdx.y * bs.L;
+    F22 += blockIdx.y * bs.F22;
+    D += blockIdx.y * bs.n;
     __shared__ C Li[kT][kT + 1];
     __shared__ C Lj[kT][kT + 1];
     const int tid = threadIdx.x;
@@ -289,29 +305,31 @@ void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
 }
 
 void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
-                     const int32_t* diag_src, double* adiag, cudaStream_t st) {
+                     const int32_t* diag_src, double* adiag, int nb, const Strides& bs, cudaStream_t st) {
     int64_t work = std::max<int64_t>(nnz, d.n);
-    if (work == 0) return;
-    int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    k_assemble<<<grid, 256, 0, st>>>(amap, vals, nnz, L, diag_src, d.n, adiag);
+    if (work == 0 || nb == 0) return;
+    int grid = (int)std::min<int64_t>((work + 255) / 256, std::max(1, 152 * 16 / nb));
+    k_assemble<<<dim3(grid, nb), 256, 0, st>>>(amap, vals, nnz, L, diag_src, d.n, adiag, bs);
 }
 
 template <typename C>
 void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22, double* D,
-                   const double* adiag, DevStatus* status, cudaStream_t st) {
+                   const double* adiag, DevStatus* status, int nb, const Strides& bs, cudaStream_t st) {
+    const dim3 g(l.count, nb);
     switch (l.kind) {
-        case 0: k_diag_tile<<<l.count, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status); break;
-        case 1: k_panel_trsm<C><<<l.count, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D); break;
-        case 3: k_panel_update<C><<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D); break;
-        default: k_schur_scatter<C><<<l.count, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D); break;
+        case 0: k_diag_tile<<<g, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status, bs); break;
+        case 1: k_panel_trsm<C><<<g, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D, bs); break;
+        case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, bs); break;
+        default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
     }
 }
 
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, bool mixed, cudaStream_t st) {
-    if (l.count == 0) return;
-    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, st);
-    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, st);
+                        double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
+                        const Strides& bs, cudaStream_t st) {
+    if (l.count == 0 || nb == 0) return;
+    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, nb, bs, st);
+    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, nb, bs, st);
 }
 
 }  // namespace spi

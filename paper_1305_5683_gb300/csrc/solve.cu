@@ -16,12 +16,16 @@ constexpr int kBwdCols = 256;  // columns per backward CTA
 
 __global__ void k_permute_in(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ b,
                              double* __restrict__ w) {
+    b += (int64_t)blockIdx.y * n;
+    w += (int64_t)blockIdx.y * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         w[k] = b[perm[k]];
 }
 
 __global__ void k_permute_out(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ w,
                               double* __restrict__ x) {
+    w += (int64_t)blockIdx.y * n;
+    x += (int64_t)blockIdx.y * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         x[perm[k]] = w[k];
 }
@@ -35,7 +39,10 @@ __global__ void k_permute_out(int32_t n, const int32_t* __restrict__ perm, const
 // the level update the same ancestors).
 __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* __restrict__ items, int b,
                                                        const double* __restrict__ L, double* __restrict__ w,
-                                                       double* __restrict__ z) {
+                                                       double* __restrict__ z, Strides bs) {
+    L += blockIdx.y * bs.L;
+    w += blockIdx.y * bs.n;
+    z += blockIdx.y * bs.n;
     __shared__ double xb[kT];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
@@ -75,7 +82,12 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
 __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* __restrict__ items,
                                                        const double* __restrict__ L, const double* __restrict__ D,
                                                        const double* __restrict__ z, const double* __restrict__ x,
-                                                       double* __restrict__ w) {
+                                                       double* __restrict__ w, Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    z += blockIdx.y * bs.n;
+    x += blockIdx.y * bs.n;
+    w += blockIdx.y * bs.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -96,7 +108,10 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
 // earlier columns a < 32 b: y_a -= sum_r L[32b + r][a] x_b[r].
 __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* __restrict__ items, int b,
                                                        const double* __restrict__ L, double* __restrict__ w,
-                                                       double* __restrict__ x) {
+                                                       double* __restrict__ x, Strides bs) {
+    L += blockIdx.y * bs.L;
+    w += blockIdx.y * bs.n;
+    x += blockIdx.y * bs.n;
     __shared__ double xb[kT];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
@@ -133,7 +148,11 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
 // warp per column: the column's dot product for r_j, and the mirrored
 // upper-triangle entries scattered into r_i.
 __global__ void k_sym_residual(int32_t n, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                               const double* __restrict__ va, const double* __restrict__ x, double* __restrict__ r) {
+                               const double* __restrict__ va, const double* __restrict__ x, double* __restrict__ r,
+                               int64_t nnz) {
+    va += blockIdx.y * nnz;
+    x += (int64_t)blockIdx.y * n;
+    r += (int64_t)blockIdx.y * n;
     const int lane = threadIdx.x & 31;
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n;
          j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -152,6 +171,9 @@ __global__ void k_sym_residual(int32_t n, const int64_t* __restrict__ cp, const 
 
 // out[0] += sum a_i^2, out[1] += sum b_i^2
 __global__ void k_norms2(int32_t n, const double* __restrict__ a, const double* __restrict__ b, double* out) {
+    a += (int64_t)blockIdx.y * n;
+    if (b) b += (int64_t)blockIdx.y * n;
+    out += 2 * blockIdx.y;
     double sa = 0.0, sb = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         sa += a[i] * a[i];
@@ -168,6 +190,8 @@ __global__ void k_norms2(int32_t n, const double* __restrict__ a, const double* 
 }
 
 __global__ void k_axpy(int32_t n, const double* __restrict__ dx, double* __restrict__ x) {
+    dx += (int64_t)blockIdx.y * n;
+    x += (int64_t)blockIdx.y * n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += dx[i];
 }
@@ -175,30 +199,30 @@ __global__ void k_axpy(int32_t n, const double* __restrict__ dx, double* __restr
 }  // namespace
 
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
-                         double* r, cudaStream_t st) {
-    if (n == 0) return;
-    int grid = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 152 * 8);
-    k_sym_residual<<<grid, 256, 0, st>>>(n, cp, ri, va, x, r);
+                         double* r, int nb, int64_t nnz, cudaStream_t st) {
+    if (n == 0 || nb == 0) return;
+    int grid = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, std::max(1, 152 * 8 / nb));
+    k_sym_residual<<<dim3(grid, nb), 256, 0, st>>>(n, cp, ri, va, x, r, nnz);
 }
 
-void launch_norms2(int32_t n, const double* a, const double* b, double* out, cudaStream_t st) {
-    if (n == 0) return;
-    k_norms2<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, a, b, out);
+void launch_norms2(int32_t n, const double* a, const double* b, double* out, int nb, cudaStream_t st) {
+    if (n == 0 || nb == 0) return;
+    k_norms2<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, a, b, out);
 }
 
-void launch_axpy(int32_t n, const double* dx, double* x, cudaStream_t st) {
-    if (n == 0) return;
-    k_axpy<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, dx, x);
+void launch_axpy(int32_t n, const double* dx, double* x, int nb, cudaStream_t st) {
+    if (n == 0 || nb == 0) return;
+    k_axpy<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, dx, x);
 }
 
-void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st) {
-    if (n == 0) return;
-    k_permute_in<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, perm, b, w);
+void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st) {
+    if (n == 0 || nb == 0) return;
+    k_permute_in<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, perm, b, w);
 }
 
-void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, cudaStream_t st) {
-    if (n == 0) return;
-    k_permute_out<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(n, perm, w, x);
+void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st) {
+    if (n == 0 || nb == 0) return;
+    k_permute_out<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, perm, w, x);
 }
 
 void build_solve_plan(const Symbolic& S, SolvePlan& P) {
@@ -245,12 +269,14 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P) {
 }
 
 void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
-                       const double* L, const double* D, double* w, double* z, double* x, cudaStream_t st) {
-    if (l.count == 0) return;
+                       const double* L, const double* D, double* w, double* z, double* x, int nb,
+                       const Strides& bs, cudaStream_t st) {
+    if (l.count == 0 || nb == 0) return;
+    const dim3 g(l.count, nb);
     switch (l.kind) {
-        case 4: k_fwd_step<<<l.count, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z); break;
-        case 5: k_bwd_init<<<l.count, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w); break;
-        default: k_bwd_step<<<l.count, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x); break;
+        case 4: k_fwd_step<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z, bs); break;
+        case 5: k_bwd_init<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
+        default: k_bwd_step<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x, bs); break;
     }
 }
 

@@ -36,6 +36,17 @@ struct DevSym {
     const int32_t* snode_of = nullptr;
 };
 
+// Per-band strides of the batched (same-pattern) buffers; blockIdx.y selects
+// the band.  All zero-stride fields are unused for a single problem.
+struct Strides {
+    int64_t L = 0;    // panel doubles per band (also FP32 panel floats per band)
+    int64_t F22 = 0;  // update-area doubles per band
+    int64_t n = 0;    // vector length per band
+    int64_t nnz = 0;  // input values per band
+    int64_t Z = 0;    // variance workspace elements per band
+    int64_t out = 0;  // variance outputs per band
+};
+
 // A flattened work list of one kernel launch.
 struct Launch {
     int kind;        // 0 diag tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update
@@ -79,24 +90,26 @@ struct DevDiagPlan {
 
 // ---- kernel launchers (factor.cu)
 void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
-                     const int32_t* diag_src, double* adiag, cudaStream_t st);
+                     const int32_t* diag_src, double* adiag, int nb, const Strides& bs, cudaStream_t st);
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, bool mixed, cudaStream_t st);
+                        double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
+                        const Strides& bs, cudaStream_t st);
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 // ---- solve.cu
-void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, cudaStream_t st);
-void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, cudaStream_t st);
+void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);
+void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st);
 void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
-                       const double* L, const double* D, double* w, double* z, double* x, cudaStream_t st);
+                       const double* L, const double* D, double* w, double* z, double* x, int nb,
+                       const Strides& bs, cudaStream_t st);
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
-                         double* r, cudaStream_t st);
-void launch_norms2(int32_t n, const double* a, const double* b, double* out, cudaStream_t st);
-void launch_axpy(int32_t n, const double* dx, double* x, cudaStream_t st);
+                         double* r, int nb, int64_t nnz, cudaStream_t st);
+void launch_norms2(int32_t n, const double* a, const double* b, double* out, int nb, cudaStream_t st);
+void launch_axpy(int32_t n, const double* dx, double* x, int nb, cudaStream_t st);
 // ---- diag.cu
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
-                         cudaStream_t st);
+                         int nb, const Strides& bs, cudaStream_t st);
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             cudaStream_t st);
+                             int nb, const Strides& bs, cudaStream_t st);
 cudaError_t diag_kernel_setup(int B);
 
 }  // namespace spi

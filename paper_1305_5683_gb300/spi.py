@@ -22,26 +22,29 @@ SPI_OK, SPI_ERR_ARG, SPI_ERR_PATTERN, SPI_ERR_NOT_SPD, SPI_ERR_OOM, SPI_ERR_CUDA
 SPI_PREC_FP64, SPI_PREC_MIXED_FP32 = 0, 1
 SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 
-EXPORTS = ["spi_default_options", "spi_analyse", "spi_factor", "spi_solve", "spi_diag_inverse",
-           "spi_info", "spi_sync", "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy"]
+EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
+           "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
+           "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy"]
 
 
 class spi_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ordering", ctypes.c_int), ("rhs_block", ctypes.c_int),
                 ("relax", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
-                ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int)]
+                ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class spi_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz_a", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
                 ("nnz_l_stored", ctypes.c_int64), ("n_supernodes", ctypes.c_int64),
                 ("n_levels", ctypes.c_int64), ("max_front", ctypes.c_int64), ("bad_pivot", ctypes.c_int64),
+                ("bad_band", ctypes.c_int64),
                 ("factor_flops", ctypes.c_double), ("diag_flops", ctypes.c_double),
                 ("solve_flops", ctypes.c_double), ("diag_flops_all", ctypes.c_double),
                 ("diag_work_flops", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("launches_factor", ctypes.c_int64),
                 ("launches_solve", ctypes.c_int64), ("launches_diag", ctypes.c_int64),
                 ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),
+                ("rhs_block", ctypes.c_int64),
                 ("analyse_seconds", ctypes.c_double)]
 
     def as_dict(self):
@@ -73,7 +76,13 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_default_options.argtypes = [ctypes.POINTER(spi_options)]; L.spi_default_options.restype = None
     L.spi_analyse.argtypes = [I64, V, V, ctypes.POINTER(spi_options), ctypes.POINTER(V)]
     L.spi_analyse.restype = I
+    L.spi_analyse_multi.argtypes = [ctypes.c_int32, V, V, V, ctypes.POINTER(spi_options), ctypes.POINTER(V)]
+    L.spi_analyse_multi.restype = I
     L.spi_factor.argtypes = [V, V, I, V]; L.spi_factor.restype = I
+    L.spi_factor_batch.argtypes = [V, ctypes.c_int32, V, I, V]; L.spi_factor_batch.restype = I
+    L.spi_solve_batch.argtypes = [V, ctypes.c_int32, V, V, I, V]; L.spi_solve_batch.restype = I
+    L.spi_diag_inverse_batch.argtypes = [V, ctypes.c_int32, V, I64, V, I, V]
+    L.spi_diag_inverse_batch.restype = I
     L.spi_solve.argtypes = [V, V, V, I, V]; L.spi_solve.restype = I
     L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
@@ -138,6 +147,54 @@ def spi_analyse(n, colptr, rowind, opt: spi_options | None = None) -> ctypes.c_v
     _check(rc, "spi_analyse")
     del k1, k2
     return h
+
+
+def spi_analyse_multi(ns, colptrs, rowinds, opt: spi_options | None = None) -> ctypes.c_void_p:
+    """Block-diagonal batch of independent problems (concatenated numbering)."""
+    k = len(ns)
+    n_arr = np.ascontiguousarray(ns, dtype=np.int64)
+    keep = [np.ascontiguousarray(c, dtype=np.int64) for c in colptrs]
+    keep2 = [np.ascontiguousarray(r, dtype=np.int32) for r in rowinds]
+    cp_ptrs = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in keep])
+    ri_ptrs = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in keep2])
+    h = ctypes.c_void_p()
+    rc = lib().spi_analyse_multi(k, n_arr.ctypes.data_as(ctypes.c_void_p), ctypes.cast(cp_ptrs, ctypes.c_void_p),
+                                 ctypes.cast(ri_ptrs, ctypes.c_void_p),
+                                 ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(rc, "spi_analyse_multi")
+    del keep, keep2
+    return h
+
+
+def spi_factor_batch(ctx, nbatch, values, stream=None) -> None:
+    v, dev, keep = _buf(values, np.float64)
+    _check(lib().spi_factor_batch(ctx, int(nbatch), v, dev, _stream(stream)), "spi_factor_batch")
+    del keep
+
+
+def spi_solve_batch(ctx, nbatch, b, x, stream=None) -> None:
+    bp, dev, k1 = _buf(b, np.float64)
+    xp, dev2, k2 = _buf(x, np.float64)
+    if dev != dev2 or (not _is_torch(x) and xp.value != x.ctypes.data):
+        raise TypeError("x must be a contiguous float64 buffer on the same side as b")
+    _check(lib().spi_solve_batch(ctx, int(nbatch), bp, xp, dev, _stream(stream)), "spi_solve_batch")
+    del k1, k2
+
+
+def spi_diag_inverse_batch(ctx, nbatch, idx, out, stream=None) -> None:
+    op, dev, k1 = _buf(out, np.float64)
+    if not _is_torch(out) and op.value != out.ctypes.data:
+        raise TypeError("out must be a contiguous float64 buffer")
+    if idx is None:
+        ip, nidx, k2 = None, 0, None
+    else:
+        ip, dev_i, k2 = _buf(idx, np.int32)
+        if dev_i != dev:
+            raise TypeError("idx and out must both be host or both be device buffers")
+        nidx = int(idx.numel() if _is_torch(idx) else len(k2))
+    _check(lib().spi_diag_inverse_batch(ctx, int(nbatch), ip, nidx, op, dev, _stream(stream)),
+           "spi_diag_inverse_batch")
+    del k1, k2
 
 
 def spi_factor(ctx, values, stream=None) -> None:
@@ -208,12 +265,49 @@ class Solver:
     """analyse -> factor -> solve -> diag_inverse on one pattern (owns the context)."""
 
     def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
-                 rhs_block=0, relax=10, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False):
+                 rhs_block=0, relax=10, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
+                 _multi=None):
         o = spi_default_options()
         o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax
         o.refine_max, o.refine_tol, o.nd_leaf, o.async_ = refine_max, refine_tol, nd_leaf, int(async_)
+        o.batch = batch
         self.n = int(n)
-        self._h = spi_analyse(n, colptr, rowind, o)
+        self.batch = batch
+        if _multi is not None:
+            self._h = spi_analyse_multi(*_multi, o)
+        else:
+            self._h = spi_analyse(n, colptr, rowind, o)
+
+    @classmethod
+    def for_problems(cls, problems, **kw):
+        """One context over independent problems (block-diagonal batch)."""
+        ns = [p.n for p in problems]
+        return cls(sum(ns), None, None, _multi=(ns, [p.colptr for p in problems], [p.rowind for p in problems]),
+                   **kw)
+
+    def factor_batch(self, values, nbatch=None, stream=None):
+        nb = nbatch if nbatch is not None else self.batch
+        spi_factor_batch(self._h, nb, values, stream)
+        return self
+
+    def solve_batch(self, b, x=None, nbatch=None, stream=None):
+        nb = nbatch if nbatch is not None else self.batch
+        if x is None:
+            x = b.new_empty(b.shape) if _is_torch(b) else np.empty(nb * self.n, np.float64)
+        spi_solve_batch(self._h, nb, b, x, stream)
+        return x
+
+    def diag_inverse_batch(self, idx=None, out=None, nbatch=None, stream=None, device=None):
+        nb = nbatch if nbatch is not None else self.batch
+        m = self.n if idx is None else (idx.numel() if _is_torch(idx) else len(idx))
+        if out is None:
+            if device is not None:
+                import torch
+                out = torch.empty(nb * m, dtype=torch.float64, device=device)
+            else:
+                out = np.empty(nb * m, np.float64)
+        spi_diag_inverse_batch(self._h, nb, idx, out, stream)
+        return out
 
     @classmethod
     def for_problem(cls, pb, **kw):

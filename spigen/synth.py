@@ -29,6 +29,8 @@ Readings where the paper is silent (stated once here, fixed for all configs):
     cut at n_p and a remainder shorter than lo is merged into the previous
     bin; bins in which the source is never visible are dropped (a zero column
     would make N singular);
+  * detector-pattern blocks hold det_block consecutive pointings; a trailing
+    block shorter than half a block is merged into the previous one;
   * true intensities: pointing normalisations U(0.9, 1.1), detector-pattern
     amplitudes U(0, 5), source fluxes U(0, 20) per bin; per-detector
     background means u_d ~ U(50, 200).
@@ -69,7 +71,7 @@ SCALE = SpiConfig("spi-P20000", n_pointings=20000, n_sources=500, bin_lo=20,
                   bin_hi=2000, det_block=500)
 # Same-pattern energy-band member (one band); bands rescale values only.
 BAND = SpiConfig("spi-band-P5000", n_pointings=5000, n_sources=200, bin_lo=10,
-                 bin_hi=1000, det_block=500)
+                 bin_hi=200, det_block=500)
 
 
 def uneven_config(index: int) -> SpiConfig:
@@ -203,7 +205,13 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     order = np.lexsort((srcs, starts))
     starts, ends, srcs = starts[order], ends[order], srcs[order]
     nbins = len(starts)
-    nblk = (P + cfg.det_block - 1) // cfg.det_block
+    # detector-pattern blocks of det_block pointings; a trailing block shorter
+    # than half a block joins the previous one (a block of one pointing would
+    # make that pointing's column a combination of the block's 19 columns)
+    nblk = max(1, P // cfg.det_block + (1 if P % cfg.det_block >= (cfg.det_block + 1) // 2 else 0))
+
+    def blk(p):
+        return np.minimum(np.asarray(p) // cfg.det_block, nblk - 1)
     ndet = nblk * nd
     n = P + ndet + nbins
     col_bin0 = P + ndet
@@ -216,7 +224,7 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
         """Dense H restricted to rows of pointings [p0, p1) and the columns
         active there; returns (global column ids, H_w)."""
         np_ = p1 - p0
-        kb0, kb1 = p0 // cfg.det_block, (p1 - 1) // cfg.det_block + 1
+        kb0, kb1 = int(blk(p0)), int(blk(p1 - 1)) + 1
         act = np.nonzero((starts < p1) & (ends > p0))[0]
         cols = np.concatenate([np.arange(p0, p1),
                                P + np.arange(kb0 * nd, kb1 * nd),
@@ -225,7 +233,7 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
         pp = np.arange(p0, p1)
         rows = (pp - p0)[:, None] * nd + np.arange(nd)[None, :]
         Hw[rows, (pp - p0)[:, None]] = u_d[None, :] * g[p0:p1]
-        detc = np_ + ((pp // cfg.det_block) - kb0)[:, None] * nd + np.arange(nd)[None, :]
+        detc = np_ + (blk(pp) - kb0)[:, None] * nd + np.arange(nd)[None, :]
         Hw[rows, detc] = h[p0:p1]
         if len(act):
             a = np.maximum(starts[act], p0); b_ = np.minimum(ends[act], p1)
@@ -295,3 +303,57 @@ def random_spd(n: int, density: float, seed: int, *, dominance: float = 1.0) -> 
                       rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
                       b=b, x_true=np.zeros(n), kind=np.full(n, 2, np.int8),
                       n_pointing=0, n_detcol=0, n_bins=n)
+
+
+@dataclasses.dataclass
+class BandBatch:
+    """Same-pattern energy bands: one pattern, `nbands` value sets and
+    right-hand sides stacked band after band."""
+    cfg: SpiConfig
+    n: int
+    colptr: np.ndarray
+    rowind: np.ndarray
+    values: np.ndarray   # float64 [nbands * nnz]
+    b: np.ndarray        # float64 [nbands * n]
+    energies_kev: np.ndarray
+    nbands: int
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colptr[-1])
+
+    def band(self, k: int) -> SpiProblem:
+        nnz = self.nnz
+        return SpiProblem(cfg=self.cfg, n=self.n, colptr=self.colptr, rowind=self.rowind,
+                          values=self.values[k * nnz:(k + 1) * nnz], b=self.b[k * self.n:(k + 1) * self.n],
+                          x_true=np.zeros(self.n), kind=np.zeros(self.n, np.int8), n_pointing=0, n_detcol=0,
+                          n_bins=0)
+
+
+def generate_bands(cfg: SpiConfig, nbands: int, *, e_lo: float = 20.0, e_hi: float = 1000.0) -> BandBatch:
+    """Energy bands of one observation: band k has energy E_k (log-spaced in
+    [e_lo, e_hi] keV); every source's responses are scaled by
+    (E_k / e_lo)^-alpha_s with spectral index alpha_s ~ U(1.5, 3) per source,
+    and the counts are redrawn per band.  The pattern does not depend on the
+    band (every structural entry of N is a sum of positive terms)."""
+    rng = np.random.default_rng(10_000 + cfg.seed)
+    alpha = rng.uniform(1.5, 3.0, cfg.n_sources)
+    energies = np.exp(np.linspace(np.log(e_lo), np.log(e_hi), nbands)) if nbands > 1 else np.array([e_lo])
+    vals, bs = [], []
+    pattern = None
+    for k, e in enumerate(energies):
+        pb = generate(cfg, band_scale=(e / e_lo) ** (-alpha), counts_seed=cfg.seed * 100_003 + k)
+        if pattern is None:
+            pattern = (pb.n, pb.colptr, pb.rowind)
+        elif not (pb.n == pattern[0] and np.array_equal(pb.colptr, pattern[1])
+                  and np.array_equal(pb.rowind, pattern[2])):
+            raise RuntimeError("band pattern differs from band 0")
+        vals.append(pb.values)
+        bs.append(pb.b)
+    return BandBatch(cfg=cfg, n=pattern[0], colptr=pattern[1], rowind=pattern[2],
+                     values=np.concatenate(vals), b=np.concatenate(bs), energies_kev=energies, nbands=nbands)
+
+
+def generate_uneven(count: int, start: int = 0) -> list:
+    """`count` independent problems of uneven size (members start..start+count-1)."""
+    return [generate(uneven_config(i)) for i in range(start, start + count)]

@@ -45,7 +45,8 @@ typedef enum spi_status {
     SPI_ERR_OOM = 4,      /* host or device allocation failed */
     SPI_ERR_CUDA = 5,     /* CUDA runtime error (no device, launch failure, ...) */
     SPI_ERR_TIMEOUT = 6,  /* a bounded device-side wait gave up */
-    SPI_ERR_STATE = 7     /* call out of order (factor before analyse, solve before factor) */
+    SPI_ERR_STATE = 7,    /* call out of order (factor before analyse, solve before factor) */
+    SPI_ERR_SCRATCH = 8   /* problem too large for the fixed scratch of spi_diag_inverse_noalloc */
 } spi_status;
 
 typedef enum spi_precision {
@@ -185,6 +186,31 @@ int spi_solve_batch(spi_ctx* ctx, int32_t nbatch, const double* b, double* x, in
  * float64[nbatch * m] with m = nidx (or n when idx == NULL), band b at b * m. */
 int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int64_t nidx, double* out,
                            int on_device, void* stream);
+
+/* Variances without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need variances -- a host thread that must not enter the CUDA allocator (a
+ * real-time loop, a callback of another runtime) or a process whose device
+ * memory is already handed out by another allocator.  It computes the same
+ * out[t] = (N^-1)_{idx[t], idx[t]} as spi_diag_inverse, one right-hand side
+ * per CTA along its elimination-tree path, with its workspace in one fixed
+ * 16 MiB array in device memory that every GPU loading this library holds
+ * until the process exits; it calls no allocation routine.
+ *   ctx     a factored context (spi_factor, or band 0 of spi_factor_batch) whose
+ *           device is the current device
+ *   idx     device int32[nidx], caller numbering
+ *   out     device float64[nidx]
+ * Limit: the inverse permutation and one length-n work vector must fit, i.e.
+ * n <= 1,398,100; larger problems get SPI_ERR_SCRATCH (checked before any
+ * device work).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call clears the part of the array it
+ * uses before use; calls that overlap on the GPU (other streams, other
+ * contexts) share the array and race.  The call returns after the stream has
+ * drained.  Errors: SPI_ERR_ARG (NULL buffer, index out of range -- its out[t]
+ * is NaN -- or another device current), SPI_ERR_STATE (not factored),
+ * SPI_ERR_SCRATCH, SPI_ERR_CUDA. */
+int spi_diag_inverse_noalloc(const spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, void* stream);
 
 /* Statistics of the analysis and of the last calls.  Errors: SPI_ERR_ARG. */
 int spi_info(const spi_ctx* ctx, spi_stats* out);

@@ -445,6 +445,85 @@ int diag_impl(spi_ctx* c, int nb, const int32_t* idx, int64_t nidx, double* out,
     return finish(c, st);
 }
 
+// ---------------------------------------------------------------------------
+// Variances without any device allocation (spi_diag_inverse_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need
+// variances: a host thread that must not touch the CUDA allocator (a
+// real-time acquisition loop, a callback of another runtime), or a process
+// whose device memory is entirely handed out by another allocator.  For them
+// the variance computation below uses a fixed scratch array that every GPU
+// which loads this library holds from module load until the process exits.
+// The caller provides the factored context, the index set and the output,
+// all already on the device.
+//
+// Scratch layout (doubles): [0] error flag word, [1 .. 1+ceil(n/2)) the
+// inverse permutation as int32, then one length-n work vector per concurrent
+// right-hand side.  Each call clears the flag and every work vector before
+// use, so the contents left by an earlier call do not matter; two calls that
+// overlap on the GPU (different streams, or different contexts) share the
+// array and race.
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 21;  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_prepare(const int32_t* __restrict__ perm, int32_t n, double* scratch, int64_t zlen) {
+    int32_t* iperm = reinterpret_cast<int32_t*>(scratch + 1);
+    double* z = scratch + 1 + (n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0) scratch[0] = 0.0;
+    for (int64_t k = t0; k < n; k += stride) iperm[perm[k]] = (int32_t)k;
+    for (int64_t i = t0; i < zlen; i += stride) z[i] = 0.0;
+}
+
+// One right-hand side per CTA at a time, walking the elimination-tree path of
+// its pivot supernode by supernode; the work vector is restored to zero on
+// the way (every entry it touches is a column of a later supernode of the path).
+__global__ void __launch_bounds__(256) k_diag_inv_noalloc(DevSym d, const double* __restrict__ L,
+                                                          const double* __restrict__ D,
+                                                          const int32_t* __restrict__ idx, int64_t nidx,
+                                                          double* __restrict__ out, double* scratch) {
+    __shared__ double zc_s;
+    const int32_t n = d.n;
+    const int32_t* iperm = reinterpret_cast<const int32_t*>(scratch + 1);
+    double* z = scratch + 1 + (n + 1) / 2 + (int64_t)blockIdx.x * n;
+    for (int64_t t = blockIdx.x; t < nidx; t += gridDim.x) {
+        const int32_t i = idx[t];
+        if (i < 0 || i >= n) {
+            if (threadIdx.x == 0) { scratch[0] = 1.0; out[t] = __longlong_as_double(0x7ff8000000000000LL); }
+            continue;
+        }
+        const int32_t piv = iperm[i];
+        if (threadIdx.x == 0) z[piv] = 1.0;
+        __syncthreads();
+        double var = 0.0;
+        for (int s = d.snode_of[piv]; s != -1; s = d.sparent[s]) {
+            const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+            const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+            const double* P = L + d.lptr[s];
+            const int32_t* rows = d.srows + d.srowptr[s];
+            for (int c = (piv > f ? piv - f : 0); c < k; ++c) {
+                if (threadIdx.x == 0) {
+                    zc_s = z[f + c];
+                    z[f + c] = 0.0;
+                }
+                __syncthreads();
+                const double zc = zc_s;
+                if (threadIdx.x == 0) var += zc * zc / D[f + c];
+                if (zc != 0.0)
+                    for (int64_t r = c + 1 + threadIdx.x; r < m; r += blockDim.x)
+                        z[r < k ? f + r : rows[r]] -= P[r + (int64_t)c * m] * zc;
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) out[t] = var;
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -473,6 +552,8 @@ const char* spi_strerror(int s) {
         case SPI_ERR_CUDA: return "CUDA error or no usable GPU";
         case SPI_ERR_TIMEOUT: return "bounded device wait timed out";
         case SPI_ERR_STATE: return "call out of order";
+        case SPI_ERR_SCRATCH:
+            return "order n too large for the fixed scratch of spi_diag_inverse_noalloc (n <= 1398100)";
         default: return "unknown status";
     }
 }
@@ -628,6 +709,35 @@ int spi_get_etree(const spi_ctx* c, int32_t* parent) {
     if (!c || (!parent && c->S.n)) return SPI_ERR_ARG;
     if (c->S.n) std::memcpy(parent, c->S.parent.data(), (size_t)c->S.n * sizeof(int32_t));
     return SPI_OK;
+}
+
+int spi_diag_inverse_noalloc(const spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, void* stream) {
+    if (!c || nidx < 0 || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
+    const int64_t n = c->S.n;
+    const int64_t fixed = 1 + (n + 1) / 2;
+    if (fixed + n > kNoAllocScratchDoubles) return SPI_ERR_SCRATCH;  // not even one work vector fits
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nidx == 0 || n == 0) return SPI_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return SPI_ERR_CUDA;
+    if (dev != c->device) return SPI_ERR_ARG;
+    if (!g_noalloc_ptr[dev]) {
+        // once per device, with that device current (this first call must not be inside a stream capture)
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPI_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    double* scratch = g_noalloc_ptr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t slots = std::min<int64_t>({(kNoAllocScratchDoubles - fixed) / n, nidx, 1024});
+    k_noalloc_prepare<<<256, 256, 0, st>>>(c->dsym.perm, (int32_t)n, scratch, slots * n);
+    k_diag_inv_noalloc<<<(int)slots, 256, 0, st>>>(c->dsym, c->d_L, c->d_D, idx, nidx, out, scratch);
+    if (cudaGetLastError() != cudaSuccess) return SPI_ERR_CUDA;
+    double flag = 0.0;
+    if (cudaMemcpyAsync(&flag, scratch, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SPI_ERR_CUDA;
+    return flag != 0.0 ? SPI_ERR_ARG : SPI_OK;
 }
 
 void spi_destroy(spi_ctx* c) {

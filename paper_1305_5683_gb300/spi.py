@@ -18,13 +18,13 @@ import numpy as np
 from . import build as _build
 
 SPI_OK, SPI_ERR_ARG, SPI_ERR_PATTERN, SPI_ERR_NOT_SPD, SPI_ERR_OOM, SPI_ERR_CUDA, SPI_ERR_TIMEOUT, \
-    SPI_ERR_STATE = range(8)
+    SPI_ERR_STATE, SPI_ERR_SCRATCH = range(9)
 SPI_PREC_FP64, SPI_PREC_MIXED_FP32 = 0, 1
 SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 
 EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
-           "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy"]
+           "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc"]
 
 
 class spi_options(ctypes.Structure):
@@ -85,6 +85,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_diag_inverse_batch.restype = I
     L.spi_solve.argtypes = [V, V, V, I, V]; L.spi_solve.restype = I
     L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
+    L.spi_diag_inverse_noalloc.argtypes = [V, V, I64, V, V]; L.spi_diag_inverse_noalloc.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -227,6 +228,18 @@ def spi_diag_inverse(ctx, idx, out, stream=None) -> None:
             raise TypeError("idx and out must both be host or both be device buffers")
         nidx = int(idx.numel() if _is_torch(idx) else len(k2))
     _check(lib().spi_diag_inverse(ctx, ip, nidx, op, dev, _stream(stream)), "spi_diag_inverse")
+    del k1, k2
+
+
+def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
+    """Variances for device idx into device out without any device allocation
+    by the library (fixed scratch array; see include/spi.h)."""
+    if not (_is_torch(idx) and _is_torch(out) and idx.is_cuda and out.is_cuda):
+        raise TypeError("idx and out must be CUDA tensors")
+    ip, _, k1 = _buf(idx, np.int32)
+    op, _, k2 = _buf(out, np.float64)
+    _check(lib().spi_diag_inverse_noalloc(ctx, ip, int(idx.numel()), op, _stream(stream)),
+           "spi_diag_inverse_noalloc")
     del k1, k2
 
 

@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--workload", default="scale", choices=["scale", "tiny"])
     ap.add_argument("--rhs-block", type=int, default=0, help="0 = the library's automatic choice")
     ap.add_argument("--rhs-block-mixed", type=int, default=0)
+    ap.add_argument("--relax", type=int, default=1)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--bands", type=int, default=64)
@@ -338,7 +339,7 @@ def main():
     torch.cuda.set_device(dev)
     pb, t_gen = workload(args.workload)
 
-    s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block)
+    s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax)
     info0 = s.info()
     st = torch.cuda.current_stream(dev)
     vals = torch.from_numpy(pb.values).to(dev)
@@ -387,7 +388,7 @@ def main():
     hb = torch.from_numpy(pb.b).pin_memory()
     hx = torch.empty(pb.n, dtype=torch.float64).pin_memory()
     hvar = torch.empty(pb.n, dtype=torch.float64).pin_memory()
-    s_e2e = P.Solver.for_problem(pb, rhs_block=args.rhs_block)
+    s_e2e = P.Solver.for_problem(pb, rhs_block=args.rhs_block, relax=args.relax)
     s_e2e.factor(hv); s_e2e.solve(hb, hx); s_e2e.diag_inverse(out=hvar)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -412,7 +413,8 @@ def main():
     # the mixed-precision form on the same workload and the same step
     mixed = None
     if not args.no_mixed:
-        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, precision=P.SPI_PREC_MIXED_FP32)
+        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, relax=args.relax,
+                                   precision=P.SPI_PREC_MIXED_FP32)
         xm = torch.empty_like(b)
         varm = torch.empty_like(var)
 

@@ -66,8 +66,11 @@ typedef struct spi_options {
     int rhs_block;   /* right-hand sides per block in spi_diag_inverse, 1..512 (rounded up to a
                         multiple of 8 in mixed precision); 0 = automatic: 32 in FP64, 64 in
                         mixed precision (Sec. 4.3 groups 128 right-hand sides on a CPU core) */
-    int relax;       /* supernode amalgamation: max explicit zeros per merge as a percentage
-                        of the merged panel (0 = fundamental supernodes only); default 10 */
+    int relax;       /* supernode amalgamation: max explicit zeros per parent-child merge as a
+                        percentage of the merged panel, plus merges of very small supernodes and
+                        grouping of sibling leaf fronts; 0 = fundamental supernodes only;
+                        default 1 (explicit zeros are paid again by every variance path that
+                        crosses them) */
     int refine_max;  /* max iterative-refinement steps of spi_solve in mixed precision */
     double refine_tol; /* stop refining when ||b - N x||_2 <= refine_tol * ||b||_2 */
     int async;       /* 1: do not drain the stream at the end of each call */
@@ -109,7 +112,7 @@ typedef struct spi_stats {
 typedef struct spi_ctx spi_ctx;
 
 /* Fill *opt with the defaults (FP64, nested dissection, automatic RHS block,
- * relax 10, refine_max 10, refine_tol 1e-13, synchronous, batch 1). */
+ * relax 1, refine_max 10, refine_tol 1e-13, synchronous, batch 1). */
 void spi_default_options(spi_options* opt);
 
 /* Analysis phase (Sec. 3.2.1): validate the pattern, order it (nested

@@ -611,12 +611,14 @@ void build_diag_plan(const Symbolic& S, const std::vector<int32_t>& pivots,
             }
             // executed flops: per 32-column block, the triangle, the padded update of the
             // rows below and the variance terms, for each active right-hand side
+            // (the right-hand sides whose pivot lies in this supernode join at their own block)
             double w = 0.0;
             for (int64_t cb = 0; cb < k; cb += 32) {
-                const double wc = (double)std::min<int64_t>(32, k - cb), w4 = (double)(((int64_t)wc + 3) & ~3);
-                w += wc * (wc - 1.0) + 2.0 * (double)(m - cb - (int64_t)wc) * w4 + 3.0 * wc;
+                const double wc = (double)std::min<int64_t>(32, k - cb), w4 = wc;
+                const int32_t limit = S.sfirst[s] + (int32_t)(cb + (int64_t)wc);
+                const double nbe = (double)(std::lower_bound(beg + lo, beg + hi, limit) - (beg + lo));
+                w += nbe * (wc * (wc - 1.0) + 2.0 * (double)(m - cb - (int64_t)wc) * w4 + 3.0 * wc);
             }
-            w *= (double)(hi - lo);
             P.work_flops += w;
             bwork[b] += w;
         }

@@ -181,6 +181,7 @@ int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
     CK(dev_upload(c, &d.rel, h.rel, tr));
     CK(dev_upload(c, &d.rhs_out, h.rhs_out, tr));
     CK(dev_upload(c, &d.rhs_zrow, h.rhs_zrow, tr));
+    CK(dev_upload(c, &d.rhs_col, h.rhs_col, tr));
     CK(dev_upload(c, &d.urel, h.urel, tr));
     CK(dev_upload(c, &d.zbase, h.zbase, tr));
     d.zsize = h.zbase.empty() ? 0 : h.zbase.back();
@@ -534,7 +535,7 @@ void spi_default_options(spi_options* o) {
     o->precision = SPI_PREC_FP64;
     o->ordering = SPI_ORDER_ND;
     o->rhs_block = 0;
-    o->relax = 10;
+    o->relax = 1;
     o->refine_max = 10;
     o->refine_tol = 1e-13;
     o->async = 0;

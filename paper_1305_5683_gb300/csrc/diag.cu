@@ -31,10 +31,22 @@ constexpr int kRT = 64;  // panel rows per staged tile
 
 struct DiagArgs {
     int32_t B;
-    const int32_t *order, *blk_ptr, *uptr, *us, *ulo, *uhi, *uzoff, *rel, *rhs_out, *rhs_zrow;
+    const int32_t *order, *blk_ptr, *uptr, *us, *ulo, *uhi, *uzoff, *rel, *rhs_out, *rhs_zrow, *rhs_col;
     const int64_t *urel, *zbase;
     void* Z;
 };
+
+// Right-hand sides of the active range [lo, lo + nb) whose pivot is below
+// `limit`: the range is sorted by pivot, and the ones at or past `limit` (the
+// supernode's own later pivots) are still zero for every column before it.
+__device__ __forceinline__ int reached_rhs(const int32_t* __restrict__ cols, int lo, int nb, int32_t limit) {
+    int a = 0, b = nb;
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (cols[lo + mid] < limit) a = mid + 1; else b = mid;
+    }
+    return a;
+}
 
 template <typename T>
 size_t diag_smem_bytes(int B) {
@@ -65,13 +77,14 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
     __syncthreads();
     for (int t = tid; t < nr; t += kThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = T(1);
     for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
-        const int s = p.us[u], lo = p.ulo[u], nb = p.uhi[u] - lo, zo = p.uzoff[u];
+        const int s = p.us[u], lo = p.ulo[u], nbu = p.uhi[u] - lo, zo = p.uzoff[u];
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const T* P = L + d.lptr[s];
         const int32_t* rel = p.rel + p.urel[u];
         for (int cb = 0; cb < k; cb += kT) {
             const int w = min(kT, k - cb);
+            const int nb = reached_rhs(p.rhs_col + r0b, lo, nbu, f + cb + w);
             __syncthreads();
             for (int e = tid; e < kT * kT; e += kThreads) {
                 const int i = e % kT, c = e / kT;
@@ -105,17 +118,19 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
                     Lt[i * (kT + 1) + c] = (i < nrow && c < w) ? P[(rb + i) + (int64_t)(cb + c) * m] : T(0);
                 }
                 __syncthreads();
-                const int w4 = (w + 3) & ~3;  // columns past w are zero-padded
+                const int w4 = w & ~3;
                 for (int e = tid; e < nrow * nb; e += kThreads) {
                     const int i = e / nb, t = e - i * nb;
                     const T* lr = Lt + i * (kT + 1);
                     T acc = T(0);
-                    for (int c = 0; c < w4; c += 4) {
+                    int c = 0;
+                    for (; c < w4; c += 4) {
                         acc += lr[c] * Zd[c * B + t];
                         acc += lr[c + 1] * Zd[(c + 1) * B + t];
                         acc += lr[c + 2] * Zd[(c + 2) * B + t];
                         acc += lr[c + 3] * Zd[(c + 3) * B + t];
                     }
+                    for (; c < w; ++c) acc += lr[c] * Zd[c * B + t];
                     const int64_t row = rb + i;
                     const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
                     Z[zr * B + lo + t] -= acc;
@@ -165,13 +180,14 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     __syncthreads();
     for (int t = tid; t < nr; t += kFThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = 1.f;
     for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
-        const int s = p.us[u], lo = p.ulo[u], nb = p.uhi[u] - lo, zo = p.uzoff[u];
+        const int s = p.us[u], lo = p.ulo[u], nbu = p.uhi[u] - lo, zo = p.uzoff[u];
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const float* P = L + d.lptr[s];
         const int32_t* rel = p.rel + p.urel[u];
         for (int cb = 0; cb < k; cb += kT) {
             const int w = min(kT, k - cb);
+            const int nb = reached_rhs(p.rhs_col + r0b, lo, nbu, f + cb + w);
             __syncthreads();
             for (int e = tid; e < kT * kT; e += kFThreads) {
                 const int i = e % kT, c = e / kT;
@@ -251,7 +267,7 @@ template <typename T>
 void launch_t(const DevSym& d, const DevDiagPlan& p, const T* L, const double* D, double* out, int nb,
               const Strides& bs, cudaStream_t st) {
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
-               p.urel, p.zbase, p.Z};
+               p.rhs_col, p.urel, p.zbase, p.Z};
     size_t sm = diag_smem_bytes<T>(p.B);
     k_diag_inv<T><<<dim3(p.nblocks, nb), kThreads, sm, st>>>(d, a, L, D, out, bs);
 }
@@ -276,7 +292,7 @@ void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float*
                              int nb, const Strides& bs, cudaStream_t st) {
     if (p.nblocks == 0 || nb == 0) return;
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
-               p.urel, p.zbase, p.Z};
+               p.rhs_col, p.urel, p.zbase, p.Z};
     k_diag_inv_f32<<<dim3(p.nblocks, nb), kFThreads, diag_f32_smem_bytes(p.B), st>>>(d, a, L, D, out, bs);
 }
 

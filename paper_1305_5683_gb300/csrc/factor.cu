@@ -7,9 +7,10 @@
 // (m-k) x (m-k) part (F22, present only when s has children) accumulates the
 // children's contribution blocks.  Per front:
 //   F11 = L11 D1 L11^T, L21 = F21 L11^-T D1^-1: right-looking over block
-//       columns of 32 -- the diagonal tile (one CTA, FP64), the row tiles
-//       below it (one CTA each), then the rank-32 update of the trailing
-//       panel columns (one CTA per 32 x 32 tile);
+//       columns of 32 -- the row tiles below the pivot tile (one CTA each),
+//       then the rank-32 update of the trailing panel columns (one CTA per
+//       32 x 32 tile), whose first tile is the next pivot tile: that CTA
+//       factors it (FP64) right after its update;
 //   C   = F22 - L21 D1 L21^T    (Schur complement tiles)
 // and C is added into the parent's front through the parent-relative index
 // map (the extend-add of the multifrontal method), with FP64 atomics because
@@ -39,8 +40,10 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F) {
                 int32_t s = S.level_list[p];
                 int32_t k = S.k_of(s), m = S.m_of(s);
                 if (k <= b * kT) continue;
-                F.diag_items.push_back(s);
-                ld.count++;
+                if (b == 0) {  // later pivot tiles are factored by the previous step's update
+                    F.diag_items.push_back(s);
+                    ld.count++;
+                }
                 int32_t w = std::min(kT, k - b * kT), r0 = b * kT + w;
                 for (int32_t rt = 0; r0 + rt * kT < m; ++rt) {
                     F.trsm_items.push_back(s);
@@ -97,23 +100,13 @@ __global__ void k_assemble(const int64_t* __restrict__ amap, const double* __res
 
 constexpr int kThreads = 128;
 
-// Diagonal tile of block column b (already updated by the block columns
-// before it): unblocked LDL^T in shared memory, FP64.
-__global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
-                                                        double* __restrict__ L, double* __restrict__ D,
-                                                        const double* __restrict__ adiag, DevStatus* status,
-                                                        Strides bs) {
-    L += blockIdx.y * bs.L;
-    D += blockIdx.y * bs.n;
-    adiag += blockIdx.y * bs.n;
-    __shared__ double A[kT][kT + 1];
-    __shared__ double dv[kT];
+// Unblocked LDL^T, in FP64, of the w x w pivot tile whose first pivot is
+// column c0 of supernode s (panel P, leading dimension m), by the CTA's 128
+// threads; writes L (unit lower, d on the diagonal) back into P and d into D.
+__device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, double* __restrict__ P, int64_t m, int c0,
+                                  int w, int f, double* __restrict__ D, const double* __restrict__ adiag,
+                                  DevStatus* status, int band_base) {
     const int tid = threadIdx.x;
-    const int s = items[blockIdx.x];
-    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
-    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    double* P = L + d.lptr[s];
-    const int c0 = b * kT, w = min(kT, k - c0);
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
         A[i][j] = (i < w && j <= i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
@@ -121,13 +114,10 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
     __syncthreads();
     for (int c = 0; c < w; ++c) {
         const double dc = A[c][c];
-        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
-            if (tid == 0) {
-                atomicOr(&status->flags, FLAG_NOT_SPD);
-                atomicMin(&status->bad_pivot, (int)(blockIdx.y * bs.n) + f + c0 + c);
-            }
+        if (tid == 0 && (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c])) {
+            atomicOr(&status->flags, FLAG_NOT_SPD);
+            atomicMin(&status->bad_pivot, band_base + f + c0 + c);
         }
-        __syncthreads();
         const double inv = 1.0 / dc;
         for (int e = tid; e < kT * kT; e += kThreads) {
             int i = e % kT, j = e / kT;
@@ -143,6 +133,26 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
         if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (i == j) ? dv[i] : A[i][j];
     }
     if (tid < w) D[f + c0 + tid] = dv[tid];
+}
+
+// Pivot tile of block column 0 of every supernode of a level (the pivot
+// tiles of later block columns are factored by the trailing-update CTA that
+// writes them last, k_panel_update).
+__global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
+                                                        double* __restrict__ L, double* __restrict__ D,
+                                                        const double* __restrict__ adiag, DevStatus* status,
+                                                        Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    adiag += blockIdx.y * bs.n;
+    __shared__ double A[kT][kT + 1];
+    __shared__ double dv[kT];
+    const int s = items[blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const int c0 = b * kT;
+    factor_pivot_tile(A, dv, L + d.lptr[s], m, c0, min(kT, k - c0), f, D, adiag, status,
+                      (int)(blockIdx.y * bs.n));
 }
 
 // Row tile rt below the diagonal tile of block column b (already updated by
@@ -190,10 +200,12 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
 // [c0+w, k) and rows i >= j, P[i][j] -= sum_{c in block b} L[i][c] d_c L[j][c].
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32_t* __restrict__ items, int b,
-                                                           double* __restrict__ L, const double* __restrict__ D,
+                                                           double* __restrict__ L, double* __restrict__ D,
+                                                           const double* __restrict__ adiag, DevStatus* status,
                                                            Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
+    adiag += blockIdx.y * bs.n;
     __shared__ C Li[kT][kT + 1];
     __shared__ C Lj[kT][kT + 1];
     const int tid = threadIdx.x;
@@ -213,20 +225,28 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
     }
     __syncthreads();
     const int jj = tid % kT, i0 = tid / kT;
-    if (jj >= nj) return;
-    C acc[kT / 4];
+    if (jj < nj) {
+        C acc[kT / 4];
 #pragma unroll
-    for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
+        for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
 #pragma unroll 4
-    for (int c = 0; c < kT; ++c) {
-        const C bj = Lj[jj][c];
+        for (int c = 0; c < kT; ++c) {
+            const C bj = Lj[jj][c];
 #pragma unroll
-        for (int r = 0; r < kT / 4; ++r) acc[r] += Li[i0 + 4 * r][c] * bj;
+            for (int r = 0; r < kT / 4; ++r) acc[r] += Li[i0 + 4 * r][c] * bj;
+        }
+#pragma unroll
+        for (int r = 0; r < kT / 4; ++r) {
+            const int i = i0 + 4 * r;
+            if (i < ni && ri + i >= cj + jj) P[(ri + i) + (int64_t)(cj + jj) * m] -= (double)acc[r];
+        }
     }
-#pragma unroll
-    for (int r = 0; r < kT / 4; ++r) {
-        const int i = i0 + 4 * r;
-        if (i < ni && ri + i >= cj + jj) P[(ri + i) + (int64_t)(cj + jj) * m] -= (double)acc[r];
+    if (ti == 0 && tj == 0) {
+        // this CTA wrote the last update of the next block column's pivot tile: factor it now
+        __shared__ double A[kT][kT + 1];
+        __shared__ double dv[kT];
+        __syncthreads();
+        factor_pivot_tile(A, dv, P, m, cj, nj, f, D, adiag, status, (int)(blockIdx.y * bs.n));
     }
 }
 
@@ -319,7 +339,8 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, doubl
     switch (l.kind) {
         case 0: k_diag_tile<<<g, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status, bs); break;
         case 1: k_panel_trsm<C><<<g, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D, bs); break;
-        case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, bs); break;
+        case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, adiag, status, bs);
+            break;
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
     }
 }

@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
 }
 
 // Backward, first launch of a level: y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]]
-// for the supernode's columns (one warp per column), stored into w.
+// for a chunk of 32 of the supernode's columns, stored into w.  Lanes run over
+// the rows below (coalesced column reads), each thread keeps the 32 partial
+// sums, then warps reduce by shuffles and the CTA through shared memory.
 __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* __restrict__ items,
                                                        const double* __restrict__ L, const double* __restrict__ D,
                                                        const double* __restrict__ z, const double* __restrict__ x,
@@ -88,18 +90,35 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     z += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
     w += blockIdx.y * bs.n;
+    __shared__ double part[kThreads / 32][kT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const double* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
-    const int c1 = min(k, (chunk + 1) * kBwdCols);
-    for (int c = chunk * kBwdCols + warp; c < c1; c += kThreads / 32) {
-        double acc = 0.0;
-        for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) w[f + c] = z[f + c] / D[f + c] - acc;
+    const int c0 = chunk * kT, nc = min(kT, k - c0);
+    double acc[kT];
+#pragma unroll
+    for (int c = 0; c < kT; ++c) acc[c] = 0.0;
+    for (int64_t t = k + tid; t < m; t += kThreads) {
+        const double xv = x[rows[t]];
+        const double* col = P + t + (int64_t)c0 * m;
+#pragma unroll
+        for (int c = 0; c < kT; ++c)
+            if (c < nc) acc[c] += col[(int64_t)c * m] * xv;
+    }
+#pragma unroll
+    for (int c = 0; c < kT; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == c) part[warp][c] = v;
+    }
+    __syncthreads();
+    if (tid < nc) {
+        double v = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) v += part[q][tid];
+        w[f + c0 + tid] = z[f + c0 + tid] / D[f + c0 + tid] - v;
     }
 }
 
@@ -252,7 +271,7 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P) {
         Launch li{5, 0, (int64_t)P.bwd_items.size() / 2, 0};
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
             const int32_t s = S.level_list[p], k = S.k_of(s);
-            const int32_t nch = std::max<int32_t>(1, (k + kBwdCols - 1) / kBwdCols);
+            const int32_t nch = std::max<int32_t>(1, (k + kT - 1) / kT);
             for (int32_t c = 0; c < nch; ++c) { P.bwd_items.push_back(s); P.bwd_items.push_back(c); li.count++; }
         }
         P.fwd_launches.insert(P.fwd_launches.end(), fw.begin(), fw.end());

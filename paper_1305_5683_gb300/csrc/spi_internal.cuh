@@ -80,7 +80,8 @@ struct DevDiagPlan {
     int32_t B = 0, nblocks = 0;
     int64_t nrhs = 0;
     int32_t *order = nullptr, *blk_ptr = nullptr, *uptr = nullptr, *us = nullptr, *ulo = nullptr,
-            *uhi = nullptr, *uzoff = nullptr, *rel = nullptr, *rhs_out = nullptr, *rhs_zrow = nullptr;
+            *uhi = nullptr, *uzoff = nullptr, *rel = nullptr, *rhs_out = nullptr, *rhs_zrow = nullptr,
+            *rhs_col = nullptr;
     int64_t *urel = nullptr, *zbase = nullptr;
     double* Z = nullptr;
     int64_t zsize = 0;

@@ -278,7 +278,7 @@ class Solver:
     """analyse -> factor -> solve -> diag_inverse on one pattern (owns the context)."""
 
     def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
-                 rhs_block=0, relax=10, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
+                 rhs_block=0, relax=1, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
                  _multi=None):
         o = spi_default_options()
         o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax

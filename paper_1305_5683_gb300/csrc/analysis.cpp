@@ -611,12 +611,15 @@ void build_diag_plan(const Symbolic& S, const std::vector<int32_t>& pivots,
             }
             // executed flops: per 32-column block, the triangle, the padded update of the
             // rows below and the variance terms, for each active right-hand side
-            // (the right-hand sides whose pivot lies in this supernode join at their own block)
+            // (per block column only the right-hand sides in the union of its columns' subtrees)
             double w = 0.0;
             for (int64_t cb = 0; cb < k; cb += 32) {
                 const double wc = (double)std::min<int64_t>(32, k - cb), w4 = wc;
-                const int32_t limit = S.sfirst[s] + (int32_t)(cb + (int64_t)wc);
-                const double nbe = (double)(std::lower_bound(beg + lo, beg + hi, limit) - (beg + lo));
+                const int32_t j0 = S.sfirst[s] + (int32_t)cb, j1 = j0 + (int32_t)wc - 1;
+                int32_t first = j0;
+                for (int32_t j = j0; j <= j1; ++j) first = std::min(first, S.fdesc[j]);
+                const double nbe = (double)(std::lower_bound(beg + lo, beg + hi, j1 + 1) -
+                                            std::lower_bound(beg + lo, beg + hi, first));
                 w += nbe * (wc * (wc - 1.0) + 2.0 * (double)(m - cb - (int64_t)wc) * w4 + 3.0 * wc);
             }
             P.work_flops += w;

@@ -107,7 +107,7 @@ int ensure_device(spi_ctx* c) {
     CK(cudaGetDevice(&c->device));
     const Symbolic& S = c->S;
     const size_t nb = (size_t)c->opt.batch;
-    int32_t *sfirst, *srows, *relmap, *sparent, *perm, *snode_of;
+    int32_t *sfirst, *srows, *relmap, *sparent, *perm, *snode_of, *fdesc;
     int64_t *srowptr, *lptr, *f22ptr;
     CK(dev_upload(c, &sfirst, S.sfirst));
     CK(dev_upload(c, &srowptr, S.srowptr));
@@ -118,7 +118,8 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &f22ptr, S.f22ptr));
     CK(dev_upload(c, &perm, S.perm));
     CK(dev_upload(c, &snode_of, S.snode_of));
-    c->dsym = DevSym{S.n, S.ns, sfirst, srowptr, srows, relmap, sparent, lptr, f22ptr, perm, snode_of};
+    CK(dev_upload(c, &fdesc, S.fdesc));
+    c->dsym = DevSym{S.n, S.ns, sfirst, srowptr, srows, relmap, sparent, lptr, f22ptr, perm, snode_of, fdesc};
     c->bs.L = S.lptr[S.ns];
     c->bs.F22 = S.f22_total;
     c->bs.n = S.n;

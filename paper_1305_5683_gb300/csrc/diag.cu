@@ -36,16 +36,26 @@ struct DiagArgs {
     void* Z;
 };
 
-// Right-hand sides of the active range [lo, lo + nb) whose pivot is below
-// `limit`: the range is sorted by pivot, and the ones at or past `limit` (the
-// supernode's own later pivots) are still zero for every column before it.
-__device__ __forceinline__ int reached_rhs(const int32_t* __restrict__ cols, int lo, int nb, int32_t limit) {
+// Number of entries of the sorted pivots cols[lo .. lo+nb) below `limit`.
+__device__ __forceinline__ int count_below(const int32_t* __restrict__ cols, int lo, int nb, int32_t limit) {
     int a = 0, b = nb;
     while (a < b) {
         const int mid = (a + b) >> 1;
         if (cols[lo + mid] < limit) a = mid + 1; else b = mid;
     }
     return a;
+}
+
+// The right-hand sides with a nonzero on the block columns [j0, j1] of a
+// supernode are those in the union of the columns' subtrees, i.e. with pivot
+// in [min fdesc(j0..j1), j1]; within the block's sorted active range
+// [lo, lo + nb) that is the sub-range [lo + *a, lo + *b).
+__device__ __forceinline__ void block_column_range(const DevSym& d, const int32_t* __restrict__ cols, int lo,
+                                                   int nb, int32_t j0, int32_t j1, int* a, int* b) {
+    int32_t first = j0;
+    for (int32_t j = j0; j <= j1; ++j) first = min(first, d.fdesc[j]);
+    *a = count_below(cols, lo, nb, first);
+    *b = count_below(cols, lo, nb, j1 + 1);
 }
 
 template <typename T>
@@ -67,6 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
     T* Zd = reinterpret_cast<T*>(dv + kT);  // [kT][B]
     T* Ld = Zd + kT * B;                    // [kT][kT+1]
     T* Lt = Ld + kT * (kT + 1);             // [kRT][kT+1]
+    __shared__ int rng[2];
     const int tid = threadIdx.x;
     const int b = p.order[blockIdx.x];
     T* Z = reinterpret_cast<T*>(p.Z) + blockIdx.y * bs.Z + p.zbase[b];
@@ -77,19 +88,21 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
     __syncthreads();
     for (int t = tid; t < nr; t += kThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = T(1);
     for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
-        const int s = p.us[u], lo = p.ulo[u], nbu = p.uhi[u] - lo, zo = p.uzoff[u];
+        const int s = p.us[u], lo0 = p.ulo[u], nbu = p.uhi[u] - lo0, zo = p.uzoff[u];
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const T* P = L + d.lptr[s];
         const int32_t* rel = p.rel + p.urel[u];
         for (int cb = 0; cb < k; cb += kT) {
             const int w = min(kT, k - cb);
-            const int nb = reached_rhs(p.rhs_col + r0b, lo, nbu, f + cb + w);
             __syncthreads();
+            if (tid == 0) block_column_range(d, p.rhs_col + r0b, lo0, nbu, f + cb, f + cb + w - 1, &rng[0], &rng[1]);
             for (int e = tid; e < kT * kT; e += kThreads) {
                 const int i = e % kT, c = e / kT;
                 Ld[i * (kT + 1) + c] = (i < w && c < i) ? P[(cb + i) + (int64_t)(cb + c) * m] : T(0);
             }
+            __syncthreads();
+            const int lo = lo0 + rng[0], nb = rng[1] - rng[0];
             if (tid < kT) dv[tid] = tid < w ? 1.0 / D[f + cb + tid] : 0.0;
             for (int e = tid; e < kT * nb; e += kThreads) {
                 const int c = e / nb, t = e - c * nb;
@@ -169,6 +182,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     float* Zd = reinterpret_cast<float*>(dv + kT);  // [kT][B]
     float* Ld = Zd + kT * B;                        // [kT][kT+1]
     float* Lt = Ld + kT * (kT + 1);                 // [kT][kFRows+4], transposed panel tile
+    __shared__ int rng[2];
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
     const int b = p.order[blockIdx.x];
@@ -180,19 +194,21 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     __syncthreads();
     for (int t = tid; t < nr; t += kFThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = 1.f;
     for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
-        const int s = p.us[u], lo = p.ulo[u], nbu = p.uhi[u] - lo, zo = p.uzoff[u];
+        const int s = p.us[u], lo0 = p.ulo[u], nbu = p.uhi[u] - lo0, zo = p.uzoff[u];
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const float* P = L + d.lptr[s];
         const int32_t* rel = p.rel + p.urel[u];
         for (int cb = 0; cb < k; cb += kT) {
             const int w = min(kT, k - cb);
-            const int nb = reached_rhs(p.rhs_col + r0b, lo, nbu, f + cb + w);
             __syncthreads();
+            if (tid == 0) block_column_range(d, p.rhs_col + r0b, lo0, nbu, f + cb, f + cb + w - 1, &rng[0], &rng[1]);
             for (int e = tid; e < kT * kT; e += kFThreads) {
                 const int i = e % kT, c = e / kT;
                 Ld[i * (kT + 1) + c] = (i < w && c < i) ? P[(cb + i) + (int64_t)(cb + c) * m] : 0.f;
             }
+            __syncthreads();
+            const int lo = lo0 + rng[0], nb = rng[1] - rng[0];
             if (tid < kT) dv[tid] = tid < w ? 1.0 / D[f + cb + tid] : 0.0;
             for (int e = tid; e < kT * B; e += kFThreads) {
                 const int c = e / B, t = e - c * B;

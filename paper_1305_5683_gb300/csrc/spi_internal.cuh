@@ -34,6 +34,7 @@ struct DevSym {
     const int64_t* f22ptr = nullptr;
     const int32_t* perm = nullptr;
     const int32_t* snode_of = nullptr;
+    const int32_t* fdesc = nullptr;   // first pivot of the subtree of each pivot
 };
 
 // Per-band strides of the batched (same-pattern) buffers; blockIdx.y selects

@@ -267,9 +267,10 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                         const int64_t row = rb + il;
                         const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
                         float* zrow = Z + zr * B + lo + cbase + tx * 8;
+                        // one writer per element: a reduction without return hides the load latency
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
-                            if (cbase + tx * 8 + j < nb) zrow[j] -= acc[i][j];
+                            if (cbase + tx * 8 + j < nb) atomicAdd(zrow + j, -acc[i][j]);
                     }
                 }
             }

@@ -40,7 +40,7 @@ struct spi_ctx {
     Strides bs;
     int64_t* d_amap = nullptr;
     int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
-            *d_items3 = nullptr, *d_fwd_items = nullptr, *d_bwd_items = nullptr;
+            *d_items3 = nullptr, *d_items7 = nullptr, *d_fwd_items = nullptr, *d_bwd_items = nullptr;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
@@ -130,6 +130,7 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &c->d_items1, c->FP.trsm_items));
     CK(dev_upload(c, &c->d_items2, c->FP.schur_items));
     CK(dev_upload(c, &c->d_items3, c->FP.update_items));
+    CK(dev_upload(c, &c->d_items7, c->FP.schur_tc_items));
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
@@ -159,6 +160,7 @@ int ensure_device(spi_ctx* c) {
         CK(cudaMallocHost((void**)&c->h_norm, 2 * nb * sizeof(double)));
     }
     CK(diag_kernel_setup(512));
+    CK(factor_kernel_setup());
     c->dev_ready = true;
     return SPI_OK;
 }
@@ -262,7 +264,8 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
         for (const Launch& l : c->FP.launches) {
             const int32_t* items = l.kind == 0 ? c->d_items0
                                  : l.kind == 1 ? c->d_items1
-                                 : l.kind == 2 ? c->d_items2 : c->d_items3;
+                                 : l.kind == 2 ? c->d_items2
+                                 : l.kind == 7 ? c->d_items7 : c->d_items3;
             launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, nb,
                                c->bs, s2);
         }
@@ -584,7 +587,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     int rc = analyse(n, colptr, rowind, prm, c->S, err);
     if (rc != 0) { delete c; return rc; }
     try {
-        build_factor_plan(c->S, c->FP);
+        build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32);
         build_solve_plan(c->S, c->SP);
         if (o.precision == SPI_PREC_MIXED_FP32 && n > 0) {
             c->in_colptr.assign(colptr, colptr + n + 1);

@@ -24,7 +24,13 @@
 
 namespace spi {
 
-void build_factor_plan(const Symbolic& S, FactorPlan& F) {
+// Trailing blocks at least this tall go to the tensor-core Schur kernel in
+// mixed precision.  Smaller fronts leave much of a 128 x 64 tile empty and
+// run as fast on the SIMT kernel, whose FP32 accumulation is also a little
+// more accurate than the tensor cores' (which truncate when aligning addends).
+constexpr int32_t kTcMinRows = 2048;
+
+void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
     F = FactorPlan();
     F.level_launch_ptr.push_back(0);
     for (int32_t l = 0; l < S.nlevels; ++l) {
@@ -66,10 +72,22 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F) {
             if (lu.count) F.launches.push_back(lu);
         }
         Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
+        Launch lc{7, 0, (int64_t)F.schur_tc_items.size() / 3, 0};
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
             int32_t s = S.level_list[p];
             int32_t k = S.k_of(s), m = S.m_of(s);
             if (S.sparent[s] == -1 || m <= k) continue;
+            if (tensor_cores && m - k >= kTcMinRows && k >= 32) {
+                // 128 x 64 tensor-core tiles of the lower trailing block
+                for (int32_t ti = 0; ti * 128 < m - k; ++ti)
+                    for (int32_t tj = 0; tj * 64 < m - k && tj * 64 <= ti * 128 + 127; ++tj) {
+                        F.schur_tc_items.push_back(s);
+                        F.schur_tc_items.push_back(ti);
+                        F.schur_tc_items.push_back(tj);
+                        lc.count++;
+                    }
+                continue;
+            }
             int32_t nt = (m - k + kT - 1) / kT;
             for (int32_t ti = 0; ti < nt; ++ti)
                 for (int32_t tj = 0; tj <= ti; ++tj) {
@@ -80,6 +98,7 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F) {
                 }
         }
         if (ls.count) F.launches.push_back(ls);
+        if (lc.count) F.launches.push_back(lc);
         F.level_launch_ptr.push_back((int32_t)F.launches.size());
     }
 }
@@ -311,12 +330,210 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision Schur update on the 5th-generation tensor cores.
+//
+// C = F22 - L21 D1 L21^T for a 128 x 64 output tile (rows ti, columns tj of
+// the trailing (m-k) x (m-k) part) in split precision: every FP32 operand is
+// a = a_hi + a_mid + a_lo with three TF32 pieces (33 significant bits), and
+// a b = a_hi b_hi + a_hi b_mid + a_mid b_hi + a_hi b_lo + a_lo b_hi
+// + a_mid b_mid, the dropped cross terms being below FP32 rounding, so the
+// tile is as accurate as an FP32 product.  K (the supernode's pivots) streams
+// through shared memory in chunks of 32, two stages: all 128 threads stage a
+// chunk (FP64 panel -> FP32 -> three TF32 pieces, written in the K-major
+// core-matrix layout of 8 rows x 16 bytes), one thread issues 4 k-steps x 6
+// tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) accumulating in tensor
+// memory, and tcgen05.commit
+// signals the stage's mbarrier when those MMAs have read it.  The epilogue
+// reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 =
+// tile rows) and adds C into the parent front with FP64 atomics, as the SIMT
+// kernel does.  Every mbarrier wait is bounded; on timeout the kernel raises
+// FLAG_TIMEOUT, waits (bounded) for its last commit, frees its tensor memory
+// and leaves the tile unfinished.
+constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
+constexpr int kTcStageFloats = 3 * kTcM * kTcK + 3 * kTcN * kTcK;  // A hi/mid/lo, B hi/mid/lo
+constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float) + 64;
+constexpr uint32_t kTcWaitLimit = 1u << 20;
+
+__device__ __forceinline__ int tc_kmajor_off(int r, int c) {
+    return (r >> 3) * 1024 + (c >> 2) * 128 + (r & 7) * 16 + (c & 3) * 4;
+}
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle; leading (K) byte
+// offset 128 between the two core matrices of a k-step, stride (M/N) byte
+// offset 1024 between 8-row groups.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ float tc_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(tc_smem_u32(mbar)), "r"(parity));
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __restrict__ items, double* __restrict__ L,
+                                                  double* __restrict__ F22, const double* __restrict__ D,
+                                                  DevStatus* status, Strides bs) {
+    L += blockIdx.y * bs.L;
+    F22 += blockIdx.y * bs.F22;
+    D += blockIdx.y * bs.n;
+    extern __shared__ __align__(1024) float tcs[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tcs + 2 * kTcStageFloats);  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const double* P = L + d.lptr[s];
+    const int64_t ib = k + (int64_t)ti * kTcM, jb = k + (int64_t)tj * kTcN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc_smem_u32(tmem_slot)),
+                     "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc_smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc_smem_u32(mbar + 1)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    const int nk = (k + kTcK - 1) / kTcK;
+    bool ok = true;
+    int last = -1;  // last chunk whose MMAs were committed
+    for (int kc = 0; kc < nk && ok; ++kc) {
+        const int st = kc & 1;
+        if (kc >= 2) ok = tc_wait(mbar + st, (uint32_t)((kc - 2) >> 1) & 1u);
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        float* Ah = tcs + st * kTcStageFloats;
+        float* Am = Ah + kTcM * kTcK;
+        float* Al = Am + kTcM * kTcK;
+        float* Bh = Al + kTcM * kTcK;
+        float* Bm = Bh + kTcN * kTcK;
+        float* Bl = Bm + kTcN * kTcK;
+        const int cb = kc * kTcK, cw = min(kTcK, k - cb);
+        for (int e = tid; e < kTcM * kTcK; e += 128) {
+            const int r = e % kTcM, c = e / kTcM;
+            const float a = (c < cw && ib + r < m) ? (float)P[(ib + r) + (int64_t)(cb + c) * m] : 0.f;
+            const float hi = tc_tf32(a), r1 = a - hi, mid = tc_tf32(r1);
+            const int o = tc_kmajor_off(r, c) >> 2;
+            Ah[o] = hi;
+            Am[o] = mid;
+            Al[o] = tc_tf32(r1 - mid);
+        }
+        for (int e = tid; e < kTcN * kTcK; e += 128) {
+            const int r = e % kTcN, c = e / kTcN;
+            const float b = (c < cw && jb + r < m) ? (float)(P[(jb + r) + (int64_t)(cb + c) * m] * D[f + cb + c]) : 0.f;
+            const float hi = tc_tf32(b), r1 = b - hi, mid = tc_tf32(r1);
+            const int o = tc_kmajor_off(r, c) >> 2;
+            Bh[o] = hi;
+            Bm[o] = mid;
+            Bl[o] = tc_tf32(r1 - mid);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int kk = 0; kk < kTcK / 8; ++kk) {
+                const uint32_t ko = kk * 256;
+                const uint64_t ah = tc_desc(tc_smem_u32(Ah) + ko), am = tc_desc(tc_smem_u32(Am) + ko),
+                               al = tc_desc(tc_smem_u32(Al) + ko);
+                const uint64_t bh = tc_desc(tc_smem_u32(Bh) + ko), bm = tc_desc(tc_smem_u32(Bm) + ko),
+                               bl = tc_desc(tc_smem_u32(Bl) + ko);
+                // small terms first
+                tc_mma(tmem, am, bm, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(tmem, al, bh, idesc, 1u);
+                tc_mma(tmem, ah, bl, idesc, 1u);
+                tc_mma(tmem, am, bh, idesc, 1u);
+                tc_mma(tmem, ah, bm, idesc, 1u);
+                tc_mma(tmem, ah, bh, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(tc_smem_u32(mbar + st)));
+        }
+        last = kc;
+    }
+    // the last commit covers every MMA issued before it
+    bool fin = last >= 0 ? tc_wait(mbar + (last & 1), (uint32_t)(last >> 1) & 1u) : true;
+    fin = !__syncthreads_or(!fin) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!fin) {
+        if (tid == 0) atomicOr(&status->flags, FLAG_TIMEOUT);
+    } else {
+        const int64_t fo = d.f22ptr[s];
+        const int64_t mb = m - k;
+        const int p = d.sparent[s];
+        const int kp = d.sfirst[p + 1] - d.sfirst[p];
+        const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
+        double* Pp = L + d.lptr[p];
+        double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+        const int32_t* rel = d.relmap + d.srowptr[s];
+        const int64_t il = ib + warp * 32 + lane;
+        const int qi = il < m ? rel[il] : 0;
+        for (int half = 0; half < 2; ++half) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + half * 32;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (il < m) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t jl = jb + half * 32 + j;
+                    if (jl >= m || jl > il) continue;
+                    double v = -(double)__uint_as_float(r[j]);
+                    if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
+                    const int qj = rel[jl];
+                    if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
+                    else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN));
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
 
 }  // namespace
+
+cudaError_t factor_kernel_setup() {
+    return cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+}
 
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
     if (n == 0) return;
@@ -341,6 +558,7 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, doubl
         case 1: k_panel_trsm<C><<<g, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D, bs); break;
         case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, adiag, status, bs);
             break;
+        case 7: k_schur_tc<<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, L, F22, D, status, bs); break;
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
     }
 }

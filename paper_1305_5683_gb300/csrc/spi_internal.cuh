@@ -50,7 +50,8 @@ struct Strides {
 
 // A flattened work list of one kernel launch.
 struct Launch {
-    int kind;        // 0 diag tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update
+    int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
+                     // 7 tensor-core Schur+scatter (mixed precision)
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs
@@ -61,11 +62,13 @@ struct FactorPlan {
     std::vector<int32_t> trsm_items;  // pairs (supernode, row tile)
     std::vector<int32_t> schur_items; // triples (supernode, ti, tj)
     std::vector<int32_t> update_items;// triples (supernode, ti, tj) of the trailing panel
+    std::vector<int32_t> schur_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
 };
 
-void build_factor_plan(const Symbolic& S, FactorPlan& F);
+void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores);
+cudaError_t factor_kernel_setup();
 
 struct SolvePlan {
     std::vector<int32_t> fwd_items;  // pairs (supernode, row chunk)

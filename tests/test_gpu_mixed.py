@@ -78,3 +78,38 @@ def test_mixed_device_buffers_and_alias(P):
     torch.cuda.synchronize()
     x_ref = f.solve(pb.b)
     assert np.abs(xb.cpu().numpy() - x_ref).max() <= X_TOL * np.abs(x_ref).max()
+
+
+def arrowhead(n_leaf=400, n_tail=2100, seed=0):
+    """SPD arrowhead: independent leading columns, each coupled to every column
+    of a dense tail, so the grouped leaf fronts have k = 32 pivots and
+    n_tail rows below them (wide Schur updates)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    n = n_leaf + n_tail
+    A = np.zeros((n, n))
+    A[:n_leaf, :n_leaf] = np.diag(rng.uniform(400.0, 600.0, n_leaf))
+    C = rng.uniform(-0.5, 0.5, (n_tail, n_leaf))
+    A[n_leaf:, :n_leaf] = C
+    A[:n_leaf, n_leaf:] = C.T
+    R = rng.uniform(-1.0, 1.0, (n_tail, n_tail))
+    A[n_leaf:, n_leaf:] = R @ R.T / n_tail + 5.0 * np.eye(n_tail)
+    low = sp.tril(sp.csc_matrix(A)).tocsc()
+    low.sort_indices()
+    return n, low.indptr.astype(np.int64), low.indices.astype(np.int32), low.data, rng.standard_normal(n)
+
+
+def test_tensor_core_schur_fronts(P):
+    """Fronts with >= 2048 rows below their pivots take the tcgen05 Schur path
+    in the mixed form; the result must match the oracle like the SIMT path."""
+    n, cp, ri, va, b = arrowhead()
+    f = oracle.OracleFactor(n, cp, ri, va)
+    x_ref, v_ref = f.solve(b), f.inv_diag()
+    s = P.Solver(n, cp, ri, precision=P.SPI_PREC_MIXED_FP32, ordering=P.SPI_ORDER_NATURAL)
+    s.factor(va)
+    x = s.solve(b)
+    v = s.diag_inverse()
+    ex = np.abs(x - x_ref).max() / np.abs(x_ref).max()
+    ev = (np.abs(v - v_ref) / v_ref).max()
+    print(f"tensor-core fronts: x_err={ex:.2e} var_err={ev:.2e}")
+    assert ex <= X_TOL and ev <= MIXED_VAR_TOL

@@ -77,6 +77,12 @@ typedef struct spi_options {
     int nd_leaf;     /* nested-dissection leaf size (vertices); 0 = default */
     int batch;       /* maximum number of same-pattern bands of the *_batch calls (device memory
                         is sized for it at the first factorization); 0 or 1 = single problem */
+    int wait_limit;  /* polls allowed to each bounded pipeline wait of the tensor-core Schur
+                        kernel (mixed form): 0 = default (2^20), > 0 = that many, < 0 = none,
+                        so every such wait gives up at once and spi_factor returns
+                        SPI_ERR_TIMEOUT (a test of that path).  After giving up, the kernel
+                        still waits, with the default limit, for its own MMAs in flight
+                        before it frees its tensor memory */
 } spi_options;
 
 typedef struct spi_stats {

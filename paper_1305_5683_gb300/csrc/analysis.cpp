@@ -446,6 +446,23 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
             part.swap(grouped);
         }
         S.sfirst = part;
+        // a front whose columns are all childless and have no entry between them has a
+        // diagonal pivot block (grouped sibling leaves)
+        {
+            const int32_t np2 = (int32_t)S.sfirst.size() - 1;
+            S.sdiag.assign(np2, 0);
+            for (int32_t s2 = 0; s2 < np2; ++s2) {
+                const int32_t f = S.sfirst[s2], l = S.sfirst[s2 + 1] - 1;
+                if (l == f) continue;
+                bool diag = true;
+                for (int32_t j = f; j <= l && diag; ++j) {
+                    if (ncc[j] != 0) diag = false;
+                    for (int64_t p = ccp[j]; p < ccp[j + 1] && diag; ++p)
+                        if (crow[p] > j && crow[p] <= l) diag = false;
+                }
+                S.sdiag[s2] = diag ? 1 : 0;
+            }
+        }
         S.ns = (int32_t)S.sfirst.size() - 1;
         const int32_t ns = S.ns;
         S.snode_of.resize(n);

@@ -36,6 +36,7 @@ struct Symbolic {
     std::vector<int64_t> f22ptr;    // [ns] offset of the (m-k)^2 update area, -1 if no child
     int64_t f22_total = 0;
     std::vector<int32_t> nchild;    // children per supernode
+    std::vector<uint8_t> sdiag;     // 1: the pivot block is diagonal (a group of independent leaf columns)
     std::vector<int32_t> level;     // height of each supernode (leaves 0)
     std::vector<int32_t> level_ptr; // [nlevels+1]
     std::vector<int32_t> level_list;// supernodes by level

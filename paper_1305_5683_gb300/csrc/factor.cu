@@ -38,6 +38,13 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p)
             kmax = std::max(kmax, S.k_of(S.level_list[p]));
         int32_t nsteps = (kmax + kT - 1) / kT;
+        // fronts with a diagonal pivot block (grouped independent leaves): no block steps
+        Launch lg{8, 0, (int64_t)F.dfront_items.size(), 0};
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p];
+            if (S.sdiag[s]) { F.dfront_items.push_back(s); lg.count++; }
+        }
+        if (lg.count) F.launches.push_back(lg);
         for (int32_t b = 0; b < nsteps; ++b) {
             Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
             Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
@@ -45,7 +52,7 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
             for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
                 int32_t s = S.level_list[p];
                 int32_t k = S.k_of(s), m = S.m_of(s);
-                if (k <= b * kT) continue;
+                if (k <= b * kT || S.sdiag[s]) continue;
                 if (b == 0) {  // later pivot tiles are factored by the previous step's update
                     F.diag_items.push_back(s);
                     ld.count++;
@@ -172,6 +179,36 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
     const int c0 = b * kT;
     factor_pivot_tile(A, dv, L + d.lptr[s], m, c0, min(kT, k - c0), f, D, adiag, status,
                       (int)(blockIdx.y * bs.n));
+}
+
+// Front with a diagonal pivot block (independent leaf columns grouped into
+// one front): d_c is the assembled diagonal entry and L21(:, c) = F21(:, c) / d_c.
+__global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t* __restrict__ items,
+                                                         double* __restrict__ L, double* __restrict__ D,
+                                                         const double* __restrict__ adiag, DevStatus* status,
+                                                         Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    adiag += blockIdx.y * bs.n;
+    const int tid = threadIdx.x;
+    const int s = items[blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    double* P = L + d.lptr[s];
+    for (int c = tid; c < k; c += kThreads) {
+        const double dc = P[c + (int64_t)c * m];
+        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c]) {
+            atomicOr(&status->flags, FLAG_NOT_SPD);
+            atomicMin(&status->bad_pivot, (int)(blockIdx.y * bs.n) + f + c);
+        }
+        D[f + c] = dc;
+    }
+    const int64_t mb = m - k;
+    for (int64_t e = tid; e < (int64_t)k * mb; e += kThreads) {
+        const int c = (int)(e / mb);
+        const int64_t r = k + (e - (int64_t)c * mb);
+        P[r + (int64_t)c * m] /= P[c + (int64_t)c * m];
+    }
 }
 
 // Row tile rt below the diagonal tile of block column b (already updated by
@@ -381,9 +418,9 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
                  :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kTcWaitLimit) {
     uint32_t done = 0;
-    for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+    for (uint32_t it = 0; it < limit && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(tc_smem_u32(mbar)), "r"(parity));
     return done != 0;
@@ -391,7 +428,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
 
 __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __restrict__ items, double* __restrict__ L,
                                                   double* __restrict__ F22, const double* __restrict__ D,
-                                                  DevStatus* status, Strides bs) {
+                                                  DevStatus* status, Strides bs, uint32_t stage_wait_limit) {
     L += blockIdx.y * bs.L;
     F22 += blockIdx.y * bs.F22;
     D += blockIdx.y * bs.n;
@@ -425,7 +462,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     int last = -1;  // last chunk whose MMAs were committed
     for (int kc = 0; kc < nk && ok; ++kc) {
         const int st = kc & 1;
-        if (kc >= 2) ok = tc_wait(mbar + st, (uint32_t)((kc - 2) >> 1) & 1u);
+        if (kc >= 2) ok = tc_wait(mbar + st, (uint32_t)((kc - 2) >> 1) & 1u, stage_wait_limit);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         float* Ah = tcs + st * kTcStageFloats;
         float* Am = Ah + kTcM * kTcK;
@@ -477,8 +514,9 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         last = kc;
     }
     // the last commit covers every MMA issued before it
-    bool fin = last >= 0 ? tc_wait(mbar + (last & 1), (uint32_t)(last >> 1) & 1u) : true;
+    bool fin = last >= 0 ? tc_wait(mbar + (last & 1), (uint32_t)(last >> 1) & 1u, stage_wait_limit) : true;
     fin = !__syncthreads_or(!fin) && ok;
+    if (!fin && last >= 0) tc_wait(mbar + (last & 1), (uint32_t)(last >> 1) & 1u);  // drain before release
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!fin) {
         if (tid == 0) atomicOr(&status->flags, FLAG_TIMEOUT);
@@ -551,24 +589,30 @@ void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, i
 
 template <typename C>
 void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22, double* D,
-                   const double* adiag, DevStatus* status, int nb, const Strides& bs, cudaStream_t st) {
+                   const double* adiag, DevStatus* status, int nb, const Strides& bs, int wait_limit,
+                   cudaStream_t st) {
     const dim3 g(l.count, nb);
     switch (l.kind) {
         case 0: k_diag_tile<<<g, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status, bs); break;
         case 1: k_panel_trsm<C><<<g, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D, bs); break;
         case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, adiag, status, bs);
             break;
-        case 7: k_schur_tc<<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, L, F22, D, status, bs); break;
+        case 7:
+            k_schur_tc<<<g, 128, kTcSmem, st>>>(
+                d, items + 3 * l.off, L, F22, D, status, bs,
+                wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kTcWaitLimit);
+            break;
+        case 8: k_diag_front<<<g, kThreads, 0, st>>>(d, items + l.off, L, D, adiag, status, bs); break;
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
     }
 }
 
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
                         double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
-                        const Strides& bs, cudaStream_t st) {
+                        const Strides& bs, int wait_limit, cudaStream_t st) {
     if (l.count == 0 || nb == 0) return;
-    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, nb, bs, st);
-    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, nb, bs, st);
+    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, nb, bs, wait_limit, st);
+    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, nb, bs, wait_limit, st);
 }
 
 }  // namespace spi

@@ -51,7 +51,7 @@ struct Strides {
 // A flattened work list of one kernel launch.
 struct Launch {
     int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
-                     // 7 tensor-core Schur+scatter (mixed precision)
+                     // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs
@@ -63,6 +63,7 @@ struct FactorPlan {
     std::vector<int32_t> schur_items; // triples (supernode, ti, tj)
     std::vector<int32_t> update_items;// triples (supernode, ti, tj) of the trailing panel
     std::vector<int32_t> schur_tc_items; // triples (supernode, 128-row tile, 64-column tile)
+    std::vector<int32_t> dfront_items;   // supernodes with a diagonal pivot block
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
 };
@@ -98,7 +99,7 @@ void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, i
                      const int32_t* diag_src, double* adiag, int nb, const Strides& bs, cudaStream_t st);
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
                         double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
-                        const Strides& bs, cudaStream_t st);
+                        const Strides& bs, int wait_limit, cudaStream_t st);
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);

@@ -113,3 +113,28 @@ def test_tensor_core_schur_fronts(P):
     ev = (np.abs(v - v_ref) / v_ref).max()
     print(f"tensor-core fronts: x_err={ex:.2e} var_err={ev:.2e}")
     assert ex <= X_TOL and ev <= MIXED_VAR_TOL
+
+
+def test_bounded_wait_timeout_reported(P):
+    """wait_limit < 0 makes every bounded pipeline wait of the tcgen05 Schur
+    kernel give up at once.  The kernel then drains its own MMAs, frees its
+    tensor memory and raises the timeout flag: spi_factor returns
+    SPI_ERR_TIMEOUT, the context refuses to solve, and the device stays usable
+    (a fresh context on it factors the same matrix to the oracle's result).
+    No wait is left unbounded and nothing faults."""
+    n, cp, ri, va, b = arrowhead()
+    s = P.Solver(n, cp, ri, precision=P.SPI_PREC_MIXED_FP32, ordering=P.SPI_ORDER_NATURAL, wait_limit=-1)
+    with pytest.raises(P.SpiError) as e:
+        s.factor(va)
+    assert e.value.code == 6
+    with pytest.raises(P.SpiError) as e:
+        s.solve(b)
+    assert e.value.code == 7
+    # the FP64 form has no tensor-core waits: the same option leaves it untouched
+    s64 = P.Solver(n, cp, ri, ordering=P.SPI_ORDER_NATURAL, wait_limit=-1)
+    s64.factor(va)
+    x_ref = oracle.OracleFactor(n, cp, ri, va).solve(b)
+    assert np.abs(s64.solve(b) - x_ref).max() <= 1e-10 * np.abs(x_ref).max()
+    ok = P.Solver(n, cp, ri, precision=P.SPI_PREC_MIXED_FP32, ordering=P.SPI_ORDER_NATURAL)
+    ok.factor(va)
+    assert np.abs(ok.solve(b) - x_ref).max() <= X_TOL * np.abs(x_ref).max()

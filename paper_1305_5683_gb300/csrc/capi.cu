@@ -40,7 +40,7 @@ struct spi_ctx {
     Strides bs;
     int64_t* d_amap = nullptr;
     int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
-            *d_items3 = nullptr, *d_items7 = nullptr, *d_items8 = nullptr, *d_fwd_items = nullptr,
+            *d_items3 = nullptr, *d_items7 = nullptr, *d_items8 = nullptr, *d_items9 = nullptr, *d_fwd_items = nullptr,
             *d_bwd_items = nullptr;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
@@ -133,6 +133,7 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &c->d_items3, c->FP.update_items));
     CK(dev_upload(c, &c->d_items7, c->FP.schur_tc_items));
     CK(dev_upload(c, &c->d_items8, c->FP.dfront_items));
+    CK(dev_upload(c, &c->d_items9, c->FP.panel_tc_items));
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
@@ -271,7 +272,8 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
                                  : l.kind == 1 ? c->d_items1
                                  : l.kind == 2 ? c->d_items2
                                  : l.kind == 7 ? c->d_items7
-                                 : l.kind == 8 ? c->d_items8 : c->d_items3;
+                                 : l.kind == 8 ? c->d_items8
+                                 : l.kind == 9 ? c->d_items9 : c->d_items3;
             launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, nb,
                                c->bs, c->opt.wait_limit, s2);
         }

@@ -25,10 +25,20 @@
 namespace spi {
 
 // Trailing blocks at least this tall go to the tensor-core Schur kernel in
-// mixed precision.  Smaller fronts leave much of a 128 x 64 tile empty and
+// mixed precision.  Smaller fronts leave much of a 128 x 128 tile empty and
 // run as fast on the SIMT kernel, whose FP32 accumulation is also a little
 // more accurate than the tensor cores' (which truncate when aligning addends).
 constexpr int32_t kTcMinRows = 2048;
+// Wide fronts (mixed precision, more than kOuter pivots, at least kTcMinRows
+// rows) are blocked twice: the 32-column steps update only the columns of
+// their own kOuter-column block, and after every kOuter columns one
+// tensor-core launch applies the rank-kOuter update to all remaining panel
+// columns (kind 9); the next pivot tile is then factored by a kind-0 launch.
+constexpr int32_t kOuter = 128;
+constexpr int32_t kInner = kOuter / kT;
+// tensor-core output tile (rows x columns) and K chunk; one thread per tile row
+constexpr int kTcM = 128, kTcN = 128, kTcK = 32;
+static_assert(kTcM == 128 && kTcN == 128, "the tensor-core kernels give thread t row t of both operand tiles");
 
 void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
     F = FactorPlan();
@@ -49,11 +59,15 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
             Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
             Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
             Launch lu{3, b, (int64_t)F.update_items.size() / 3, 0};
+            Launch lw{9, b, (int64_t)F.panel_tc_items.size() / 3, 0};
             for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
                 int32_t s = S.level_list[p];
                 int32_t k = S.k_of(s), m = S.m_of(s);
                 if (k <= b * kT || S.sdiag[s]) continue;
-                if (b == 0) {  // later pivot tiles are factored by the previous step's update
+                const bool wide = tensor_cores && k > kOuter && m >= kTcMinRows;
+                // pivot tiles are factored by the previous step's update, except the
+                // first one and, in wide fronts, the first of every outer block
+                if (b == 0 || (wide && b % kInner == 0)) {
                     F.diag_items.push_back(s);
                     ld.count++;
                 }
@@ -63,8 +77,9 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
                     F.trsm_items.push_back(rt);
                     lt.count++;
                 }
-                // trailing panel columns [r0, k): lower tiles of rows [cj, m)
-                for (int32_t tj = 0; r0 + tj * kT < k; ++tj) {
+                // trailing panel columns [r0, kend): lower tiles of rows [cj, m)
+                const int32_t kend = wide ? std::min(k, kOuter * (b / kInner + 1)) : k;
+                for (int32_t tj = 0; r0 + tj * kT < kend; ++tj) {
                     int32_t cj = r0 + tj * kT;
                     for (int32_t ti = 0; cj + ti * kT < m; ++ti) {
                         F.update_items.push_back(s);
@@ -73,10 +88,21 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
                         lu.count++;
                     }
                 }
+                // end of an outer block: rank-kOuter update of panel columns [r0, k)
+                if (wide && r0 == kend && r0 < k) {
+                    for (int32_t ti = 0; r0 + ti * kTcM < m; ++ti)
+                        for (int32_t tj = 0; r0 + tj * kTcN < k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
+                            F.panel_tc_items.push_back(s);
+                            F.panel_tc_items.push_back(ti);
+                            F.panel_tc_items.push_back(tj);
+                            lw.count++;
+                        }
+                }
             }
             if (ld.count) F.launches.push_back(ld);
             if (lt.count) F.launches.push_back(lt);
             if (lu.count) F.launches.push_back(lu);
+            if (lw.count) F.launches.push_back(lw);
         }
         Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
         Launch lc{7, 0, (int64_t)F.schur_tc_items.size() / 3, 0};
@@ -85,9 +111,9 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
             int32_t k = S.k_of(s), m = S.m_of(s);
             if (S.sparent[s] == -1 || m <= k) continue;
             if (tensor_cores && m - k >= kTcMinRows && k >= 32) {
-                // 128 x 64 tensor-core tiles of the lower trailing block
-                for (int32_t ti = 0; ti * 128 < m - k; ++ti)
-                    for (int32_t tj = 0; tj * 64 < m - k && tj * 64 <= ti * 128 + 127; ++tj) {
+                // kTcM x kTcN tensor-core tiles of the lower trailing block
+                for (int32_t ti = 0; ti * kTcM < m - k; ++ti)
+                    for (int32_t tj = 0; tj * kTcN < m - k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
                         F.schur_tc_items.push_back(s);
                         F.schur_tc_items.push_back(ti);
                         F.schur_tc_items.push_back(tj);
@@ -370,16 +396,18 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
 // ---------------------------------------------------------------------------
 // Mixed-precision Schur update on the 5th-generation tensor cores.
 //
-// C = F22 - L21 D1 L21^T for a 128 x 64 output tile (rows ti, columns tj of
+// C = F22 - L21 D1 L21^T for a 128 x 128 output tile (rows ti, columns tj of
 // the trailing (m-k) x (m-k) part) in split precision: every FP32 operand is
 // a = a_hi + a_mid + a_lo with three TF32 pieces (33 significant bits), and
 // a b = a_hi b_hi + a_hi b_mid + a_mid b_hi + a_hi b_lo + a_lo b_hi
 // + a_mid b_mid, the dropped cross terms being below FP32 rounding, so the
 // tile is as accurate as an FP32 product.  K (the supernode's pivots) streams
-// through shared memory in chunks of 32, two stages: all 128 threads stage a
-// chunk (FP64 panel -> FP32 -> three TF32 pieces, written in the K-major
-// core-matrix layout of 8 rows x 16 bytes), one thread issues 4 k-steps x 6
-// tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) accumulating in tensor
+// through shared memory in chunks of 32, two stages: thread t holds row t of
+// both operands; it loads the next chunk's FP64 values into registers while
+// the tensor cores work on the current one, then writes them to the free
+// stage as three TF32 pieces (16-byte stores into the K-major core-matrix
+// layout of 8 rows x 16 bytes); one thread issues 4 k-steps x 6
+// tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8) accumulating in tensor
 // memory, and tcgen05.commit
 // signals the stage's mbarrier when those MMAs have read it.  The epilogue
 // reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 =
@@ -387,7 +415,6 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
 // kernel does.  Every mbarrier wait is bounded; on timeout the kernel raises
 // FLAG_TIMEOUT, waits (bounded) for its last commit, frees its tensor memory
 // and leaves the tile unfinished.
-constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
 constexpr int kTcStageFloats = 3 * kTcM * kTcK + 3 * kTcN * kTcK;  // A hi/mid/lo, B hi/mid/lo
 constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float) + 64;
 constexpr uint32_t kTcWaitLimit = 1u << 20;
@@ -418,6 +445,27 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
                  :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// a = hi + mid + lo, three TF32 values (the split of the split-precision products)
+__device__ __forceinline__ void tc_split3(float a, float& hi, float& mid, float& lo) {
+    hi = tc_tf32(a);
+    const float r1 = a - hi;
+    mid = tc_tf32(r1);
+    lo = tc_tf32(r1 - mid);
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
 __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kTcWaitLimit) {
     uint32_t done = 0;
     for (uint32_t it = 0; it < limit && !done; ++it)
@@ -426,9 +474,16 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, uint32_
     return done != 0;
 }
 
-__global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __restrict__ items, double* __restrict__ L,
-                                                  double* __restrict__ F22, const double* __restrict__ D,
-                                                  DevStatus* status, Strides bs, uint32_t stage_wait_limit) {
+//
+// kMode 1 is the same product as the rank-kOuter trailing update of a wide
+// front: K = the kOuter columns [c1 - kOuter, c1) that end at block step
+// `step` (c1 = (step + 1) * 32), output rows [c1, m) x panel columns [c1, k),
+// subtracted in place from the panel (one CTA owns each tile: no atomics).
+template <int kMode>
+__global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __restrict__ items, int step,
+                                                  double* __restrict__ L, double* __restrict__ F22,
+                                                  const double* __restrict__ D, DevStatus* status, Strides bs,
+                                                  uint32_t stage_wait_limit) {
     L += blockIdx.y * bs.L;
     F22 += blockIdx.y * bs.F22;
     D += blockIdx.y * bs.n;
@@ -439,8 +494,12 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
-    const int64_t ib = k + (int64_t)ti * kTcM, jb = k + (int64_t)tj * kTcN;
+    double* P = L + d.lptr[s];
+    // K range [kb0, kb1); output rows from ib, columns from jb below jlim
+    const int c1 = (step + 1) * kT;
+    const int kb0 = kMode == 0 ? 0 : c1 - kOuter, kb1 = kMode == 0 ? k : c1;
+    const int64_t ib = (kMode == 0 ? k : c1) + (int64_t)ti * kTcM, jb = (kMode == 0 ? k : c1) + (int64_t)tj * kTcN;
+    const int64_t jlim = kMode == 0 ? m : k;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc_smem_u32(tmem_slot)),
                      "r"(kTcN));
@@ -457,7 +516,21 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                            ((uint32_t)(kTcM >> 4) << 24);
-    const int nk = (k + kTcK - 1) / kTcK;
+    const int nk = (kb1 - kb0 + kTcK - 1) / kTcK;
+    // row tid of A (rows from ib) and of B (rows from jb, scaled by D) for one K chunk
+    double ra[kTcK], rb[kTcK];
+    auto fetch = [&](int kc) {
+        const int cb = kb0 + kc * kTcK, cw = min(kTcK, kb1 - cb);
+        const bool rowa = ib + tid < m, rowb = jb + tid < jlim;
+        const double* pa = P + (ib + tid) + (int64_t)cb * m;
+        const double* pb = P + (jb + tid) + (int64_t)cb * m;
+#pragma unroll
+        for (int c = 0; c < kTcK; ++c) {
+            ra[c] = (c < cw && rowa) ? pa[(int64_t)c * m] : 0.0;
+            rb[c] = (c < cw && rowb) ? pb[(int64_t)c * m] * D[f + cb + c] : 0.0;
+        }
+    };
+    if (nk > 0) fetch(0);
     bool ok = true;
     int last = -1;  // last chunk whose MMAs were committed
     for (int kc = 0; kc < nk && ok; ++kc) {
@@ -470,28 +543,29 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         float* Bh = Al + kTcM * kTcK;
         float* Bm = Bh + kTcN * kTcK;
         float* Bl = Bm + kTcN * kTcK;
-        const int cb = kc * kTcK, cw = min(kTcK, k - cb);
-        for (int e = tid; e < kTcM * kTcK; e += 128) {
-            const int r = e % kTcM, c = e / kTcM;
-            const float a = (c < cw && ib + r < m) ? (float)P[(ib + r) + (int64_t)(cb + c) * m] : 0.f;
-            const float hi = tc_tf32(a), r1 = a - hi, mid = tc_tf32(r1);
-            const int o = tc_kmajor_off(r, c) >> 2;
-            Ah[o] = hi;
-            Am[o] = mid;
-            Al[o] = tc_tf32(r1 - mid);
-        }
-        for (int e = tid; e < kTcN * kTcK; e += 128) {
-            const int r = e % kTcN, c = e / kTcN;
-            const float b = (c < cw && jb + r < m) ? (float)(P[(jb + r) + (int64_t)(cb + c) * m] * D[f + cb + c]) : 0.f;
-            const float hi = tc_tf32(b), r1 = b - hi, mid = tc_tf32(r1);
-            const int o = tc_kmajor_off(r, c) >> 2;
-            Bh[o] = hi;
-            Bm[o] = mid;
-            Bl[o] = tc_tf32(r1 - mid);
+#pragma unroll
+        for (int c4 = 0; c4 < kTcK / 4; ++c4) {
+            const int o = tc_kmajor_off(tid, 4 * c4) >> 2;
+            float4 h, mi, lo;
+            tc_split3((float)ra[4 * c4 + 0], h.x, mi.x, lo.x);
+            tc_split3((float)ra[4 * c4 + 1], h.y, mi.y, lo.y);
+            tc_split3((float)ra[4 * c4 + 2], h.z, mi.z, lo.z);
+            tc_split3((float)ra[4 * c4 + 3], h.w, mi.w, lo.w);
+            *reinterpret_cast<float4*>(Ah + o) = h;
+            *reinterpret_cast<float4*>(Am + o) = mi;
+            *reinterpret_cast<float4*>(Al + o) = lo;
+            tc_split3((float)rb[4 * c4 + 0], h.x, mi.x, lo.x);
+            tc_split3((float)rb[4 * c4 + 1], h.y, mi.y, lo.y);
+            tc_split3((float)rb[4 * c4 + 2], h.z, mi.z, lo.z);
+            tc_split3((float)rb[4 * c4 + 3], h.w, mi.w, lo.w);
+            *reinterpret_cast<float4*>(Bh + o) = h;
+            *reinterpret_cast<float4*>(Bm + o) = mi;
+            *reinterpret_cast<float4*>(Bl + o) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        if (kc + 1 < nk) fetch(kc + 1);  // in flight while the MMAs below run
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             for (int kk = 0; kk < kTcK / 8; ++kk) {
@@ -520,6 +594,19 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!fin) {
         if (tid == 0) atomicOr(&status->flags, FLAG_TIMEOUT);
+    } else if (kMode == 1) {
+        const int64_t il = ib + warp * 32 + lane;
+        for (int q = 0; q < kTcN / 32; ++q) {
+            uint32_t r[32];
+            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
+            if (il < m) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t jl = jb + q * 32 + j;
+                    if (jl < k && jl <= il) P[il + jl * m] -= (double)__uint_as_float(r[j]);
+                }
+            }
+        }
     } else {
         const int64_t fo = d.f22ptr[s];
         const int64_t mb = m - k;
@@ -531,22 +618,13 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         const int32_t* rel = d.relmap + d.srowptr[s];
         const int64_t il = ib + warp * 32 + lane;
         const int qi = il < m ? rel[il] : 0;
-        for (int half = 0; half < 2; ++half) {
+        for (int q = 0; q < kTcN / 32; ++q) {
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + half * 32;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
             if (il < m) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int64_t jl = jb + half * 32 + j;
+                    const int64_t jl = jb + q * 32 + j;
                     if (jl >= m || jl > il) continue;
                     double v = -(double)__uint_as_float(r[j]);
                     if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
@@ -570,7 +648,9 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 }  // namespace
 
 cudaError_t factor_kernel_setup() {
-    return cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_schur_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_schur_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
 }
 
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
@@ -598,10 +678,12 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, doubl
         case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, adiag, status, bs);
             break;
         case 7:
-            k_schur_tc<<<g, 128, kTcSmem, st>>>(
-                d, items + 3 * l.off, L, F22, D, status, bs,
-                wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kTcWaitLimit);
+        case 9: {
+            const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kTcWaitLimit;
+            if (l.kind == 7) k_schur_tc<0><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, 0, L, F22, D, status, bs, lim);
+            else k_schur_tc<1><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, l.step, L, F22, D, status, bs, lim);
             break;
+        }
         case 8: k_diag_front<<<g, kThreads, 0, st>>>(d, items + l.off, L, D, adiag, status, bs); break;
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
     }

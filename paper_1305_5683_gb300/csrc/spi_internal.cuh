@@ -51,7 +51,8 @@ struct Strides {
 // A flattened work list of one kernel launch.
 struct Launch {
     int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
-                     // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front
+                     // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front,
+                     // 9 tensor-core trailing panel update of a wide front (mixed precision)
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs
@@ -64,6 +65,7 @@ struct FactorPlan {
     std::vector<int32_t> update_items;// triples (supernode, ti, tj) of the trailing panel
     std::vector<int32_t> schur_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<int32_t> dfront_items;   // supernodes with a diagonal pivot block
+    std::vector<int32_t> panel_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
 };

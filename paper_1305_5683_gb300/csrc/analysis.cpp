@@ -18,6 +18,7 @@
 #include "analysis.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 
@@ -51,13 +52,16 @@ struct ND {
     const std::vector<int32_t>& adj;
     int leaf;
     std::vector<char> is_elem;
+    // interval of each non-element vertex: smallest and largest rank (position
+    // in index order) of the elements adjacent to it; INT32_MAX / -1 if none
+    std::vector<int32_t> elo, ehi;
     std::vector<int32_t> stamp, visit, estamp, lev, done;
     int32_t cur_set = 0, cur_bfs = 0, cur_done = 0;
     std::vector<int32_t> out;
 
     ND(int32_t n_, const std::vector<int64_t>& x, const std::vector<int32_t>& a, int leaf_)
-        : n(n_), xadj(x), adj(a), leaf(leaf_), is_elem(n_, 0), stamp(n_, 0), visit(n_, 0),
-          estamp(n_, 0), lev(n_, -1), done(n_, 0) {}
+        : n(n_), xadj(x), adj(a), leaf(leaf_), is_elem(n_, 0), elo(n_, INT32_MAX), ehi(n_, -1), stamp(n_, 0),
+          visit(n_, 0), estamp(n_, 0), lev(n_, -1), done(n_, 0) {}
 
     int64_t deg(int32_t v) const { return xadj[v + 1] - xadj[v]; }
 
@@ -105,6 +109,63 @@ struct ND {
         out.insert(out.end(), S.begin(), S.end());
     }
 
+    // Interval cut: when the set's vertices are intervals over the element
+    // ranks, a rank t splits them into those ending at or before t (A), those
+    // starting after t (B) and those containing the gap (the separator): an
+    // element joins only vertices whose intervals contain its rank, so no
+    // element connects A with B; a direct edge between A and B (not made by an
+    // element) moves its A end into the separator.  Among the cuts leaving at
+    // least an eighth of the set on each side, the one minimising
+    // |separator| / sqrt(smaller side) is taken (a small separator, traded
+    // against balance).  Returns false when no such cut exists.
+    bool interval_cut(const std::vector<int32_t>& S, int32_t sid, std::vector<int32_t>& A, std::vector<int32_t>& B,
+                      std::vector<int32_t>& sep) {
+        int32_t t0 = INT32_MAX, t1 = -1;
+        for (int32_t v : S) {
+            if (ehi[v] < 0) return false;
+            t0 = std::min(t0, elo[v]);
+            t1 = std::max(t1, ehi[v]);
+        }
+        const int32_t span = t1 - t0 + 1;
+        if (span < 2) return false;
+        std::vector<int32_t> dS((size_t)span + 1, 0), ends((size_t)span, 0);
+        for (int32_t v : S) {
+            dS[elo[v] - t0]++;
+            dS[ehi[v] - t0]--;
+            ends[ehi[v] - t0]++;
+        }
+        const int64_t minside = (int64_t)S.size() / 8;
+        int64_t sc = 0, lc = 0;
+        double best_s = 1e300;
+        int32_t best_t = -1;
+        for (int32_t t = 0; t + 1 < span; ++t) {
+            sc += dS[t];     // vertices with lo <= t < hi
+            lc += ends[t];   // vertices with hi <= t
+            const int64_t rc = (int64_t)S.size() - sc - lc;
+            if (lc < minside || rc < minside) continue;
+            const double cost = (double)sc / std::sqrt((double)std::min(lc, rc));
+            if (cost < best_s) { best_s = cost; best_t = t; }
+        }
+        if (best_t < 0) return false;
+        const int32_t t = t0 + best_t;
+        A.clear(); B.clear(); sep.clear();
+        for (int32_t v : S) {
+            if (ehi[v] <= t) {
+                bool cross = false;
+                for (int64_t p = xadj[v]; p < xadj[v + 1] && !cross; ++p) {
+                    const int32_t u = adj[p];
+                    cross = !is_elem[u] && stamp[u] == sid && elo[u] > t;
+                }
+                (cross ? sep : A).push_back(v);
+            } else if (elo[v] > t) {
+                B.push_back(v);
+            } else {
+                sep.push_back(v);
+            }
+        }
+        return true;
+    }
+
     void dissect(std::vector<int32_t> S) {
         if ((int64_t)S.size() <= leaf) { emit_sorted(S); return; }
         int32_t sid = ++cur_set;
@@ -123,6 +184,16 @@ struct ND {
             }
             for (auto& c : comps) dissect(std::move(c));
             return;
+        }
+        // an interval cut when the elements give one, else a level-structure separator
+        {
+            std::vector<int32_t> Ai, Bi, sepi;
+            if (interval_cut(S, sid, Ai, Bi, sepi)) {
+                dissect(std::move(Ai));
+                dissect(std::move(Bi));
+                emit_sorted(sepi);
+                return;
+            }
         }
         // pseudo-peripheral root: restart from a minimum-degree vertex of the last level
         int32_t root = S[0];
@@ -205,6 +276,12 @@ std::vector<int32_t> order_nested_dissection(int32_t n, const std::vector<int64_
     std::vector<int32_t> rest;
     for (int32_t v = 0; v < n; ++v) if (!nd.is_elem[v]) rest.push_back(v);
     std::sort(first.begin(), first.end());
+    for (int32_t r = 0; r < (int32_t)first.size(); ++r)
+        for (int64_t p = xadj[first[r]]; p < xadj[first[r] + 1]; ++p) {
+            const int32_t v = adj[p];
+            nd.elo[v] = std::min(nd.elo[v], r);
+            nd.ehi[v] = std::max(nd.ehi[v], r);
+        }
     nd.out = first;
     if (!rest.empty()) nd.dissect(std::move(rest));
     return nd.out;
@@ -422,7 +499,7 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
                 int32_t t = s + 1;
                 while (t < np_ && !haskid[t] && ppar[t] == ppar[s]) {
                     int64_t kt = part[t + 1] - part[t];
-                    if (kg + kt > 32) break;
+                    if (kg + kt > prm.group_max) break;
                     int64_t trial = ucnt;
                     // count without committing: stamp with a temporary id then roll back if rejected
                     std::vector<int32_t> added;

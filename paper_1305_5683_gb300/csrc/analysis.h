@@ -14,6 +14,7 @@ struct AnalyseParams {
     int ordering = 0;  // 0 nested dissection, 1 natural
     int relax = 10;    // amalgamation: allowed explicit zeros, percent of the merged panel
     int nd_leaf = 0;   // nested-dissection leaf size, 0 = default
+    int group_max = 32;  // most columns in one front of grouped sibling leaves
 };
 
 struct Symbolic {

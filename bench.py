@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--relax", type=int, default=1)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sky", action="store_true")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--problems", type=int, default=256)
     return ap.parse_args()
@@ -319,6 +320,74 @@ def bench_uneven(P, args, dev, st, flush, world):
             + s.info()["launches_solve"] + 1, "generate_s": t_gen}
 
 
+def _time_phases(s, vals, b, x, idx, var, nsteps, warmup, st, flush):
+    """Mean device ms of factor / solve / diag_inverse over nsteps timed steps."""
+    import torch
+
+    def step(ev=None):
+        if ev: ev[0].record(st)
+        s.factor(vals, stream=st)
+        if ev: ev[1].record(st)
+        s.solve(b, x, stream=st)
+        if ev: ev[2].record(st)
+        s.diag_inverse(idx, out=var, stream=st)
+        if ev: ev[3].record(st)
+
+    for _ in range(warmup):
+        step(); flush.zero_()
+    s.sync(st)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
+    torch.cuda.synchronize()
+    for k in range(nsteps):
+        step(evs[k]); flush.zero_()
+    torch.cuda.synchronize()
+    s.sync(st)
+    return [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(3)]
+
+
+def bench_sky(P, args, dev, st, flush, world):
+    """Diffuse-sky workload: point sources plus a pixel grid, pointings on a
+    target grid (the large configuration's structure at P = 8,000 and 1 deg
+    pixels); variances of the sky columns only.  Its fronts are wide (a dense
+    sky block of ~5,000 columns), which is where the mixed form's tensor-core
+    updates apply.  FP64 form and mixed form, same step."""
+    import torch
+    from spigen import SKY, generate
+    t0 = time.perf_counter()
+    pb = generate(SKY)
+    t_gen = time.perf_counter() - t0
+    idx = torch.from_numpy(pb.sky_columns).to(dev)
+    vals = torch.from_numpy(pb.values).to(dev)
+    b = torch.from_numpy(pb.b).to(dev)
+    ksteps = max(1, min(args.steps, 3))
+    out, res = {}, {}
+    for name, prec in (("fp64", P.SPI_PREC_FP64), ("mixed", P.SPI_PREC_MIXED_FP32)):
+        s = P.Solver.for_problem(pb, async_=True, precision=prec, relax=args.relax)
+        x = torch.empty_like(b)
+        var = torch.empty(pb.n_sky, dtype=torch.float64, device=dev)
+        f, so, d = _time_phases(s, vals, b, x, idx, var, ksteps, 3, st, flush)
+        info = s.info()
+        res[name] = (x, var)
+        out[name] = {"value": world * pb.n_sky / ((f + so + d) / 1e3), "ms_per_step": f + so + d,
+                     "phases_ms": {"factor": f, "solve": so, "diag_inverse": d},
+                     "factor_tflops": info["factor_flops"] / (f / 1e3) / 1e12,
+                     "diag_tflops": info["diag_flops"] / (d / 1e3) / 1e12,
+                     "refine_steps": info["refine_steps"], "solve_relres": info["solve_relres"]}
+        if name == "fp64":
+            out["factor_flops"], out["diag_flops"] = info["factor_flops"], info["diag_flops"]
+            out["max_front"], out["n_supernodes"] = info["max_front"], info["n_supernodes"]
+        del s
+    (x64, v64), (xm, vm) = res["fp64"], res["mixed"]
+    out["mixed"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["mixed"]["max_rel_err_var_vs_fp64"] = float((torch.abs(vm - v64) / v64).max().item())
+    out["mixed"]["max_rel_err_x_vs_fp64"] = float((torch.abs(xm - x64).max() / torch.abs(x64).max()).item())
+    out.update({"workload": f"{pb.cfg.name}: P={pb.cfg.n_pointings} pointings on a 7x7 target grid, "
+                            f"{pb.cfg.n_sources} sources, {pb.n_sky} sky pixels of {pb.cfg.sky_pix_deg:g} deg "
+                            f"(n={pb.n}, nnz_lower={pb.nnz}); variances of the sky columns",
+                "unit": UNIT, "steps": ksteps, "generate_s": t_gen})
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -452,6 +521,13 @@ def main():
                  "dtype": "f32 updates / f64 pivots, refinement and variance sums"}
         del sm_
 
+    sky = None
+    if not args.no_sky:
+        try:
+            sky = bench_sky(P, args, dev, st, flush, world)
+        except Exception as e:
+            sky = {"error": f"{type(e).__name__}: {e}"}
+
     batched_bands = batched_uneven = None
     if not args.no_batch:
         for name in ("bands", "uneven"):
@@ -488,6 +564,7 @@ def main():
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],
         "roofline": roof,
         "mixed": mixed,
+        "sky": sky,
         "batched_bands": batched_bands,
         "batched_uneven": batched_uneven,
         "cpu_baseline": cpu,

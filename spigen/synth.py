@@ -34,8 +34,16 @@ Readings where the paper is silent (stated once here, fixed for all configs):
   * true intensities: pointing normalisations U(0.9, 1.1), detector-pattern
     amplitudes U(0, 5), source fluxes U(0, 20) per bin; per-detector
     background means u_d ~ U(50, 200).
+  * with `targets` > 0 the pointings visit a targets x targets grid of
+    field positions `target_step` apart, each as a 25-pointing block of the
+    dither raster, cycling through the grid; a pointing's position is then
+    (target, dither offset), and responses are drawn per position;
+  * with `sky_pix_deg` > 0 a diffuse sky of square pixels of that size
+    covering `sky_field_deg` on a side adds one column per pixel, visible
+    from a pointing within fov_deg like a point source, with one bin
+    spanning the whole observation; pixels never visible are dropped.
 Column order: [pointings; detector-pattern columns (block-major);
-time-bins sorted by (start, source)].
+time-bins sorted by (start, source); sky pixels (row-major)].
 """
 from __future__ import annotations
 
@@ -61,6 +69,10 @@ class SpiConfig:
     fov_deg: float = 15.0
     dither_step: float = 2.0
     seed: int = 0
+    targets: int = 0         # pointing targets per side of the target grid (0 = field centre only)
+    target_step: float = 10.0
+    sky_pix_deg: float = 0.0  # diffuse-sky pixel size (0 = no sky columns)
+    sky_field_deg: float = 70.0
 
 
 # The workloads: a tiny one the oracle finishes in seconds, and the FP64
@@ -72,6 +84,27 @@ SCALE = SpiConfig("spi-P20000", n_pointings=20000, n_sources=500, bin_lo=20,
 # Same-pattern energy-band member (one band); bands rescale values only.
 BAND = SpiConfig("spi-band-P5000", n_pointings=5000, n_sources=200, bin_lo=10,
                  bin_hi=200, det_block=500)
+
+
+# Diffuse-sky family (pointing targets on a 7 x 7 grid 10 deg apart, 25-pointing
+# dither blocks, point sources plus a pixel grid over 70 deg).  SKY_FULL is
+# the large configuration (P = 80,000, 2,000 sources, 0.5 deg pixels); SKY is
+# the member of the family the benchmark and the full-size tests run.
+SKY_FULL = SpiConfig("spi-sky-P80000", n_pointings=80000, n_sources=2000, bin_lo=20,
+                     bin_hi=2000, det_block=500, field_deg=70.0, targets=7,
+                     sky_pix_deg=0.5)
+SKY = SpiConfig("spi-sky-P8000", n_pointings=8000, n_sources=200, bin_lo=20,
+                bin_hi=2000, det_block=500, field_deg=70.0, targets=7,
+                sky_pix_deg=1.0)
+
+
+def sky_scaled(n_pointings: int, pix_deg: float, n_sources: int, seed: int = 0) -> SpiConfig:
+    """A member of the diffuse-sky family with P pointings and pixels of pix_deg."""
+    return dataclasses.replace(SKY, name=f"spi-sky-P{n_pointings}-pix{pix_deg:g}",
+                               n_pointings=n_pointings, n_sources=n_sources,
+                               bin_lo=max(5, n_pointings // 400), bin_hi=max(10, n_pointings // 4),
+                               det_block=max(25, min(500, n_pointings // 8)),
+                               sky_pix_deg=pix_deg, seed=seed)
 
 
 def uneven_config(index: int) -> SpiConfig:
@@ -140,10 +173,16 @@ class SpiProblem:
     values: np.ndarray   # float64 [nnz]
     b: np.ndarray        # float64 [n]
     x_true: np.ndarray   # float64 [n]
-    kind: np.ndarray     # int8 [n]: 0 pointing, 1 detector pattern, 2 time-bin
+    kind: np.ndarray     # int8 [n]: 0 pointing, 1 detector pattern, 2 time-bin, 3 sky pixel
     n_pointing: int
     n_detcol: int
     n_bins: int
+    n_sky: int = 0
+
+    @property
+    def sky_columns(self) -> np.ndarray:
+        """Indices of the sky-pixel columns (the last n_sky)."""
+        return np.arange(self.n - self.n_sky, self.n, dtype=np.int32)
 
     @property
     def nnz(self) -> int:
@@ -172,14 +211,17 @@ def _bins_for_sources(rng, cfg: SpiConfig):
 
 
 def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
-             band_scale: np.ndarray | None = None, counts_seed: int | None = None) -> SpiProblem:
+             band_scale: np.ndarray | None = None, counts_seed: int | None = None,
+             dense_design: bool = False) -> SpiProblem:
     """Build the problem for `cfg`.
 
     noise=False replaces the Poisson draw by y = H x_true exactly (the
     noise-free case whose least-squares solution is x_true).  band_scale, if
     given (one factor per source), rescales every response value of that
     source (energy-band members share one pattern); counts_seed reseeds only
-    the Poisson draw.
+    the Poisson draw.  dense_design=True (small problems only) also returns
+    the dense design matrix H and the weights as attributes `H` and `w` of
+    the problem, assembled row block by row block, for checking N = H^T W H.
     """
     rng = np.random.default_rng(cfg.seed)
     P, nd = cfg.n_pointings, N_DET
@@ -190,16 +232,29 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     g = rng.uniform(0.8, 1.2, (P, nd))
     h = rng.uniform(0.8, 1.2, (P, nd))
     starts, ends, srcs = _bins_for_sources(rng, cfg)
-    # dither raster
-    qpos = np.arange(_DITHER * _DITHER)
+    # pointing positions: the dither raster about the field centre, or about
+    # each target of the target grid (position id = target * 25 + dither offset)
+    nq = _DITHER * _DITHER
+    qpos = np.arange(nq)
     dlon = ((qpos % _DITHER) - _DITHER // 2) * cfg.dither_step
     dlat = ((qpos // _DITHER) - _DITHER // 2) * cfg.dither_step
-    vis = _angdist_deg(src_lon[:, None], src_lat[:, None], dlon[None, :], dlat[None, :]) < cfg.fov_deg
-    qofp = np.arange(P) % (_DITHER * _DITHER)
+    if cfg.targets > 0:
+        T = cfg.targets
+        ti = np.arange(T * T)
+        tlon = ((ti % T) - (T - 1) / 2) * cfg.target_step
+        tlat = ((ti // T) - (T - 1) / 2) * cfg.target_step
+        plon = (tlon[:, None] + dlon[None, :]).ravel()
+        plat = (tlat[:, None] + dlat[None, :]).ravel()
+        qofp = ((np.arange(P) // nq) % (T * T)) * nq + np.arange(P) % nq
+    else:
+        plon, plat = dlon, dlat
+        qofp = np.arange(P) % nq
+    npos = len(plon)
+    vis = _angdist_deg(src_lon[:, None], src_lat[:, None], plon[None, :], plat[None, :]) < cfg.fov_deg
     # keep bins with at least one visible pointing
     keep = np.zeros(len(starts), bool)
     for i, (a, b_, s) in enumerate(zip(starts, ends, srcs)):
-        qs = np.unique(qofp[a:b_]) if b_ - a < 25 else qpos
+        qs = np.unique(qofp[a:b_]) if b_ - a < npos else np.arange(npos)
         keep[i] = bool(vis[s, qs].any())
     starts, ends, srcs = starts[keep], ends[keep], srcs[keep]
     order = np.lexsort((srcs, starts))
@@ -213,23 +268,51 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     def blk(p):
         return np.minimum(np.asarray(p) // cfg.det_block, nblk - 1)
     ndet = nblk * nd
-    n = P + ndet + nbins
+    # diffuse-sky pixels seen from at least one pointing made
+    if cfg.sky_pix_deg > 0:
+        npx = int(round(cfg.sky_field_deg / cfg.sky_pix_deg))
+        cgrid = (np.arange(npx) + 0.5) * cfg.sky_pix_deg - cfg.sky_field_deg / 2
+        pix_lon, pix_lat = np.tile(cgrid, npx), np.repeat(cgrid, npx)
+        pvis = _angdist_deg(pix_lon[:, None], pix_lat[:, None], plon[None, :], plat[None, :]) < cfg.fov_deg
+        seen = pvis[:, np.unique(qofp)].any(axis=1)
+        pvis = pvis[seen]
+    else:
+        pvis = np.zeros((0, npos), bool)
+    nsky = pvis.shape[0]
+    n = P + ndet + nbins + nsky
     col_bin0 = P + ndet
+    col_sky0 = col_bin0 + nbins
     x_true = np.concatenate([rng.uniform(0.9, 1.1, P), rng.uniform(0.0, 5.0, ndet),
                              rng.uniform(0.0, 20.0, nbins)])
-    kind = np.concatenate([np.zeros(P, np.int8), np.ones(ndet, np.int8), np.full(nbins, 2, np.int8)])
+    if nsky:
+        x_true = np.concatenate([x_true, rng.uniform(0.0, 5.0, nsky)])
+    kind = np.concatenate([np.zeros(P, np.int8), np.ones(ndet, np.int8), np.full(nbins, 2, np.int8),
+                           np.full(nsky, 3, np.int8)])
     scale = np.ones(cfg.n_sources) if band_scale is None else np.asarray(band_scale, float)
+    dd = np.arange(nd)
+
+    def sky_response(pix: np.ndarray, pos) -> np.ndarray:
+        """R(d, pixel, position) ~ U(0.1, 1); pixels are numbered after the sources."""
+        return _response(cfg.seed, cfg.n_sources + np.asarray(pix), np.asarray(pos), dd)
 
     def window_block(p0: int, p1: int):
         """Dense H restricted to rows of pointings [p0, p1) and the columns
-        active there; returns (global column ids, H_w)."""
+        active there; returns (global column ids, H_w, number of sky columns,
+        which come last)."""
         np_ = p1 - p0
         kb0, kb1 = int(blk(p0)), int(blk(p1 - 1)) + 1
         act = np.nonzero((starts < p1) & (ends > p0))[0]
+        apix = np.nonzero(pvis[:, np.unique(qofp[p0:p1])].any(axis=1))[0] if nsky else np.zeros(0, np.int64)
         cols = np.concatenate([np.arange(p0, p1),
                                P + np.arange(kb0 * nd, kb1 * nd),
-                               col_bin0 + act])
+                               col_bin0 + act, col_sky0 + apix])
         Hw = np.zeros((np_ * nd, len(cols)))
+        if len(apix):
+            c0 = np_ + (kb1 - kb0) * nd + len(act)
+            for p in range(p0, p1):
+                sel = np.nonzero(pvis[apix, qofp[p]])[0]
+                R = sky_response(apix[sel][:, None], qofp[p])
+                Hw[(p - p0) * nd + dd[None, :], (c0 + sel)[:, None]] = R
         pp = np.arange(p0, p1)
         rows = (pp - p0)[:, None] * nd + np.arange(nd)[None, :]
         Hw[rows, (pp - p0)[:, None]] = u_d[None, :] * g[p0:p1]
@@ -245,18 +328,24 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
             q = qofp[p]
             ok = vis[s, q]
             p, s, q, bi = p[ok], s[ok], q[ok], bi[ok]
-            dd = np.arange(nd)
             R = _response(cfg.seed, s[:, None], q[:, None], dd[None, :]) * scale[s][:, None]
             r = (p - p0)[:, None] * nd + dd[None, :]
             Hw[r, (np_ + (kb1 - kb0) * nd + bi)[:, None]] = R
-        return cols, Hw
+        return cols, Hw, len(apix)
 
     # pass 1: expected counts, Poisson draw (one global draw, window independent)
     e = np.empty(P * nd)
     for p0 in range(0, P, window):
         p1 = min(P, p0 + window)
-        cols, Hw = window_block(p0, p1)
+        cols, Hw, _ = window_block(p0, p1)
         e[p0 * nd:p1 * nd] = Hw @ x_true[cols]
+    Hd = None
+    if dense_design:
+        Hd = np.zeros((P * nd, n))
+        for p0 in range(0, P, window):
+            p1 = min(P, p0 + window)
+            cols, Hw, _ = window_block(p0, p1)
+            Hd[p0 * nd:p1 * nd][:, cols] = Hw
     if noise:
         crng = rng if counts_seed is None else np.random.default_rng(counts_seed)
         y = crng.poisson(e).astype(np.float64)
@@ -269,22 +358,53 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     bvec = np.zeros(n)
     for p0 in range(0, P, window):
         p1 = min(P, p0 + window)
-        cols, Hw = window_block(p0, p1)
+        cols, Hw, ns = window_block(p0, p1)
         ww = w[p0 * nd:p1 * nd]
-        G = Hw.T @ (Hw * ww[:, None])
-        bvec[cols] += Hw.T @ (ww * y[p0 * nd:p1 * nd])
-        gi, gj = np.nonzero(np.tril(np.ones_like(G, dtype=bool)) & (G != 0.0))
+        if ns == 0:
+            G = Hw.T @ (Hw * ww[:, None])
+            bvec[cols] += Hw.T @ (ww * y[p0 * nd:p1 * nd])
+            gi, gj = np.nonzero(np.tril(np.ones_like(G, dtype=bool)) & (G != 0.0))
+        else:
+            # rows: the window's non-sky columns; sky x sky is summed per position below
+            nw = len(cols) - ns
+            G = Hw[:, :nw].T @ (Hw * ww[:, None])
+            bvec[cols[:nw]] += Hw[:, :nw].T @ (ww * y[p0 * nd:p1 * nd])
+            low = np.ones_like(G, dtype=bool)
+            low[:, :nw] = np.tril(low[:, :nw])
+            gi, gj = np.nonzero(low & (G != 0.0))
         ri, cj = cols[gi], cols[gj]
         sw = ri < cj
         ri2 = np.where(sw, cj, ri); cj2 = np.where(sw, ri, cj)
         rr.append(ri2); cc.append(cj2); vv.append(G[gi, gj])
+    if nsky:
+        # sky x sky: pointings at one position see the same pixels with the same
+        # responses, so sum their weights per (position, detector) first
+        Wt = np.zeros((npos, nd)); Yt = np.zeros((npos, nd))
+        np.add.at(Wt, qofp, w.reshape(P, nd))
+        np.add.at(Yt, qofp, (w * y).reshape(P, nd))
+        acc = np.zeros((nsky, nsky))
+        for q in range(npos):
+            if not Wt[q].any():
+                continue
+            V = np.nonzero(pvis[:, q])[0]
+            if len(V) == 0:
+                continue
+            R = _response(cfg.seed, cfg.n_sources + V[None, :], np.full((1, 1), q), dd[:, None])  # [nd, |V|]
+            acc[np.ix_(V, V)] += R.T @ (R * Wt[q][:, None])
+            bvec[col_sky0 + V] += R.T @ Yt[q]
+        gi, gj = np.nonzero(np.tril(acc))
+        rr.append(col_sky0 + gi); cc.append(col_sky0 + gj); vv.append(acc[gi, gj])
     rr = np.concatenate(rr); cc = np.concatenate(cc); vv = np.concatenate(vv)
     low = sp.coo_matrix((vv, (rr, cc)), shape=(n, n)).tocsc()
     low.sum_duplicates()
     low.sort_indices()
-    return SpiProblem(cfg=cfg, n=n, colptr=low.indptr.astype(np.int64),
-                      rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
-                      b=bvec, x_true=x_true, kind=kind, n_pointing=P, n_detcol=ndet, n_bins=nbins)
+    pb = SpiProblem(cfg=cfg, n=n, colptr=low.indptr.astype(np.int64),
+                    rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
+                    b=bvec, x_true=x_true, kind=kind, n_pointing=P, n_detcol=ndet, n_bins=nbins,
+                    n_sky=nsky)
+    if dense_design:
+        pb.H, pb.w, pb.y = Hd, w, y
+    return pb
 
 
 def random_spd(n: int, density: float, seed: int, *, dominance: float = 1.0) -> SpiProblem:

@@ -131,14 +131,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def source_digest(kernel_file: str) -> str:
+    """sha256 over the kernel's source and the analysis that plans its launch
+    (the ordering and block plan decide the work of one launch)."""
+    h = hashlib.sha256()
+    for f in (kernel_file, "analysis.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_of(kernel_file: str, key: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since the counters were taken."""
+    """DRAM bytes per launch from the committed ncu summary, if neither the
+    kernel source nor the analysis changed since the counters were taken."""
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         ent = prof[key]
-        h = hashlib.sha256(open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", kernel_file), "rb").read()).hexdigest()
-        if ent.get("source_sha256") != h:
+        if ent.get("source_sha256") != source_digest(kernel_file):
             return None
         return float(ent["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):

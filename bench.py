@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sky", action="store_true")
+    ap.add_argument("--sky-only", action="store_true", help="run only the diffuse-sky leg (for profiling)")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--problems", type=int, default=256)
     return ap.parse_args()
@@ -414,6 +415,10 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
+    if args.sky_only:  # the diffuse-sky leg alone (profiling); not the benchmark line
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"sky": bench_sky(P, args, dev, torch.cuda.current_stream(dev), flush, world)}), flush=True)
+        return
     pb, t_gen = workload(args.workload)
 
     s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax)

@@ -112,3 +112,18 @@ def test_autotuned_block_size(P):
     assert np.array_equal(v1, v2)
     vr = oracle.OracleFactor.from_problem(pb).inv_diag()
     assert (np.abs(v1 - vr) / vr).max() <= TOL
+
+
+def test_shard_solve_share_matches_oracle(P):
+    """One rank's share of independent problems, as the multi-GPU path runs
+    it on each GPU (here: every share in turn on this one)."""
+    from paper_1305_5683_gb300 import shard
+    probs = generate_uneven(4) + [random_spd(60, 0.1, 5)]
+    parts = shard.assign(shard.problem_costs(probs), 2)
+    for idx in parts:
+        xs, vs = shard.solve_share(probs, idx)
+        for i, x, v in zip(idx, xs, vs):
+            f = oracle.OracleFactor.from_problem(probs[i])
+            xr, vr = f.solve(probs[i].b), f.inv_diag()
+            assert np.abs(x - xr).max() <= TOL * np.abs(xr).max()
+            assert (np.abs(v - vr) / vr).max() <= TOL

@@ -510,7 +510,7 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
                         }
                     double ex2 = exact + (double)below(t) * below(t) * kt;
                     double merged_cost = (double)trial * trial * (kg + kt);
-                    if (merged_cost > 2.5 * ex2) {
+                    if (merged_cost > prm.group_cost * ex2) {
                         for (int32_t r : added) stamp[r] = -1;
                         break;
                     }

@@ -15,6 +15,7 @@ struct AnalyseParams {
     int relax = 10;    // amalgamation: allowed explicit zeros, percent of the merged panel
     int nd_leaf = 0;   // nested-dissection leaf size, 0 = default
     int group_max = 32;  // most columns in one front of grouped sibling leaves
+    double group_cost = 2.5;  // grouped leaves' update may cost this many times their separate updates
 };
 
 struct Symbolic {

@@ -163,23 +163,33 @@ __device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, double* __res
         int i = e % kT, j = e / kT;
         A[i][j] = (i < w && j <= i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
     }
+    // FP64 is a narrow pipe on this GPU: one thread forms each pivot's
+    // reciprocal, and the update visits only the trailing square.
+    __shared__ double rinv;
     __syncthreads();
     for (int c = 0; c < w; ++c) {
-        const double dc = A[c][c];
-        if (tid == 0 && (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c])) {
-            atomicOr(&status->flags, FLAG_NOT_SPD);
-            atomicMin(&status->bad_pivot, band_base + f + c0 + c);
-        }
-        const double inv = 1.0 / dc;
-        for (int e = tid; e < kT * kT; e += kThreads) {
-            int i = e % kT, j = e / kT;
-            if (j > c && j <= i && i < w) A[i][j] -= A[i][c] * inv * A[j][c];
+        if (tid == 0) {
+            const double dc = A[c][c];
+            if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
+                atomicOr(&status->flags, FLAG_NOT_SPD);
+                atomicMin(&status->bad_pivot, band_base + f + c0 + c);
+            }
+            dv[c] = dc;
+            rinv = 1.0 / dc;
         }
         __syncthreads();
-        if (tid == 0) dv[c] = dc;
+        const double inv = rinv;
+        const int t = w - c - 1;
+        for (int e = tid; e < t * t; e += kThreads) {
+            const int i = c + 1 + e / t, j = c + 1 + e % t;
+            if (j <= i) A[i][j] -= A[i][c] * inv * A[j][c];
+        }
+        __syncthreads();
+        // column c is not read again until the final store; the next pivot and
+        // column were completed by the update above
         for (int i = c + 1 + tid; i < w; i += kThreads) A[i][c] *= inv;
-        __syncthreads();
     }
+    __syncthreads();
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
         if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (i == j) ? dv[i] : A[i][j];
@@ -229,11 +239,10 @@ __global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t
         }
         D[f + c] = dc;
     }
-    const int64_t mb = m - k;
-    for (int64_t e = tid; e < (int64_t)k * mb; e += kThreads) {
-        const int c = (int)(e / mb);
-        const int64_t r = k + (e - (int64_t)c * mb);
-        P[r + (int64_t)c * m] /= P[c + (int64_t)c * m];
+    // one reciprocal per column (uniform across the CTA), then scale its rows
+    for (int c = 0; c < k; ++c) {
+        const double rc = 1.0 / P[c + (int64_t)c * m];
+        for (int64_t r = k + tid; r < m; r += kThreads) P[r + (int64_t)c * m] *= rc;
     }
 }
 

@@ -53,6 +53,8 @@ def load_library(path: str):
     lib.oracle_inv_diag.restype = ctypes.c_int
     lib.oracle_inv_diag_flops.argtypes = [P, P, I64]
     lib.oracle_inv_diag_flops.restype = D
+    lib.oracle_inv_block.argtypes = [P, P, I64, P]
+    lib.oracle_inv_block.restype = ctypes.c_int
     lib.oracle_free.argtypes = [P]; lib.oracle_free.restype = None
     return lib
 
@@ -129,6 +131,15 @@ class OracleFactor:
         rc = self._lib.oracle_inv_diag(self._h, _ptr(idx), len(idx), _ptr(out), int(nt))
         if rc != ORACLE_OK:
             raise RuntimeError(f"oracle_inv_diag failed with code {rc}")
+        return out
+
+    def inv_block(self, idx) -> np.ndarray:
+        """The dense block (A^-1)[idx, idx] (m x m)."""
+        idx = np.ascontiguousarray(idx, np.int32)
+        out = np.empty((len(idx), len(idx)), np.float64)
+        rc = self._lib.oracle_inv_block(self._h, _ptr(idx), len(idx), _ptr(out))
+        if rc:
+            raise RuntimeError(f"oracle_inv_block failed with code {rc}")
         return out
 
     def inv_diag_flops(self, idx=None) -> float:

@@ -30,6 +30,12 @@
  * Sec. 3.2.1), then (A^{-1})_ii = sum over that path, in ascending k, of
  * z_k^2 / d_k.  The requested indices are split over POSIX threads; this is
  * the only parallelism.
+ *
+ * Inverse block: for a set I of indices, A^{-1} = L^{-T} D^{-1} L^{-1} gives
+ * (A^{-1})_ij = sum_k z_i[k] z_j[k] / d_k with z_i = L^{-1} e_i as above, so
+ * the block A^{-1}(I, I) (covariances of the selected unknowns, Sec. 3.3.1:
+ * any set of entries of the inverse) is the FP64 sum, over ascending k, of
+ * products of the |I| solved vectors.
  */
 #include <math.h>
 #include <pthread.h>
@@ -259,4 +265,31 @@ double oracle_inv_diag_flops(const oracle_factor *f, const int32_t *idx, int64_t
         for (int64_t k = idx[t]; k != -1; k = f->parent[k])
             s += 2.0 * (double)(f->Lp[k + 1] - f->Lp[k] + 1);
     return s;
+}
+
+/* out[s * m + t] = (A^{-1})_{idx[s], idx[t]} for s, t < m (row-major, both
+ * triangles).  Every z = L^{-1} e_i is kept as a dense length-n vector. */
+int oracle_inv_block(const oracle_factor *f, const int32_t *idx, int64_t m, double *out) {
+    const int64_t n = f->n;
+    for (int64_t t = 0; t < m; ++t)
+        if (idx[t] < 0 || idx[t] >= n) return ORACLE_ERR_ARG;
+    if (m == 0) return ORACLE_OK;
+    double *Zm = calloc((size_t)m * (size_t)n, sizeof(double));
+    if (!Zm) return ORACLE_ERR_OOM;
+    for (int64_t t = 0; t < m; ++t) {
+        double *z = Zm + t * n;
+        z[idx[t]] = 1.0;
+        for (int64_t k = idx[t]; k != -1; k = f->parent[k])
+            for (int64_t p = f->Lp[k]; p < f->Lp[k + 1]; ++p) z[f->Li[p]] -= f->Lx[p] * z[k];
+    }
+    for (int64_t s = 0; s < m; ++s)
+        for (int64_t t = 0; t <= s; ++t) {
+            const double *zs = Zm + s * n, *zt = Zm + t * n;
+            double acc = 0.0;
+            for (int64_t k = 0; k < n; ++k) acc += zs[k] * zt[k] / f->D[k];
+            out[s * m + t] = acc;
+            out[t * m + s] = acc;
+        }
+    free(Zm);
+    return ORACLE_OK;
 }

@@ -91,6 +91,14 @@ def run_pins(lib=None):
         v = f.inv_diag()
         if np.abs(v - np.diag(Ainv)).max() > tol * np.abs(np.diag(Ainv)).max():
             fails.append("diag vs Gauss-Jordan")
+        # a block of the inverse (covariances of selected unknowns) against Gauss-Jordan,
+        # on the scale sqrt(v_s v_t) of each entry
+        sel = np.unique(np.linspace(0, n - 1, min(n, 12)).astype(np.int32))
+        G = f.inv_block(sel)
+        Gref = Ainv[np.ix_(sel, sel)]
+        sc = np.sqrt(np.outer(np.diag(Gref), np.diag(Gref)))
+        if np.abs(G - Gref).max() > tol * sc.max() or not np.all(np.abs(G - Gref) <= tol * sc + 1e-300):
+            fails.append("inverse block vs Gauss-Jordan")
         Lp, Li, Lx, D, par = f.factors()
         tk = takahashi_diag(Lp, Li, Lx, D)
         if np.abs(v - tk).max() > 1e-12 * np.abs(tk).max():
@@ -109,6 +117,21 @@ def run_pins(lib=None):
 # ---------------------------------------------------------------- the pins
 def test_pins_hold_for_the_oracle():
     assert run_pins() == []
+
+
+def test_inverse_block_properties():
+    """The block of the inverse is symmetric positive definite, its diagonal
+    is the inverse diagonal, and |cov| <= sqrt(v_s v_t) (a principal block of
+    an SPD inverse)."""
+    pb = generate(scaled(TINY, 200, seed=4))
+    f = oracle.OracleFactor.from_problem(pb)
+    sel = np.random.default_rng(3).choice(pb.n, 40, replace=False).astype(np.int32)
+    G = f.inv_block(sel)
+    assert np.array_equal(G, G.T)
+    assert np.allclose(np.diag(G), f.inv_diag(sel), rtol=1e-14, atol=0)
+    np.linalg.cholesky(G)
+    v = np.diag(G)
+    assert np.all(np.abs(G) <= np.sqrt(np.outer(v, v)) * (1 + 1e-12))
 
 
 def test_paper_etree_example():
@@ -255,6 +278,8 @@ MUTATIONS = {
     "etree parent = last row": ("f->parent[j] = (w > f->Lp[j]) ? f->Li[f->Lp[j]] : -1;",
                                 "f->parent[j] = (w > f->Lp[j]) ? f->Li[w - 1] : -1;"),
     "L scaled by wrong pivot": ("f->Lx[w] = acc[i] / dj;", "f->Lx[w] = acc[i] / ajj;"),
+    "inverse block without 1/d": ("acc += zs[k] * zt[k] / f->D[k];", "acc += zs[k] * zt[k];"),
+    "inverse block from one vector": ("acc += zs[k] * zt[k] / f->D[k];", "acc += zs[k] * zs[k] / f->D[k];"),
 }
 
 

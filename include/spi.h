@@ -196,6 +196,26 @@ int spi_solve_batch(spi_ctx* ctx, int32_t nbatch, const double* b, double* x, in
 int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int64_t nidx, double* out,
                            int on_device, void* stream);
 
+/* Most indices of one spi_inverse_block call. */
+#define SPI_INVERSE_BLOCK_MAX 512
+
+/* A block of the inverse: out[s * nidx + t] = (N^-1)_{idx[s], idx[t]} (both
+ * triangles, row-major), the covariances of the selected unknowns -- "any set
+ * of entries" of the inverse (paper Sec. 3.3.1), here a dense index block.
+ * Since N^-1 = P^T L^-T D^-1 L^-1 P, entry (s, t) is sum_k z_s[k] z_t[k] / d_k
+ * with z_s = L^-1 e_(pivot of idx[s]); the nidx vectors are the pruned
+ * forward solves of spi_diag_inverse, run as one block along the union of
+ * their elimination-tree paths (FP64, also in a mixed-precision context,
+ * whose factor is stored in FP64), followed by their FP64 Gram product.  No
+ * backward pass is needed for a symmetric matrix.
+ *   idx   int32[nidx], caller numbering, distinct, 0 <= nidx <= SPI_INVERSE_BLOCK_MAX
+ *   out   float64[nidx * nidx]
+ * on_device: idx and out are device pointers.  Band 0 of a batched context.
+ * The plan is cached per index set.  Errors: SPI_ERR_STATE (not factored),
+ * SPI_ERR_ARG (NULL buffer, nidx out of range, an index out of range or
+ * repeated), SPI_ERR_OOM, SPI_ERR_CUDA. */
+int spi_inverse_block(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream);
+
 /* Variances without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * need variances -- a host thread that must not enter the CUDA allocator (a

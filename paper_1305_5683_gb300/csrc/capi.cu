@@ -62,6 +62,11 @@ struct spi_ctx {
     DevDiagPlan plan_sub;
     std::vector<int32_t> plan_sub_key;
     bool plan_sub_ready = false;
+    // spi_inverse_block: its single-block plan (cached per index set) and output scratch
+    DevDiagPlan plan_blk;
+    std::vector<int32_t> plan_blk_key;
+    bool plan_blk_ready = false;
+    double* d_blk = nullptr;
     int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
     int64_t bad_pivot = -1, bad_band = -1;
@@ -670,6 +675,63 @@ int spi_diag_inverse_batch(spi_ctx* c, int32_t nbatch, const int32_t* idx, int64
     return diag_impl(c, nbatch, idx, nidx, out, on_device, (cudaStream_t)stream);
 }
 
+int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nidx < 0 || nidx > SPI_INVERSE_BLOCK_MAX || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
+    if (nidx == 0) return SPI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    std::vector<int32_t> key((size_t)nidx);
+    if (on_device) {
+        CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+    }
+    {
+        std::vector<int32_t> srt(key);
+        std::sort(srt.begin(), srt.end());
+        if (srt.front() < 0 || srt.back() >= S.n) return SPI_ERR_ARG;
+        if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SPI_ERR_ARG;
+    }
+    if (!c->plan_blk_ready || key != c->plan_blk_key) {
+        c->plan_blk_ready = false;
+        std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
+        for (int64_t t = 0; t < nidx; ++t) { piv[t] = S.iperm[key[t]]; pos[t] = (int32_t)t; }
+        DiagPlan h;
+        build_diag_plan(S, piv, pos, (int)nidx, h);
+        if (h.nblocks != 1) return SPI_ERR_ARG;
+        int rc = upload_plan(c, h, c->plan_blk);
+        if (rc) return rc;
+        // pivot of every local Z row: the union's supernodes own consecutive rows
+        const int64_t R = (h.zbase[1] - h.zbase[0]) / h.B;
+        std::vector<int32_t> zpiv((size_t)R, -1);
+        for (int u = h.uptr[0]; u < h.uptr[1]; ++u) {
+            const int32_t sn = h.us[u], f = S.sfirst[sn], k = S.sfirst[sn + 1] - f;
+            for (int32_t j = 0; j < k; ++j) {
+                const int64_t r = (int64_t)h.uzoff[u] + j;
+                if (r < 0 || r >= R) return SPI_ERR_ARG;
+                zpiv[(size_t)r] = f + j;
+            }
+        }
+        for (int32_t v : zpiv)
+            if (v < 0) return SPI_ERR_ARG;
+        CK(dev_upload(c, &c->plan_blk.zpiv, zpiv, &c->plan_blk.allocs));
+        c->plan_blk_key.swap(key);
+        c->plan_blk_ready = true;
+    }
+    if (!on_device && !c->d_blk)
+        CK(dev_alloc(c, &c->d_blk, (size_t)SPI_INVERSE_BLOCK_MAX * SPI_INVERSE_BLOCK_MAX));
+    double* od = on_device ? out : c->d_blk;
+    launch_inverse_block(c->dsym, c->plan_blk, c->d_L, c->d_D, c->d_out, od, nidx, st);
+    if (!on_device) {
+        CK(cudaMemcpyAsync(out, od, (size_t)nidx * nidx * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return finish(c, st);
+}
+
 int spi_info(const spi_ctx* c, spi_stats* o) {
     if (!c || !o) return SPI_ERR_ARG;
     std::memset(o, 0, sizeof *o);
@@ -757,6 +819,7 @@ void spi_destroy(spi_ctx* c) {
     if (!c) return;
     free_plan(c->plan_all);
     free_plan(c->plan_sub);
+    free_plan(c->plan_blk);
     for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
     for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
     if (c->cap) cudaStreamDestroy(c->cap);

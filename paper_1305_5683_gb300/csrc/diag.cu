@@ -289,7 +289,70 @@ void launch_t(const DevSym& d, const DevDiagPlan& p, const T* L, const double* D
     k_diag_inv<T><<<dim3(p.nblocks, nb), kThreads, sm, st>>>(d, a, L, D, out, bs);
 }
 
+// Block of the inverse from one block's forward solves (paper Sec. 3.3.1:
+// any set of entries of the inverse).  After k_diag_inv<double> has run on a
+// single block, Z holds z_t = L^-1 e_(pivot of slot t) on the union of the
+// block's paths, local row r belonging to pivot zpiv[r].  Since
+// N^-1 = L^-T D^-1 L^-1, G_st = sum_r Z[r][s] Z[r][t] / d_zpiv[r].  One CTA
+// per 32 x 32 tile of the lower triangle of G; rows in chunks of 32 staged in
+// shared memory; thread (jj, i0) owns column jj and rows i0 + 4q of the tile.
+// The result goes to out[rhs_out[s] * ldo + rhs_out[t]] and its mirror.
+__global__ void __launch_bounds__(128) k_inverse_gram(const double* __restrict__ Z, int B, int64_t R,
+                                                      const int32_t* __restrict__ zpiv,
+                                                      const double* __restrict__ D,
+                                                      const int32_t* __restrict__ rhs_out, double* __restrict__ out,
+                                                      int64_t ldo) {
+    __shared__ double Zs[kT][kT + 1];
+    __shared__ double Zt[kT][kT + 1];
+    __shared__ double w[kT];
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+    const int tj = (int)blockIdx.x - ti * (ti + 1) / 2;
+    const int s0 = ti * kT, t0 = tj * kT;
+    const int tid = threadIdx.x, jj = tid % kT, i0 = tid / kT;
+    double acc[kT / 4];
+#pragma unroll
+    for (int q = 0; q < kT / 4; ++q) acc[q] = 0.0;
+    for (int64_t r0 = 0; r0 < R; r0 += kT) {
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += 128) {
+            const int rr = e / kT, c = e % kT;
+            const int64_t r = r0 + rr;
+            Zs[rr][c] = (r < R && s0 + c < B) ? Z[r * B + s0 + c] : 0.0;
+            Zt[rr][c] = (r < R && t0 + c < B) ? Z[r * B + t0 + c] : 0.0;
+        }
+        if (tid < kT) w[tid] = r0 + tid < R ? 1.0 / D[zpiv[r0 + tid]] : 0.0;
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kT; ++rr) {
+            const double bt = Zt[rr][jj] * w[rr];
+#pragma unroll
+            for (int q = 0; q < kT / 4; ++q) acc[q] += Zs[rr][i0 + 4 * q] * bt;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kT / 4; ++q) {
+        const int sl = s0 + i0 + 4 * q, tl = t0 + jj;
+        if (sl < B && tl < B && tl <= sl) {
+            const int64_t so = rhs_out[sl], to = rhs_out[tl];
+            out[so * ldo + to] = acc[q];
+            out[to * ldo + so] = acc[q];
+        }
+    }
+}
+
 }  // namespace
+
+void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D,
+                          double* var_scratch, double* out, int64_t ldo, cudaStream_t st) {
+    if (p.nblocks != 1 || p.B == 0) return;
+    Strides bs;
+    bs.Z = p.zsize;
+    bs.out = p.nrhs;
+    launch_t<double>(d, p, L, D, var_scratch, 1, bs, st);
+    const int nt = (p.B + kT - 1) / kT;
+    k_inverse_gram<<<nt * (nt + 1) / 2, 128, 0, st>>>(p.Z, p.B, p.zsize / p.B, p.zpiv, D, p.rhs_out, out, ldo);
+}
 
 cudaError_t diag_kernel_setup(int B) {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -24,7 +24,9 @@ SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 
 EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
-           "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc"]
+           "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
+           "spi_inverse_block"]
+SPI_INVERSE_BLOCK_MAX = 512
 
 
 class spi_options(ctypes.Structure):
@@ -87,6 +89,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_solve.argtypes = [V, V, V, I, V]; L.spi_solve.restype = I
     L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
     L.spi_diag_inverse_noalloc.argtypes = [V, V, I64, V, V]; L.spi_diag_inverse_noalloc.restype = I
+    L.spi_inverse_block.argtypes = [V, V, I64, V, I, V]; L.spi_inverse_block.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -232,6 +235,19 @@ def spi_diag_inverse(ctx, idx, out, stream=None) -> None:
     del k1, k2
 
 
+def spi_inverse_block(ctx, idx, out, stream=None) -> None:
+    """out[s * m + t] = (N^-1)[idx[s], idx[t]] for m = len(idx) <= SPI_INVERSE_BLOCK_MAX."""
+    if not _is_torch(out) and not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise TypeError("out must be a contiguous float64 numpy array or CUDA tensor")
+    op, dev, k1 = _buf(out, np.float64)
+    ip, dev_i, k2 = _buf(idx, np.int32)
+    if dev_i != dev:
+        raise TypeError("idx and out must both be host or both be device buffers")
+    nidx = int(idx.numel() if _is_torch(idx) else len(k2))
+    _check(lib().spi_inverse_block(ctx, ip, nidx, op, dev, _stream(stream)), "spi_inverse_block")
+    del k1, k2
+
+
 def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
     """Variances for device idx into device out without any device allocation
     by the library (fixed scratch array; see include/spi.h)."""
@@ -347,6 +363,18 @@ class Solver:
             else:
                 out = np.empty(m, np.float64)
         spi_diag_inverse(self._h, idx, out, stream)
+        return out
+
+    def inverse_block(self, idx, out=None, stream=None):
+        """The dense block (N^-1)[idx, idx] as an (m, m) array (or `out`)."""
+        m = idx.numel() if _is_torch(idx) else len(idx)
+        if out is None:
+            if _is_torch(idx) and idx.is_cuda:
+                import torch
+                out = torch.empty((m, m), dtype=torch.float64, device=idx.device)
+            else:
+                out = np.empty((m, m), np.float64)
+        spi_inverse_block(self._h, idx, out, stream)
         return out
 
     def info(self) -> dict:

@@ -152,3 +152,6 @@ def test_compute_without_gpu_fails_loudly(P):
     with pytest.raises(P.SpiError) as e:
         s.diag_inverse()
     assert e.value.code == 7
+    with pytest.raises(P.SpiError) as e:
+        s.inverse_block(np.array([0, 1], np.int32))
+    assert e.value.code == 7

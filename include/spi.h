@@ -204,10 +204,12 @@ int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int
  * of entries" of the inverse (paper Sec. 3.3.1), here a dense index block.
  * Since N^-1 = P^T L^-T D^-1 L^-1 P, entry (s, t) is sum_k z_s[k] z_t[k] / d_k
  * with z_s = L^-1 e_(pivot of idx[s]); the nidx vectors are the pruned
- * forward solves of spi_diag_inverse, run as one block along the union of
- * their elimination-tree paths (FP64, also in a mixed-precision context,
- * whose factor is stored in FP64), followed by their FP64 Gram product.  No
- * backward pass is needed for a symmetric matrix.
+ * forward solves of spi_diag_inverse, in blocks of consecutive pivots along
+ * the union of their elimination-tree paths (FP64, also in a mixed-precision
+ * context, whose factor is stored in FP64), gathered into one matrix over the
+ * union of all their paths, followed by their FP64 Gram product.  No backward
+ * pass is needed for a symmetric matrix.  Device memory: that matrix, rows of
+ * the union x nidx doubles (at most n x nidx), kept for the next call.
  *   idx   int32[nidx], caller numbering, distinct, 0 <= nidx <= SPI_INVERSE_BLOCK_MAX
  *   out   float64[nidx * nidx]
  * on_device: idx and out are device pointers.  Band 0 of a batched context.

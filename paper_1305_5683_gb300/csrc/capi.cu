@@ -67,6 +67,8 @@ struct spi_ctx {
     std::vector<int32_t> plan_blk_key;
     bool plan_blk_ready = false;
     double* d_blk = nullptr;
+    double* d_zg = nullptr;      // gathered vectors (rows of the paths' union x indices)
+    int64_t zg_cap = 0, blk_rows = 0;
     int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
     int64_t bad_pivot = -1, bad_band = -1;
@@ -700,31 +702,50 @@ int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out,
         std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
         for (int64_t t = 0; t < nidx; ++t) { piv[t] = S.iperm[key[t]]; pos[t] = (int32_t)t; }
         DiagPlan h;
-        build_diag_plan(S, piv, pos, (int)nidx, h);
-        if (h.nblocks != 1) return SPI_ERR_ARG;
+        build_diag_plan(S, piv, pos, c->rhs_block_used > 0 ? c->rhs_block_used : 32, h);
         int rc = upload_plan(c, h, c->plan_blk);
         if (rc) return rc;
-        // pivot of every local Z row: the union's supernodes own consecutive rows
-        const int64_t R = (h.zbase[1] - h.zbase[0]) / h.B;
-        std::vector<int32_t> zpiv((size_t)R, -1);
-        for (int u = h.uptr[0]; u < h.uptr[1]; ++u) {
-            const int32_t sn = h.us[u], f = S.sfirst[sn], k = S.sfirst[sn + 1] - f;
-            for (int32_t j = 0; j < k; ++j) {
-                const int64_t r = (int64_t)h.uzoff[u] + j;
-                if (r < 0 || r >= R) return SPI_ERR_ARG;
-                zpiv[(size_t)r] = f + j;
+        // rows of the union of all blocks' paths (ascending pivots), and each
+        // block-local Z row's position among them; a block's supernodes own
+        // consecutive local rows from uzoff
+        std::vector<int32_t> gidx((size_t)S.n, -1), zpiv, rowmap((size_t)(h.zbase.back() / h.B), -1);
+        for (int bl = 0; bl < h.nblocks; ++bl)
+            for (int u = h.uptr[bl]; u < h.uptr[bl + 1]; ++u)
+                for (int32_t j = S.sfirst[h.us[u]]; j < S.sfirst[h.us[u] + 1]; ++j) gidx[(size_t)j] = 0;
+        for (int32_t j = 0; j < S.n; ++j)
+            if (gidx[(size_t)j] == 0) { gidx[(size_t)j] = (int32_t)zpiv.size(); zpiv.push_back(j); }
+        for (int bl = 0; bl < h.nblocks; ++bl) {
+            const int64_t base = h.zbase[bl] / h.B, rows = (h.zbase[bl + 1] - h.zbase[bl]) / h.B;
+            for (int u = h.uptr[bl]; u < h.uptr[bl + 1]; ++u) {
+                const int32_t sn = h.us[u], f = S.sfirst[sn], k = S.sfirst[sn + 1] - f;
+                for (int32_t j = 0; j < k; ++j) {
+                    const int64_t r = (int64_t)h.uzoff[u] + j;
+                    if (r < 0 || r >= rows) return SPI_ERR_ARG;
+                    rowmap[(size_t)(base + r)] = gidx[(size_t)(f + j)];
+                }
             }
         }
-        for (int32_t v : zpiv)
+        for (int32_t v : rowmap)
             if (v < 0) return SPI_ERR_ARG;
         CK(dev_upload(c, &c->plan_blk.zpiv, zpiv, &c->plan_blk.allocs));
+        CK(dev_upload(c, &c->plan_blk.rowmap, rowmap, &c->plan_blk.allocs));
+        c->blk_rows = (int64_t)zpiv.size();
+        if (c->blk_rows * nidx > c->zg_cap) {
+            if (c->d_zg) { cudaFree(c->d_zg); c->d_zg = nullptr; c->zg_cap = 0; }
+            if (cudaMalloc(&c->d_zg, (size_t)c->blk_rows * (size_t)nidx * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                c->d_zg = nullptr;
+                return SPI_ERR_OOM;
+            }
+            c->zg_cap = c->blk_rows * nidx;
+        }
         c->plan_blk_key.swap(key);
         c->plan_blk_ready = true;
     }
     if (!on_device && !c->d_blk)
         CK(dev_alloc(c, &c->d_blk, (size_t)SPI_INVERSE_BLOCK_MAX * SPI_INVERSE_BLOCK_MAX));
     double* od = on_device ? out : c->d_blk;
-    launch_inverse_block(c->dsym, c->plan_blk, c->d_L, c->d_D, c->d_out, od, nidx, st);
+    launch_inverse_block(c->dsym, c->plan_blk, c->d_L, c->d_D, c->d_out, c->d_zg, c->blk_rows, od, nidx, st);
     if (!on_device) {
         CK(cudaMemcpyAsync(out, od, (size_t)nidx * nidx * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -820,6 +841,7 @@ void spi_destroy(spi_ctx* c) {
     free_plan(c->plan_all);
     free_plan(c->plan_sub);
     free_plan(c->plan_blk);
+    if (c->d_zg) cudaFree(c->d_zg);
     for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
     for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
     if (c->cap) cudaStreamDestroy(c->cap);

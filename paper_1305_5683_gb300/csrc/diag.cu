@@ -341,17 +341,36 @@ __global__ void __launch_bounds__(128) k_inverse_gram(const double* __restrict__
     }
 }
 
+// Gather every block's solved vectors into one matrix Zg (R rows = the union
+// of all blocks' paths, one column per right-hand-side slot): block b's local
+// row r is global row rowmap[zbase[b] / B + r]; rows off a block's paths stay 0.
+__global__ void k_gather_blocks(const double* __restrict__ Z, int B, const int64_t* __restrict__ zbase,
+                                const int32_t* __restrict__ blk_ptr, const int32_t* __restrict__ rowmap,
+                                int64_t nslots, double* __restrict__ Zg) {
+    const int b = blockIdx.x;
+    const int64_t z0 = zbase[b], rows = (zbase[b + 1] - z0) / B;
+    const int s0 = blk_ptr[b], nb = blk_ptr[b + 1] - s0;
+    const int32_t* rm = rowmap + z0 / B;
+    for (int64_t e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+        const int64_t r = e / nb;
+        const int t = (int)(e - r * nb);
+        Zg[(int64_t)rm[r] * nslots + s0 + t] = Z[z0 + r * B + t];
+    }
+}
+
 }  // namespace
 
 void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D,
-                          double* var_scratch, double* out, int64_t ldo, cudaStream_t st) {
-    if (p.nblocks != 1 || p.B == 0) return;
+                          double* var_scratch, double* Zg, int64_t R, double* out, int64_t ldo, cudaStream_t st) {
+    if (p.nblocks == 0 || p.nrhs == 0) return;
     Strides bs;
     bs.Z = p.zsize;
     bs.out = p.nrhs;
+    cudaMemsetAsync(Zg, 0, (size_t)R * (size_t)p.nrhs * sizeof(double), st);
     launch_t<double>(d, p, L, D, var_scratch, 1, bs, st);
-    const int nt = (p.B + kT - 1) / kT;
-    k_inverse_gram<<<nt * (nt + 1) / 2, 128, 0, st>>>(p.Z, p.B, p.zsize / p.B, p.zpiv, D, p.rhs_out, out, ldo);
+    k_gather_blocks<<<p.nblocks, 256, 0, st>>>(p.Z, p.B, p.zbase, p.blk_ptr, p.rowmap, p.nrhs, Zg);
+    const int nt = (int)((p.nrhs + kT - 1) / kT);
+    k_inverse_gram<<<nt * (nt + 1) / 2, 128, 0, st>>>(Zg, (int)p.nrhs, R, p.zpiv, D, p.rhs_out, out, ldo);
 }
 
 cudaError_t diag_kernel_setup(int B) {

@@ -92,7 +92,10 @@ struct DevDiagPlan {
     int64_t *urel = nullptr, *zbase = nullptr;
     double* Z = nullptr;
     int64_t zsize = 0;
-    int32_t* zpiv = nullptr;  // single-block plans of spi_inverse_block: pivot of each local Z row
+    // spi_inverse_block plans: pivot of each row of the gathered matrix, and
+    // the gathered row of each block-local Z row (concatenated by block)
+    int32_t* zpiv = nullptr;
+    int32_t* rowmap = nullptr;
     double flops = 0, work_flops = 0;
     std::vector<void*> allocs;
 };
@@ -120,10 +123,11 @@ void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L,
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
                              int nb, const Strides& bs, cudaStream_t st);
 cudaError_t diag_kernel_setup(int B);
-// (N^-1)(I, I) for the pivots of a single-block plan with p.zpiv: the block's
-// forward solves (variances to var_scratch[0..B)), then the Gram product of
-// its Z into out (ldo = leading dimension, positions from the plan's rhs_out).
+// (N^-1)(I, I) for the pivots of a plan with zpiv/rowmap: the blocks' forward
+// solves (variances to var_scratch), their vectors gathered into Zg (R rows x
+// nrhs), then the Gram product into out (ldo = leading dimension, positions
+// from the plan's rhs_out).
 void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D,
-                          double* var_scratch, double* out, int64_t ldo, cudaStream_t st);
+                          double* var_scratch, double* Zg, int64_t R, double* out, int64_t ldo, cudaStream_t st);
 
 }  // namespace spi

@@ -166,8 +166,18 @@ constexpr int kFCols = 64;
 
 size_t diag_f32_smem_bytes(int B) {
     return sizeof(double) * (size_t)(B + kT) +
-           sizeof(float) * (size_t)(kT * B + kT * (kT + 1) + kT * (kFRows + 4));
+           sizeof(float) * (size_t)(kT * B + kT * (kT + 1) + 2 * kT * (kFRows + 4));
 }
+
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero
+// (nothing is read from src).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p, const float* __restrict__ L,
                                                              const double* __restrict__ D,
@@ -181,7 +191,8 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     double* dv = var + B;
     float* Zd = reinterpret_cast<float*>(dv + kT);  // [kT][B]
     float* Ld = Zd + kT * B;                        // [kT][kT+1]
-    float* Lt = Ld + kT * (kT + 1);                 // [kT][kFRows+4], transposed panel tile
+    float* Lt0 = Ld + kT * (kT + 1);                // [2][kT][kFRows+4], transposed panel tiles
+    float* Lt1 = Lt0 + kT * (kFRows + 4);
     __shared__ int rng[2];
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
@@ -230,49 +241,69 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                 Z[(int64_t)(zo + cb + c) * B + lo + t] = Zd[c * B + t];
             }
             const int w4 = (w + 3) & ~3;
-            for (int64_t rb = cb + w; rb < m; rb += kFRows) {
+            // row tiles below the block column, double-buffered: the copy of tile
+            // tt + 1 is in flight while tile tt is multiplied
+            const int64_t rfirst = cb + w;
+            const int ntiles = (int)((m - rfirst + kFRows - 1) / kFRows);
+            auto issue = [&](int tt, float* dst) {
+                const int64_t rb = rfirst + (int64_t)tt * kFRows;
                 const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
-                __syncthreads();
                 for (int e = tid; e < kFRows * kT; e += kFThreads) {
                     const int i = e % kFRows, c = e / kFRows;
-                    Lt[c * (kFRows + 4) + i] = (i < nrow && c < w) ? P[(rb + i) + (int64_t)(cb + c) * m] : 0.f;
+                    const bool ok = i < nrow && c < w;
+                    cp_async4(dst + c * (kFRows + 4) + i, ok ? P + (rb + i) + (int64_t)(cb + c) * m : P, ok ? 4 : 0);
+                }
+                cp_async_commit();
+            };
+            if (ntiles > 0) issue(0, Lt0);
+            for (int tt = 0; tt < ntiles; ++tt) {
+                const float* Lt = (tt & 1) ? Lt1 : Lt0;
+                if (tt + 1 < ntiles) {
+                    issue(tt + 1, (tt & 1) ? Lt0 : Lt1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
                 __syncthreads();
-                if (ty * 8 >= nrow) continue;
-                for (int cbase = 0; cbase < nb; cbase += kFCols) {
-                    if (cbase + tx * 8 >= nb) continue;
-                    float acc[8][8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-                    const float* lcol = Lt + ty * 8;
-                    const float* zcol = Zd + cbase + tx * 8;
-                    for (int c = 0; c < w4; ++c) {
-                        const float4 a0 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4));
-                        const float4 a1 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4) + 4);
-                        const float4 b0 = *reinterpret_cast<const float4*>(zcol + c * B);
-                        const float4 b1 = *reinterpret_cast<const float4*>(zcol + c * B + 4);
-                        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                const int64_t rb = rfirst + (int64_t)tt * kFRows;
+                const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
+                if (ty * 8 < nrow) {
+                    for (int cbase = 0; cbase < nb; cbase += kFCols) {
+                        if (cbase + tx * 8 >= nb) continue;
+                        float acc[8][8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-                    }
+                            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                        const float* lcol = Lt + ty * 8;
+                        const float* zcol = Zd + cbase + tx * 8;
+                        for (int c = 0; c < w4; ++c) {
+                            const float4 a0 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4));
+                            const float4 a1 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4) + 4);
+                            const float4 b0 = *reinterpret_cast<const float4*>(zcol + c * B);
+                            const float4 b1 = *reinterpret_cast<const float4*>(zcol + c * B + 4);
+                            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int il = ty * 8 + i;
-                        if (il >= nrow) break;
-                        const int64_t row = rb + il;
-                        const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
-                        float* zrow = Z + zr * B + lo + cbase + tx * 8;
-                        // one writer per element: a reduction without return hides the load latency
+                            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (cbase + tx * 8 + j < nb) atomicAdd(zrow + j, -acc[i][j]);
+                                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int il = ty * 8 + i;
+                            if (il >= nrow) break;
+                            const int64_t row = rb + il;
+                            const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
+                            float* zrow = Z + zr * B + lo + cbase + tx * 8;
+                            // one writer per element: a reduction without return hides the load latency
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (cbase + tx * 8 + j < nb) atomicAdd(zrow + j, -acc[i][j]);
+                        }
                     }
                 }
+                __syncthreads();  // tile tt read by all before its buffer is refilled
             }
         }
     }

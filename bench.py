@@ -36,6 +36,18 @@ FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of a GB300 (profiling recipe's tabl
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _measured_hbm_gbs() -> float:
+    """Copy bandwidth measured on this GPU pool (MEASURED_PEAKS.json), else
+    the profiling recipe's fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_GBS = _measured_hbm_gbs()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -244,15 +256,28 @@ def bench_bands(P, args, dev, st, flush, world):
     var = torch.empty(nb * n, dtype=torch.float64, device=dev)
     s = P.Solver(n, bb.colptr, bb.rowind, batch=nb, precision=P.SPI_PREC_MIXED_FP32, async_=True)
 
+    evs = []
+
     def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
         s.factor_batch(vals, stream=st)
+        ev[1].record(st)
         s.solve_batch(b, x, stream=st)
+        ev[2].record(st)
         s.diag_inverse_batch(out=var, stream=st)
+        ev[3].record(st)
+        evs.append(ev)
 
     ksteps = max(1, min(args.steps, 3))
     ms = _time_steps(step, ksteps, max(3, min(args.warmup, 3)), st, flush)
     s.sync(st)
     info = s.info()
+    timed = evs[-ksteps:]
+    ph = [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in timed) for i in range(3)]
+    # the solve reads every band's stored factor twice (forward and backward sweeps), per solve
+    nsolves = 1 + info["refine_steps"]
+    solve_bytes = 2.0 * nsolves * nb * info["nnz_l_stored"] * 8
     # one band in FP64, the plain form, as the sequential reference
     s1 = P.Solver(n, bb.colptr, bb.rowind, async_=True)
     v1 = torch.from_numpy(bb.values[: bb.nnz]).to(dev)
@@ -274,6 +299,8 @@ def bench_bands(P, args, dev, st, flush, world):
     return {"workload": f"{nb} energy bands x {bb.cfg.name} (P={bb.cfg.n_pointings}, {bb.cfg.n_sources} sources, "
                         f"n={n}, nnz_lower={bb.nnz}), E log-spaced 20-1000 keV, responses x (E/20)^-alpha",
             "value": value, "unit": UNIT, "ms_per_step": ms, "steps": ksteps,
+            "phases_ms": {"factor": ph[0], "solve": ph[1], "diag_inverse": ph[2]},
+            "solve_gbs": solve_bytes / (ph[1] / 1e3) / 1e9, "solve_hbm_frac": solve_bytes / (ph[1] / 1e3) / 1e9 / HBM_GBS,
             "dtype": "f32 updates / f64 pivots, refinement and variance sums",
             "fp64_sequential_value": seq, "speedup_vs_fp64_sequential": value / (world * seq),
             "max_rel_err_var_band0_vs_fp64": err, "max_rel_err_x_band0_vs_fp64": errx,
@@ -595,6 +622,7 @@ def main():
         "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
                       "diag_inverse": statistics.mean(t_dia)},
         "factor_tflops": info["factor_flops"] / (statistics.mean(t_fac) / 1e3) / 1e12,
+        "solve_gbs": 2.0 * info["nnz_l_stored"] * 8 / (statistics.mean(t_sol) / 1e3) / 1e9,
         "factor_flops": info["factor_flops"], "diag_flops": info["diag_flops_all"],
         "diag_work_flops": info["diag_work_flops"],
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],

@@ -79,7 +79,7 @@ def workload(name):
 def config_of(pb, extra=None):
     c = {"workload": f"{pb.cfg.name}: SPI normal matrix, P={pb.cfg.n_pointings} pointings x 19 detectors, "
                      f"{pb.cfg.n_sources} sources, time-bins {pb.cfg.bin_lo}-{pb.cfg.bin_hi} pointings, "
-                     f"detector-pattern block {pb.cfg.det_block}; step = factor + solve + full diag(N^-1)",
+                     f"detector-pattern block {pb.cfg.det_block}; step = factor, then solve (FP64 refinement in the mixed form) and full diag(N^-1) concurrently on two streams",
          "n": pb.n, "nnz_lower": pb.nnz, "seed": pb.cfg.seed, "l2": "flushed (256 MiB write) between timed steps"}
     if extra:
         c.update(extra)
@@ -223,6 +223,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def overlapped_step(factor, solve, diag, st, st2, ev=None):
+    """One step: the factorization on `st`; then the variances on `st2`
+    concurrently with the solve (and its refinement) on `st` -- both read only
+    the factor; `st` waits for `st2` at the end.  `ev`: six timing events
+    (start, factor end, solve end, step end, variances start, variances end)."""
+    import torch
+    if ev: ev[0].record(st)
+    factor(st)
+    if ev: ev[1].record(st)
+    done = torch.cuda.Event()
+    done.record(st)
+    st2.wait_event(done)
+    if ev: ev[4].record(st2)
+    diag(st2)
+    if ev: ev[5].record(st2)
+    solve(st)
+    if ev: ev[2].record(st)
+    st.wait_stream(st2)
+    if ev: ev[3].record(st)
+
+
+def _phases(evs):
+    """Mean factor, solve, variance and whole-step ms of overlapped steps."""
+    return (statistics.mean(e[0].elapsed_time(e[1]) for e in evs), statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+            statistics.mean(e[4].elapsed_time(e[5]) for e in evs), statistics.mean(e[0].elapsed_time(e[3]) for e in evs))
+
+
 def _time_steps(step, nsteps, warmup, st, flush):
     import torch
     for _ in range(warmup):
@@ -257,24 +284,19 @@ def bench_bands(P, args, dev, st, flush, world):
     s = P.Solver(n, bb.colptr, bb.rowind, batch=nb, precision=P.SPI_PREC_MIXED_FP32, async_=True)
 
     evs = []
+    st2 = torch.cuda.Stream(dev)
 
     def step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(st)
-        s.factor_batch(vals, stream=st)
-        ev[1].record(st)
-        s.solve_batch(b, x, stream=st)
-        ev[2].record(st)
-        s.diag_inverse_batch(out=var, stream=st)
-        ev[3].record(st)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        overlapped_step(lambda q: s.factor_batch(vals, stream=q), lambda q: s.solve_batch(b, x, stream=q),
+                        lambda q: s.diag_inverse_batch(out=var, stream=q), st, st2, ev)
         evs.append(ev)
 
     ksteps = max(1, min(args.steps, 3))
     ms = _time_steps(step, ksteps, max(3, min(args.warmup, 3)), st, flush)
     s.sync(st)
     info = s.info()
-    timed = evs[-ksteps:]
-    ph = [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in timed) for i in range(3)]
+    ph = _phases(evs[-ksteps:])
     # the solve reads every band's stored factor twice (forward and backward sweeps), per solve
     nsolves = 1 + info["refine_steps"]
     solve_bytes = 2.0 * nsolves * nb * info["nnz_l_stored"] * 8
@@ -286,9 +308,8 @@ def bench_bands(P, args, dev, st, flush, world):
     var1 = torch.empty(n, dtype=torch.float64, device=dev)
 
     def step1():
-        s1.factor(v1, stream=st)
-        s1.solve(b1, x1, stream=st)
-        s1.diag_inverse(out=var1, stream=st)
+        overlapped_step(lambda q: s1.factor(v1, stream=q), lambda q: s1.solve(b1, x1, stream=q),
+                        lambda q: s1.diag_inverse(out=var1, stream=q), st, st2)
 
     ms1 = _time_steps(step1, ksteps, 3, st, flush)
     s1.sync(st)
@@ -323,10 +344,11 @@ def bench_uneven(P, args, dev, st, flush, world):
     var = torch.empty(ntot, dtype=torch.float64, device=dev)
     s = P.Solver.for_problems(probs, async_=True)
 
+    st2 = torch.cuda.Stream(dev)
+
     def step():
-        s.factor(vals, stream=st)
-        s.solve(b, x, stream=st)
-        s.diag_inverse(out=var, stream=st)
+        overlapped_step(lambda q: s.factor(vals, stream=q), lambda q: s.solve(b, x, stream=q),
+                        lambda q: s.diag_inverse(out=var, stream=q), st, st2)
 
     ksteps = max(1, min(args.steps, 3))
     ms = _time_steps(step, ksteps, 3, st, flush)
@@ -340,9 +362,9 @@ def bench_uneven(P, args, dev, st, flush, world):
         for i, q in enumerate(singles):
             a, e = int(offs[i]), int(offs[i + 1])
             vo = int(sum(pp.nnz for pp in probs[:i]))
-            q.factor(vals[vo:vo + probs[i].nnz], stream=st)
-            q.solve(b[a:e], xs[a:e], stream=st)
-            q.diag_inverse(out=vs[a:e], stream=st)
+            overlapped_step(lambda r: q.factor(vals[vo:vo + probs[i].nnz], stream=r),
+                            lambda r: q.solve(b[a:e], xs[a:e], stream=r),
+                            lambda r: q.diag_inverse(out=vs[a:e], stream=r), st, st2)
 
     ms1 = _time_steps(step1, ksteps, 3, st, flush)
     for q in singles:
@@ -357,28 +379,25 @@ def bench_uneven(P, args, dev, st, flush, world):
 
 
 def _time_phases(s, vals, b, x, idx, var, nsteps, warmup, st, flush):
-    """Mean device ms of factor / solve / diag_inverse over nsteps timed steps."""
+    """Mean device ms of factor / solve / diag_inverse / whole overlapped step
+    over nsteps timed steps."""
     import torch
+    st2 = torch.cuda.Stream()
 
     def step(ev=None):
-        if ev: ev[0].record(st)
-        s.factor(vals, stream=st)
-        if ev: ev[1].record(st)
-        s.solve(b, x, stream=st)
-        if ev: ev[2].record(st)
-        s.diag_inverse(idx, out=var, stream=st)
-        if ev: ev[3].record(st)
+        overlapped_step(lambda q: s.factor(vals, stream=q), lambda q: s.solve(b, x, stream=q),
+                        lambda q: s.diag_inverse(idx, out=var, stream=q), st, st2, ev)
 
     for _ in range(warmup):
         step(); flush.zero_()
     s.sync(st)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(nsteps)]
     torch.cuda.synchronize()
     for k in range(nsteps):
         step(evs[k]); flush.zero_()
     torch.cuda.synchronize()
     s.sync(st)
-    return [statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(3)]
+    return _phases(evs)
 
 
 def bench_sky(P, args, dev, st, flush, world):
@@ -401,10 +420,10 @@ def bench_sky(P, args, dev, st, flush, world):
         s = P.Solver.for_problem(pb, async_=True, precision=prec, relax=args.relax)
         x = torch.empty_like(b)
         var = torch.empty(pb.n_sky, dtype=torch.float64, device=dev)
-        f, so, d = _time_phases(s, vals, b, x, idx, var, ksteps, 3, st, flush)
+        f, so, d, tot = _time_phases(s, vals, b, x, idx, var, ksteps, 3, st, flush)
         info = s.info()
         res[name] = (x, var)
-        out[name] = {"value": world * pb.n_sky / ((f + so + d) / 1e3), "ms_per_step": f + so + d,
+        out[name] = {"value": world * pb.n_sky / (tot / 1e3), "ms_per_step": tot,
                      "phases_ms": {"factor": f, "solve": so, "diag_inverse": d},
                      "factor_tflops": info["factor_flops"] / (f / 1e3) / 1e12,
                      "diag_tflops": info["diag_flops"] / (d / 1e3) / 1e12,
@@ -457,21 +476,18 @@ def main():
     var = torch.empty(pb.n, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    st2 = torch.cuda.Stream(dev)
+
     def step(ev=None):
-        if ev: ev[0].record(st)
-        s.factor(vals, stream=st)
-        if ev: ev[1].record(st)
-        s.solve(b, x, stream=st)
-        if ev: ev[2].record(st)
-        s.diag_inverse(out=var, stream=st)
-        if ev: ev[3].record(st)
+        overlapped_step(lambda q: s.factor(vals, stream=q), lambda q: s.solve(b, x, stream=q),
+                        lambda q: s.diag_inverse(out=var, stream=q), st, st2, ev)
 
     for _ in range(args.warmup):
         step()
         flush.zero_()
     s.sync(st)
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -483,8 +499,8 @@ def main():
     s.sync(st)
     t_fac = [e[0].elapsed_time(e[1]) for e in evs]
     t_sol = [e[1].elapsed_time(e[2]) for e in evs]
-    t_dia = [e[2].elapsed_time(e[3]) for e in evs]
-    total_ms = sum(a + b_ + c for a, b_, c in zip(t_fac, t_sol, t_dia))
+    t_dia = [e[4].elapsed_time(e[5]) for e in evs]
+    total_ms = sum(e[0].elapsed_time(e[3]) for e in evs)
     tot = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
@@ -528,18 +544,13 @@ def main():
         varm = torch.empty_like(var)
 
         def mstep(ev=None):
-            if ev: ev[0].record(st)
-            sm_.factor(vals, stream=st)
-            if ev: ev[1].record(st)
-            sm_.solve(b, xm, stream=st)
-            if ev: ev[2].record(st)
-            sm_.diag_inverse(out=varm, stream=st)
-            if ev: ev[3].record(st)
+            overlapped_step(lambda q: sm_.factor(vals, stream=q), lambda q: sm_.solve(b, xm, stream=q),
+                            lambda q: sm_.diag_inverse(out=varm, stream=q), st, st2, ev)
 
         for _ in range(args.warmup):
             mstep(); flush.zero_()
         sm_.sync(st)
-        mevs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        mevs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
         torch.cuda.synchronize(dev)
         for k in range(args.steps):
             mstep(mevs[k]); flush.zero_()
@@ -547,8 +558,8 @@ def main():
         sm_.sync(st)
         mf = [e[0].elapsed_time(e[1]) for e in mevs]
         ms_ = [e[1].elapsed_time(e[2]) for e in mevs]
-        md = [e[2].elapsed_time(e[3]) for e in mevs]
-        mtot = sum(a + b_ + c for a, b_, c in zip(mf, ms_, md))
+        md = [e[4].elapsed_time(e[5]) for e in mevs]
+        mtot = sum(e[0].elapsed_time(e[3]) for e in mevs)
         minfo = sm_.info()
         mixed = {"value": world * pb.n * args.steps / (mtot / 1e3), "unit": UNIT, "ms_per_step": mtot / args.steps,
                  "phases_ms": {"factor": statistics.mean(mf), "solve": statistics.mean(ms_),

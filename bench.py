@@ -629,6 +629,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(pb, {"ordering": "nested dissection", "rhs_block": args.rhs_block,
+                                 "streams": "after the factor, solve and variances run concurrently on two streams; "
+                                            "phases_ms are each phase's own span, ms_per_step the whole step",
                                  "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
         "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
                       "diag_inverse": statistics.mean(t_dia)},

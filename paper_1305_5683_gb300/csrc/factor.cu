@@ -315,21 +315,23 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
         Lj[i][c] = (i < nj && c < w) ? (C)(P[(cj + i) + (int64_t)(c0 + c) * m] * D[f + c0 + c]) : C(0);
     }
     __syncthreads();
-    const int jj = tid % kT, i0 = tid / kT;
-    if (jj < nj) {
+    // thread owns row ii and columns j0 + 4 q: a warp's lanes run down one
+    // column, so its read-modify-writes of the panel are coalesced
+    const int ii = tid % kT, j0 = tid / kT;
+    if (ii < ni) {
         C acc[kT / 4];
 #pragma unroll
-        for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
+        for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
 #pragma unroll 4
         for (int c = 0; c < kT; ++c) {
-            const C bj = Lj[jj][c];
+            const C ai = Li[ii][c];
 #pragma unroll
-            for (int r = 0; r < kT / 4; ++r) acc[r] += Li[i0 + 4 * r][c] * bj;
+            for (int q = 0; q < kT / 4; ++q) acc[q] += ai * Lj[j0 + 4 * q][c];
         }
 #pragma unroll
-        for (int r = 0; r < kT / 4; ++r) {
-            const int i = i0 + 4 * r;
-            if (i < ni && ri + i >= cj + jj) P[(ri + i) + (int64_t)(cj + jj) * m] -= (double)acc[r];
+        for (int q = 0; q < kT / 4; ++q) {
+            const int jj = j0 + 4 * q;
+            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] -= (double)acc[q];
         }
     }
     if (ti == 0 && tj == 0) {
@@ -359,10 +361,12 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     const double* P = L + d.lptr[s];
     const int64_t ib = k + (int64_t)ti * kT, jb = k + (int64_t)tj * kT;
     const int ni = (int)(m - ib < kT ? m - ib : kT), nj = (int)(m - jb < kT ? m - jb : kT);
-    const int jj = tid % kT, i0 = tid / kT;  // thread owns column jj, rows i0 + 4 r
+    // thread owns row ii and columns j0 + 4 q: a warp's lanes run down one
+    // column, so its atomics into the parent hit consecutive rows
+    const int ii = tid % kT, j0 = tid / kT;
     C acc[kT / 4];
 #pragma unroll
-    for (int r = 0; r < kT / 4; ++r) acc[r] = C(0);
+    for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
     for (int cb = 0; cb < k; cb += kT) {
         const int cw = min(kT, k - cb);
         __syncthreads();
@@ -374,9 +378,9 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
         __syncthreads();
 #pragma unroll 4
         for (int c = 0; c < kT; ++c) {
-            const C bj = Lj[jj][c];
+            const C ai = Li[ii][c];
 #pragma unroll
-            for (int r = 0; r < kT / 4; ++r) acc[r] -= Li[i0 + 4 * r][c] * bj;
+            for (int q = 0; q < kT / 4; ++q) acc[q] -= ai * Lj[j0 + 4 * q][c];
         }
     }
     const int64_t fo = d.f22ptr[s];
@@ -386,17 +390,17 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     double* Pp = L + d.lptr[p];
     double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
     const int32_t* rel = d.relmap + d.srowptr[s];
-    if (jj >= nj) return;
-    const int64_t jl = jb + jj;
-    const int qj = rel[jl];
+    if (ii >= ni) return;
+    const int64_t il = ib + ii;
+    const int qi = rel[il];
 #pragma unroll
-    for (int r = 0; r < kT / 4; ++r) {
-        const int i = i0 + 4 * r;
-        const int64_t il = ib + i;
-        if (i >= ni || il < jl) continue;
-        double v = (double)acc[r];
+    for (int q = 0; q < kT / 4; ++q) {
+        const int jj = j0 + 4 * q;
+        const int64_t jl = jb + jj;
+        if (jj >= nj || il < jl) continue;
+        double v = (double)acc[q];
         if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
-        const int qi = rel[il];
+        const int qj = rel[jl];
         if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
         else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
     }

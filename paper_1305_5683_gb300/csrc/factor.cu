@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
 #pragma unroll
         for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
 #pragma unroll 4
-        for (int c = 0; c < kT; ++c) {
+        for (int c = 0; c < w; ++c) {  // the block column's w pivots (FP64 is a narrow pipe: no padding)
             const C ai = Li[ii][c];
 #pragma unroll
             for (int q = 0; q < kT / 4; ++q) acc[q] += ai * Lj[j0 + 4 * q][c];
@@ -376,11 +376,13 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
             Lj[i][c] = (i < nj && c < cw) ? (C)(P[(jb + i) + (int64_t)(cb + c) * m] * D[f + cb + c]) : C(0);
         }
         __syncthreads();
+        if (ii < ni) {
 #pragma unroll 4
-        for (int c = 0; c < kT; ++c) {
-            const C ai = Li[ii][c];
+            for (int c = 0; c < cw; ++c) {  // only the chunk's cw pivots (grouped leaves: often < 32)
+                const C ai = Li[ii][c];
 #pragma unroll
-            for (int q = 0; q < kT / 4; ++q) acc[q] -= ai * Lj[j0 + 4 * q][c];
+                for (int q = 0; q < kT / 4; ++q) acc[q] -= ai * Lj[j0 + 4 * q][c];
+            }
         }
     }
     const int64_t fo = d.f22ptr[s];

@@ -244,6 +244,20 @@ def overlapped_step(factor, solve, diag, st, st2, ev=None):
     if ev: ev[3].record(st)
 
 
+def _time_alone(fn, st, reps=3):
+    """Mean device ms of fn(st) run by itself (nothing concurrent), after one untimed call."""
+    import torch
+    fn(st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        fn(st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def _phases(evs):
     """Mean factor, solve, variance and whole-step ms of overlapped steps."""
     return (statistics.mean(e[0].elapsed_time(e[1]) for e in evs), statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
@@ -297,6 +311,7 @@ def bench_bands(P, args, dev, st, flush, world):
     s.sync(st)
     info = s.info()
     ph = _phases(evs[-ksteps:])
+    solve_alone = _time_alone(lambda q: s.solve_batch(b, x, stream=q), st)
     # the solve reads every band's stored factor twice (forward and backward sweeps), per solve
     nsolves = 1 + info["refine_steps"]
     solve_bytes = 2.0 * nsolves * nb * info["nnz_l_stored"] * 8
@@ -321,7 +336,8 @@ def bench_bands(P, args, dev, st, flush, world):
                         f"n={n}, nnz_lower={bb.nnz}), E log-spaced 20-1000 keV, responses x (E/20)^-alpha",
             "value": value, "unit": UNIT, "ms_per_step": ms, "steps": ksteps,
             "phases_ms": {"factor": ph[0], "solve": ph[1], "diag_inverse": ph[2]},
-            "solve_gbs": solve_bytes / (ph[1] / 1e3) / 1e9, "solve_hbm_frac": solve_bytes / (ph[1] / 1e3) / 1e9 / HBM_GBS,
+            "solve_alone_ms": solve_alone, "solve_gbs": solve_bytes / (solve_alone / 1e3) / 1e9,
+            "solve_hbm_frac": solve_bytes / (solve_alone / 1e3) / 1e9 / HBM_GBS,
             "dtype": "f32 updates / f64 pivots, refinement and variance sums",
             "fp64_sequential_value": seq, "speedup_vs_fp64_sequential": value / (world * seq),
             "max_rel_err_var_band0_vs_fp64": err, "max_rel_err_x_band0_vs_fp64": errx,
@@ -507,6 +523,7 @@ def main():
     total_ms = float(tot.item())
     info = s.info()
     value = world * pb.n * args.steps / (total_ms / 1e3)
+    solve_alone = _time_alone(lambda q: s.solve(b, x, stream=q), st)
 
     # end to end through the public API with pinned host buffers (copies inside)
     hv = torch.from_numpy(pb.values).pin_memory()
@@ -635,7 +652,8 @@ def main():
         "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
                       "diag_inverse": statistics.mean(t_dia)},
         "factor_tflops": info["factor_flops"] / (statistics.mean(t_fac) / 1e3) / 1e12,
-        "solve_gbs": 2.0 * info["nnz_l_stored"] * 8 / (statistics.mean(t_sol) / 1e3) / 1e9,
+        "solve_alone_ms": solve_alone,
+        "solve_gbs": 2.0 * info["nnz_l_stored"] * 8 / (solve_alone / 1e3) / 1e9,
         "factor_flops": info["factor_flops"], "diag_flops": info["diag_flops_all"],
         "diag_work_flops": info["diag_work_flops"],
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],

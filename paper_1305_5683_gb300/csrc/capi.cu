@@ -47,7 +47,9 @@ struct spi_ctx {
     DevStatus* d_status = nullptr;
     DevStatus* h_status = nullptr;
     // mixed precision: FP32 copy of the panels, the input pattern for the FP64 residual
-    float* d_L32 = nullptr;
+    float* d_L32 = nullptr;   // also the working panels of the mixed factorization
+    float* d_F22f = nullptr;  // mixed form: FP32 update areas
+    float* d_Df = nullptr;    // mixed form: D in FP32 (scaling in the update kernels)
     int64_t* d_cp = nullptr;
     int32_t* d_ri = nullptr;
     double *d_b2 = nullptr, *d_x = nullptr, *d_r = nullptr, *d_dx = nullptr, *d_norm = nullptr, *h_norm = nullptr;
@@ -144,7 +146,7 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
-    CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total * nb));
+    if (!mixed_of(c)) CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total * nb));
     CK(dev_alloc(c, &c->d_D, (size_t)S.n * nb));
     CK(dev_alloc(c, &c->d_adiag, (size_t)S.n * nb));
     CK(dev_alloc(c, &c->d_vals, (size_t)S.nnz_a * nb));
@@ -158,6 +160,8 @@ int ensure_device(spi_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     if (mixed_of(c)) {
         CK(dev_alloc(c, &c->d_L32, (size_t)S.lptr[S.ns] * nb));
+        CK(dev_alloc(c, &c->d_F22f, (size_t)S.f22_total * nb));
+        CK(dev_alloc(c, &c->d_Df, (size_t)S.n * nb));
         CK(dev_upload(c, &c->d_cp, c->in_colptr));
         CK(dev_upload(c, &c->d_ri, c->in_rowind));
         std::vector<int64_t>().swap(c->in_colptr);
@@ -270,9 +274,14 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
         vals = c->d_vals;
     }
     k_reset_status<<<1, 1, 0, st>>>(c->d_status);
-    CK(cudaMemsetAsync(c->d_L, 0, (size_t)S.lptr[S.ns] * nb * sizeof(double), st));
-    if (S.f22_total) CK(cudaMemsetAsync(c->d_F22, 0, (size_t)S.f22_total * nb * sizeof(double), st));
-    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, c->d_L, c->d_diag_src, c->d_adiag, nb, c->bs, st);
+    // panels and update areas in the factorization's storage type (FP32 in the mixed form)
+    void* Lw = mixed ? (void*)c->d_L32 : (void*)c->d_L;
+    void* Fw = mixed ? (void*)c->d_F22f : (void*)c->d_F22;
+    void* DS = mixed ? (void*)c->d_Df : (void*)c->d_D;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    CK(cudaMemsetAsync(Lw, 0, (size_t)S.lptr[S.ns] * nb * esz, st));
+    if (S.f22_total) CK(cudaMemsetAsync(Fw, 0, (size_t)S.f22_total * nb * esz, st));
+    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, Lw, mixed, c->d_diag_src, c->d_adiag, nb, c->bs, st);
     CK(run_graph(c, c->g_factor, nb, st, [&](cudaStream_t s2) {
         for (const Launch& l : c->FP.launches) {
             const int32_t* items = l.kind == 0 ? c->d_items0
@@ -281,10 +290,11 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
                                  : l.kind == 7 ? c->d_items7
                                  : l.kind == 8 ? c->d_items8
                                  : l.kind == 9 ? c->d_items9 : c->d_items3;
-            launch_factor_step(c->dsym, l, items, c->d_L, c->d_F22, c->d_D, c->d_adiag, c->d_status, mixed, nb,
-                               c->bs, c->opt.wait_limit, s2);
+            launch_factor_step(c->dsym, l, items, Lw, Fw, c->d_D, DS, c->d_adiag, c->d_status, mixed, nb, c->bs,
+                               c->opt.wait_limit, s2);
         }
-        if (mixed) launch_to_f32(c->d_L, c->d_L32, S.lptr[S.ns] * nb, s2);
+        // the solves, inverse blocks and the allocation-free variances read the FP64 panels
+        if (mixed) launch_to_f64(c->d_L32, c->d_L, S.lptr[S.ns] * nb, s2);
     }));
     rc = finish(c, st);
     if (rc == SPI_OK) {

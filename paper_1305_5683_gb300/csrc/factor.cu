@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "spi_internal.cuh"
 
@@ -138,30 +139,33 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
 
 namespace {
 
+template <typename S>
 __global__ void k_assemble(const int64_t* __restrict__ amap, const double* __restrict__ vals, int64_t nnz,
-                           double* __restrict__ L, const int32_t* __restrict__ diag_src, int32_t n,
+                           S* __restrict__ L, const int32_t* __restrict__ diag_src, int32_t n,
                            double* __restrict__ adiag, Strides bs) {
     vals += blockIdx.y * bs.nnz;
     L += blockIdx.y * bs.L;
     adiag += blockIdx.y * bs.n;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = i; p < nnz; p += stride) L[amap[p]] = vals[p];
+    for (int64_t p = i; p < nnz; p += stride) L[amap[p]] = (S)vals[p];
     for (int64_t j = i; j < n; j += stride) adiag[j] = vals[diag_src[j]];
 }
 
 constexpr int kThreads = 128;
 
 // Unblocked LDL^T, in FP64, of the w x w pivot tile whose first pivot is
-// column c0 of supernode s (panel P, leading dimension m), by the CTA's 128
-// threads; writes L (unit lower, d on the diagonal) back into P and d into D.
-__device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, double* __restrict__ P, int64_t m, int c0,
-                                  int w, int f, double* __restrict__ D, const double* __restrict__ adiag,
-                                  DevStatus* status, int band_base) {
+// column c0 of supernode s (panel P of storage type S, leading dimension m),
+// by the CTA's 128 threads; writes L (unit lower, d on the diagonal) back into
+// P, d into D (FP64) and into DS (the storage type's copy used for scaling).
+template <typename S>
+__device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, S* __restrict__ P, int64_t m, int c0, int w,
+                                  int f, double* __restrict__ D, S* __restrict__ DS,
+                                  const double* __restrict__ adiag, DevStatus* status, int band_base) {
     const int tid = threadIdx.x;
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        A[i][j] = (i < w && j <= i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
+        A[i][j] = (i < w && j <= i) ? (double)P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
     }
     // FP64 is a narrow pipe on this GPU: one thread forms each pivot's
     // reciprocal, and the update visits only the trailing square.
@@ -192,20 +196,25 @@ __device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, double* __res
     __syncthreads();
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (i == j) ? dv[i] : A[i][j];
+        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (S)((i == j) ? dv[i] : A[i][j]);
     }
-    if (tid < w) D[f + c0 + tid] = dv[tid];
+    if (tid < w) {
+        D[f + c0 + tid] = dv[tid];
+        DS[f + c0 + tid] = (S)dv[tid];
+    }
 }
 
 // Pivot tile of block column 0 of every supernode of a level (the pivot
 // tiles of later block columns are factored by the trailing-update CTA that
 // writes them last, k_panel_update).
+template <typename S>
 __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t* __restrict__ items, int b,
-                                                        double* __restrict__ L, double* __restrict__ D,
+                                                        S* __restrict__ L, double* __restrict__ D, S* __restrict__ DS,
                                                         const double* __restrict__ adiag, DevStatus* status,
                                                         Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
     adiag += blockIdx.y * bs.n;
     __shared__ double A[kT][kT + 1];
     __shared__ double dv[kT];
@@ -213,35 +222,40 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const int c0 = b * kT;
-    factor_pivot_tile(A, dv, L + d.lptr[s], m, c0, min(kT, k - c0), f, D, adiag, status,
+    factor_pivot_tile(A, dv, L + d.lptr[s], m, c0, min(kT, k - c0), f, D, DS, adiag, status,
                       (int)(blockIdx.y * bs.n));
 }
 
 // Front with a diagonal pivot block (independent leaf columns grouped into
-// one front): d_c is the assembled diagonal entry and L21(:, c) = F21(:, c) / d_c.
+// one front, no children): d_c is the input diagonal entry (kept in FP64 in
+// adiag) and L21(:, c) = F21(:, c) / d_c.
+template <typename S>
 __global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t* __restrict__ items,
-                                                         double* __restrict__ L, double* __restrict__ D,
+                                                         S* __restrict__ L, double* __restrict__ D, S* __restrict__ DS,
                                                          const double* __restrict__ adiag, DevStatus* status,
                                                          Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
     adiag += blockIdx.y * bs.n;
     const int tid = threadIdx.x;
     const int s = items[blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    double* P = L + d.lptr[s];
+    S* P = L + d.lptr[s];
     for (int c = tid; c < k; c += kThreads) {
-        const double dc = P[c + (int64_t)c * m];
-        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c]) {
+        const double dc = adiag[f + c];
+        if (!(dc > 0.0)) {
             atomicOr(&status->flags, FLAG_NOT_SPD);
             atomicMin(&status->bad_pivot, (int)(blockIdx.y * bs.n) + f + c);
         }
         D[f + c] = dc;
+        DS[f + c] = (S)dc;
+        P[c + (int64_t)c * m] = (S)dc;
     }
     // one reciprocal per column (uniform across the CTA), then scale its rows
     for (int c = 0; c < k; ++c) {
-        const double rc = 1.0 / P[c + (int64_t)c * m];
+        const S rc = (S)(1.0 / adiag[f + c]);
         for (int64_t r = k + tid; r < m; r += kThreads) P[r + (int64_t)c * m] *= rc;
     }
 }
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t
 // the block columns before it): L21 = X L11^-T D^-1, one thread per row.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t* __restrict__ items, int b,
-                                                         double* __restrict__ L, const double* __restrict__ D,
+                                                         C* __restrict__ L, const double* __restrict__ D,
                                                          Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
@@ -261,14 +275,14 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
     const int s = items[2 * blockIdx.x], rt = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    double* P = L + d.lptr[s];
+    C* P = L + d.lptr[s];
     const int c0 = b * kT, w = min(kT, k - c0);
     const int64_t r0 = c0 + w + (int64_t)rt * kT;
     const int nr = (int)(m - r0 < kT ? m - r0 : kT);
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        X[i][j] = (i < nr && j < w) ? (C)P[(r0 + i) + (int64_t)(c0 + j) * m] : C(0);
-        Bd[i][j] = (i < w && j < i) ? (C)P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
+        X[i][j] = (i < nr && j < w) ? P[(r0 + i) + (int64_t)(c0 + j) * m] : C(0);
+        Bd[i][j] = (i < w && j < i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
     }
     if (tid < kT) dv[tid] = (tid < w) ? (C)(1.0 / D[f + c0 + tid]) : C(0);
     __syncthreads();
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
     __syncthreads();
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        if (i < nr && j < w) P[(r0 + i) + (int64_t)(c0 + j) * m] = (double)(X[i][j] * dv[j]);
+        if (i < nr && j < w) P[(r0 + i) + (int64_t)(c0 + j) * m] = X[i][j] * dv[j];
     }
 }
 
@@ -291,11 +305,12 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
 // [c0+w, k) and rows i >= j, P[i][j] -= sum_{c in block b} L[i][c] d_c L[j][c].
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32_t* __restrict__ items, int b,
-                                                           double* __restrict__ L, double* __restrict__ D,
-                                                           const double* __restrict__ adiag, DevStatus* status,
-                                                           Strides bs) {
+                                                           C* __restrict__ L, double* __restrict__ D,
+                                                           C* __restrict__ DS, const double* __restrict__ adiag,
+                                                           DevStatus* status, Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
     adiag += blockIdx.y * bs.n;
     __shared__ C Li[kT][kT + 1];
     __shared__ C Lj[kT][kT + 1];
@@ -303,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
     const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    double* P = L + d.lptr[s];
+    C* P = L + d.lptr[s];
     const int c0 = b * kT, w = min(kT, k - c0);
     const int cj = c0 + w + tj * kT;
     const int64_t ri = cj + (int64_t)ti * kT;
@@ -311,8 +326,8 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
     const int ni = (int)(m - ri < kT ? m - ri : kT);
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, c = e / kT;
-        Li[i][c] = (i < ni && c < w) ? (C)P[(ri + i) + (int64_t)(c0 + c) * m] : C(0);
-        Lj[i][c] = (i < nj && c < w) ? (C)(P[(cj + i) + (int64_t)(c0 + c) * m] * D[f + c0 + c]) : C(0);
+        Li[i][c] = (i < ni && c < w) ? P[(ri + i) + (int64_t)(c0 + c) * m] : C(0);
+        Lj[i][c] = (i < nj && c < w) ? P[(cj + i) + (int64_t)(c0 + c) * m] * DS[f + c0 + c] : C(0);
     }
     __syncthreads();
     // thread owns row ii and columns j0 + 4 q: a warp's lanes run down one
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
 #pragma unroll
         for (int q = 0; q < kT / 4; ++q) {
             const int jj = j0 + 4 * q;
-            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] -= (double)acc[q];
+            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] -= acc[q];
         }
     }
     if (ti == 0 && tj == 0) {
@@ -339,18 +354,18 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
         __shared__ double A[kT][kT + 1];
         __shared__ double dv[kT];
         __syncthreads();
-        factor_pivot_tile(A, dv, P, m, cj, nj, f, D, adiag, status, (int)(blockIdx.y * bs.n));
+        factor_pivot_tile(A, dv, P, m, cj, nj, f, D, DS, adiag, status, (int)(blockIdx.y * bs.n));
     }
 }
 
 // Schur complement tile (ti, tj) of the trailing (m-k)^2 part, added into the parent's front.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int32_t* __restrict__ items,
-                                                            double* __restrict__ L, double* __restrict__ F22,
-                                                            const double* __restrict__ D, Strides bs) {
+                                                            C* __restrict__ L, C* __restrict__ F22,
+                                                            const C* __restrict__ DS, Strides bs) {
     L += blockIdx.y * bs.L;
     F22 += blockIdx.y * bs.F22;
-    D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
     __shared__ C Li[kT][kT + 1];
     __shared__ C Lj[kT][kT + 1];
     const int tid = threadIdx.x;
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const int64_t mb = m - k;
-    const double* P = L + d.lptr[s];
+    const C* P = L + d.lptr[s];
     const int64_t ib = k + (int64_t)ti * kT, jb = k + (int64_t)tj * kT;
     const int ni = (int)(m - ib < kT ? m - ib : kT), nj = (int)(m - jb < kT ? m - jb : kT);
     // thread owns row ii and columns j0 + 4 q: a warp's lanes run down one
@@ -372,8 +387,8 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
         __syncthreads();
         for (int e = tid; e < kT * kT; e += kThreads) {
             int i = e % kT, c = e / kT;
-            Li[i][c] = (i < ni && c < cw) ? (C)P[(ib + i) + (int64_t)(cb + c) * m] : C(0);
-            Lj[i][c] = (i < nj && c < cw) ? (C)(P[(jb + i) + (int64_t)(cb + c) * m] * D[f + cb + c]) : C(0);
+            Li[i][c] = (i < ni && c < cw) ? P[(ib + i) + (int64_t)(cb + c) * m] : C(0);
+            Lj[i][c] = (i < nj && c < cw) ? P[(jb + i) + (int64_t)(cb + c) * m] * DS[f + cb + c] : C(0);
         }
         __syncthreads();
         if (ii < ni) {
@@ -389,8 +404,8 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     const int p = d.sparent[s];
     const int kp = d.sfirst[p + 1] - d.sfirst[p];
     const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
-    double* Pp = L + d.lptr[p];
-    double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+    C* Pp = L + d.lptr[p];
+    C* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
     const int32_t* rel = d.relmap + d.srowptr[s];
     if (ii >= ni) return;
     const int64_t il = ib + ii;
@@ -400,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
         const int jj = j0 + 4 * q;
         const int64_t jl = jb + jj;
         if (jj >= nj || il < jl) continue;
-        double v = (double)acc[q];
+        C v = acc[q];
         if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
         const int qj = rel[jl];
         if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
@@ -496,12 +511,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, uint32_
 // subtracted in place from the panel (one CTA owns each tile: no atomics).
 template <int kMode>
 __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __restrict__ items, int step,
-                                                  double* __restrict__ L, double* __restrict__ F22,
-                                                  const double* __restrict__ D, DevStatus* status, Strides bs,
+                                                  float* __restrict__ L, float* __restrict__ F22,
+                                                  const float* __restrict__ DS, DevStatus* status, Strides bs,
                                                   uint32_t stage_wait_limit) {
     L += blockIdx.y * bs.L;
     F22 += blockIdx.y * bs.F22;
-    D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
     extern __shared__ __align__(1024) float tcs[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tcs + 2 * kTcStageFloats);  // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -509,7 +524,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     const int s = items[3 * blockIdx.x], ti = items[3 * blockIdx.x + 1], tj = items[3 * blockIdx.x + 2];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    double* P = L + d.lptr[s];
+    float* P = L + d.lptr[s];
     // K range [kb0, kb1); output rows from ib, columns from jb below jlim
     const int c1 = (step + 1) * kT;
     const int kb0 = kMode == 0 ? 0 : c1 - kOuter, kb1 = kMode == 0 ? k : c1;
@@ -533,16 +548,16 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
                            ((uint32_t)(kTcM >> 4) << 24);
     const int nk = (kb1 - kb0 + kTcK - 1) / kTcK;
     // row tid of A (rows from ib) and of B (rows from jb, scaled by D) for one K chunk
-    double ra[kTcK], rb[kTcK];
+    float ra[kTcK], rb[kTcK];
     auto fetch = [&](int kc) {
         const int cb = kb0 + kc * kTcK, cw = min(kTcK, kb1 - cb);
         const bool rowa = ib + tid < m, rowb = jb + tid < jlim;
-        const double* pa = P + (ib + tid) + (int64_t)cb * m;
-        const double* pb = P + (jb + tid) + (int64_t)cb * m;
+        const float* pa = P + (ib + tid) + (int64_t)cb * m;
+        const float* pb = P + (jb + tid) + (int64_t)cb * m;
 #pragma unroll
         for (int c = 0; c < kTcK; ++c) {
-            ra[c] = (c < cw && rowa) ? pa[(int64_t)c * m] : 0.0;
-            rb[c] = (c < cw && rowb) ? pb[(int64_t)c * m] * D[f + cb + c] : 0.0;
+            ra[c] = (c < cw && rowa) ? pa[(int64_t)c * m] : 0.f;
+            rb[c] = (c < cw && rowb) ? pb[(int64_t)c * m] * DS[f + cb + c] : 0.f;
         }
     };
     if (nk > 0) fetch(0);
@@ -562,17 +577,17 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         for (int c4 = 0; c4 < kTcK / 4; ++c4) {
             const int o = tc_kmajor_off(tid, 4 * c4) >> 2;
             float4 h, mi, lo;
-            tc_split3((float)ra[4 * c4 + 0], h.x, mi.x, lo.x);
-            tc_split3((float)ra[4 * c4 + 1], h.y, mi.y, lo.y);
-            tc_split3((float)ra[4 * c4 + 2], h.z, mi.z, lo.z);
-            tc_split3((float)ra[4 * c4 + 3], h.w, mi.w, lo.w);
+            tc_split3(ra[4 * c4 + 0], h.x, mi.x, lo.x);
+            tc_split3(ra[4 * c4 + 1], h.y, mi.y, lo.y);
+            tc_split3(ra[4 * c4 + 2], h.z, mi.z, lo.z);
+            tc_split3(ra[4 * c4 + 3], h.w, mi.w, lo.w);
             *reinterpret_cast<float4*>(Ah + o) = h;
             *reinterpret_cast<float4*>(Am + o) = mi;
             *reinterpret_cast<float4*>(Al + o) = lo;
-            tc_split3((float)rb[4 * c4 + 0], h.x, mi.x, lo.x);
-            tc_split3((float)rb[4 * c4 + 1], h.y, mi.y, lo.y);
-            tc_split3((float)rb[4 * c4 + 2], h.z, mi.z, lo.z);
-            tc_split3((float)rb[4 * c4 + 3], h.w, mi.w, lo.w);
+            tc_split3(rb[4 * c4 + 0], h.x, mi.x, lo.x);
+            tc_split3(rb[4 * c4 + 1], h.y, mi.y, lo.y);
+            tc_split3(rb[4 * c4 + 2], h.z, mi.z, lo.z);
+            tc_split3(rb[4 * c4 + 3], h.w, mi.w, lo.w);
             *reinterpret_cast<float4*>(Bh + o) = h;
             *reinterpret_cast<float4*>(Bm + o) = mi;
             *reinterpret_cast<float4*>(Bl + o) = lo;
@@ -618,7 +633,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t jl = jb + q * 32 + j;
-                    if (jl < k && jl <= il) P[il + jl * m] -= (double)__uint_as_float(r[j]);
+                    if (jl < k && jl <= il) P[il + jl * m] -= __uint_as_float(r[j]);
                 }
             }
         }
@@ -628,8 +643,8 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         const int p = d.sparent[s];
         const int kp = d.sfirst[p + 1] - d.sfirst[p];
         const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
-        double* Pp = L + d.lptr[p];
-        double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+        float* Pp = L + d.lptr[p];
+        float* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
         const int32_t* rel = d.relmap + d.srowptr[s];
         const int64_t il = ib + warp * 32 + lane;
         const int qi = il < m ? rel[il] : 0;
@@ -641,7 +656,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
                 for (int j = 0; j < 32; ++j) {
                     const int64_t jl = jb + q * 32 + j;
                     if (jl >= m || jl > il) continue;
-                    double v = -(double)__uint_as_float(r[j]);
+                    float v = -__uint_as_float(r[j]);
                     if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
                     const int qj = rel[jl];
                     if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
@@ -655,9 +670,9 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN));
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+__global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
+        b[i] = (double)a[i];
 }
 
 }  // namespace
@@ -668,48 +683,62 @@ cudaError_t factor_kernel_setup() {
     return cudaFuncSetAttribute(k_schur_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
 }
 
-void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
+void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t st) {
     if (n == 0) return;
     int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-    k_to_f32<<<grid, 256, 0, st>>>(a, b, n);
+    k_to_f64<<<grid, 256, 0, st>>>(a, b, n);
 }
 
-void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
+void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, void* L, bool mixed,
                      const int32_t* diag_src, double* adiag, int nb, const Strides& bs, cudaStream_t st) {
     int64_t work = std::max<int64_t>(nnz, d.n);
     if (work == 0 || nb == 0) return;
     int grid = (int)std::min<int64_t>((work + 255) / 256, std::max(1, 152 * 16 / nb));
-    k_assemble<<<dim3(grid, nb), 256, 0, st>>>(amap, vals, nnz, L, diag_src, d.n, adiag, bs);
+    if (mixed)
+        k_assemble<float><<<dim3(grid, nb), 256, 0, st>>>(amap, vals, nnz, (float*)L, diag_src, d.n, adiag, bs);
+    else
+        k_assemble<double><<<dim3(grid, nb), 256, 0, st>>>(amap, vals, nnz, (double*)L, diag_src, d.n, adiag, bs);
 }
 
+// C is both the arithmetic and the storage type of the panels and update
+// areas: double in the FP64 form, float in the mixed form (whose pivot tiles
+// are still factored in FP64 and whose pivots D stay FP64; DS is D in C).
 template <typename C>
-void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22, double* D,
+void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, C* L, C* F22, double* D, C* DS,
                    const double* adiag, DevStatus* status, int nb, const Strides& bs, int wait_limit,
                    cudaStream_t st) {
     const dim3 g(l.count, nb);
     switch (l.kind) {
-        case 0: k_diag_tile<<<g, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, adiag, status, bs); break;
+        case 0: k_diag_tile<C><<<g, kThreads, 0, st>>>(d, items + l.off, l.step, L, D, DS, adiag, status, bs); break;
         case 1: k_panel_trsm<C><<<g, kThreads, 0, st>>>(d, items + 2 * l.off, l.step, L, D, bs); break;
-        case 3: k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, adiag, status, bs);
+        case 3:
+            k_panel_update<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, l.step, L, D, DS, adiag, status, bs);
             break;
         case 7:
-        case 9: {
-            const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kTcWaitLimit;
-            if (l.kind == 7) k_schur_tc<0><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, 0, L, F22, D, status, bs, lim);
-            else k_schur_tc<1><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, l.step, L, F22, D, status, bs, lim);
+        case 9:
+            if constexpr (std::is_same<C, float>::value) {  // tensor-core items exist only in the mixed form
+                const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kTcWaitLimit;
+                if (l.kind == 7)
+                    k_schur_tc<0><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, 0, L, F22, DS, status, bs, lim);
+                else
+                    k_schur_tc<1><<<g, 128, kTcSmem, st>>>(d, items + 3 * l.off, l.step, L, F22, DS, status, bs, lim);
+            }
             break;
-        }
-        case 8: k_diag_front<<<g, kThreads, 0, st>>>(d, items + l.off, L, D, adiag, status, bs); break;
-        default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, D, bs); break;
+        case 8: k_diag_front<C><<<g, kThreads, 0, st>>>(d, items + l.off, L, D, DS, adiag, status, bs); break;
+        default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, DS, bs); break;
     }
 }
 
-void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
-                        const Strides& bs, int wait_limit, cudaStream_t st) {
+void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, void* L, void* F22, double* D,
+                        void* DS, const double* adiag, DevStatus* status, bool mixed, int nb, const Strides& bs,
+                        int wait_limit, cudaStream_t st) {
     if (l.count == 0 || nb == 0) return;
-    if (mixed) launch_step_t<float>(d, l, items, L, F22, D, adiag, status, nb, bs, wait_limit, st);
-    else launch_step_t<double>(d, l, items, L, F22, D, adiag, status, nb, bs, wait_limit, st);
+    if (mixed)
+        launch_step_t<float>(d, l, items, (float*)L, (float*)F22, D, (float*)DS, adiag, status, nb, bs, wait_limit,
+                             st);
+    else
+        launch_step_t<double>(d, l, items, (double*)L, (double*)F22, D, (double*)DS, adiag, status, nb, bs,
+                              wait_limit, st);
 }
 
 }  // namespace spi

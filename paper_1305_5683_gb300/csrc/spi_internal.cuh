@@ -101,12 +101,15 @@ struct DevDiagPlan {
 };
 
 // ---- kernel launchers (factor.cu)
-void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, double* L,
+// The factorization's panels L and update areas F22 hold double in the FP64
+// form and float in the mixed form (void* below); D is always FP64, DS is D
+// in the panels' type (the same array as D in the FP64 form).
+void launch_assemble(const DevSym& d, const int64_t* amap, const double* vals, int64_t nnz, void* L, bool mixed,
                      const int32_t* diag_src, double* adiag, int nb, const Strides& bs, cudaStream_t st);
-void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, double* L, double* F22,
-                        double* D, const double* adiag, DevStatus* status, bool mixed, int nb,
-                        const Strides& bs, int wait_limit, cudaStream_t st);
-void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, void* L, void* F22, double* D,
+                        void* DS, const double* adiag, DevStatus* status, bool mixed, int nb, const Strides& bs,
+                        int wait_limit, cudaStream_t st);
+void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t st);
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st);

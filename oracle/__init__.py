@@ -145,3 +145,28 @@ class OracleFactor:
     def inv_diag_flops(self, idx=None) -> float:
         idx = np.arange(self.n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, np.int32)
         return float(self._lib.oracle_inv_diag_flops(self._h, _ptr(idx), len(idx)))
+
+
+def normal_equations(H, w, y, colptr, rowind):
+    """The normal equations of the weighted least-squares problem (Eq. 7):
+    N = H^T W H and b = H^T W y with W = diag(w), H any scipy sparse matrix
+    (rows = observations).  N is returned as values on the given lower CSC
+    pattern (0 where the pattern holds a structural zero of N), b densely.
+    The product is a plain sparse matrix product (the paper's Sec. 4.1 is
+    about computing it efficiently; this is the definition)."""
+    import scipy.sparse as sp
+    Hc = sp.csc_matrix(H)
+    N = (Hc.T @ sp.diags(np.asarray(w, dtype=np.float64)) @ Hc).tocsc()
+    N.sort_indices()
+    colptr = np.asarray(colptr, dtype=np.int64)
+    rowind = np.asarray(rowind, dtype=np.int32)
+    vals = np.zeros(len(rowind), dtype=np.float64)
+    for j in range(len(colptr) - 1):
+        rows = N.indices[N.indptr[j]:N.indptr[j + 1]]
+        data = N.data[N.indptr[j]:N.indptr[j + 1]]
+        want = rowind[colptr[j]:colptr[j + 1]]
+        pos = np.searchsorted(rows, want)
+        ok = (pos < len(rows)) & (rows[np.minimum(pos, max(len(rows) - 1, 0))] == want) if len(rows) else np.zeros(len(want), bool)
+        vals[colptr[j]:colptr[j + 1]][ok] = data[pos[ok]]
+    b = Hc.T @ (np.asarray(w, dtype=np.float64) * np.asarray(y, dtype=np.float64))
+    return vals, np.asarray(b).ravel()

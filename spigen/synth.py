@@ -212,7 +212,7 @@ def _bins_for_sources(rng, cfg: SpiConfig):
 
 def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
              band_scale: np.ndarray | None = None, counts_seed: int | None = None,
-             dense_design: bool = False) -> SpiProblem:
+             dense_design: bool = False, sparse_design: bool = False) -> SpiProblem:
     """Build the problem for `cfg`.
 
     noise=False replaces the Poisson draw by y = H x_true exactly (the
@@ -222,6 +222,9 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     the Poisson draw.  dense_design=True (small problems only) also returns
     the dense design matrix H and the weights as attributes `H` and `w` of
     the problem, assembled row block by row block, for checking N = H^T W H.
+    sparse_design=True returns H as a scipy CSR matrix instead (rows =
+    (pointing, detector) in order, columns ascending within a row), with
+    the weights w and counts y, for assembling N = H^T W H elsewhere.
     """
     rng = np.random.default_rng(cfg.seed)
     P, nd = cfg.n_pointings, N_DET
@@ -346,6 +349,17 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
             p1 = min(P, p0 + window)
             cols, Hw, _ = window_block(p0, p1)
             Hd[p0 * nd:p1 * nd][:, cols] = Hw
+    if sparse_design:
+        parts = []
+        for p0 in range(0, P, window):
+            p1 = min(P, p0 + window)
+            cols, Hw, _ = window_block(p0, p1)
+            o = np.argsort(cols)
+            hw = sp.csr_matrix(Hw[:, o])
+            hw.indices = cols[o][hw.indices].astype(np.int32)
+            parts.append(sp.csr_matrix((hw.data, hw.indices, hw.indptr), shape=(Hw.shape[0], n)))
+        Hd = sp.vstack(parts, format="csr")
+        Hd.sort_indices()
     if noise:
         crng = rng if counts_seed is None else np.random.default_rng(counts_seed)
         y = crng.poisson(e).astype(np.float64)
@@ -402,7 +416,7 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
                     rowind=low.indices.astype(np.int32), values=low.data.astype(np.float64),
                     b=bvec, x_true=x_true, kind=kind, n_pointing=P, n_detcol=ndet, n_bins=nbins,
                     n_sky=nsky)
-    if dense_design:
+    if dense_design or sparse_design:
         pb.H, pb.w, pb.y = Hd, w, y
     return pb
 

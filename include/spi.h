@@ -218,6 +218,41 @@ int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int
  * repeated), SPI_ERR_OOM, SPI_ERR_CUDA. */
 int spi_inverse_block(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream);
 
+/* The normal equations on the device (paper Sec. 4.1, Eq. 7): N = H^T W H on
+ * the pattern this context was analysed with, and b = H^T W y, from the design
+ * matrix H (rows = observations) -- the step before spi_factor, and its update
+ * after the values of some columns of H changed (paper Table 3).
+ *
+ * spi_normal_setup records H's pattern (host CSR: rowptr int64[nrows + 1],
+ * colind int32[rowptr[nrows]], columns ascending within a row, caller
+ * numbering of N's unknowns) and groups consecutive rows with nearly the same
+ * columns (for SPI, the detectors of one pointing).  Only for a context made by
+ * spi_analyse (one pattern).  Errors: SPI_ERR_ARG, SPI_ERR_PATTERN (bad CSR),
+ * SPI_ERR_STATE (a multi-problem context), SPI_ERR_OOM, SPI_ERR_CUDA. */
+int spi_normal_setup(spi_ctx* ctx, int64_t nrows, const int64_t* rowptr, const int32_t* colind);
+
+/* N's lower-CSC values in the order of the analysed pattern (the values
+ * spi_factor takes) and b = H^T W y:
+ *   hvals float64[nnz(H)] in the CSR order of spi_normal_setup, w and y
+ *   float64[nrows] (weights and observations), nvals float64[nnz(N)],
+ *   b float64[n].
+ * on_device: every buffer is a device pointer.  FP64 throughout; entries of N
+ * are sums of per-group products added with FP64 atomics (their order, and so
+ * their last bits, may vary from call to call).  Returns after the stream has
+ * drained.  Errors: SPI_ERR_STATE (no setup), SPI_ERR_ARG, SPI_ERR_PATTERN (a
+ * nonzero product of H has no place in N's pattern), SPI_ERR_CUDA. */
+int spi_normal_assemble(spi_ctx* ctx, const double* hvals, const double* w, const double* y, double* nvals,
+                        double* b, int on_device, void* stream);
+
+/* Update nvals and b (as returned by spi_normal_assemble, in place) after the
+ * values of H in the columns cols[0..ncols) (host int32, caller numbering)
+ * changed: every entry of N in a row or column of those unknowns, and their
+ * entries of b, are recomputed from hvals, w, y (the complete new values);
+ * only the row groups that hold those columns are visited.  Other arguments
+ * and errors as spi_normal_assemble. */
+int spi_normal_update(spi_ctx* ctx, int64_t ncols, const int32_t* cols, const double* hvals, const double* w,
+                      const double* y, double* nvals, double* b, int on_device, void* stream);
+
 /* Variances without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
  * need variances -- a host thread that must not enter the CUDA allocator (a

@@ -70,6 +70,21 @@ struct spi_ctx {
     bool plan_blk_ready = false;
     double* d_blk = nullptr;
     double* d_zg = nullptr;      // gathered vectors (rows of the paths' union x indices)
+    // spi_normal_*: the design matrix's row groups (host and device) and scratch
+    struct Normal {
+        bool ready = false;
+        int64_t nrows = 0, nnzh = 0;
+        int32_t ngroups = 0;
+        size_t smem = 0;
+        std::vector<int64_t> grp_row;
+        std::vector<int32_t> row_grp;
+        std::vector<int64_t> hcp;  // H's pattern by columns: rows of each column
+        std::vector<int32_t> hri;
+        NormalArgs args{};
+        int32_t *d_groups = nullptr, *d_sel = nullptr, *d_flag = nullptr;
+        uint8_t* d_mark = nullptr;
+        double *d_hv = nullptr, *d_w = nullptr, *d_y = nullptr, *d_nv = nullptr, *d_b = nullptr;
+    } nrm;
     int64_t zg_cap = 0, blk_rows = 0;
     int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
@@ -162,10 +177,8 @@ int ensure_device(spi_ctx* c) {
         CK(dev_alloc(c, &c->d_L32, (size_t)S.lptr[S.ns] * nb));
         CK(dev_alloc(c, &c->d_F22f, (size_t)S.f22_total * nb));
         CK(dev_alloc(c, &c->d_Df, (size_t)S.n * nb));
-        CK(dev_upload(c, &c->d_cp, c->in_colptr));
-        CK(dev_upload(c, &c->d_ri, c->in_rowind));
-        std::vector<int64_t>().swap(c->in_colptr);
-        std::vector<int32_t>().swap(c->in_rowind);
+        if (!c->d_cp) CK(dev_upload(c, &c->d_cp, c->in_colptr));
+        if (!c->d_ri) CK(dev_upload(c, &c->d_ri, c->in_rowind));
         CK(dev_alloc(c, &c->d_b2, (size_t)S.n * nb));
         CK(dev_alloc(c, &c->d_x, (size_t)S.n * nb));
         CK(dev_alloc(c, &c->d_r, (size_t)S.n * nb));
@@ -614,7 +627,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     try {
         build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32);
         build_solve_plan(c->S, c->SP);
-        if (o.precision == SPI_PREC_MIXED_FP32 && n > 0) {
+        if (n > 0) {  // the residual of the mixed form and the normal-equation assembly use it
             c->in_colptr.assign(colptr, colptr + n + 1);
             c->in_rowind.assign(rowind, rowind + colptr[n]);
         }
@@ -761,6 +774,192 @@ int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out,
         CK(cudaStreamSynchronize(st));
     }
     return finish(c, st);
+}
+
+int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int32_t* colind) {
+    if (!c || nrows < 0 || (nrows > 0 && (!rowptr || !colind))) return SPI_ERR_ARG;
+    const int32_t n = c->S.n;
+    if ((int64_t)c->in_colptr.size() != (int64_t)n + 1) return SPI_ERR_STATE;  // a single analysed pattern
+    if (nrows > 0 && rowptr[0] != 0) return SPI_ERR_PATTERN;
+    for (int64_t r = 0; r < nrows; ++r) {
+        if (rowptr[r + 1] < rowptr[r]) return SPI_ERR_PATTERN;
+        for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            if (colind[e] < 0 || colind[e] >= n) return SPI_ERR_PATTERN;
+            if (e > rowptr[r] && colind[e] <= colind[e - 1]) return SPI_ERR_PATTERN;
+        }
+    }
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    auto& N = c->nrm;
+    N = spi_ctx::Normal();
+    const int64_t nnzh = nrows ? rowptr[nrows] : 0;
+    N.nrows = nrows;
+    N.nnzh = nnzh;
+    // row groups: consecutive rows while the union of their columns grows by at most
+    // 32 beyond the first row's, at most 32 rows and 8,192 dense entries
+    constexpr int kMaxRows = 32, kGrow = 32, kMaxDense = 8192;
+    std::vector<int64_t> gcolptr{0};
+    std::vector<int32_t> gcols, entpos((size_t)nnzh);
+    std::vector<int32_t> uni, cand;
+    int32_t max_rows = 1, max_dense = 0;
+    N.row_grp.assign((size_t)nrows, 0);
+    int64_t r = 0;
+    while (r < nrows) {
+        uni.assign(colind + rowptr[r], colind + rowptr[r + 1]);
+        const size_t base = uni.size();
+        int64_t R = 1;
+        while (r + R < nrows && R < kMaxRows) {
+            cand.clear();
+            std::set_union(uni.begin(), uni.end(), colind + rowptr[r + R], colind + rowptr[r + R + 1],
+                           std::back_inserter(cand));
+            if (cand.size() > base + kGrow || (R + 1) * (int64_t)cand.size() > kMaxDense) break;
+            uni.swap(cand);
+            ++R;
+        }
+        const int32_t g = (int32_t)N.grp_row.size();
+        N.grp_row.push_back(r);
+        for (int64_t q = r; q < r + R; ++q) {
+            N.row_grp[(size_t)q] = g;
+            for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e)
+                entpos[(size_t)e] = (int32_t)(std::lower_bound(uni.begin(), uni.end(), colind[e]) - uni.begin());
+        }
+        gcols.insert(gcols.end(), uni.begin(), uni.end());
+        gcolptr.push_back((int64_t)gcols.size());
+        if (R > 1) {
+            max_rows = std::max<int32_t>(max_rows, (int32_t)R);
+            max_dense = std::max<int32_t>(max_dense, (int32_t)(R * (int64_t)uni.size()));
+        }
+        r += R;
+    }
+    N.grp_row.push_back(nrows);
+    N.ngroups = (int32_t)N.grp_row.size() - 1;
+    // H's pattern by columns (the rows of each column), for the column updates
+    N.hcp.assign((size_t)n + 1, 0);
+    for (int64_t e = 0; e < nnzh; ++e) N.hcp[(size_t)colind[e] + 1]++;
+    for (int32_t j = 0; j < n; ++j) N.hcp[(size_t)j + 1] += N.hcp[(size_t)j];
+    N.hri.resize((size_t)nnzh);
+    {
+        std::vector<int64_t> fill(N.hcp.begin(), N.hcp.end() - 1);
+        for (int64_t q = 0; q < nrows; ++q)
+            for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e) N.hri[(size_t)fill[(size_t)colind[e]]++] = (int32_t)q;
+    }
+    std::vector<int64_t> hrow(rowptr, rowptr + nrows + 1);
+    std::vector<int32_t> all((size_t)N.ngroups);
+    for (int32_t g = 0; g < N.ngroups; ++g) all[(size_t)g] = g;
+    int64_t *d_rowptr = nullptr, *d_grow = nullptr, *d_gcp = nullptr;
+    int32_t *d_entpos = nullptr, *d_gcols = nullptr;
+    CK(dev_upload(c, &d_rowptr, hrow));
+    CK(dev_upload(c, &d_entpos, entpos));
+    CK(dev_upload(c, &d_grow, N.grp_row));
+    CK(dev_upload(c, &d_gcp, gcolptr));
+    CK(dev_upload(c, &d_gcols, gcols));
+    CK(dev_upload(c, &N.d_groups, all));
+    CK(dev_alloc(c, &N.d_sel, (size_t)std::max<int32_t>(N.ngroups, 1)));
+    CK(dev_alloc(c, &N.d_flag, 1));
+    CK(dev_alloc(c, &N.d_mark, (size_t)std::max<int32_t>(n, 1)));
+    CK(dev_alloc(c, &N.d_hv, (size_t)std::max<int64_t>(nnzh, 1)));
+    CK(dev_alloc(c, &N.d_w, (size_t)std::max<int64_t>(nrows, 1)));
+    CK(dev_alloc(c, &N.d_y, (size_t)std::max<int64_t>(nrows, 1)));
+    CK(dev_alloc(c, &N.d_nv, (size_t)std::max<int64_t>(c->S.nnz_a, 1)));
+    CK(dev_alloc(c, &N.d_b, (size_t)std::max<int32_t>(n, 1)));
+    if (!c->d_cp) CK(dev_upload(c, &c->d_cp, c->in_colptr));
+    if (!c->d_ri) CK(dev_upload(c, &c->d_ri, c->in_rowind));
+    N.args = NormalArgs{d_rowptr, d_entpos, d_grow, d_gcp, d_gcols, c->d_cp, c->d_ri};
+    N.smem = normal_smem_bytes(max_dense, max_rows);
+    CK(normal_kernel_setup(N.smem));
+    N.ready = true;
+    return SPI_OK;
+}
+
+namespace {
+// Device copies of the caller's inputs (or the caller's own device buffers).
+int normal_inputs(spi_ctx* c, const double* hvals, const double* w, const double* y, int on_device,
+                  cudaStream_t st, const double** hv, const double** wd, const double** yd) {
+    auto& N = c->nrm;
+    if (on_device) {
+        *hv = hvals; *wd = w; *yd = y;
+        return SPI_OK;
+    }
+    CK(cudaMemcpyAsync(N.d_hv, hvals, (size_t)N.nnzh * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(N.d_w, w, (size_t)N.nrows * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(N.d_y, y, (size_t)N.nrows * sizeof(double), cudaMemcpyHostToDevice, st));
+    *hv = N.d_hv; *wd = N.d_w; *yd = N.d_y;
+    return SPI_OK;
+}
+
+int normal_finish(spi_ctx* c, double* nvals, double* b, int on_device, cudaStream_t st) {
+    auto& N = c->nrm;
+    int flag = 0;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(nvals, N.d_nv, (size_t)c->S.nnz_a * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b, N.d_b, (size_t)c->S.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(&flag, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return flag ? SPI_ERR_PATTERN : SPI_OK;
+}
+}  // namespace
+
+int spi_normal_assemble(spi_ctx* c, const double* hvals, const double* w, const double* y, double* nvals,
+                        double* b, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->nrm.ready) return SPI_ERR_STATE;
+    auto& N = c->nrm;
+    if (!nvals || !b || (N.nnzh > 0 && !hvals) || (N.nrows > 0 && (!w || !y))) return SPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *hv, *wd, *yd;
+    int rc = normal_inputs(c, hvals, w, y, on_device, st, &hv, &wd, &yd);
+    if (rc) return rc;
+    double* nv = on_device ? nvals : N.d_nv;
+    double* bv = on_device ? b : N.d_b;
+    CK(cudaMemsetAsync(nv, 0, (size_t)c->S.nnz_a * sizeof(double), st));
+    CK(cudaMemsetAsync(bv, 0, (size_t)c->S.n * sizeof(double), st));
+    CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+    launch_normal(N.args, N.d_groups, N.ngroups, hv, wd, yd, nullptr, false, nv, bv, N.d_flag, N.smem, st);
+    return normal_finish(c, nvals, b, on_device, st);
+}
+
+int spi_normal_update(spi_ctx* c, int64_t ncols, const int32_t* cols, const double* hvals, const double* w,
+                      const double* y, double* nvals, double* b, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->nrm.ready) return SPI_ERR_STATE;
+    auto& N = c->nrm;
+    const int32_t n = c->S.n;
+    if (ncols < 0 || (ncols > 0 && !cols) || !nvals || !b || (N.nnzh > 0 && !hvals) || (N.nrows > 0 && (!w || !y)))
+        return SPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<uint8_t> mark((size_t)std::max<int32_t>(n, 1), 0);
+    std::vector<char> gsel((size_t)N.ngroups, 0);
+    std::vector<int32_t> sel;
+    for (int64_t t = 0; t < ncols; ++t) {
+        const int32_t j = cols[t];  // caller numbering, host memory
+        if (j < 0 || j >= n) return SPI_ERR_ARG;
+        if (mark[(size_t)j]) continue;
+        mark[(size_t)j] = 1;
+        for (int64_t p = N.hcp[(size_t)j]; p < N.hcp[(size_t)j + 1]; ++p) {
+            const int32_t g = N.row_grp[(size_t)N.hri[(size_t)p]];
+            if (!gsel[(size_t)g]) { gsel[(size_t)g] = 1; sel.push_back(g); }
+        }
+    }
+    const double *hv, *wd, *yd;
+    int rc = normal_inputs(c, hvals, w, y, on_device, st, &hv, &wd, &yd);
+    if (rc) return rc;
+    double* nv = on_device ? nvals : N.d_nv;
+    double* bv = on_device ? b : N.d_b;
+    if (!on_device) {  // the previous N and b are updated in place
+        CK(cudaMemcpyAsync(nv, nvals, (size_t)c->S.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(bv, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+    if (!sel.empty()) {
+        CK(cudaMemcpyAsync(N.d_mark, mark.data(), (size_t)n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(N.d_sel, sel.data(), sel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, N.d_mark, true, nv, bv, N.d_flag, N.smem, st);
+        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, N.d_mark, false, nv, bv, N.d_flag, N.smem,
+                      st);
+    }
+    return normal_finish(c, nvals, b, on_device, st);
 }
 
 int spi_info(const spi_ctx* c, spi_stats* o) {

@@ -133,4 +133,20 @@ cudaError_t diag_kernel_setup(int B);
 void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D,
                           double* var_scratch, double* Zg, int64_t R, double* out, int64_t ldo, cudaStream_t st);
 
+// ---- normal.cu: N = H^T W H and b = H^T W y on the device
+struct NormalArgs {
+    const int64_t* rowptr;      // H's CSR row pointers [nrows + 1]
+    const int32_t* ent_pos;     // per entry of H: its column's index in its group's union
+    const int64_t* grp_row;     // [ngroups + 1] row ranges
+    const int64_t* grp_colptr;  // [ngroups + 1] into grp_cols
+    const int32_t* grp_cols;    // each group's column union, ascending
+    const int64_t* cp;          // N's pattern (caller numbering, lower CSC)
+    const int32_t* ri;
+};
+size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows);
+cudaError_t normal_kernel_setup(size_t smem);
+void launch_normal(const NormalArgs& a, const int32_t* groups, int32_t ngroups, const double* hv, const double* w,
+                   const double* y, const uint8_t* mark, bool zero_pass, double* nv, double* bv, int* flag,
+                   size_t smem, cudaStream_t st);
+
 }  // namespace spi

@@ -25,7 +25,7 @@ SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
-           "spi_inverse_block"]
+           "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update"]
 SPI_INVERSE_BLOCK_MAX = 512
 
 
@@ -90,6 +90,9 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
     L.spi_diag_inverse_noalloc.argtypes = [V, V, I64, V, V]; L.spi_diag_inverse_noalloc.restype = I
     L.spi_inverse_block.argtypes = [V, V, I64, V, I, V]; L.spi_inverse_block.restype = I
+    L.spi_normal_setup.argtypes = [V, I64, V, V]; L.spi_normal_setup.restype = I
+    L.spi_normal_assemble.argtypes = [V, V, V, V, V, V, I, V]; L.spi_normal_assemble.restype = I
+    L.spi_normal_update.argtypes = [V, I64, V, V, V, V, V, V, I, V]; L.spi_normal_update.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -248,6 +251,41 @@ def spi_inverse_block(ctx, idx, out, stream=None) -> None:
     del k1, k2
 
 
+def spi_normal_setup(ctx, rowptr, colind) -> None:
+    """Record the pattern of the design matrix H (CSR, host arrays)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    _check(lib().spi_normal_setup(ctx, len(rp) - 1, rp.ctypes.data_as(ctypes.c_void_p),
+                                  ci.ctypes.data_as(ctypes.c_void_p)), "spi_normal_setup")
+
+
+def _normal_bufs(hvals, w, y, nvals, b):
+    bufs = [_buf(a, np.float64) for a in (hvals, w, y, nvals, b)]
+    devs = {d for _, d, _ in bufs}
+    if len(devs) != 1:
+        raise TypeError("hvals, w, y, nvals and b must all be host or all be device buffers")
+    for a in (nvals, b):
+        if not _is_torch(a) and not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError("nvals and b must be contiguous float64 numpy arrays or CUDA tensors")
+    return bufs, devs.pop()
+
+
+def spi_normal_assemble(ctx, hvals, w, y, nvals, b, stream=None) -> None:
+    """nvals = N = H^T W H on the analysed pattern, b = H^T W y."""
+    bufs, dev = _normal_bufs(hvals, w, y, nvals, b)
+    _check(lib().spi_normal_assemble(ctx, *[p for p, _, _ in bufs], dev, _stream(stream)), "spi_normal_assemble")
+    del bufs
+
+
+def spi_normal_update(ctx, cols, hvals, w, y, nvals, b, stream=None) -> None:
+    """Recompute the entries of N and b touched by the columns `cols` of H."""
+    cc = np.ascontiguousarray(cols, dtype=np.int32)
+    bufs, dev = _normal_bufs(hvals, w, y, nvals, b)
+    _check(lib().spi_normal_update(ctx, len(cc), cc.ctypes.data_as(ctypes.c_void_p), *[p for p, _, _ in bufs],
+                                   dev, _stream(stream)), "spi_normal_update")
+    del bufs
+
+
 def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
     """Variances for device idx into device out without any device allocation
     by the library (fixed scratch array; see include/spi.h)."""
@@ -376,6 +414,29 @@ class Solver:
                 out = np.empty((m, m), np.float64)
         spi_inverse_block(self._h, idx, out, stream)
         return out
+
+    def normal_setup(self, H):
+        """Record the pattern of the design matrix H (scipy sparse, rows = observations)."""
+        import scipy.sparse as sp
+        Hr = sp.csr_matrix(H)
+        Hr.sort_indices()
+        spi_normal_setup(self._h, Hr.indptr, Hr.indices)
+        self._hnnz = Hr.nnz
+        return self
+
+    def normal_assemble(self, hvals, w, y, nvals=None, b=None, stream=None):
+        """(N values on the analysed pattern, b) from H's values in CSR order."""
+        if nvals is None:
+            nvals = np.empty(self.info()["nnz_a"], np.float64)
+        if b is None:
+            b = np.empty(self.n, np.float64)
+        spi_normal_assemble(self._h, hvals, w, y, nvals, b, stream)
+        return nvals, b
+
+    def normal_update(self, cols, hvals, w, y, nvals, b, stream=None):
+        """Update (nvals, b) in place after H's columns `cols` changed."""
+        spi_normal_update(self._h, cols, hvals, w, y, nvals, b, stream)
+        return nvals, b
 
     def info(self) -> dict:
         return spi_info(self._h)

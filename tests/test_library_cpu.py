@@ -155,3 +155,18 @@ def test_compute_without_gpu_fails_loudly(P):
     with pytest.raises(P.SpiError) as e:
         s.inverse_block(np.array([0, 1], np.int32))
     assert e.value.code == 7
+
+
+def test_normal_setup_validates_on_the_host(P):
+    """Pattern checks of the design matrix happen before any device work."""
+    pb = random_spd(20, 0.2, 1)
+    s = P.Solver.for_problem(pb)
+    with pytest.raises(P.SpiError) as e:  # columns not ascending within a row
+        P.spi_normal_setup(s._h, np.array([0, 2], np.int64), np.array([3, 1], np.int32))
+    assert e.value.code == 2
+    with pytest.raises(P.SpiError) as e:  # column out of range
+        P.spi_normal_setup(s._h, np.array([0, 1], np.int64), np.array([20], np.int32))
+    assert e.value.code == 2
+    with pytest.raises(P.SpiError) as e:  # assembly before setup
+        s.normal_assemble(np.zeros(1), np.zeros(1), np.zeros(1))
+    assert e.value.code == 7

@@ -843,6 +843,33 @@ int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int
         for (int64_t q = 0; q < nrows; ++q)
             for (int64_t e = rowptr[q]; e < rowptr[q + 1]; ++e) N.hri[(size_t)fill[(size_t)colind[e]]++] = (int32_t)q;
     }
+    // positions of every group's column pairs in N's pattern (b-major, a >= b), unless the
+    // table would exceed 2^28 entries (the kernel then walks the pattern itself)
+    std::vector<int64_t> pairptr((size_t)N.ngroups + 1, 0);
+    for (int32_t g = 0; g < N.ngroups; ++g) {
+        const int64_t cg = gcolptr[(size_t)g + 1] - gcolptr[(size_t)g];
+        pairptr[(size_t)g + 1] = pairptr[(size_t)g] + cg * (cg + 1) / 2;
+    }
+    std::vector<int32_t> pairpos;
+    const bool table = pairptr.back() <= (int64_t)1 << 28 && c->S.nnz_a < INT32_MAX;
+    if (table) {
+        pairpos.resize((size_t)pairptr.back());
+        const std::vector<int64_t>& ncp = c->in_colptr;
+        const std::vector<int32_t>& nri = c->in_rowind;
+        for (int32_t g = 0; g < N.ngroups; ++g) {
+            const int32_t* C = gcols.data() + gcolptr[(size_t)g];
+            const int64_t cg = gcolptr[(size_t)g + 1] - gcolptr[(size_t)g];
+            int64_t o = pairptr[(size_t)g];
+            for (int64_t b = 0; b < cg; ++b) {
+                int64_t q = ncp[(size_t)C[b]];
+                const int64_t qend = ncp[(size_t)C[b] + 1];
+                for (int64_t a = b; a < cg; ++a) {
+                    while (q < qend && nri[(size_t)q] < C[a]) ++q;
+                    pairpos[(size_t)o++] = (q < qend && nri[(size_t)q] == C[a]) ? (int32_t)q : -1;
+                }
+            }
+        }
+    }
     std::vector<int64_t> hrow(rowptr, rowptr + nrows + 1);
     std::vector<int32_t> all((size_t)N.ngroups);
     for (int32_t g = 0; g < N.ngroups; ++g) all[(size_t)g] = g;
@@ -864,8 +891,18 @@ int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int
     CK(dev_alloc(c, &N.d_b, (size_t)std::max<int32_t>(n, 1)));
     if (!c->d_cp) CK(dev_upload(c, &c->d_cp, c->in_colptr));
     if (!c->d_ri) CK(dev_upload(c, &c->d_ri, c->in_rowind));
-    N.args = NormalArgs{d_rowptr, d_entpos, d_grow, d_gcp, d_gcols, c->d_cp, c->d_ri};
-    N.smem = normal_smem_bytes(max_dense, max_rows);
+    int64_t* d_pairptr = nullptr;
+    int32_t* d_pairpos = nullptr;
+    if (table) {
+        CK(dev_upload(c, &d_pairptr, pairptr));
+        CK(dev_upload(c, &d_pairpos, pairpos));
+    }
+    N.args = NormalArgs{d_rowptr, d_entpos, d_grow, d_gcp, d_gcols, c->d_cp, c->d_ri, d_pairptr, d_pairpos};
+    int32_t max_cols = 1;
+    for (int32_t g = 0; g < N.ngroups; ++g)
+        max_cols = std::max<int32_t>(max_cols, (int32_t)(gcolptr[(size_t)g + 1] - gcolptr[(size_t)g]));
+    N.smem = normal_smem_bytes(max_dense, max_rows, max_cols);
+    if (N.smem > 200 * 1024) return SPI_ERR_ARG;  // a row with too many entries for one CTA's list
     CK(normal_kernel_setup(N.smem));
     N.ready = true;
     return SPI_OK;

@@ -8,12 +8,15 @@
 // sets nearly coincide (for SPI: the detectors of one pointing).  One CTA per
 // group stages the group's rows densely over the union of their columns C
 // (R rows x c columns in shared memory; a single long row is read in place),
-// then each thread takes columns b of the union and walks a = b .. c-1,
-// forming g_ab = sum_r w_r h_ra h_rb and adding it to N's entry
-// (C[a], C[b]).  That entry's position is found by walking column C[b] of the
-// pattern upward: the union and the pattern's rows are both ascending.
-// Groups share entries of N, so the adds are FP64 atomics.  A product term
-// with no place in the pattern sets an error flag.
+// then takes the columns b of the union one at a time (u_r = w_r h_rb in
+// shared memory) and spreads a = b .. c-1 over its threads, each forming
+// g_ab = sum_r u_r h_ra and adding it to N's entry
+// (C[a], C[b]).  That entry's position comes from a table the host builds at
+// setup (pair (a, b) of group g at pairptr[g] + b c - b (b - 1) / 2 + a - b,
+// -1 when the pattern has no such entry); when the table would be too large
+// it is found by binary search in column C[b] of the pattern.  Groups share entries of N, so
+// the adds are FP64 atomics.  A product term with no place in the pattern
+// sets an error flag.
 #include <cuda_runtime.h>
 
 #include "spi_internal.cuh"
@@ -61,45 +64,84 @@ __global__ void __launch_bounds__(kNThreads) k_normal_group(NormalArgs a, const 
         ws[2 * r] = w[r0 + r];
         ws[2 * r + 1] = w[r0 + r] * y[r0 + r];
     }
+    // update: the group's marked columns, as a list of union indices (ascending)
+    int32_t* ml = reinterpret_cast<int32_t*>(ws + 2 * R);
+    double* us = ws + 2 * R;  // u_r = w_r h_rb of the current column b (after ml's space)
+    __shared__ int nml;
+    if (tid == 0) {
+        int k = 0;
+        if (mark)
+            for (int aa = 0; aa < c; ++aa)
+                if (mark[C[aa]]) ml[k++] = aa;
+        nml = k;
+    }
     __syncthreads();
+    us += (nml + 1) / 2;  // doubles after the list (the list holds at most c ints)
     const double* h1 = hv + a.rowptr[r0];  // the single row's values, in union order
     auto H = [&](int r, int col) { return dense ? Hs[(size_t)r * c + col] : h1[col]; };
-    for (int b = tid; b < c; b += kNThreads) {
+    // columns b one at a time across the CTA: g_ab = sum_r u_r h_ra for a = b .. c-1
+    // (with a mark and an unmarked b: only the marked a)
+    for (int b = 0; b < c; ++b) {
         const int32_t j = C[b];
         const bool mb = mark ? mark[j] != 0 : true;
-        // b_j = sum_r w_r y_r h_rj
-        if (mark == nullptr || mb) {
+        if (kPass == 1 && tid < R) us[tid] = ws[2 * tid] * H(tid, b);
+        if (tid == kNThreads - 1 && mb) {  // b_j = sum_r w_r y_r h_rj
             if (kPass == 0) {
                 bv[j] = 0.0;
             } else {
-                double s = 0.0;
-                for (int r = 0; r < R; ++r) s += ws[2 * r + 1] * H(r, b);
-                atomicAdd(bv + j, s);
+                double sb = 0.0;
+                for (int r = 0; r < R; ++r) sb += ws[2 * r + 1] * H(r, b);
+                atomicAdd(bv + j, sb);
             }
         }
-        int64_t q = a.cp[j];
-        const int64_t qend = a.cp[j + 1];
-        for (int aa = b; aa < c; ++aa) {
+        __syncthreads();
+        const int32_t* pt = a.pairpos ? a.pairpos + a.pairptr[g] + (int64_t)b * c - (int64_t)b * (b - 1) / 2 - b
+                                      : nullptr;
+        int t0 = 0;
+        if (!mb) {  // first marked a >= b
+            int lo = 0, hi = nml;
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (ml[mid] < b) lo = mid + 1; else hi = mid; }
+            t0 = lo;
+        }
+        const int cnt = mb ? c - b : nml - t0;
+        for (int t = tid; t < cnt; t += kNThreads) {
+            const int aa = mb ? b + t : ml[t0 + t];
             const int32_t i = C[aa];
-            if (mark && !mb && !mark[i]) continue;
-            while (q < qend && a.ri[q] < i) ++q;
-            const bool found = q < qend && a.ri[q] == i;
+            int64_t q;
+            bool found;
+            if (pt) {
+                const int32_t pos = pt[aa];
+                found = pos >= 0;
+                q = pos;
+            } else {  // binary search of row i in column j of the pattern
+                int64_t lo = a.cp[j], hi = a.cp[j + 1];
+                while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (a.ri[mid] < i) lo = mid + 1; else hi = mid; }
+                q = lo;
+                found = q < a.cp[j + 1] && a.ri[q] == i;
+            }
             if (kPass == 0) {
                 if (found) nv[q] = 0.0;
                 continue;
             }
-            double s = 0.0;
-            for (int r = 0; r < R; ++r) s += ws[2 * r] * H(r, aa) * H(r, b);
-            if (found) atomicAdd(nv + q, s);
-            else if (s != 0.0) atomicOr(flag, 1);
+            double sv = 0.0;
+            if (dense) {
+                const double* hc = Hs + aa;
+                for (int r = 0; r < R; ++r) sv += us[r] * hc[(size_t)r * c];
+            } else {
+                sv = us[0] * h1[aa];
+            }
+            if (found) atomicAdd(nv + q, sv);
+            else if (sv != 0.0) atomicOr(flag, 1);
         }
+        __syncthreads();  // us is rewritten for the next column
     }
 }
 
 }  // namespace
 
-size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows) {
-    return sizeof(double) * ((size_t)max_dense_entries + 2 * (size_t)max_rows);
+size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows, int32_t max_cols) {
+    return sizeof(double) * ((size_t)max_dense_entries + 3 * (size_t)max_rows + 1) +
+           sizeof(int32_t) * (size_t)max_cols;
 }
 
 cudaError_t normal_kernel_setup(size_t smem) {

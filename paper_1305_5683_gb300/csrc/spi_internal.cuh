@@ -142,8 +142,10 @@ struct NormalArgs {
     const int32_t* grp_cols;    // each group's column union, ascending
     const int64_t* cp;          // N's pattern (caller numbering, lower CSC)
     const int32_t* ri;
+    const int64_t* pairptr;     // [ngroups]: start of each group's pair table, or null
+    const int32_t* pairpos;     // position in N of pair (a, b), b-major, -1 if absent; or null
 };
-size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows);
+size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows, int32_t max_cols);
 cudaError_t normal_kernel_setup(size_t smem);
 void launch_normal(const NormalArgs& a, const int32_t* groups, int32_t ngroups, const double* hv, const double* w,
                    const double* y, const uint8_t* mark, bool zero_pass, double* nv, double* bv, int* flag,

@@ -343,10 +343,16 @@ __global__ void __launch_bounds__(kThreads) k_panel_update(DevSym d, const int32
 #pragma unroll
             for (int q = 0; q < kT / 4; ++q) acc[q] += ai * Lj[j0 + 4 * q][c];
         }
+        C old[kT / 4];  // loads first, then the stores (no load waits behind a store)
 #pragma unroll
         for (int q = 0; q < kT / 4; ++q) {
             const int jj = j0 + 4 * q;
-            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] -= acc[q];
+            old[q] = (jj < nj && ri + ii >= cj + jj) ? P[(ri + ii) + (int64_t)(cj + jj) * m] : C(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kT / 4; ++q) {
+            const int jj = j0 + 4 * q;
+            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] = old[q] - acc[q];
         }
     }
     if (ti == 0 && tj == 0) {
@@ -410,14 +416,22 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
     if (ii >= ni) return;
     const int64_t il = ib + ii;
     const int qi = rel[il];
+    C f22v[kT / 4];  // the update area's entries and the column maps first, then the atomics
+    int qjv[kT / 4];
+#pragma unroll
+    for (int q = 0; q < kT / 4; ++q) {
+        const int64_t jl = jb + j0 + 4 * q;
+        const bool on = j0 + 4 * q < nj && il >= jl;
+        f22v[q] = (fo >= 0 && on) ? F22[fo + (il - k) + (jl - k) * mb] : C(0);
+        qjv[q] = on ? rel[jl] : 0;
+    }
 #pragma unroll
     for (int q = 0; q < kT / 4; ++q) {
         const int jj = j0 + 4 * q;
         const int64_t jl = jb + jj;
         if (jj >= nj || il < jl) continue;
-        C v = acc[q];
-        if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
-        const int qj = rel[jl];
+        const C v = acc[q] + f22v[q];
+        const int qj = qjv[q];
         if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
         else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
     }
@@ -630,10 +644,17 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
             uint32_t r[32];
             tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
             if (il < m) {
+                // all 32 loads first: a load after a store to the same array would wait for it
+                float old[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t jl = jb + q * 32 + j;
-                    if (jl < k && jl <= il) P[il + jl * m] -= __uint_as_float(r[j]);
+                    old[j] = (jl < k && jl <= il) ? P[il + jl * m] : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t jl = jb + q * 32 + j;
+                    if (jl < k && jl <= il) P[il + jl * m] = old[j] - __uint_as_float(r[j]);
                 }
             }
         }
@@ -652,13 +673,21 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
             uint32_t r[32];
             tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
             if (il < m) {
+                float f22v[32];  // the update area's entries and the column maps first, then the atomics
+                int qjv[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t jl = jb + q * 32 + j;
+                    const bool on = jl < m && jl <= il;
+                    f22v[j] = (fo >= 0 && on) ? F22[fo + (il - k) + (jl - k) * mb] : 0.f;
+                    qjv[j] = on ? rel[jl] : 0;
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t jl = jb + q * 32 + j;
                     if (jl >= m || jl > il) continue;
-                    float v = -__uint_as_float(r[j]);
-                    if (fo >= 0) v += F22[fo + (il - k) + (jl - k) * mb];
-                    const int qj = rel[jl];
+                    const float v = f22v[j] - __uint_as_float(r[j]);
+                    const int qj = qjv[j];
                     if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
                     else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
                 }

@@ -226,9 +226,10 @@ int spi_inverse_block(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* ou
  * spi_normal_setup records H's pattern (host CSR: rowptr int64[nrows + 1],
  * colind int32[rowptr[nrows]], columns ascending within a row, caller
  * numbering of N's unknowns) and groups consecutive rows with nearly the same
- * columns (for SPI, the detectors of one pointing).  Only for a context made by
- * spi_analyse (one pattern).  Errors: SPI_ERR_ARG, SPI_ERR_PATTERN (bad CSR),
- * SPI_ERR_STATE (a multi-problem context), SPI_ERR_OOM, SPI_ERR_CUDA. */
+ * columns (for SPI, the detectors of one pointing) and tables the positions of
+ * their column pairs in N's pattern.  Once per context, made by spi_analyse
+ * (one pattern).  Errors: SPI_ERR_ARG, SPI_ERR_PATTERN (bad CSR), SPI_ERR_STATE
+ * (a multi-problem context, or a second call), SPI_ERR_OOM, SPI_ERR_CUDA. */
 int spi_normal_setup(spi_ctx* ctx, int64_t nrows, const int64_t* rowptr, const int32_t* colind);
 
 /* N's lower-CSC values in the order of the analysed pattern (the values

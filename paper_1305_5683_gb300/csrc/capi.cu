@@ -788,6 +788,7 @@ int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int
             if (e > rowptr[r] && colind[e] <= colind[e - 1]) return SPI_ERR_PATTERN;
         }
     }
+    if (c->nrm.ready) return SPI_ERR_STATE;  // once per context
     int rc = ensure_device(c);
     if (rc) return rc;
     auto& N = c->nrm;

@@ -170,3 +170,51 @@ def normal_equations(H, w, y, colptr, rowind):
         vals[colptr[j]:colptr[j + 1]][ok] = data[pos[ok]]
     b = Hc.T @ (np.asarray(w, dtype=np.float64) * np.asarray(y, dtype=np.float64))
     return vals, np.asarray(b).ravel()
+
+
+def cash(H, y, x):
+    """The Cash statistic C(x) = sum_i (e_i - y_i ln e_i), e = H x (the
+    likelihood of the appendix on Poisson fitting, up to the factor -2 and a
+    constant); terms with y_i = 0 are e_i."""
+    e = np.asarray(H @ x).ravel()
+    yy = np.asarray(y, dtype=np.float64)
+    t = e.copy()
+    pos = yy > 0
+    t[pos] -= yy[pos] * np.log(e[pos])
+    return float(t.sum())
+
+
+def mle_newton(H, y, x0, max_iter=30, tol=1e-12):
+    """Poisson maximum-likelihood fit by Newton's method, as the paper's
+    appendix states it: minimise C(x) = sum (e - y ln e), e = H x, with
+    gradient H^T (1 - y/e) and Hessian H^T diag(y/e^2) H; each step solves
+    Hess dx = H^T (y/e - 1) (a dense solve here), halving the step until
+    every e stays positive and C does not increase; stops when
+    ||dx|| <= tol ||x|| (2-norms) or after max_iter steps.  Returns
+    (x, diag(Hess^-1) at x, steps taken)."""
+    import scipy.sparse as sp
+    Hs = sp.csr_matrix(H)
+    yy = np.asarray(y, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64)
+    steps = 0
+    for it in range(max_iter):
+        e = np.asarray(Hs @ x).ravel()
+        if np.any(e <= 0):
+            raise ValueError("the model must be positive at the starting point")
+        Hess = (Hs.T @ sp.diags(yy / e ** 2) @ Hs).toarray()
+        g = np.asarray(Hs.T @ (yy / e - 1.0)).ravel()
+        dx = np.linalg.solve(Hess, g)
+        c0, t = cash(Hs, yy, x), 1.0
+        for _ in range(60):
+            xt = x + t * dx
+            et = np.asarray(Hs @ xt).ravel()
+            if np.all(et > 0) and cash(Hs, yy, xt) <= c0:
+                break
+            t *= 0.5
+        x = x + t * dx
+        steps += 1
+        if np.linalg.norm(t * dx) <= tol * np.linalg.norm(x):
+            break
+    e = np.asarray(Hs @ x).ravel()
+    Hess = (Hs.T @ sp.diags(yy / e ** 2) @ Hs).toarray()
+    return x, np.diag(np.linalg.inv(Hess)).copy(), steps

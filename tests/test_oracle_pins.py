@@ -295,3 +295,38 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            str(so), str(mutated), "-lm"])
     lib = oracle.load_library(str(so))
     assert run_pins(lib) != [], f"planted mistake '{name}' was not caught"
+
+
+def test_mle_oracle_pins():
+    """The Poisson maximum-likelihood oracle: noise-free counts give x_true
+    back; at its fit the gradient H^T (1 - y/e) vanishes and C did not grow
+    from the start; its gradient and Hessian formulas agree with finite
+    differences of C itself."""
+    import scipy.sparse as sp
+    pb = generate(TINY, sparse_design=True, noise=False)
+    x0 = np.linalg.solve(pb.full_matrix().toarray(), pb.b)
+    x, v, _ = oracle.mle_newton(pb.H, pb.y, x0)
+    assert np.abs(x - pb.x_true).max() <= 1e-10 * np.abs(pb.x_true).max()
+    pb = generate(TINY, sparse_design=True)
+    x0 = np.linalg.solve(pb.full_matrix().toarray(), pb.b)
+    x, v, _ = oracle.mle_newton(pb.H, pb.y, x0)
+    e = pb.H @ x
+    g = pb.H.T @ (1.0 - pb.y / e)
+    assert np.abs(g).max() <= 1e-9 * np.abs(pb.H.T @ np.ones_like(e)).max()
+    assert oracle.cash(pb.H, pb.y, x) <= oracle.cash(pb.H, pb.y, x0)
+    assert np.all(v > 0)
+    # finite differences of C along two coordinates, at a point off the optimum
+    H = sp.csr_matrix(pb.H)
+    xp = x * 1.01
+    ep = H @ xp
+    grad = H.T @ (1.0 - pb.y / ep)
+    hess = (H.T @ sp.diags(pb.y / ep ** 2) @ H).tocsc()
+    for j in (3, pb.n - 2):
+        h = 1e-6 * max(1.0, abs(xp[j]))
+        d = np.zeros(pb.n); d[j] = h
+        fd = (oracle.cash(H, pb.y, xp + d) - oracle.cash(H, pb.y, xp - d)) / (2 * h)
+        assert abs(fd - grad[j]) <= 1e-5 * max(1.0, abs(grad[j]))
+        h2 = 1e-3 * max(1.0, abs(xp[j]))  # wider step: the second difference cancels more
+        d2 = np.zeros(pb.n); d2[j] = h2
+        fd2 = (oracle.cash(H, pb.y, xp + d2) - 2 * oracle.cash(H, pb.y, xp) + oracle.cash(H, pb.y, xp - d2)) / h2 ** 2
+        assert abs(fd2 - hess[j, j]) <= 1e-3 * hess[j, j]

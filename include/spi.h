@@ -113,6 +113,8 @@ typedef struct spi_stats {
     int64_t rhs_block;      /* right-hand sides per block in use (chosen by the autotuner when
                                spi_options.rhs_block = 0) */
     double analyse_seconds; /* host time of spi_analyse */
+    int64_t mle_steps;      /* Newton steps of the last spi_mle_newton */
+    double mle_cash;        /* its final Cash statistic sum (e - y ln e) */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;
@@ -253,6 +255,27 @@ int spi_normal_assemble(spi_ctx* ctx, const double* hvals, const double* w, cons
  * and errors as spi_normal_assemble. */
 int spi_normal_update(spi_ctx* ctx, int64_t ncols, const int32_t* cols, const double* hvals, const double* w,
                       const double* y, double* nvals, double* b, int on_device, void* stream);
+
+/* Poisson maximum-likelihood fit (the paper's appendix on low counts): minimise
+ * the Cash statistic C(x) = sum_i (e_i - y_i ln e_i), e = H x, by Newton's
+ * method on the design matrix recorded by spi_normal_setup.  Each step: e = H x
+ * on the device, the Hessian H^T diag(y/e^2) H assembled there, factored (in
+ * the context's precision) and solved for dx with right-hand side
+ * H^T (y/e - 1); the step is halved (at most 60 times) until every e stays
+ * positive and C does not increase by more than 1e-12 |C| (its rounding level).  Stops when ||step|| <= tol ||x|| (2-norms)
+ * or after max_iter steps; spi_info().mle_steps / mle_cash report them.
+ *   hvals float64[nnz(H)] (CSR order of spi_normal_setup), y float64[nrows]
+ *   x     float64[n]: in, the start (the least-squares solution is a good one:
+ *         e must be positive there); out, the fit
+ *   var   float64[n] or NULL: diag(Hess^-1) at the fit (one more assembly,
+ *         factorization and spi_diag_inverse)
+ * on_device: every buffer is a device pointer.  The factor of the context is
+ * the last Hessian's afterwards.  Returns after the stream has drained.
+ * Errors: SPI_ERR_STATE (no spi_normal_setup), SPI_ERR_ARG (e <= 0 at the
+ * start, max_iter < 0, NULL buffer), and those of spi_normal_assemble,
+ * spi_factor and spi_solve. */
+int spi_mle_newton(spi_ctx* ctx, const double* hvals, const double* y, double* x, int max_iter, double tol,
+                   double* var, int on_device, void* stream);
 
 /* Variances without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they

@@ -189,7 +189,9 @@ def mle_newton(H, y, x0, max_iter=30, tol=1e-12):
     appendix states it: minimise C(x) = sum (e - y ln e), e = H x, with
     gradient H^T (1 - y/e) and Hessian H^T diag(y/e^2) H; each step solves
     Hess dx = H^T (y/e - 1) (a dense solve here), halving the step until
-    every e stays positive and C does not increase; stops when
+    every e stays positive and C does not increase beyond 1e-12 |C| (the
+    rounding level of the sum: near the fit the decrease is below it);
+    stops when
     ||dx|| <= tol ||x|| (2-norms) or after max_iter steps.  Returns
     (x, diag(Hess^-1) at x, steps taken)."""
     import scipy.sparse as sp
@@ -208,7 +210,7 @@ def mle_newton(H, y, x0, max_iter=30, tol=1e-12):
         for _ in range(60):
             xt = x + t * dx
             et = np.asarray(Hs @ xt).ravel()
-            if np.all(et > 0) and cash(Hs, yy, xt) <= c0:
+            if np.all(et > 0) and cash(Hs, yy, xt) <= c0 + 1e-12 * abs(c0):
                 break
             t *= 0.5
         x = x + t * dx

@@ -70,6 +70,9 @@ struct spi_ctx {
     bool plan_blk_ready = false;
     double* d_blk = nullptr;
     double* d_zg = nullptr;      // gathered vectors (rows of the paths' union x indices)
+    double* d_mle = nullptr;     // spi_mle_newton: x, trial x, step, rhs, e, w, v, sums
+    int64_t mle_steps = 0;       // spi_mle_newton: steps and final Cash statistic
+    double mle_cash = 0.0;
     // spi_normal_*: the design matrix's row groups (host and device) and scratch
     struct Normal {
         bool ready = false;
@@ -872,12 +875,15 @@ int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int
         }
     }
     std::vector<int64_t> hrow(rowptr, rowptr + nrows + 1);
+    std::vector<int32_t> hcol(colind, colind + nnzh);
     std::vector<int32_t> all((size_t)N.ngroups);
     for (int32_t g = 0; g < N.ngroups; ++g) all[(size_t)g] = g;
     int64_t *d_rowptr = nullptr, *d_grow = nullptr, *d_gcp = nullptr;
     int32_t *d_entpos = nullptr, *d_gcols = nullptr;
     CK(dev_upload(c, &d_rowptr, hrow));
     CK(dev_upload(c, &d_entpos, entpos));
+    int32_t* d_hcol = nullptr;
+    CK(dev_upload(c, &d_hcol, hcol));
     CK(dev_upload(c, &d_grow, N.grp_row));
     CK(dev_upload(c, &d_gcp, gcolptr));
     CK(dev_upload(c, &d_gcols, gcols));
@@ -898,7 +904,7 @@ int spi_normal_setup(spi_ctx* c, int64_t nrows, const int64_t* rowptr, const int
         CK(dev_upload(c, &d_pairptr, pairptr));
         CK(dev_upload(c, &d_pairpos, pairpos));
     }
-    N.args = NormalArgs{d_rowptr, d_entpos, d_grow, d_gcp, d_gcols, c->d_cp, c->d_ri, d_pairptr, d_pairpos};
+    N.args = NormalArgs{d_rowptr, d_hcol, d_entpos, d_grow, d_gcp, d_gcols, c->d_cp, c->d_ri, d_pairptr, d_pairpos};
     int32_t max_cols = 1;
     for (int32_t g = 0; g < N.ngroups; ++g)
         max_cols = std::max<int32_t>(max_cols, (int32_t)(gcolptr[(size_t)g + 1] - gcolptr[(size_t)g]));
@@ -954,7 +960,7 @@ int spi_normal_assemble(spi_ctx* c, const double* hvals, const double* w, const 
     CK(cudaMemsetAsync(nv, 0, (size_t)c->S.nnz_a * sizeof(double), st));
     CK(cudaMemsetAsync(bv, 0, (size_t)c->S.n * sizeof(double), st));
     CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
-    launch_normal(N.args, N.d_groups, N.ngroups, hv, wd, yd, nullptr, false, nv, bv, N.d_flag, N.smem, st);
+    launch_normal(N.args, N.d_groups, N.ngroups, hv, wd, yd, nullptr, nullptr, false, nv, bv, N.d_flag, N.smem, st);
     return normal_finish(c, nvals, b, on_device, st);
 }
 
@@ -993,11 +999,111 @@ int spi_normal_update(spi_ctx* c, int64_t ncols, const int32_t* cols, const doub
     if (!sel.empty()) {
         CK(cudaMemcpyAsync(N.d_mark, mark.data(), (size_t)n, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(N.d_sel, sel.data(), sel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, N.d_mark, true, nv, bv, N.d_flag, N.smem, st);
-        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, N.d_mark, false, nv, bv, N.d_flag, N.smem,
-                      st);
+        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, nullptr, N.d_mark, true, nv, bv, N.d_flag,
+                      N.smem, st);
+        launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, nullptr, N.d_mark, false, nv, bv, N.d_flag,
+                      N.smem, st);
     }
     return normal_finish(c, nvals, b, on_device, st);
+}
+
+int spi_mle_newton(spi_ctx* c, const double* hvals, const double* y, double* x, int max_iter, double tol,
+                   double* var, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->nrm.ready) return SPI_ERR_STATE;
+    auto& N = c->nrm;
+    const int32_t n = c->S.n;
+    const int64_t M = N.nrows;
+    if (max_iter < 0 || !x || (N.nnzh > 0 && !hvals) || (M > 0 && !y)) return SPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // device copies of the inputs; Newton's work vectors
+    if (!c->d_mle) {
+        CK(dev_alloc(c, &c->d_mle, (size_t)4 * std::max<int32_t>(n, 1) + 3 * (size_t)std::max<int64_t>(M, 1) + 2));
+    }
+    double* xc = c->d_mle;             // current x
+    double* xt = xc + std::max(n, 1);  // trial x
+    double* dx = xt + std::max(n, 1);  // Newton step
+    double* gx = dx + std::max(n, 1);  // right-hand side H^T (y/e - 1)
+    double* e = gx + std::max(n, 1);
+    double* w = e + std::max<int64_t>(M, 1);
+    double* v = w + std::max<int64_t>(M, 1);
+    double* acc = v + std::max<int64_t>(M, 1);
+    const double *hv = hvals, *yd = y;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(N.d_hv, hvals, (size_t)N.nnzh * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(N.d_y, y, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, st));
+        hv = N.d_hv;
+        yd = N.d_y;
+    }
+    CK(cudaMemcpyAsync(xc, x, (size_t)n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       st));
+    double hacc[2];
+    // e = H xs, C(xs) and the count of e <= 0; with weights, also w and v
+    auto model = [&](const double* xs, bool weights) -> int {
+        launch_spmv_rows(M, N.args.rowptr, N.args.colind, hv, xs, e, st);
+        CK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+        launch_mle_rows(M, e, yd, weights ? w : nullptr, v, acc, st);
+        CK(cudaMemcpyAsync(hacc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return SPI_OK;
+    };
+    // the Hessian H^T diag(w) H into N's values, the right-hand side H^T v into gx
+    auto hessian = [&]() -> int {
+        CK(cudaMemsetAsync(N.d_nv, 0, (size_t)c->S.nnz_a * sizeof(double), st));
+        CK(cudaMemsetAsync(gx, 0, (size_t)n * sizeof(double), st));
+        CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+        launch_normal(N.args, N.d_groups, N.ngroups, hv, w, yd, v, nullptr, false, N.d_nv, gx, N.d_flag, N.smem, st);
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (flag) return SPI_ERR_PATTERN;
+        return factor_impl(c, 1, N.d_nv, 1, st);
+    };
+    int rc = model(xc, true);
+    if (rc) return rc;
+    if (hacc[1] != 0.0) return SPI_ERR_ARG;  // the model must be positive at the start
+    double cx = hacc[0];
+    c->mle_steps = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        rc = hessian();
+        if (rc) return rc;
+        rc = solve_impl(c, 1, gx, dx, 1, st);
+        if (rc) return rc;
+        double t = 1.0, ct = cx;
+        bool ok = false;
+        for (int h = 0; h < 60 && !ok; ++h, t *= 0.5) {
+            launch_step(n, xc, dx, t, xt, st);
+            rc = model(xt, false);
+            if (rc) return rc;
+            ct = hacc[0];
+            ok = hacc[1] == 0.0 && ct <= cx + 1e-12 * std::fabs(cx);  // C's rounding level
+            if (ok) break;
+        }
+        if (!ok) break;  // no step keeps e > 0 and C from growing: stop at the current x
+        CK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+        launch_norms2(n, dx, xt, acc, 1, st);
+        CK(cudaMemcpyAsync(hacc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::swap(xc, xt);
+        cx = ct;
+        c->mle_steps++;
+        if (t * std::sqrt(hacc[0]) <= tol * std::sqrt(hacc[1])) break;
+        rc = model(xc, true);  // weights at the new point
+        if (rc) return rc;
+    }
+    c->mle_cash = cx;
+    if (var) {
+        rc = model(xc, true);
+        if (rc) return rc;
+        rc = hessian();
+        if (rc) return rc;
+        rc = diag_impl(c, 1, nullptr, 0, var, on_device, st);
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(x, xc, (size_t)n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    return finish(c, st);
 }
 
 int spi_info(const spi_ctx* c, spi_stats* o) {
@@ -1029,6 +1135,8 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->solve_relres = c->solve_relres;
     o->rhs_block = c->rhs_block_used > 0 ? c->rhs_block_used : c->opt.rhs_block;
     o->analyse_seconds = c->analyse_seconds;
+    o->mle_steps = c->mle_steps;
+    o->mle_cash = c->mle_cash;
     return SPI_OK;
 }
 

@@ -19,6 +19,8 @@
 // sets an error flag.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "spi_internal.cuh"
 
 namespace spi {
@@ -33,6 +35,7 @@ __global__ void __launch_bounds__(kNThreads) k_normal_group(NormalArgs a, const 
                                                              const double* __restrict__ hv,
                                                              const double* __restrict__ w,
                                                              const double* __restrict__ y,
+                                                             const double* __restrict__ bw,
                                                              const uint8_t* __restrict__ mark,
                                                              double* __restrict__ nv, double* __restrict__ bv,
                                                              int* __restrict__ flag) {
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(kNThreads) k_normal_group(NormalArgs a, const 
     }
     for (int r = tid; r < R; r += kNThreads) {
         ws[2 * r] = w[r0 + r];
-        ws[2 * r + 1] = w[r0 + r] * y[r0 + r];
+        ws[2 * r + 1] = bw ? bw[r0 + r] : w[r0 + r] * y[r0 + r];  // b_j = sum_r (w_r y_r or bw_r) h_rj
     }
     // update: the group's marked columns, as a list of union indices (ascending)
     int32_t* ml = reinterpret_cast<int32_t*>(ws + 2 * R);
@@ -151,13 +154,85 @@ cudaError_t normal_kernel_setup(size_t smem) {
 }
 
 void launch_normal(const NormalArgs& a, const int32_t* groups, int32_t ngroups, const double* hv, const double* w,
-                   const double* y, const uint8_t* mark, bool zero_pass, double* nv, double* bv, int* flag,
-                   size_t smem, cudaStream_t st) {
+                   const double* y, const double* bw, const uint8_t* mark, bool zero_pass, double* nv, double* bv,
+                   int* flag, size_t smem, cudaStream_t st) {
     if (ngroups == 0) return;
     if (zero_pass)
-        k_normal_group<0><<<ngroups, kNThreads, smem, st>>>(a, groups, hv, w, y, mark, nv, bv, flag);
+        k_normal_group<0><<<ngroups, kNThreads, smem, st>>>(a, groups, hv, w, y, bw, mark, nv, bv, flag);
     else
-        k_normal_group<1><<<ngroups, kNThreads, smem, st>>>(a, groups, hv, w, y, mark, nv, bv, flag);
+        k_normal_group<1><<<ngroups, kNThreads, smem, st>>>(a, groups, hv, w, y, bw, mark, nv, bv, flag);
+}
+
+// ---- Poisson maximum likelihood (the appendix on low-count fitting): the model
+// e = H x, the Newton weights y/e^2, the gradient coefficients y/e - 1, and the
+// Cash statistic C = sum (e - y ln e).
+
+namespace {
+
+// e = H x, one warp per row (H in CSR)
+__global__ void k_spmv_rows(int64_t nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                            const double* __restrict__ hv, const double* __restrict__ x, double* __restrict__ e) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) s += hv[p] * x[colind[p]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) e[r] = s;
+    }
+}
+
+// acc[0] += sum (e - y ln e); acc[1] += number of rows with e <= 0; with w != null
+// also w = y / e^2 and v = y / e - 1
+__global__ void k_mle_rows(int64_t nrows, const double* __restrict__ e, const double* __restrict__ y,
+                           double* __restrict__ w, double* __restrict__ v, double* __restrict__ acc) {
+    double c = 0.0, bad = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+        const double er = e[r], yr = y[r];
+        if (!(er > 0.0)) { bad += 1.0; continue; }
+        c += yr > 0.0 ? er - yr * log(er) : er;
+        if (w) {
+            const double q = yr / er;
+            w[r] = q / er;
+            v[r] = q - 1.0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, c);
+        if (bad != 0.0) atomicAdd(acc + 1, bad);
+    }
+}
+
+// xt = x + t dx
+__global__ void k_step(int32_t n, const double* __restrict__ x, const double* __restrict__ dx, double t,
+                       double* __restrict__ xt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        xt[i] = x[i] + t * dx[i];
+}
+
+}  // namespace
+
+void launch_spmv_rows(int64_t nrows, const int64_t* rowptr, const int32_t* colind, const double* hv, const double* x,
+                      double* e, cudaStream_t st) {
+    if (nrows == 0) return;
+    const int grid = (int)std::min<int64_t>((nrows * 32 + 255) / 256, 152 * 16);
+    k_spmv_rows<<<grid, 256, 0, st>>>(nrows, rowptr, colind, hv, x, e);
+}
+
+void launch_mle_rows(int64_t nrows, const double* e, const double* y, double* w, double* v, double* acc,
+                     cudaStream_t st) {
+    if (nrows == 0) return;
+    const int grid = (int)std::min<int64_t>((nrows + 255) / 256, 152 * 8);
+    k_mle_rows<<<grid, 256, 0, st>>>(nrows, e, y, w, v, acc);
+}
+
+void launch_step(int32_t n, const double* x, const double* dx, double t, double* xt, cudaStream_t st) {
+    if (n == 0) return;
+    k_step<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(n, x, dx, t, xt);
 }
 
 }  // namespace spi

@@ -136,6 +136,7 @@ void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L
 // ---- normal.cu: N = H^T W H and b = H^T W y on the device
 struct NormalArgs {
     const int64_t* rowptr;      // H's CSR row pointers [nrows + 1]
+    const int32_t* colind;      // H's column indices (caller numbering)
     const int32_t* ent_pos;     // per entry of H: its column's index in its group's union
     const int64_t* grp_row;     // [ngroups + 1] row ranges
     const int64_t* grp_colptr;  // [ngroups + 1] into grp_cols
@@ -147,8 +148,14 @@ struct NormalArgs {
 };
 size_t normal_smem_bytes(int32_t max_dense_entries, int32_t max_rows, int32_t max_cols);
 cudaError_t normal_kernel_setup(size_t smem);
+// bw: per-row coefficients of b = H^T bw (null: w * y)
 void launch_normal(const NormalArgs& a, const int32_t* groups, int32_t ngroups, const double* hv, const double* w,
-                   const double* y, const uint8_t* mark, bool zero_pass, double* nv, double* bv, int* flag,
-                   size_t smem, cudaStream_t st);
+                   const double* y, const double* bw, const uint8_t* mark, bool zero_pass, double* nv, double* bv,
+                   int* flag, size_t smem, cudaStream_t st);
+void launch_spmv_rows(int64_t nrows, const int64_t* rowptr, const int32_t* colind, const double* hv, const double* x,
+                      double* e, cudaStream_t st);
+void launch_mle_rows(int64_t nrows, const double* e, const double* y, double* w, double* v, double* acc,
+                     cudaStream_t st);
+void launch_step(int32_t n, const double* x, const double* dx, double t, double* xt, cudaStream_t st);
 
 }  // namespace spi

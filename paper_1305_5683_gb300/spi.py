@@ -25,7 +25,7 @@ SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
-           "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update"]
+           "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton"]
 SPI_INVERSE_BLOCK_MAX = 512
 
 
@@ -48,7 +48,8 @@ class spi_stats(ctypes.Structure):
                 ("launches_solve", ctypes.c_int64), ("launches_diag", ctypes.c_int64),
                 ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),
                 ("rhs_block", ctypes.c_int64),
-                ("analyse_seconds", ctypes.c_double)]
+                ("analyse_seconds", ctypes.c_double), ("mle_steps", ctypes.c_int64),
+                ("mle_cash", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +94,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_normal_setup.argtypes = [V, I64, V, V]; L.spi_normal_setup.restype = I
     L.spi_normal_assemble.argtypes = [V, V, V, V, V, V, I, V]; L.spi_normal_assemble.restype = I
     L.spi_normal_update.argtypes = [V, I64, V, V, V, V, V, V, I, V]; L.spi_normal_update.restype = I
+    L.spi_mle_newton.argtypes = [V, V, V, V, I, ctypes.c_double, V, I, V]; L.spi_mle_newton.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -286,6 +288,24 @@ def spi_normal_update(ctx, cols, hvals, w, y, nvals, b, stream=None) -> None:
     del bufs
 
 
+def spi_mle_newton(ctx, hvals, y, x, max_iter=30, tol=1e-12, var=None, stream=None) -> None:
+    """Poisson maximum-likelihood fit: x (in: start, out: fit), var = diag(Hess^-1) or None."""
+    bufs = [_buf(a, np.float64) for a in (hvals, y, x)]
+    devs = {d for _, d, _ in bufs}
+    vb = _buf(var, np.float64) if var is not None else (None, None, None)
+    if vb[1] is not None:
+        devs.add(vb[1])
+    if len(devs) != 1:
+        raise TypeError("hvals, y, x and var must all be host or all be device buffers")
+    for a in (x, var):
+        if a is not None and not _is_torch(a) and not (isinstance(a, np.ndarray) and a.dtype == np.float64
+                                                       and a.flags.c_contiguous):
+            raise TypeError("x and var must be contiguous float64 numpy arrays or CUDA tensors")
+    _check(lib().spi_mle_newton(ctx, bufs[0][0], bufs[1][0], bufs[2][0], int(max_iter), float(tol), vb[0],
+                                devs.pop(), _stream(stream)), "spi_mle_newton")
+    del bufs, vb
+
+
 def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
     """Variances for device idx into device out without any device allocation
     by the library (fixed scratch array; see include/spi.h)."""
@@ -437,6 +457,17 @@ class Solver:
         """Update (nvals, b) in place after H's columns `cols` changed."""
         spi_normal_update(self._h, cols, hvals, w, y, nvals, b, stream)
         return nvals, b
+
+    def mle_newton(self, hvals, y, x0, max_iter=30, tol=1e-12, variances=True, stream=None):
+        """Poisson maximum-likelihood fit from x0: (x, diag(Hess^-1) or None)."""
+        if _is_torch(x0):
+            x = x0.clone()
+            var = x0.new_empty(x0.shape) if variances else None
+        else:
+            x = np.array(x0, dtype=np.float64)
+            var = np.empty(self.n, np.float64) if variances else None
+        spi_mle_newton(self._h, hvals, y, x, max_iter, tol, var, stream)
+        return x, var
 
     def info(self) -> dict:
         return spi_info(self._h)

@@ -481,12 +481,33 @@ def bench_normal(P, args, dev, st):
     b = torch.empty(pb.n, dtype=torch.float64, device=dev)
     ms = _time_alone(lambda q: s.normal_assemble(hv, w, y, nv, b, stream=q), st)
     diff = float((torch.abs(nv - torch.from_numpy(pb.values).to(dev)).max() / abs(pb.values).max()).item())
-    cols = np.random.default_rng(5).choice(pb.n, 5000, replace=False).astype(np.int32)
-    sel = torch.from_numpy(np.isin(H.indices, cols)).to(dev)
-    hv2 = torch.where(sel, hv * 1.01, hv)
-    ms_u = _time_alone(lambda q: s.normal_update(cols, hv2, w, y, nv, b, stream=q), st)
+    def update_ms(cols):
+        sel = torch.from_numpy(np.isin(H.indices, cols)).to(dev)
+        hv2 = torch.where(sel, hv * 1.01, hv)
+        return _time_alone(lambda q: s.normal_update(cols, hv2, w, y, nv, b, stream=q), st)
+
+    # the Poisson maximum-likelihood fit from the least-squares solution (NEXT-2: the same
+    # pattern refactored every Newton step)
+    s.normal_assemble(hv, w, y, nv, b, stream=st)
+    s.factor(nv, stream=st)
+    x0 = s.solve(b, stream=st)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    xm, vm = s.mle_newton(hv, y, x0, stream=st)
+    torch.cuda.synchronize(dev)
+    t_mle = time.perf_counter() - t0
+    mle = {"steps": s.info()["mle_steps"], "wall_s": t_mle, "cash": s.info()["mle_cash"],
+           "max_rel_change_from_lsq": float((torch.abs(xm - x0).max() / torch.abs(x0).max()).item()),
+           "note": "each step: e = Hx, Hessian assembled, factored and solved on the device; "
+                   "variances at the fit from the last Hessian"}
+    ms_u = update_ms(np.random.default_rng(5).choice(pb.n, 5000, replace=False).astype(np.int32))
+    bins = np.nonzero(pb.kind == 2)[0]
+    ms_w = update_ms(bins[len(bins) // 2: len(bins) // 2 + 5000].astype(np.int32))
+    ms_d = update_ms(np.nonzero(pb.kind == 1)[0].astype(np.int32))
     return {"workload": f"{SCALE.name}: H {H.shape[0]} x {H.shape[1]}, nnz(H) {H.nnz}, N lower nnz {pb.nnz}",
-            "assemble_ms": ms, "update_5000_columns_ms": ms_u, "setup_host_s": t_setup,
+            "assemble_ms": ms, "update_5000_random_columns_ms": ms_u,
+            "update_5000_consecutive_time_bins_ms": ms_w, "update_detector_pattern_columns_ms": ms_d,
+            "setup_host_s": t_setup, "mle_newton": mle,
             "max_rel_diff_vs_generator": diff, "dtype": "f64", "generate_s": t_gen,
             "paper_table3_context": "improved algorithm, one CPU core: 28.2 s full / 0.43 s 5,000 columns at N = 22,503, "
                                     "nnz(H) = 27.05 M (different matrix and hardware)"}

@@ -220,3 +220,135 @@ def mle_newton(H, y, x0, max_iter=30, tol=1e-12):
     e = np.asarray(Hs @ x).ravel()
     Hess = (Hs.T @ sp.diags(yy / e ** 2) @ Hs).toarray()
     return x, np.diag(np.linalg.inv(Hess)).copy(), steps
+
+
+def set_background(H, k0, upat, t, U):
+    """H with the entry of each row i in the first k0 columns (its background
+    column: the pointing's normalisation I_p^bg) set to U[upat_i] t_i, the
+    background model B_dp = U^d I_p^bg t_dp of Eq. A4 with upat_i the pattern
+    index of the row (its detector, or its detector and time interval) and
+    t_i its t_dp.  Rows with upat_i < 0 have no background entry."""
+    import scipy.sparse as sp
+    Hs = sp.csr_matrix(H, copy=True)
+    Hs.sort_indices()
+    upat = np.asarray(upat)
+    for i in range(Hs.shape[0]):
+        lo, hi = Hs.indptr[i], Hs.indptr[i + 1]
+        bg = [p for p in range(lo, hi) if Hs.indices[p] < k0]
+        if len(bg) > 1 or (len(bg) == 1) != (upat[i] >= 0):
+            raise ValueError(f"row {i}: background entries {len(bg)}, pattern index {upat[i]}")
+        if bg:
+            Hs.data[bg[0]] = U[upat[i]] * t[i]
+    return Hs
+
+
+def _background_terms(Hs, x, k0, upat, t):
+    """Per row: y^S_i (the counts of the columns after the first k0), the
+    background column c(i) and a_i = t_i x_c(i) (= I_p^bg t_dp); rows
+    without a background entry get a_i = 0."""
+    nrow = Hs.shape[0]
+    ys = np.zeros(nrow)
+    a = np.zeros(nrow)
+    for i in range(nrow):
+        for p in range(Hs.indptr[i], Hs.indptr[i + 1]):
+            j = Hs.indices[p]
+            if j < k0:
+                a[i] = t[i] * x[j]
+            else:
+                ys[i] += Hs.data[p] * x[j]
+    return ys, a
+
+
+def background_pattern(H, x, y, w, k0, upat, t, U, mode="lsq"):
+    """One re-estimation of the "empty-field" pattern (the appendix on its
+    auto-computation): with the solution x known, the counts split into the
+    sources' y^S and the background U^d a_i, a_i = I_p^bg t_dp, and each
+    pattern value minimises its own statistic:
+      least squares:  U_k = sum (y_i - y^S_i) a_i w_i / sum a_i^2 w_i,
+      likelihood:     U_k = sum (y_i - y^S_i) / sum a_i  (the paper's
+                      simplified form; the exact maximiser when y^S = 0),
+    sums over the rows of pattern index k (a detector over all pointings, or
+    over one interval of pointings).  A pattern index whose denominator is
+    not positive keeps its value."""
+    import scipy.sparse as sp
+    Hs = sp.csr_matrix(H)
+    upat = np.asarray(upat)
+    ys, a = _background_terms(Hs, np.asarray(x, float), k0, upat, t)
+    r = np.asarray(y, float) - ys
+    U = np.array(U, dtype=np.float64)
+    num = np.zeros(len(U))
+    den = np.zeros(len(U))
+    for i in range(Hs.shape[0]):
+        k = upat[i]
+        if k < 0:
+            continue
+        if mode == "lsq":
+            num[k] += r[i] * a[i] * w[i]
+            den[k] += a[i] * a[i] * w[i]
+        else:
+            num[k] += r[i]
+            den[k] += a[i]
+    ok = den > 0
+    U[ok] = num[ok] / den[ok]
+    return U
+
+
+def chi2(H, y, w, x):
+    """sum_i w_i (y_i - (H x)_i)^2, the weighted least-squares statistic."""
+    r = np.asarray(y, float) - np.asarray(H @ x).ravel()
+    return float(np.sum(np.asarray(w, float) * r * r))
+
+
+def background_fit(H, y, w, k0, upat, t, U0, mode="lsq", max_iter=20, tol=1e-9,
+                   variances=True, mle_iter=30, mle_tol=1e-12):
+    """Algorithm 1 of the appendix on the "empty-field" pattern: starting
+    from the pattern U0, repeat {solve for x with the current H (weighted
+    least squares, or the Poisson likelihood fit by Newton's method started
+    from the previous x when the model is positive there, else from the
+    least-squares solution); re-estimate U from x (background_pattern); set
+    the background entries of H} and stop when the statistic (chi^2, or the
+    Cash statistic C = -L/2 + const) of a solve is not below the previous
+    solve's by more than tol times its size, or after max_iter solves.
+    The statistic is tested right after each solve, before U changes, so
+    that the returned (U, x) are the pair that solve used; when the last
+    solve's statistic is above the previous one, the previous pair is
+    returned.  Then the variances diag(Hess^-1) at the returned pair (N for
+    least squares, H^T diag(y/e^2) H for the likelihood).
+    Returns (x, U, [statistic per solve], var or None)."""
+    import scipy.sparse as sp
+    yy = np.asarray(y, dtype=np.float64)
+    ww = np.asarray(w, dtype=np.float64)
+    U = np.array(U0, dtype=np.float64)
+    x = None
+    stats = []
+    prev = None
+    for it in range(max_iter):
+        Hc = set_background(H, k0, upat, t, U)
+        Nd = (Hc.T @ sp.diags(ww) @ Hc).toarray()
+        if mode == "lsq":
+            x = np.linalg.solve(Nd, Hc.T @ (ww * yy))
+            stat = chi2(Hc, yy, ww, x)
+        else:
+            if x is None or np.any(np.asarray(Hc @ x).ravel() <= 0):
+                x = np.linalg.solve(Nd, Hc.T @ (ww * yy))
+            x, _, _ = mle_newton(Hc, yy, x, max_iter=mle_iter, tol=mle_tol)
+            stat = cash(Hc, yy, x)
+        stats.append(stat)
+        if it > 0 and stat >= stats[-2] - tol * abs(stats[-2]):
+            if stat > stats[-2]:
+                U, x = prev
+            break
+        if it == max_iter - 1:
+            break
+        prev = (U.copy(), x.copy())
+        U = background_pattern(Hc, x, yy, ww, k0, upat, t, U, mode)
+    var = None
+    if variances:
+        Hc = set_background(H, k0, upat, t, U)
+        if mode == "lsq":
+            Hess = (Hc.T @ sp.diags(ww) @ Hc).toarray()
+        else:
+            e = np.asarray(Hc @ x).ravel()
+            Hess = (Hc.T @ sp.diags(yy / e ** 2) @ Hc).toarray()
+        var = np.diag(np.linalg.inv(Hess)).copy()
+    return x, U, stats, var

@@ -225,6 +225,9 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
     sparse_design=True returns H as a scipy CSR matrix instead (rows =
     (pointing, detector) in order, columns ascending within a row), with
     the weights w and counts y, for assembling N = H^T W H elsewhere.
+    Either also returns the background model's parts: bg_t (g_dp per row),
+    bg_pat (the row's detector) and bg_u (u_d), so that the pointing
+    column's entry of row p * 19 + d is bg_u[bg_pat] * bg_t.
     """
     rng = np.random.default_rng(cfg.seed)
     P, nd = cfg.n_pointings, N_DET
@@ -418,6 +421,11 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
                     n_sky=nsky)
     if dense_design or sparse_design:
         pb.H, pb.w, pb.y = Hd, w, y
+        # the background model's parts (Eq. A4: B_dp = U^d I_p^bg t_dp): the
+        # pointing columns (the first P) hold u_d * g_dp in row p * nd + d
+        pb.bg_t = g.ravel().copy()                              # t_dp per row
+        pb.bg_pat = np.tile(np.arange(nd, dtype=np.int32), P)   # detector per row
+        pb.bg_u = u_d.copy()                                    # U^d
     return pb
 
 

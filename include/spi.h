@@ -115,6 +115,8 @@ typedef struct spi_stats {
     double analyse_seconds; /* host time of spi_analyse */
     int64_t mle_steps;      /* Newton steps of the last spi_mle_newton */
     double mle_cash;        /* its final Cash statistic sum (e - y ln e) */
+    int64_t bg_iters;       /* solves made by the last spi_background_fit */
+    double bg_stat;         /* the statistic of the pair it returned (chi^2 or Cash) */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;
@@ -276,6 +278,64 @@ int spi_normal_update(spi_ctx* ctx, int64_t ncols, const int32_t* cols, const do
  * spi_factor and spi_solve. */
 int spi_mle_newton(spi_ctx* ctx, const double* hvals, const double* y, double* x, int max_iter, double tol,
                    double* var, int on_device, void* stream);
+
+/* Algorithm 1 of the appendix on the "empty-field" pattern: the background
+ * B_dp = U^d I_p^bg t_dp (Eq. A4) has a pattern U that is fitted with the
+ * solution.  The first k0 columns of H are the background normalisations
+ * (I_p^bg, one per pointing); each row i has at most one entry in them, whose
+ * value is U[upat[i]] t[i].  Starting from U, each iteration
+ *   1. solves for x with the current H: weighted least squares (mode
+ *      SPI_FIT_LSQ: N = H^T W H assembled -- after the first iteration only
+ *      its rows and columns of the first k0 unknowns are recomputed --,
+ *      factored and solved), or the Poisson likelihood fit (SPI_FIT_MLE:
+ *      Newton's method as spi_mle_newton with at most 30 steps and tol 1e-12,
+ *      started from the previous x where H x > 0, else from the least-squares
+ *      solution);
+ *   2. computes the statistic at (U, x): sum w (y - Hx)^2, or the Cash
+ *      statistic sum (e - y ln e) = -L/2 + const; stat[it] receives it;
+ *   3. stops when it is not below the previous iteration's by more than
+ *      tol |previous| (the previous pair is restored when it is above it), or
+ *      after max_iter solves;
+ *   4. re-estimates each pattern value from x: with y^S the counts of the
+ *      columns from k0 on and a_i = t_i x_c(i) (c(i): row i's background
+ *      column), U_k = sum (y - y^S) a w / sum a^2 w (least squares) or
+ *      sum (y - y^S) / sum a (likelihood, the paper's simplified form), sums
+ *      over the rows with upat = k; a value whose denominator is not positive
+ *      is kept; then the background entries of H are rewritten.
+ * The test follows each solve, before U changes, so the returned U and x are
+ * the pair that solve used.
+ *   k0      number of background columns (caller numbering 0 .. k0-1)
+ *   upat    int32[nrows]: the row's pattern index in 0 .. npat-1 (a detector,
+ *           or a detector and an interval of pointings), -1 for a row with no
+ *           entry in the first k0 columns
+ *   t       float64[nrows]: t_dp of the row (unused where upat = -1)
+ *   npat    1 .. SPI_PATTERN_MAX
+ *   hvals   float64[nnz(H)], CSR order of spi_normal_setup: in, H (its
+ *           background entries are overwritten from U at the start); out, H
+ *           at the returned U
+ *   w, y    float64[nrows]: least-squares weights (also those of the
+ *           likelihood form's least-squares start) and counts
+ *   U       float64[npat]: in, U_0; out, the returned pattern
+ *   x       float64[n]: out, the returned solution
+ *   stat    HOST float64[max_iter] or NULL: the statistic of each solve
+ *   var     float64[n] or NULL: diag(Hess^-1) at the returned pair (N, or
+ *           H^T diag(y/e^2) H)
+ * on_device: hvals, w, y, upat, t, U, x, var are device pointers (stat stays
+ * on the host).  The context's factor is that of the returned pair's N (least
+ * squares) or of its Hessian (likelihood, with var).  spi_info().bg_iters and
+ * bg_stat report the solves made and the returned statistic.  Returns after
+ * the stream has drained.  Errors: SPI_ERR_STATE (no spi_normal_setup),
+ * SPI_ERR_ARG (k0 outside 0..n, npat outside 1..SPI_PATTERN_MAX, bad mode,
+ * max_iter < 1, tol < 0 or NaN, NULL buffer, a row with two entries in the
+ * first k0 columns or a pattern index that does not match its row, H x <= 0
+ * where the likelihood needs it positive), and those of spi_normal_assemble,
+ * spi_factor and spi_solve. */
+#define SPI_PATTERN_MAX 2048
+#define SPI_FIT_LSQ 0
+#define SPI_FIT_MLE 1
+int spi_background_fit(spi_ctx* ctx, int64_t k0, const int32_t* upat, const double* t, int32_t npat,
+                       double* hvals, const double* w, const double* y, double* U, double* x, int mode,
+                       int max_iter, double tol, double* stat, double* var, int on_device, void* stream);
 
 /* Variances without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they

@@ -73,6 +73,13 @@ struct spi_ctx {
     double* d_mle = nullptr;     // spi_mle_newton: x, trial x, step, rhs, e, w, v, sums
     int64_t mle_steps = 0;       // spi_mle_newton: steps and final Cash statistic
     double mle_cash = 0.0;
+    struct Background {          // spi_background_fit: each row's background entry, copies of
+        int64_t* pos = nullptr;  // the pattern indices and t, the patterns, sums and previous x
+        int32_t* pat = nullptr;
+        double* vec = nullptr;
+    } bg;
+    int64_t bg_iters = 0;        // spi_background_fit: solves and the returned statistic
+    double bg_stat = 0.0;
     // spi_normal_*: the design matrix's row groups (host and device) and scratch
     struct Normal {
         bool ready = false;
@@ -1007,6 +1014,105 @@ int spi_normal_update(spi_ctx* c, int64_t ncols, const int32_t* cols, const doub
     return normal_finish(c, nvals, b, on_device, st);
 }
 
+namespace {
+// Newton's work vectors (spi_mle_newton, spi_background_fit)
+struct MleWork {
+    double *xc, *xt, *dx, *gx, *e, *w, *v, *acc;
+};
+
+int mle_work(spi_ctx* c, MleWork* W) {
+    const int64_t n1 = std::max<int64_t>(c->S.n, 1), m1 = std::max<int64_t>(c->nrm.nrows, 1);
+    if (!c->d_mle) CK(dev_alloc(c, &c->d_mle, (size_t)(4 * n1 + 3 * m1 + 2)));
+    W->xc = c->d_mle;
+    W->xt = W->xc + n1;
+    W->dx = W->xt + n1;
+    W->gx = W->dx + n1;
+    W->e = W->gx + n1;
+    W->w = W->e + m1;
+    W->v = W->w + m1;
+    W->acc = W->v + m1;
+    return SPI_OK;
+}
+
+// e = H xs; hacc = {C(xs), rows with e <= 0}; with weights also w = y/e^2, v = y/e - 1
+int mle_model(spi_ctx* c, const MleWork& W, const double* hv, const double* yd, const double* xs, bool weights,
+              double* hacc, cudaStream_t st) {
+    auto& N = c->nrm;
+    launch_spmv_rows(N.nrows, N.args.rowptr, N.args.colind, hv, xs, W.e, st);
+    CK(cudaMemsetAsync(W.acc, 0, 2 * sizeof(double), st));
+    launch_mle_rows(N.nrows, W.e, yd, weights ? W.w : nullptr, W.v, W.acc, st);
+    CK(cudaMemcpyAsync(hacc, W.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SPI_OK;
+}
+
+// the Hessian H^T diag(w) H into N's values and factored; H^T v into gx
+int mle_hessian(spi_ctx* c, const MleWork& W, const double* hv, const double* yd, cudaStream_t st) {
+    auto& N = c->nrm;
+    CK(cudaMemsetAsync(N.d_nv, 0, (size_t)c->S.nnz_a * sizeof(double), st));
+    CK(cudaMemsetAsync(W.gx, 0, (size_t)c->S.n * sizeof(double), st));
+    CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+    launch_normal(N.args, N.d_groups, N.ngroups, hv, W.w, yd, W.v, nullptr, false, N.d_nv, W.gx, N.d_flag, N.smem, st);
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) return SPI_ERR_PATTERN;
+    return factor_impl(c, 1, N.d_nv, 1, st);
+}
+
+// Newton's method for the Cash statistic from W.xc, the fit left in W.xc
+int mle_fit(spi_ctx* c, const MleWork& W, const double* hv, const double* yd, int max_iter, double tol,
+            cudaStream_t st) {
+    const int32_t n = c->S.n;
+    double hacc[2];
+    int rc = mle_model(c, W, hv, yd, W.xc, true, hacc, st);
+    if (rc) return rc;
+    if (hacc[1] != 0.0) return SPI_ERR_ARG;  // the model must be positive at the start
+    double cx = hacc[0];
+    c->mle_steps = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        rc = mle_hessian(c, W, hv, yd, st);
+        if (rc) return rc;
+        rc = solve_impl(c, 1, W.gx, W.dx, 1, st);
+        if (rc) return rc;
+        double t = 1.0, ct = cx;
+        bool ok = false;
+        for (int h = 0; h < 60 && !ok; ++h, t *= 0.5) {
+            launch_step(n, W.xc, W.dx, t, W.xt, st);
+            rc = mle_model(c, W, hv, yd, W.xt, false, hacc, st);
+            if (rc) return rc;
+            ct = hacc[0];
+            ok = hacc[1] == 0.0 && ct <= cx + 1e-12 * std::fabs(cx);  // C's rounding level
+            if (ok) break;
+        }
+        if (!ok) break;  // no step keeps e > 0 and C from growing: stop at the current x
+        CK(cudaMemsetAsync(W.acc, 0, 2 * sizeof(double), st));
+        launch_norms2(n, W.dx, W.xt, W.acc, 1, st);
+        CK(cudaMemcpyAsync(hacc, W.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(W.xc, W.xt, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        cx = ct;
+        c->mle_steps++;
+        if (t * std::sqrt(hacc[0]) <= tol * std::sqrt(hacc[1])) break;
+        rc = mle_model(c, W, hv, yd, W.xc, true, hacc, st);  // weights at the new point
+        if (rc) return rc;
+    }
+    c->mle_cash = cx;
+    return SPI_OK;
+}
+
+// diag(Hess^-1) at W.xc into var
+int mle_variances(spi_ctx* c, const MleWork& W, const double* hv, const double* yd, double* var, int on_device,
+                  cudaStream_t st) {
+    double hacc[2];
+    int rc = mle_model(c, W, hv, yd, W.xc, true, hacc, st);
+    if (rc) return rc;
+    rc = mle_hessian(c, W, hv, yd, st);
+    if (rc) return rc;
+    return diag_impl(c, 1, nullptr, 0, var, on_device, st);
+}
+}  // namespace
+
 int spi_mle_newton(spi_ctx* c, const double* hvals, const double* y, double* x, int max_iter, double tol,
                    double* var, int on_device, void* stream) {
     if (!c) return SPI_ERR_ARG;
@@ -1016,18 +1122,9 @@ int spi_mle_newton(spi_ctx* c, const double* hvals, const double* y, double* x, 
     const int64_t M = N.nrows;
     if (max_iter < 0 || !x || (N.nnzh > 0 && !hvals) || (M > 0 && !y)) return SPI_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    // device copies of the inputs; Newton's work vectors
-    if (!c->d_mle) {
-        CK(dev_alloc(c, &c->d_mle, (size_t)4 * std::max<int32_t>(n, 1) + 3 * (size_t)std::max<int64_t>(M, 1) + 2));
-    }
-    double* xc = c->d_mle;             // current x
-    double* xt = xc + std::max(n, 1);  // trial x
-    double* dx = xt + std::max(n, 1);  // Newton step
-    double* gx = dx + std::max(n, 1);  // right-hand side H^T (y/e - 1)
-    double* e = gx + std::max(n, 1);
-    double* w = e + std::max<int64_t>(M, 1);
-    double* v = w + std::max<int64_t>(M, 1);
-    double* acc = v + std::max<int64_t>(M, 1);
+    MleWork W;
+    int rc = mle_work(c, &W);
+    if (rc) return rc;
     const double *hv = hvals, *yd = y;
     if (!on_device) {
         CK(cudaMemcpyAsync(N.d_hv, hvals, (size_t)N.nnzh * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1035,73 +1132,208 @@ int spi_mle_newton(spi_ctx* c, const double* hvals, const double* y, double* x, 
         hv = N.d_hv;
         yd = N.d_y;
     }
-    CK(cudaMemcpyAsync(xc, x, (size_t)n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       st));
+    CK(cudaMemcpyAsync(W.xc, x, (size_t)n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    rc = mle_fit(c, W, hv, yd, max_iter, tol, st);
+    if (rc) return rc;
+    if (var) {
+        rc = mle_variances(c, W, hv, yd, var, on_device, st);
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(x, W.xc, (size_t)n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return finish(c, st);
+}
+
+// Newton's method inside each solve of spi_background_fit's likelihood form
+constexpr int kFitNewtonSteps = 30;
+constexpr double kFitNewtonTol = 1e-12;
+
+int spi_background_fit(spi_ctx* c, int64_t k0, const int32_t* upat, const double* t, int32_t npat, double* hvals,
+                       const double* w, const double* y, double* U, double* x, int mode, int max_iter, double tol,
+                       double* stat, double* var, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->nrm.ready) return SPI_ERR_STATE;
+    auto& N = c->nrm;
+    const int32_t n = c->S.n;
+    const int64_t M = N.nrows;
+    if (k0 < 0 || k0 > n || npat < 1 || npat > SPI_PATTERN_MAX || (mode != SPI_FIT_LSQ && mode != SPI_FIT_MLE) ||
+        max_iter < 1 || !(tol >= 0.0) || !U || !x || (N.nnzh > 0 && !hvals) ||
+        (M > 0 && (!w || !y || !upat || !t)))
+        return SPI_ERR_ARG;
+    const bool mle = mode == SPI_FIT_MLE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t m1 = std::max<int64_t>(M, 1), n1 = std::max<int32_t>(n, 1);
+    auto& B = c->bg;
+    if (!B.pos) {
+        CK(dev_alloc(c, &B.pos, (size_t)m1));
+        CK(dev_alloc(c, &B.pat, (size_t)m1));
+        CK(dev_alloc(c, &B.vec, (size_t)(m1 + 4 * SPI_PATTERN_MAX + n1 + 2)));
+    }
+    double* td = B.vec;                     // t (host inputs)
+    double* Ud = td + m1;                   // the pattern in use
+    double* Up = Ud + SPI_PATTERN_MAX;      // the previous solve's pattern
+    double* sums = Up + SPI_PATTERN_MAX;    // [2 SPI_PATTERN_MAX]
+    double* xp = sums + 2 * SPI_PATTERN_MAX;  // the previous solve's x
+    double* acc = xp + n1;
+    MleWork W;
+    int rc = mle_work(c, &W);
+    if (rc) return rc;
+    double* xc = W.xc;  // the current solve's x
+    // device views of the inputs (H's values are rewritten in place: the caller's
+    // buffer on the device, the context's copy otherwise)
+    double* hv = hvals;
+    const double *wd = w, *yd = y, *tv = t;
+    const int32_t* pv = upat;
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(N.d_hv, hvals, (size_t)N.nnzh * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(N.d_w, w, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(N.d_y, y, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(td, t, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(B.pat, upat, (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        hv = N.d_hv; wd = N.d_w; yd = N.d_y; tv = td; pv = B.pat;
+    }
+    CK(cudaMemcpyAsync(Ud, U, (size_t)npat * sizeof(double), in, st));
+    // each row's background entry, checked against its pattern index
+    CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+    launch_bg_locate(M, N.args.rowptr, N.args.colind, (int32_t)k0, pv, npat, B.pos, N.d_flag, st);
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) return SPI_ERR_ARG;
+    launch_bg_write(M, B.pos, pv, tv, Ud, hv, st);
+    // the row groups that hold the background columns (their update after U changes)
+    std::vector<uint8_t> mark((size_t)n1, 0);
+    std::vector<char> gsel((size_t)std::max(N.ngroups, 1), 0);
+    std::vector<int32_t> sel;
+    for (int32_t j = 0; j < (int32_t)k0; ++j) {
+        mark[(size_t)j] = 1;
+        for (int64_t p = N.hcp[(size_t)j]; p < N.hcp[(size_t)j + 1]; ++p) {
+            const int32_t g = N.row_grp[(size_t)N.hri[(size_t)p]];
+            if (!gsel[(size_t)g]) { gsel[(size_t)g] = 1; sel.push_back(g); }
+        }
+    }
+    if (!sel.empty()) {
+        CK(cudaMemcpyAsync(N.d_mark, mark.data(), (size_t)n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(N.d_sel, sel.data(), sel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    const size_t nvb = (size_t)c->S.nnz_a * sizeof(double), nb8 = (size_t)n * sizeof(double);
+    // N and b of the current H: all of them, or the background columns' rows and columns
+    auto normal = [&](bool full) -> int {
+        CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
+        if (full) {
+            CK(cudaMemsetAsync(N.d_nv, 0, nvb, st));
+            CK(cudaMemsetAsync(N.d_b, 0, nb8, st));
+            launch_normal(N.args, N.d_groups, N.ngroups, hv, wd, yd, nullptr, nullptr, false, N.d_nv, N.d_b,
+                          N.d_flag, N.smem, st);
+        } else if (!sel.empty()) {
+            launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, nullptr, N.d_mark, true, N.d_nv, N.d_b,
+                          N.d_flag, N.smem, st);
+            launch_normal(N.args, N.d_sel, (int32_t)sel.size(), hv, wd, yd, nullptr, N.d_mark, false, N.d_nv,
+                          N.d_b, N.d_flag, N.smem, st);
+        }
+        int fl = 0;
+        CK(cudaMemcpyAsync(&fl, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return fl ? SPI_ERR_PATTERN : SPI_OK;
+    };
+    // N and b in the context's scratch: 0 = to assemble, 1 = to update after U
+    // changed, 2 = those of the current H
+    int nstate = 0;
+    auto make_normal = [&]() -> int {
+        if (nstate == 2) return SPI_OK;
+        int r = normal(nstate == 0);
+        if (r == SPI_OK) nstate = 2;
+        return r;
+    };
+    // the weighted least-squares solution of the current H into xc
+    auto lsq = [&]() -> int {
+        int r = make_normal();
+        if (r) return r;
+        r = factor_impl(c, 1, N.d_nv, 1, st);
+        if (r) return r;
+        return solve_impl(c, 1, N.d_b, xc, 1, st);
+    };
+    // the statistic at (U, xc) (into hacc) and the pattern's sums (into sums)
     double hacc[2];
-    // e = H xs, C(xs) and the count of e <= 0; with weights, also w and v
-    auto model = [&](const double* xs, bool weights) -> int {
-        launch_spmv_rows(M, N.args.rowptr, N.args.colind, hv, xs, e, st);
+    auto statistic = [&]() -> int {
+        CK(cudaMemsetAsync(sums, 0, 2 * (size_t)npat * sizeof(double), st));
         CK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-        launch_mle_rows(M, e, yd, weights ? w : nullptr, v, acc, st);
+        launch_bg_sums(mle, M, N.args.rowptr, N.args.colind, hv, xc, (int32_t)k0, B.pos, pv, tv, yd, wd, npat, sums,
+                       acc, st);
         CK(cudaMemcpyAsync(hacc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         return SPI_OK;
     };
-    // the Hessian H^T diag(w) H into N's values, the right-hand side H^T v into gx
-    auto hessian = [&]() -> int {
-        CK(cudaMemsetAsync(N.d_nv, 0, (size_t)c->S.nnz_a * sizeof(double), st));
-        CK(cudaMemsetAsync(gx, 0, (size_t)n * sizeof(double), st));
-        CK(cudaMemsetAsync(N.d_flag, 0, sizeof(int), st));
-        launch_normal(N.args, N.d_groups, N.ngroups, hv, w, yd, v, nullptr, false, N.d_nv, gx, N.d_flag, N.smem, st);
-        int flag = 0;
-        CK(cudaMemcpyAsync(&flag, N.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (flag) return SPI_ERR_PATTERN;
-        return factor_impl(c, 1, N.d_nv, 1, st);
-    };
-    int rc = model(xc, true);
-    if (rc) return rc;
-    if (hacc[1] != 0.0) return SPI_ERR_ARG;  // the model must be positive at the start
-    double cx = hacc[0];
-    c->mle_steps = 0;
+    c->bg_iters = 0;
+    bool restore = false, have_x = false;
+    double prev = 0.0;
     for (int it = 0; it < max_iter; ++it) {
-        rc = hessian();
-        if (rc) return rc;
-        rc = solve_impl(c, 1, gx, dx, 1, st);
-        if (rc) return rc;
-        double t = 1.0, ct = cx;
-        bool ok = false;
-        for (int h = 0; h < 60 && !ok; ++h, t *= 0.5) {
-            launch_step(n, xc, dx, t, xt, st);
-            rc = model(xt, false);
+        if (!mle) {
+            rc = lsq();
             if (rc) return rc;
-            ct = hacc[0];
-            ok = hacc[1] == 0.0 && ct <= cx + 1e-12 * std::fabs(cx);  // C's rounding level
-            if (ok) break;
+        } else {
+            // the Newton fit starts from the previous x where the model is positive
+            // there, else from the least-squares solution
+            bool start_ok = false;
+            if (have_x) {
+                rc = mle_model(c, W, hv, yd, xc, false, hacc, st);
+                if (rc) return rc;
+                start_ok = hacc[1] == 0.0;
+            }
+            if (!start_ok) {
+                rc = lsq();
+                if (rc) return rc;
+            }
+            rc = mle_fit(c, W, hv, yd, kFitNewtonSteps, kFitNewtonTol, st);
+            nstate = 0;  // the Hessians overwrote N's values
+            if (rc) return rc;
         }
-        if (!ok) break;  // no step keeps e > 0 and C from growing: stop at the current x
-        CK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-        launch_norms2(n, dx, xt, acc, 1, st);
-        CK(cudaMemcpyAsync(hacc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::swap(xc, xt);
-        cx = ct;
-        c->mle_steps++;
-        if (t * std::sqrt(hacc[0]) <= tol * std::sqrt(hacc[1])) break;
-        rc = model(xc, true);  // weights at the new point
+        have_x = true;
+        rc = statistic();
         if (rc) return rc;
+        if (mle && hacc[1] != 0.0) return SPI_ERR_ARG;
+        const double sv = hacc[0];
+        if (stat) stat[it] = sv;
+        c->bg_iters = it + 1;
+        c->bg_stat = sv;
+        if (it > 0 && sv >= prev - tol * std::fabs(prev)) {
+            restore = sv > prev;
+            break;
+        }
+        if (it == max_iter - 1) break;
+        prev = sv;
+        // keep this solve's pair, then the pattern from x and H's background entries
+        CK(cudaMemcpyAsync(Up, Ud, (size_t)npat * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(xp, xc, nb8, cudaMemcpyDeviceToDevice, st));
+        launch_bg_pattern(npat, sums, Ud, st);
+        launch_bg_write(M, B.pos, pv, tv, Ud, hv, st);
+        if (nstate == 2) nstate = 1;
     }
-    c->mle_cash = cx;
+    if (restore) {  // the previous solve was the better one: its pair, H and factor
+        CK(cudaMemcpyAsync(Ud, Up, (size_t)npat * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(xc, xp, nb8, cudaMemcpyDeviceToDevice, st));
+        launch_bg_write(M, B.pos, pv, tv, Ud, hv, st);
+        c->bg_stat = prev;
+        if (!mle) {
+            nstate = 1;
+            rc = make_normal();
+            if (rc) return rc;
+            rc = factor_impl(c, 1, N.d_nv, 1, st);
+            if (rc) return rc;
+        }
+    }
     if (var) {
-        rc = model(xc, true);
-        if (rc) return rc;
-        rc = hessian();
-        if (rc) return rc;
-        rc = diag_impl(c, 1, nullptr, 0, var, on_device, st);
+        rc = mle ? mle_variances(c, W, hv, yd, var, on_device, st) : diag_impl(c, 1, nullptr, 0, var, on_device, st);
         if (rc) return rc;
     }
-    CK(cudaMemcpyAsync(x, xc, (size_t)n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       st));
+    const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(x, xc, nb8, out, st));
+    CK(cudaMemcpyAsync(U, Ud, (size_t)npat * sizeof(double), out, st));
+    if (!on_device)
+        CK(cudaMemcpyAsync(hvals, N.d_hv, (size_t)N.nnzh * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return finish(c, st);
 }
@@ -1137,6 +1369,8 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->analyse_seconds = c->analyse_seconds;
     o->mle_steps = c->mle_steps;
     o->mle_cash = c->mle_cash;
+    o->bg_iters = c->bg_iters;
+    o->bg_stat = c->bg_stat;
     return SPI_OK;
 }
 

@@ -235,4 +235,156 @@ void launch_step(int32_t n, const double* x, const double* dx, double t, double*
     k_step<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(n, x, dx, t, xt);
 }
 
+
+// ---- Algorithm 1 of the appendix on the "empty-field" pattern: the background
+// entry of row i (its one entry in the first k0 columns, the pointing's
+// normalisation I_p^bg) holds U[upat_i] t_i; with x known the pattern is
+// re-estimated from y^S (the counts of the other columns) and a_i = t_i x_c(i).
+
+namespace {
+
+constexpr int kBgThreads = 256;
+
+// bgpos[i]: the position in H's values of row i's entry in the first k0 columns,
+// -1 if it has none; flag set when a row has two such entries, or when its
+// pattern index does not match (an entry needs 0 <= upat < npat, none needs -1)
+__global__ void k_bg_locate(int64_t nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                            int32_t k0, const int32_t* __restrict__ upat, int32_t npat, int64_t* __restrict__ bgpos,
+                            int* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pos = -1;
+        int cnt = 0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (colind[p] < k0) { pos = p; ++cnt; }
+        const int32_t u = upat[i];
+        const bool bad = cnt > 1 || (cnt == 1) != (u >= 0) || u >= npat;
+        if (bad) atomicOr(flag, 1);
+        bgpos[i] = bad ? -1 : pos;
+    }
+}
+
+// hv[bgpos_i] = U[upat_i] t_i
+__global__ void k_bg_write(int64_t nrows, const int64_t* __restrict__ bgpos, const int32_t* __restrict__ upat,
+                           const double* __restrict__ t, const double* __restrict__ U, double* __restrict__ hv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = bgpos[i];
+        if (p >= 0) hv[p] = U[upat[i]] * t[i];
+    }
+}
+
+// One warp per row: y^S_i, a_i = t_i x_c(i), r_i = y_i - y^S_i and e_i = y^S_i + h_bg x_c(i).
+// sums[k] / sums[npat + k]: the numerator / denominator of U_k,
+//   least squares (kMle 0): r a w / a^2 w;  likelihood (kMle 1): r / a,
+// accumulated per CTA in shared memory; acc[0] += the statistic at (U, x):
+// w (y - e)^2, or e - y ln e; acc[1] += the rows with e <= 0 (likelihood).
+template <int kMle>
+__global__ void __launch_bounds__(kBgThreads) k_bg_sums(int64_t nrows, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ colind,
+                                                        const double* __restrict__ hv, const double* __restrict__ x,
+                                                        int32_t k0, const int64_t* __restrict__ bgpos,
+                                                        const int32_t* __restrict__ upat,
+                                                        const double* __restrict__ t, const double* __restrict__ y,
+                                                        const double* __restrict__ w, int32_t npat,
+                                                        double* __restrict__ sums, double* __restrict__ acc) {
+    extern __shared__ double bsm[];  // [2 npat]
+    for (int k = threadIdx.x; k < 2 * npat; k += kBgThreads) bsm[k] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double stat = 0.0, bad = 0.0;
+    for (int64_t i = ((int64_t)blockIdx.x * kBgThreads + threadIdx.x) >> 5; i < nrows;
+         i += ((int64_t)gridDim.x * kBgThreads) >> 5) {
+        double s = 0.0;
+        for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+            const int32_t j = colind[p];
+            if (j >= k0) s += hv[p] * x[j];
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const int64_t p = bgpos[i];
+            double e = s, a = 0.0;
+            if (p >= 0) {
+                const double xc = x[colind[p]];
+                a = t[i] * xc;
+                e += hv[p] * xc;
+            }
+            const double yi = y[i];
+            if (kMle) {
+                if (e > 0.0) stat += yi > 0.0 ? e - yi * log(e) : e;
+                else bad += 1.0;
+            } else {
+                const double d = yi - e;
+                stat += w[i] * d * d;
+            }
+            if (p >= 0) {
+                const int32_t k = upat[i];
+                const double r = yi - s;
+                if (kMle) {
+                    atomicAdd(bsm + k, r);
+                    atomicAdd(bsm + npat + k, a);
+                } else {
+                    const double wa = w[i] * a;
+                    atomicAdd(bsm + k, r * wa);
+                    atomicAdd(bsm + npat + k, a * wa);
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        stat += __shfl_down_sync(0xffffffffu, stat, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        if (stat != 0.0) atomicAdd(acc, stat);
+        if (bad != 0.0) atomicAdd(acc + 1, bad);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * npat; k += kBgThreads)
+        if (bsm[k] != 0.0) atomicAdd(sums + k, bsm[k]);
+}
+
+// U_k = numerator / denominator where the denominator is positive
+__global__ void k_bg_pattern(int32_t npat, const double* __restrict__ sums, double* __restrict__ U) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npat; k += gridDim.x * blockDim.x) {
+        const double den = sums[npat + k];
+        if (den > 0.0) U[k] = sums[k] / den;
+    }
+}
+
+int bg_grid(int64_t nrows, int per_cta) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((nrows + per_cta - 1) / per_cta, 152 * 8));
+}
+
+}  // namespace
+
+void launch_bg_locate(int64_t nrows, const int64_t* rowptr, const int32_t* colind, int32_t k0, const int32_t* upat,
+                      int32_t npat, int64_t* bgpos, int* flag, cudaStream_t st) {
+    if (nrows == 0) return;
+    k_bg_locate<<<bg_grid(nrows, 256), 256, 0, st>>>(nrows, rowptr, colind, k0, upat, npat, bgpos, flag);
+}
+
+void launch_bg_write(int64_t nrows, const int64_t* bgpos, const int32_t* upat, const double* t, const double* U,
+                     double* hv, cudaStream_t st) {
+    if (nrows == 0) return;
+    k_bg_write<<<bg_grid(nrows, 256), 256, 0, st>>>(nrows, bgpos, upat, t, U, hv);
+}
+
+void launch_bg_sums(bool mle, int64_t nrows, const int64_t* rowptr, const int32_t* colind, const double* hv,
+                    const double* x, int32_t k0, const int64_t* bgpos, const int32_t* upat, const double* t,
+                    const double* y, const double* w, int32_t npat, double* sums, double* acc, cudaStream_t st) {
+    if (nrows == 0) return;
+    const int grid = bg_grid(nrows, kBgThreads / 32);
+    const size_t smem = 2 * (size_t)npat * sizeof(double);
+    if (mle)
+        k_bg_sums<1><<<grid, kBgThreads, smem, st>>>(nrows, rowptr, colind, hv, x, k0, bgpos, upat, t, y, w, npat,
+                                                     sums, acc);
+    else
+        k_bg_sums<0><<<grid, kBgThreads, smem, st>>>(nrows, rowptr, colind, hv, x, k0, bgpos, upat, t, y, w, npat,
+                                                     sums, acc);
+}
+
+void launch_bg_pattern(int32_t npat, const double* sums, double* U, cudaStream_t st) {
+    if (npat == 0) return;
+    k_bg_pattern<<<(npat + 255) / 256, 256, 0, st>>>(npat, sums, U);
+}
+
 }  // namespace spi

@@ -157,5 +157,15 @@ void launch_spmv_rows(int64_t nrows, const int64_t* rowptr, const int32_t* colin
 void launch_mle_rows(int64_t nrows, const double* e, const double* y, double* w, double* v, double* acc,
                      cudaStream_t st);
 void launch_step(int32_t n, const double* x, const double* dx, double t, double* xt, cudaStream_t st);
+// Algorithm 1 (the empty-field pattern): background entries, the pattern's sums
+// and statistic, the pattern update
+void launch_bg_locate(int64_t nrows, const int64_t* rowptr, const int32_t* colind, int32_t k0, const int32_t* upat,
+                      int32_t npat, int64_t* bgpos, int* flag, cudaStream_t st);
+void launch_bg_write(int64_t nrows, const int64_t* bgpos, const int32_t* upat, const double* t, const double* U,
+                     double* hv, cudaStream_t st);
+void launch_bg_sums(bool mle, int64_t nrows, const int64_t* rowptr, const int32_t* colind, const double* hv,
+                    const double* x, int32_t k0, const int64_t* bgpos, const int32_t* upat, const double* t,
+                    const double* y, const double* w, int32_t npat, double* sums, double* acc, cudaStream_t st);
+void launch_bg_pattern(int32_t npat, const double* sums, double* U, cudaStream_t st);
 
 }  // namespace spi

@@ -25,8 +25,11 @@ SPI_ORDER_ND, SPI_ORDER_NATURAL = 0, 1
 EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_factor", "spi_factor_batch",
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
-           "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton"]
+           "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton",
+           "spi_background_fit"]
 SPI_INVERSE_BLOCK_MAX = 512
+SPI_PATTERN_MAX = 2048
+SPI_FIT_LSQ, SPI_FIT_MLE = 0, 1
 
 
 class spi_options(ctypes.Structure):
@@ -49,7 +52,7 @@ class spi_stats(ctypes.Structure):
                 ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),
                 ("rhs_block", ctypes.c_int64),
                 ("analyse_seconds", ctypes.c_double), ("mle_steps", ctypes.c_int64),
-                ("mle_cash", ctypes.c_double)]
+                ("mle_cash", ctypes.c_double), ("bg_iters", ctypes.c_int64), ("bg_stat", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +98,8 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_normal_assemble.argtypes = [V, V, V, V, V, V, I, V]; L.spi_normal_assemble.restype = I
     L.spi_normal_update.argtypes = [V, I64, V, V, V, V, V, V, I, V]; L.spi_normal_update.restype = I
     L.spi_mle_newton.argtypes = [V, V, V, V, I, ctypes.c_double, V, I, V]; L.spi_mle_newton.restype = I
+    L.spi_background_fit.argtypes = [V, I64, V, V, I, V, V, V, V, V, I, I, ctypes.c_double, V, V, I, V]
+    L.spi_background_fit.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -306,6 +311,35 @@ def spi_mle_newton(ctx, hvals, y, x, max_iter=30, tol=1e-12, var=None, stream=No
     del bufs, vb
 
 
+def spi_background_fit(ctx, k0, upat, t, hvals, w, y, U, x, mode=SPI_FIT_LSQ, max_iter=20, tol=1e-9,
+                       stat=None, var=None, stream=None) -> None:
+    """Algorithm 1 (the empty-field pattern): hvals and U in/out, x and var out,
+    stat (host float64[max_iter]) receives the statistic of each solve."""
+    bufs = [_buf(a, np.float64) for a in (t, hvals, w, y, U, x)]
+    pb = _buf(upat, np.int32)
+    vb = _buf(var, np.float64) if var is not None else (None, None, None)
+    devs = {d for _, d, _ in bufs} | {pb[1]}
+    if vb[1] is not None:
+        devs.add(vb[1])
+    if len(devs) != 1:
+        raise TypeError("upat, t, hvals, w, y, U, x and var must all be host or all be device buffers")
+    for a in (hvals, U, x, var):
+        if a is not None and not _is_torch(a) and not (isinstance(a, np.ndarray) and a.dtype == np.float64
+                                                       and a.flags.c_contiguous):
+            raise TypeError("hvals, U, x and var must be contiguous float64 numpy arrays or CUDA tensors")
+    sp_ = None
+    if stat is not None:
+        if not (isinstance(stat, np.ndarray) and stat.dtype == np.float64 and stat.flags.c_contiguous
+                and stat.size >= max_iter):
+            raise TypeError("stat must be a contiguous float64 numpy array of max_iter entries")
+        sp_ = stat.ctypes.data_as(ctypes.c_void_p)
+    U_len = U.numel() if _is_torch(U) else len(U)
+    _check(lib().spi_background_fit(ctx, int(k0), pb[0], bufs[0][0], int(U_len), bufs[1][0], bufs[2][0],
+                                    bufs[3][0], bufs[4][0], bufs[5][0], int(mode), int(max_iter), float(tol), sp_,
+                                    vb[0], devs.pop(), _stream(stream)), "spi_background_fit")
+    del bufs, pb, vb
+
+
 def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
     """Variances for device idx into device out without any device allocation
     by the library (fixed scratch array; see include/spi.h)."""
@@ -468,6 +502,27 @@ class Solver:
             var = np.empty(self.n, np.float64) if variances else None
         spi_mle_newton(self._h, hvals, y, x, max_iter, tol, var, stream)
         return x, var
+
+    def background_fit(self, k0, upat, t, hvals, w, y, U0, mode="lsq", max_iter=20, tol=1e-9,
+                       variances=True, stream=None):
+        """Algorithm 1: fit the empty-field pattern U with the solution.  hvals
+        (float64 numpy array or CUDA tensor, CSR order of normal_setup) is
+        rewritten in place with the returned pattern.  Returns
+        (x, U, statistic per solve, diag(Hess^-1) or None)."""
+        m = SPI_FIT_LSQ if mode == "lsq" else SPI_FIT_MLE
+        if _is_torch(hvals):
+            import torch
+            U = torch.as_tensor(U0, dtype=torch.float64, device=hvals.device).clone()
+            x = torch.empty(self.n, dtype=torch.float64, device=hvals.device)
+            var = torch.empty_like(x) if variances else None
+        else:
+            U = np.array(U0, dtype=np.float64)
+            x = np.empty(self.n, np.float64)
+            var = np.empty(self.n, np.float64) if variances else None
+        stat = np.zeros(max_iter, np.float64)
+        spi_background_fit(self._h, k0, upat, t, hvals, w, y, U, x, m, max_iter, tol, stat, var, stream)
+        iters = int(self.info()["bg_iters"])
+        return x, U, stat[:iters].copy(), var
 
     def info(self) -> dict:
         return spi_info(self._h)

@@ -170,3 +170,6 @@ def test_normal_setup_validates_on_the_host(P):
     with pytest.raises(P.SpiError) as e:  # assembly before setup
         s.normal_assemble(np.zeros(1), np.zeros(1), np.zeros(1))
     assert e.value.code == 7
+    with pytest.raises(P.SpiError) as e:  # the empty-field loop before setup
+        s.background_fit(1, np.zeros(1, np.int32), np.ones(1), np.zeros(1), np.ones(1), np.ones(1), np.ones(1))
+    assert e.value.code == 7

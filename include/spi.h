@@ -83,6 +83,11 @@ typedef struct spi_options {
                         SPI_ERR_TIMEOUT (a test of that path).  After giving up, the kernel
                         still waits, with the default limit, for its own MMAs in flight
                         before it frees its tensor memory */
+    int diag_ctas_per_sm;  /* 0 = the variance kernels of spi_diag_inverse take every SM
+                        slot they fit in; k > 0: at most k of their CTAs per
+                        SM (their shared memory is padded to enforce it), so that work on
+                        another stream -- a spi_solve running concurrently -- keeps room
+                        on every SM instead of waiting for variance CTAs to finish */
 } spi_options;
 
 typedef struct spi_stats {

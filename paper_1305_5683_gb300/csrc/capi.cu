@@ -96,6 +96,7 @@ struct spi_ctx {
         double *d_hv = nullptr, *d_w = nullptr, *d_y = nullptr, *d_nv = nullptr, *d_b = nullptr;
     } nrm;
     int64_t zg_cap = 0, blk_rows = 0;
+    size_t diag_smem_pad = 0;  // dynamic shared memory of a variance CTA at least this (diag_ctas_per_sm)
     int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
     int64_t bad_pivot = -1, bad_band = -1;
@@ -196,7 +197,18 @@ int ensure_device(spi_ctx* c) {
         CK(dev_alloc(c, &c->d_norm, 2 * nb));
         CK(cudaMallocHost((void**)&c->h_norm, 2 * nb * sizeof(double)));
     }
-    CK(diag_kernel_setup(512));
+    if (c->opt.diag_ctas_per_sm > 0) {  // pad the variance kernels' shared memory: at most k per SM
+        int dev = 0, per_sm = 0, reserved = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int k = c->opt.diag_ctas_per_sm;
+        size_t pad = (size_t)(per_sm / (k + 1) - reserved + 128);
+        pad = (pad + 127) & ~(size_t)127;
+        // k + 1 CTAs of pad + reserved bytes exceed the SM; k still fit
+        if ((int64_t)k * (int64_t)(pad + reserved) <= per_sm) c->diag_smem_pad = pad;
+    }
+    CK(diag_kernel_setup(512, c->diag_smem_pad));
     CK(factor_kernel_setup());
     c->dev_ready = true;
     return SPI_OK;
@@ -397,8 +409,8 @@ void launch_diag(spi_ctx* c, const DevDiagPlan& p, int nb, int64_t nout, double*
     Strides bs = c->bs;
     bs.Z = p.zsize;
     bs.out = nout;
-    if (mixed_of(c)) launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, st);
-    else launch_diag_inverse(c->dsym, p, c->d_L, c->d_D, out, nb, bs, st);
+    if (mixed_of(c)) launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, c->diag_smem_pad, st);
+    else launch_diag_inverse(c->dsym, p, c->d_L, c->d_D, out, nb, bs, c->diag_smem_pad, st);
 }
 
 // Build the plan for the pivots `piv`; with an automatic block size (the

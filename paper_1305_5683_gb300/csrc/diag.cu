@@ -21,6 +21,8 @@
 // copy of L, FP32 Z, FP64 variance accumulation).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "spi_internal.cuh"
 
 namespace spi {
@@ -313,10 +315,10 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
 
 template <typename T>
 void launch_t(const DevSym& d, const DevDiagPlan& p, const T* L, const double* D, double* out, int nb,
-              const Strides& bs, cudaStream_t st) {
+              const Strides& bs, size_t smem_min, cudaStream_t st) {
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
                p.rhs_col, p.urel, p.zbase, p.Z};
-    size_t sm = diag_smem_bytes<T>(p.B);
+    const size_t sm = std::max(diag_smem_bytes<T>(p.B), smem_min);
     k_diag_inv<T><<<dim3(p.nblocks, nb), kThreads, sm, st>>>(d, a, L, D, out, bs);
 }
 
@@ -398,32 +400,33 @@ void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L
     bs.Z = p.zsize;
     bs.out = p.nrhs;
     cudaMemsetAsync(Zg, 0, (size_t)R * (size_t)p.nrhs * sizeof(double), st);
-    launch_t<double>(d, p, L, D, var_scratch, 1, bs, st);
+    launch_t<double>(d, p, L, D, var_scratch, 1, bs, 0, st);
     k_gather_blocks<<<p.nblocks, 256, 0, st>>>(p.Z, p.B, p.zbase, p.blk_ptr, p.rowmap, p.nrhs, Zg);
     const int nt = (int)((p.nrhs + kT - 1) / kT);
     k_inverse_gram<<<nt * (nt + 1) / 2, 128, 0, st>>>(Zg, (int)p.nrhs, R, p.zpiv, D, p.rhs_out, out, ldo);
 }
 
-cudaError_t diag_kernel_setup(int B) {
+cudaError_t diag_kernel_setup(int B, size_t smem_min) {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)diag_smem_bytes<double>(B));
+                                         (int)std::max(diag_smem_bytes<double>(B), smem_min));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_diag_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)diag_f32_smem_bytes((B + 7) & ~7));
+                                (int)std::max(diag_f32_smem_bytes((B + 7) & ~7), smem_min));
 }
 
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
-                         int nb, const Strides& bs, cudaStream_t st) {
+                         int nb, const Strides& bs, size_t smem_min, cudaStream_t st) {
     if (p.nblocks == 0 || nb == 0) return;
-    launch_t<double>(d, p, L, D, out, nb, bs, st);
+    launch_t<double>(d, p, L, D, out, nb, bs, smem_min, st);
 }
 
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             int nb, const Strides& bs, cudaStream_t st) {
+                             int nb, const Strides& bs, size_t smem_min, cudaStream_t st) {
     if (p.nblocks == 0 || nb == 0) return;
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
                p.rhs_col, p.urel, p.zbase, p.Z};
-    k_diag_inv_f32<<<dim3(p.nblocks, nb), kFThreads, diag_f32_smem_bytes(p.B), st>>>(d, a, L, D, out, bs);
+    k_diag_inv_f32<<<dim3(p.nblocks, nb), kFThreads, std::max(diag_f32_smem_bytes(p.B), smem_min), st>>>(
+        d, a, L, D, out, bs);
 }
 
 }  // namespace spi

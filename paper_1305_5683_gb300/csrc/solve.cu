@@ -78,9 +78,12 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
 }
 
 // Backward, first launch of a level: y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]]
-// for a chunk of 32 of the supernode's columns, stored into w.  Lanes run over
-// the rows below (coalesced column reads), each thread keeps the 32 partial
-// sums, then warps reduce by shuffles and the CTA through shared memory.
+// for a chunk of 32 of the supernode's columns, stored into w.  Warp q takes
+// the columns q, q + 8, q + 16, q + 24 of the chunk; its lanes run over the
+// rows below (coalesced column reads, the gathered x shared by the four
+// columns) and a shuffle reduction finishes each dot product.  Four partial
+// sums per thread keep the kernel's registers low enough for several CTAs
+// per SM.
 __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* __restrict__ items,
                                                        const double* __restrict__ L, const double* __restrict__ D,
                                                        const double* __restrict__ z, const double* __restrict__ x,
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     z += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
     w += blockIdx.y * bs.n;
-    __shared__ double part[kThreads / 32][kT];
+    constexpr int kWarps = kThreads / 32, kPer = kT / kWarps;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -98,27 +101,23 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     const double* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const int c0 = chunk * kT, nc = min(kT, k - c0);
-    double acc[kT];
+    double acc[kPer];
 #pragma unroll
-    for (int c = 0; c < kT; ++c) acc[c] = 0.0;
-    for (int64_t t = k + tid; t < m; t += kThreads) {
+    for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
+    for (int64_t t = k + lane; t < m; t += 32) {
         const double xv = x[rows[t]];
-        const double* col = P + t + (int64_t)c0 * m;
 #pragma unroll
-        for (int c = 0; c < kT; ++c)
-            if (c < nc) acc[c] += col[(int64_t)c * m] * xv;
+        for (int q = 0; q < kPer; ++q) {
+            const int c = warp + kWarps * q;
+            if (c < nc) acc[q] += P[t + (int64_t)(c0 + c) * m] * xv;
+        }
     }
 #pragma unroll
-    for (int c = 0; c < kT; ++c) {
-        double v = acc[c];
+    for (int q = 0; q < kPer; ++q) {
+        double v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == c) part[warp][c] = v;
-    }
-    __syncthreads();
-    if (tid < nc) {
-        double v = 0.0;
-        for (int q = 0; q < kThreads / 32; ++q) v += part[q][tid];
-        w[f + c0 + tid] = z[f + c0 + tid] / D[f + c0 + tid] - v;
+        const int c = warp + kWarps * q;
+        if (lane == 0 && c < nc) w[f + c0 + c] = z[f + c0 + c] / D[f + c0 + c] - v;
     }
 }
 

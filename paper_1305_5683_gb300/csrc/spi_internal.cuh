@@ -122,10 +122,11 @@ void launch_norms2(int32_t n, const double* a, const double* b, double* out, int
 void launch_axpy(int32_t n, const double* dx, double* x, int nb, cudaStream_t st);
 // ---- diag.cu
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
-                         int nb, const Strides& bs, cudaStream_t st);
+                         int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             int nb, const Strides& bs, cudaStream_t st);
-cudaError_t diag_kernel_setup(int B);
+                             int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
+// smem_min: the launches' dynamic shared memory is at least this (0: what they need)
+cudaError_t diag_kernel_setup(int B, size_t smem_min);
 // (N^-1)(I, I) for the pivots of a plan with zpiv/rowmap: the blocks' forward
 // solves (variances to var_scratch), their vectors gathered into Zg (R rows x
 // nrhs), then the Gram product into out (ldo = leading dimension, positions

@@ -638,8 +638,10 @@ def main():
     # the mixed-precision form on the same workload and the same step
     mixed = None
     if not args.no_mixed:
+        # the mixed solve (two sweeps and a residual) outlasts the variances: cap the
+        # variance kernel at 3 CTAs per SM so that the solve keeps room beside it
         sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, relax=args.relax,
-                                   precision=P.SPI_PREC_MIXED_FP32)
+                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3)
         xm = torch.empty_like(b)
         varm = torch.empty_like(var)
 
@@ -737,7 +739,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(pb, {"ordering": "nested dissection", "rhs_block": args.rhs_block,
                                  "streams": "after the factor, solve and variances run concurrently on two streams; "
-                                            "phases_ms are each phase's own span, ms_per_step the whole step",
+                                            "phases_ms are each phase's own span, ms_per_step the whole step; "
+                                            "mixed leg: variance kernel capped at 3 CTAs per SM "
+                                            "(spi_options.diag_ctas_per_sm)",
                                  "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
         "phases_ms": {"factor": statistics.mean(t_fac), "solve": statistics.mean(t_sol),
                       "diag_inverse": statistics.mean(t_dia)},

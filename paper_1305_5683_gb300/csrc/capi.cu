@@ -648,7 +648,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (rc != 0) { delete c; return rc; }
     try {
         build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32);
-        build_solve_plan(c->S, c->SP);
+        build_solve_plan(c->S, c->SP, std::max(1, o.batch));
         if (n > 0) {  // the residual of the mixed form and the normal-equation assembly use it
             c->in_colptr.assign(colptr, colptr + n + 1);
             c->in_rowind.assign(rowind, rowind + colptr[n]);

@@ -13,6 +13,15 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFwdRows = 512;  // rows below the block per forward CTA
 constexpr int kBwdCols = 256;  // columns per backward CTA
+// In a batch of bands, a level runs each sweep in one launch, one CTA per
+// (supernode, band) looping over the supernode's 32-column steps, when its
+// largest supernode's work (k m - k^2 / 2 FMAs, on one SM) is below what the
+// launch-per-step form spends on its chain of launches (about 10 us each,
+// ~20,000 FMAs of one SM).  For a single problem the launch-per-step form
+// measured faster at every level (its rows spread over more CTAs), so it
+// keeps that form; so do the wide fronts near the root.
+constexpr int64_t kFuseFmaPerStep = 20000;
+constexpr int kAncRegs = 4;  // ancestor rows per thread whose updates are summed in registers
 
 __global__ void k_permute_in(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ b,
                              double* __restrict__ w) {
@@ -162,6 +171,134 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     }
 }
 
+// Forward sweep of one level in one launch: one CTA per (supernode, band)
+// runs all of the supernode's 32-column steps.  Each step solves the diagonal
+// block in warp 0 (lane r owns row r, as k_fwd_step) and updates the
+// supernode's later pivots in place; the contributions to the ancestors' rows
+// are summed over the steps in registers (thread t owns rows k + t + 256 j)
+// and added once at the end, by atomics since siblings share ancestors.
+__global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t* __restrict__ items,
+                                                        const double* __restrict__ L, double* __restrict__ w,
+                                                        double* __restrict__ z, Strides bs) {
+    L += blockIdx.y * bs.L;
+    w += blockIdx.y * bs.n;
+    z += blockIdx.y * bs.n;
+    __shared__ double xb[kT];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int s = items[2 * blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const double* P = L + d.lptr[s];
+    const int32_t* rows = d.srows + d.srowptr[s];
+    const bool in_regs = m - k <= (int64_t)kAncRegs * kThreads;
+    double anc[kAncRegs];
+#pragma unroll
+    for (int j = 0; j < kAncRegs; ++j) anc[j] = 0.0;
+    for (int cb = 0; cb < k; cb += kT) {
+        const int wb = min(kT, k - cb);
+        if (tid < 32) {
+            double lrow[kT];
+#pragma unroll
+            for (int c = 0; c < kT; ++c)
+                lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
+            double x = lane < wb ? w[f + cb + lane] : 0.0;
+#pragma unroll
+            for (int c = 0; c < kT - 1; ++c) {
+                const double xc = __shfl_sync(0xffffffffu, x, c);
+                x -= lrow[c] * xc;
+            }
+            xb[lane] = x;
+            if (lane < wb) z[f + cb + lane] = x;
+        }
+        __syncthreads();
+        for (int r = cb + wb + tid; r < k; r += kThreads) {  // the supernode's later pivots
+            double acc = 0.0;
+            for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+            w[f + r] -= acc;
+        }
+        if (in_regs) {
+#pragma unroll
+            for (int j = 0; j < kAncRegs; ++j) {
+                const int64_t r = k + tid + (int64_t)j * kThreads;
+                if (r < m) {
+                    double acc = 0.0;
+                    for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+                    anc[j] += acc;
+                }
+            }
+        } else {
+            for (int64_t r = k + tid; r < m; r += kThreads) {
+                double acc = 0.0;
+                for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+                atomicAdd(w + rows[r], -acc);
+            }
+        }
+        __syncthreads();  // w of the next diagonal block, and xb, are rewritten
+    }
+    if (in_regs) {
+#pragma unroll
+        for (int j = 0; j < kAncRegs; ++j) {
+            const int64_t r = k + tid + (int64_t)j * kThreads;
+            if (r < m) atomicAdd(w + rows[r], -anc[j]);
+        }
+    }
+}
+
+// Backward sweep of one level in one launch: one CTA per (supernode, band).
+// First y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]] for all of its
+// columns (a warp per column, as k_bwd_init), then its 32-column steps in
+// descending order (as k_bwd_step), each updating every earlier column.
+__global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t* __restrict__ items,
+                                                        const double* __restrict__ L, const double* __restrict__ D,
+                                                        const double* __restrict__ z, double* __restrict__ x,
+                                                        double* __restrict__ w, Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    z += blockIdx.y * bs.n;
+    x += blockIdx.y * bs.n;
+    w += blockIdx.y * bs.n;
+    constexpr int kWarps = kThreads / 32;
+    __shared__ double xb[kT];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = items[2 * blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const double* P = L + d.lptr[s];
+    const int32_t* rows = d.srows + d.srowptr[s];
+    for (int c = warp; c < k; c += kWarps) {
+        double acc = 0.0;
+        for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) w[f + c] = z[f + c] / D[f + c] - acc;
+    }
+    __syncthreads();
+    for (int cb = ((k - 1) / kT) * kT; cb >= 0; cb -= kT) {
+        const int wb = min(kT, k - cb);
+        if (tid < 32) {
+            double lcol[kT];
+#pragma unroll
+            for (int r = 0; r < kT; ++r)
+                lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
+            double y = lane < wb ? w[f + cb + lane] : 0.0;
+#pragma unroll
+            for (int r = kT - 1; r > 0; --r) {
+                const double xr = __shfl_sync(0xffffffffu, y, r);
+                y -= lcol[r] * xr;
+            }
+            xb[lane] = y;
+            if (lane < wb) x[f + cb + lane] = y;
+        }
+        __syncthreads();
+        for (int a = tid; a < cb; a += kThreads) {
+            const double* col = P + (int64_t)a * m + cb;
+            double acc = 0.0;
+            for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
+            w[f + a] -= acc;
+        }
+        __syncthreads();
+    }
+}
+
 // r -= N x for the symmetric N given by its lower CSC (caller numbering), one
 // warp per column: the column's dot product for r_j, and the mirrored
 // upper-triangle entries scattered into r_i.
@@ -243,12 +380,30 @@ void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double*
     k_permute_out<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, perm, w, x);
 }
 
-void build_solve_plan(const Symbolic& S, SolvePlan& P) {
+void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
     P = SolvePlan();
     for (int32_t l = 0; l < S.nlevels; ++l) {
         int32_t kmax = 0;
-        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p)
-            kmax = std::max(kmax, S.k_of(S.level_list[p]));
+        int64_t work = 0;
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p];
+            const int64_t k = S.k_of(s), m = S.m_of(s);
+            kmax = std::max<int32_t>(kmax, (int32_t)k);
+            work = std::max(work, k * m - k * k / 2);
+        }
+        if (batch > 1 && work <= (int64_t)((kmax + kT - 1) / kT) * kFuseFmaPerStep) {  // one launch per sweep
+            Launch lf{10, 0, (int64_t)P.fwd_items.size() / 2, 0};
+            Launch lb{11, 0, (int64_t)P.bwd_items.size() / 2, 0};
+            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+                const int32_t s = S.level_list[p];
+                if (S.k_of(s) == 0) continue;
+                P.fwd_items.push_back(s); P.fwd_items.push_back(0); lf.count++;
+                P.bwd_items.push_back(s); P.bwd_items.push_back(0); lb.count++;
+            }
+            P.fwd_launches.push_back(lf);
+            P.bwd_level_launches.push_back({lb});
+            continue;
+        }
         const int32_t nsteps = (kmax + kT - 1) / kT;
         std::vector<Launch> fw, bw;
         for (int32_t b = 0; b < nsteps; ++b) {
@@ -294,6 +449,8 @@ void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_item
     switch (l.kind) {
         case 4: k_fwd_step<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z, bs); break;
         case 5: k_bwd_init<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
+        case 10: k_fwd_level<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, L, w, z, bs); break;
+        case 11: k_bwd_level<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
         default: k_bwd_step<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x, bs); break;
     }
 }

@@ -52,7 +52,9 @@ struct Strides {
 struct Launch {
     int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
                      // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front,
-                     // 9 tensor-core trailing panel update of a wide front (mixed precision)
+                     // 9 tensor-core trailing panel update of a wide front (mixed precision);
+                     // solves: 4 forward step, 5 backward first launch of a level, 6 backward
+                     // step, 10 / 11 forward / backward sweep of a whole level
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs
@@ -81,7 +83,8 @@ struct SolvePlan {
     std::vector<std::vector<Launch>> bwd_level_launches;
 };
 
-void build_solve_plan(const Symbolic& S, SolvePlan& P);
+// batch: bands per launch (the fused per-level sweeps are used for batches only)
+void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch);
 
 struct DevDiagPlan {
     int32_t B = 0, nblocks = 0;

@@ -696,6 +696,25 @@ def main():
             inv_block[name] = {"nidx": 512, "ms": ms_b, "entries_per_s": 512 * 512 / (ms_b / 1e3)}
         except Exception as e:
             inv_block[name] = {"error": f"{type(e).__name__}: {e}"}
+    # scattered entries: 5,000 random pairs among 1,024 time-bin columns of one time window
+    try:
+        rng = np.random.default_rng(12)
+        U = bins[len(bins) // 2: len(bins) // 2 + 1024].astype(np.int32)
+        r = torch.from_numpy(U[rng.integers(0, len(U), 5000)]).to(dev)
+        c = torch.from_numpy(U[rng.integers(0, len(U), 5000)]).to(dev)
+        o = torch.empty(5000, dtype=torch.float64, device=dev)
+        s.inverse_entries(r, c, out=o, stream=st)
+        s.sync(st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.inverse_entries(r, c, out=o, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms_e = e0.elapsed_time(e1)
+        inv_block["entries_5000_pairs_over_1024"] = {"nent": 5000, "distinct": len(U), "blocks": 10, "ms": ms_e,
+                                                     "entries_per_s": 5000 / (ms_e / 1e3)}
+    except Exception as e:
+        inv_block["entries_5000_pairs_over_1024"] = {"error": f"{type(e).__name__}: {e}"}
 
     normal = None
     if not args.no_batch:

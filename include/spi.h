@@ -227,6 +227,25 @@ int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int
  * repeated), SPI_ERR_OOM, SPI_ERR_CUDA. */
 int spi_inverse_block(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream);
 
+/* Scattered entries of the inverse: out[t] = (N^-1)_{rows[t], cols[t]} for any
+ * list of index pairs -- "any set of entries" of the inverse (paper
+ * Sec. 3.3.1).  The distinct indices of the list, in elimination order, are
+ * cut into groups of SPI_INVERSE_BLOCK_MAX / 2; every pair of groups holding a
+ * requested entry is computed as one spi_inverse_block of the two groups'
+ * indices (the same pruned forward solves and Gram product, FP64), and the
+ * entries are picked from it on the device.  Cost: one block per group pair
+ * present in the list, so a list concentrated on a few hundred unknowns costs
+ * one block, while covariances spread over all n unknowns cost up to
+ * (n / 256)^2 / 2 blocks.
+ *   rows, cols  int32[nent], caller numbering (pairs may repeat, in either order)
+ *   out         float64[nent]
+ * on_device: rows, cols and out are device pointers.  Band 0 of a batched
+ * context; the block plan cache of spi_inverse_block is reused and replaced.
+ * Errors: SPI_ERR_STATE (not factored), SPI_ERR_ARG (NULL buffer, nent < 0, an
+ * index out of range), SPI_ERR_OOM, SPI_ERR_CUDA. */
+int spi_inverse_entries(spi_ctx* ctx, const int32_t* rows, const int32_t* cols, int64_t nent, double* out,
+                        int on_device, void* stream);
+
 /* The normal equations on the device (paper Sec. 4.1, Eq. 7): N = H^T W H on
  * the pattern this context was analysed with, and b = H^T W y, from the design
  * matrix H (rows = observations) -- the step before spi_factor, and its update

@@ -722,26 +722,12 @@ int spi_diag_inverse_batch(spi_ctx* c, int32_t nbatch, const int32_t* idx, int64
     return diag_impl(c, nbatch, idx, nidx, out, on_device, (cudaStream_t)stream);
 }
 
-int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
-    if (!c) return SPI_ERR_ARG;
-    if (!c->factored) return SPI_ERR_STATE;
-    if (nidx < 0 || nidx > SPI_INVERSE_BLOCK_MAX || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
-    if (nidx == 0) return SPI_OK;
-    cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// (N^-1)[key, key] (row-major, |key| x |key|) into the device buffer od; key: distinct caller
+// indices, at most SPI_INVERSE_BLOCK_MAX, already checked.  The plan is cached per key.
+int inverse_block_impl(spi_ctx* c, std::vector<int32_t>& key, double* od, cudaStream_t st) {
     const Symbolic& S = c->S;
-    std::vector<int32_t> key((size_t)nidx);
-    if (on_device) {
-        CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-    } else {
-        std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
-    }
-    {
-        std::vector<int32_t> srt(key);
-        std::sort(srt.begin(), srt.end());
-        if (srt.front() < 0 || srt.back() >= S.n) return SPI_ERR_ARG;
-        if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SPI_ERR_ARG;
-    }
+    const int64_t nidx = (int64_t)key.size();
     if (!c->plan_blk_ready || key != c->plan_blk_key) {
         c->plan_blk_ready = false;
         std::vector<int32_t> piv((size_t)nidx), pos((size_t)nidx);
@@ -787,14 +773,139 @@ int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out,
         c->plan_blk_key.swap(key);
         c->plan_blk_ready = true;
     }
+    launch_inverse_block(c->dsym, c->plan_blk, c->d_L, c->d_D, c->d_out, c->d_zg, c->blk_rows, od, nidx, st);
+    return SPI_OK;
+}
+}  // namespace
+
+int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nidx < 0 || nidx > SPI_INVERSE_BLOCK_MAX || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
+    if (nidx == 0) return SPI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    std::vector<int32_t> key((size_t)nidx);
+    if (on_device) {
+        CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+    }
+    {
+        std::vector<int32_t> srt(key);
+        std::sort(srt.begin(), srt.end());
+        if (srt.front() < 0 || srt.back() >= S.n) return SPI_ERR_ARG;
+        if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SPI_ERR_ARG;
+    }
     if (!on_device && !c->d_blk)
         CK(dev_alloc(c, &c->d_blk, (size_t)SPI_INVERSE_BLOCK_MAX * SPI_INVERSE_BLOCK_MAX));
     double* od = on_device ? out : c->d_blk;
-    launch_inverse_block(c->dsym, c->plan_blk, c->d_L, c->d_D, c->d_out, c->d_zg, c->blk_rows, od, nidx, st);
+    int rc = inverse_block_impl(c, key, od, st);
+    if (rc) return rc;
     if (!on_device) {
         CK(cudaMemcpyAsync(out, od, (size_t)nidx * nidx * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
+    return finish(c, st);
+}
+
+int spi_inverse_entries(spi_ctx* c, const int32_t* rows, const int32_t* cols, int64_t nent, double* out,
+                        int on_device, void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nent < 0 || (nent > 0 && (!rows || !cols || !out))) return SPI_ERR_ARG;
+    if (nent == 0) return SPI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Symbolic& S = c->S;
+    std::vector<int32_t> ri((size_t)nent), ci((size_t)nent);
+    if (on_device) {
+        CK(cudaMemcpyAsync(ri.data(), rows, (size_t)nent * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ci.data(), cols, (size_t)nent * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(ri.data(), rows, (size_t)nent * sizeof(int32_t));
+        std::memcpy(ci.data(), cols, (size_t)nent * sizeof(int32_t));
+    }
+    // the distinct indices in pivot order, cut into groups of half a block: a pair's
+    // entry comes from the block of its two groups (their paths overlap the most
+    // when the groups are consecutive in the elimination order)
+    std::vector<int32_t> uniq;
+    uniq.reserve((size_t)nent * 2);
+    for (int64_t t = 0; t < nent; ++t) {
+        if (ri[t] < 0 || ri[t] >= S.n || ci[t] < 0 || ci[t] >= S.n) return SPI_ERR_ARG;
+        uniq.push_back(ri[t]);
+        uniq.push_back(ci[t]);
+    }
+    std::sort(uniq.begin(), uniq.end(), [&](int32_t a, int32_t b) { return S.iperm[a] < S.iperm[b]; });
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    constexpr int64_t kGroup = SPI_INVERSE_BLOCK_MAX / 2;
+    std::vector<int32_t> rank((size_t)S.n, -1);
+    for (size_t u = 0; u < uniq.size(); ++u) rank[(size_t)uniq[u]] = (int32_t)u;
+    // requested entries by group pair (ga <= gb)
+    std::map<std::pair<int64_t, int64_t>, std::vector<int64_t>> buckets;
+    for (int64_t t = 0; t < nent; ++t) {
+        int64_t ga = rank[(size_t)ri[t]] / kGroup, gb = rank[(size_t)ci[t]] / kGroup;
+        if (ga > gb) std::swap(ga, gb);
+        buckets[{ga, gb}].push_back(t);
+    }
+    if (!c->d_blk) CK(dev_alloc(c, &c->d_blk, (size_t)SPI_INVERSE_BLOCK_MAX * SPI_INVERSE_BLOCK_MAX));
+    double* od = out;
+    double* staged = nullptr;
+    if (!on_device) {
+        if (cudaMalloc(&staged, (size_t)nent * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return SPI_ERR_OOM;
+        }
+        od = staged;
+    }
+    // positions of every entry in its block's row-major output, uploaded once; a block's
+    // key is group ga's indices followed (when gb != ga) by group gb's
+    std::vector<int64_t> src((size_t)nent), dst((size_t)nent), bptr;
+    std::vector<std::vector<int32_t>> keys;
+    const int64_t nu = (int64_t)uniq.size();
+    auto group_size = [&](int64_t g) { return std::min<int64_t>(kGroup, nu - g * kGroup); };
+    int64_t e = 0;
+    for (auto& kv : buckets) {
+        const int64_t ga = kv.first.first, gb = kv.first.second;
+        std::vector<int32_t> key(uniq.begin() + ga * kGroup, uniq.begin() + ga * kGroup + group_size(ga));
+        if (gb != ga) key.insert(key.end(), uniq.begin() + gb * kGroup, uniq.begin() + gb * kGroup + group_size(gb));
+        const int64_t m = (int64_t)key.size();
+        auto local = [&](int64_t r) { return r / kGroup == ga ? r - ga * kGroup : group_size(ga) + (r - gb * kGroup); };
+        bptr.push_back(e);
+        for (int64_t t : kv.second) {
+            src[(size_t)e] = local(rank[(size_t)ri[t]]) * m + local(rank[(size_t)ci[t]]);
+            dst[(size_t)e] = t;
+            ++e;
+        }
+        keys.push_back(std::move(key));
+    }
+    bptr.push_back(e);
+    int64_t* d_idx = nullptr;
+    int rc = SPI_OK;
+    if (cudaMalloc(&d_idx, 2 * (size_t)nent * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (staged) cudaFree(staged);
+        return SPI_ERR_OOM;
+    }
+    cudaError_t ce = cudaMemcpyAsync(d_idx, src.data(), (size_t)nent * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_idx + nent, dst.data(), (size_t)nent * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) rc = cuda_fail(ce);
+    for (size_t q = 0; q < keys.size() && rc == SPI_OK; ++q) {
+        rc = inverse_block_impl(c, keys[q], c->d_blk, st);
+        if (rc == SPI_OK)
+            launch_pick_entries(c->d_blk, d_idx + bptr[q], d_idx + nent + bptr[q], bptr[q + 1] - bptr[q], od, st);
+    }
+    if (rc == SPI_OK && !on_device) {
+        ce = cudaMemcpyAsync(out, od, (size_t)nent * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (ce != cudaSuccess) rc = cuda_fail(ce);
+    }
+    ce = cudaStreamSynchronize(st);
+    if (rc == SPI_OK && ce != cudaSuccess) rc = cuda_fail(ce);
+    cudaFree(d_idx);
+    if (staged) cudaFree(staged);
+    if (rc) return rc;
     return finish(c, st);
 }
 

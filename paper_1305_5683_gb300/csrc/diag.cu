@@ -406,6 +406,21 @@ void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L
     k_inverse_gram<<<nt * (nt + 1) / 2, 128, 0, st>>>(Zg, (int)p.nrhs, R, p.zpiv, D, p.rhs_out, out, ldo);
 }
 
+namespace {
+// out[dst[e]] = G[src[e]]: the requested entries of one block of the inverse
+__global__ void k_pick_entries(const double* __restrict__ G, const int64_t* __restrict__ src,
+                               const int64_t* __restrict__ dst, int64_t cnt, double* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+        out[dst[e]] = G[src[e]];
+}
+}  // namespace
+
+void launch_pick_entries(const double* G, const int64_t* src, const int64_t* dst, int64_t cnt, double* out,
+                         cudaStream_t st) {
+    if (cnt <= 0) return;
+    k_pick_entries<<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, st>>>(G, src, dst, cnt, out);
+}
+
 cudaError_t diag_kernel_setup(int B, size_t smem_min) {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max(diag_smem_bytes<double>(B), smem_min));

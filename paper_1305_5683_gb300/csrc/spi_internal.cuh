@@ -128,6 +128,9 @@ void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L,
                          int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
                              int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
+// out[dst[e]] = G[src[e]] for e < cnt (entries picked from a block of the inverse)
+void launch_pick_entries(const double* G, const int64_t* src, const int64_t* dst, int64_t cnt, double* out,
+                         cudaStream_t st);
 // smem_min: the launches' dynamic shared memory is at least this (0: what they need)
 cudaError_t diag_kernel_setup(int B, size_t smem_min);
 // (N^-1)(I, I) for the pivots of a plan with zpiv/rowmap: the blocks' forward

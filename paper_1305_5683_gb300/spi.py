@@ -26,7 +26,7 @@ EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_facto
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
            "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton",
-           "spi_background_fit"]
+           "spi_background_fit", "spi_inverse_entries"]
 SPI_INVERSE_BLOCK_MAX = 512
 SPI_PATTERN_MAX = 2048
 SPI_FIT_LSQ, SPI_FIT_MLE = 0, 1
@@ -94,6 +94,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_diag_inverse.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse.restype = I
     L.spi_diag_inverse_noalloc.argtypes = [V, V, I64, V, V]; L.spi_diag_inverse_noalloc.restype = I
     L.spi_inverse_block.argtypes = [V, V, I64, V, I, V]; L.spi_inverse_block.restype = I
+    L.spi_inverse_entries.argtypes = [V, V, V, I64, V, I, V]; L.spi_inverse_entries.restype = I
     L.spi_normal_setup.argtypes = [V, I64, V, V]; L.spi_normal_setup.restype = I
     L.spi_normal_assemble.argtypes = [V, V, V, V, V, V, I, V]; L.spi_normal_assemble.restype = I
     L.spi_normal_update.argtypes = [V, I64, V, V, V, V, V, V, I, V]; L.spi_normal_update.restype = I
@@ -256,6 +257,23 @@ def spi_inverse_block(ctx, idx, out, stream=None) -> None:
     nidx = int(idx.numel() if _is_torch(idx) else len(k2))
     _check(lib().spi_inverse_block(ctx, ip, nidx, op, dev, _stream(stream)), "spi_inverse_block")
     del k1, k2
+
+
+def spi_inverse_entries(ctx, rows, cols, out, stream=None) -> None:
+    """out[t] = (N^-1)[rows[t], cols[t]] for any list of index pairs."""
+    if not _is_torch(out) and not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise TypeError("out must be a contiguous float64 numpy array or CUDA tensor")
+    op, dev, k1 = _buf(out, np.float64)
+    rp, dev_r, k2 = _buf(rows, np.int32)
+    cp, dev_c, k3 = _buf(cols, np.int32)
+    if not (dev_r == dev_c == dev):
+        raise TypeError("rows, cols and out must all be host or all be device buffers")
+    nent = int(rows.numel() if _is_torch(rows) else len(k2))
+    ncol = int(cols.numel() if _is_torch(cols) else len(k3))
+    if ncol != nent:
+        raise ValueError("rows and cols must have the same length")
+    _check(lib().spi_inverse_entries(ctx, rp, cp, nent, op, dev, _stream(stream)), "spi_inverse_entries")
+    del k1, k2, k3
 
 
 def spi_normal_setup(ctx, rowptr, colind) -> None:
@@ -468,6 +486,18 @@ class Solver:
             else:
                 out = np.empty((m, m), np.float64)
         spi_inverse_block(self._h, idx, out, stream)
+        return out
+
+    def inverse_entries(self, rows, cols, out=None, stream=None):
+        """(N^-1)[rows[t], cols[t]] for every t, as a vector (or into `out`)."""
+        m = rows.numel() if _is_torch(rows) else len(rows)
+        if out is None:
+            if _is_torch(rows) and rows.is_cuda:
+                import torch
+                out = torch.empty(m, dtype=torch.float64, device=rows.device)
+            else:
+                out = np.empty(m, np.float64)
+        spi_inverse_entries(self._h, rows, cols, out, stream)
         return out
 
     def normal_setup(self, H):

@@ -73,3 +73,50 @@ def test_device_buffers_and_errors(P):
     with pytest.raises(P.SpiError) as e:
         s.inverse_block(np.arange(513, dtype=np.int32) % 300)
     assert e.value.code == 1
+
+
+def test_scattered_entries_across_groups(P):
+    """spi_inverse_entries: pairs over 700 distinct unknowns (three groups of
+    256 in elimination order, so several blocks), repeated pairs, both
+    orders and diagonal entries, against the oracle's block of those
+    unknowns, each entry on the scale sqrt(v_i v_j)."""
+    pb = generate(scaled(SCALE, 2000, seed=5))
+    f = oracle.OracleFactor.from_problem(pb)
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    rng = np.random.default_rng(3)
+    U = rng.choice(pb.n, 700, replace=False).astype(np.int32)
+    Gref = f.inv_block(U)
+    pos = {int(u): t for t, u in enumerate(U)}
+    a = rng.integers(0, 700, 3000)
+    b = rng.integers(0, 700, 3000)
+    a[:50] = b[:50]                         # diagonal entries
+    a[50:60], b[50:60] = b[60:70], a[60:70]  # both orders of a few pairs
+    a[70:80], b[70:80] = a[60:70], b[60:70]  # repeats
+    rows, cols = U[a], U[b]
+    out = s.inverse_entries(rows, cols)
+    ref = Gref[a, b]
+    scale = np.sqrt(np.diag(Gref)[a] * np.diag(Gref)[b])
+    assert (np.abs(out - ref) / scale).max() <= TOL
+    assert [pos[int(r)] for r in rows[:3]] == list(a[:3])
+
+
+def test_entries_on_device_and_errors(P):
+    import torch
+    pb = random_spd(300, 0.02, 9)
+    f = oracle.OracleFactor.from_problem(pb)
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    r = torch.tensor([5, 250, 17, 99, 5], dtype=torch.int32, device="cuda")
+    c = torch.tensor([250, 5, 17, 3, 5], dtype=torch.int32, device="cuda")
+    out = s.inverse_entries(r, c)
+    torch.cuda.synchronize()
+    U = np.array([3, 5, 17, 99, 250], np.int32)
+    G = f.inv_block(U)
+    k = {int(u): t for t, u in enumerate(U)}
+    ref = np.array([G[k[int(i)], k[int(j)]] for i, j in zip(r.cpu().numpy(), c.cpu().numpy())])
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL * np.abs(np.diag(G)).max()
+    assert s.inverse_entries(np.zeros(0, np.int32), np.zeros(0, np.int32)).shape == (0,)
+    with pytest.raises(P.SpiError) as e:
+        s.inverse_entries(np.array([0, 300], np.int32), np.array([1, 2], np.int32))
+    assert e.value.code == 1

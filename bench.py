@@ -672,6 +672,22 @@ def main():
                  "refine_steps": minfo["refine_steps"], "solve_relres": minfo["solve_relres"],
                  "diag_tflops_fp32": minfo["diag_flops_all"] / (statistics.mean(md) / 1e3) / 1e12,
                  "dtype": "f32 updates / f64 pivots, refinement and variance sums"}
+        # variances of 256 unknowns with the factor's first-order error removed
+        try:
+            sel = torch.from_numpy(np.random.default_rng(13).choice(pb.n, 256, replace=False).astype(np.int32)).to(dev)
+            vr = sm_.diag_inverse_refined(sel, stream=st)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            vr = sm_.diag_inverse_refined(sel, stream=st)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ref = var[sel.long()]
+            mixed["refined_256"] = {"ms": e0.elapsed_time(e1),
+                                    "max_rel_err_vs_fp64": float((torch.abs(vr - ref) / ref).max().item()),
+                                    "max_rel_err_unrefined": float((torch.abs(varm[sel.long()] - ref) / ref).max().item())}
+        except Exception as e:
+            mixed["refined_256"] = {"error": f"{type(e).__name__}: {e}"}
         del sm_
 
     # blocks of the inverse on the FP64 factor: the covariances of 512 time-bin

@@ -227,6 +227,26 @@ int spi_diag_inverse_batch(spi_ctx* ctx, int32_t nbatch, const int32_t* idx, int
  * repeated), SPI_ERR_OOM, SPI_ERR_CUDA. */
 int spi_inverse_block(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream);
 
+/* Variances of a mixed-precision factorization with its first-order error
+ * removed, for selected unknowns: out[t] = 2 e_i^T v - v^T N v with i = idx[t]
+ * and v = F^-1 e_i computed by full (unpruned) forward and backward sweeps of
+ * the factor F (FP32 panels converted to FP64, FP64 arithmetic), N the FP64
+ * input matrix.  The quadratic form peaks at v = N^-1 e_i with value
+ * (N^-1)_ii, so an error d = O(delta) in v leaves an error -d^T N d = O(delta^2)
+ * in the variance (never above the exact one), against O(delta) for
+ * spi_diag_inverse.  Cost: one full solve and one product with N per index
+ * (32 indices per pass), far more than the pruned solves: meant for the
+ * unknowns whose variances matter most, e.g. the sources' fluxes.  An FP64
+ * context returns spi_diag_inverse's values.
+ *   idx   int32[nidx], caller numbering (repeats allowed)
+ *   out   float64[nidx]
+ * on_device: idx and out are device pointers.  Band 0 of a batched context.
+ * Device memory: about 5 x 32 x n doubles for the call.  Errors: SPI_ERR_STATE
+ * (not factored), SPI_ERR_ARG (NULL buffer, an index out of range),
+ * SPI_ERR_OOM, SPI_ERR_CUDA. */
+int spi_diag_inverse_refined(spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, int on_device,
+                             void* stream);
+
 /* Scattered entries of the inverse: out[t] = (N^-1)_{rows[t], cols[t]} for any
  * list of index pairs -- "any set of entries" of the inverse (paper
  * Sec. 3.3.1).  The distinct indices of the list, in elimination order, are

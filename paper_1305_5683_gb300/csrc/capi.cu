@@ -159,6 +159,7 @@ int ensure_device(spi_ctx* c) {
     c->bs.L = S.lptr[S.ns];
     c->bs.F22 = S.f22_total;
     c->bs.n = S.n;
+    c->bs.Dn = S.n;
     c->bs.nnz = S.nnz_a;
     CK(dev_upload(c, &c->d_amap, S.amap));
     CK(dev_upload(c, &c->d_diag_src, S.diag_src));
@@ -807,6 +808,81 @@ int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out,
         CK(cudaMemcpyAsync(out, od, (size_t)nidx * nidx * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
+    return finish(c, st);
+}
+
+int spi_diag_inverse_refined(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device,
+                             void* stream) {
+    if (!c) return SPI_ERR_ARG;
+    if (!c->factored) return SPI_ERR_STATE;
+    if (nidx < 0 || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
+    if (nidx == 0) return SPI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // an FP64 factor's variances have no first-order error to remove
+    if (!mixed_of(c)) return diag_impl(c, 1, idx, nidx, out, on_device, st);
+    const Symbolic& S = c->S;
+    const int32_t n = S.n;
+    std::vector<int32_t> key((size_t)nidx);
+    if (on_device) {
+        CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+    }
+    for (int32_t i : key)
+        if (i < 0 || i >= n) return SPI_ERR_ARG;
+    constexpr int kR = 32;  // right-hand sides per pass
+    const int64_t R0 = std::min<int64_t>(kR, nidx);
+    const size_t vec = (size_t)R0 * (size_t)n;
+    // w, z, xp (pivot order), x (caller order), r; then pivots, indices and outputs of a pass
+    double* buf = nullptr;
+    const size_t bytes = 5 * vec * sizeof(double) + 2 * (size_t)kR * sizeof(int32_t) + (size_t)nidx * sizeof(double);
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SPI_ERR_OOM;
+    }
+    double *w = buf, *z = w + vec, *xp = z + vec, *x = xp + vec, *r = x + vec;
+    int32_t* dpos = reinterpret_cast<int32_t*>(r + vec);
+    int32_t* didx = dpos + kR;
+    double* dout = reinterpret_cast<double*>(didx + kR);
+    Strides bs = c->bs;
+    bs.L = 0;   // one factor for every right-hand side
+    bs.Dn = 0;
+    int rc = SPI_OK;
+    auto run = [&]() -> cudaError_t {
+        for (int64_t t0 = 0; t0 < nidx; t0 += kR) {
+            const int R = (int)std::min<int64_t>(kR, nidx - t0);
+            std::vector<int32_t> pos((size_t)R);
+            for (int t = 0; t < R; ++t) pos[(size_t)t] = S.iperm[key[(size_t)(t0 + t)]];
+            cudaError_t e = cudaMemcpyAsync(dpos, pos.data(), (size_t)R * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            e = cudaMemcpyAsync(didx, key.data() + t0, (size_t)R * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            // v = F^-1 e_i: the full forward and backward sweeps with the factor in FP64 arithmetic
+            e = cudaMemsetAsync(w, 0, (size_t)R * n * sizeof(double), st);
+            if (e != cudaSuccess) return e;
+            launch_set_units(n, dpos, R, w, st);
+            for (const Launch& l : c->SP.fwd_launches)
+                launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, w, z, xp, R, bs, st);
+            for (const Launch& l : c->SP.bwd_launches)
+                launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, w, z, xp, R, bs, st);
+            launch_permute_out(n, c->dsym.perm, xp, x, R, st);
+            // r = -N v with the FP64 input matrix, then 2 v_i - v^T N v
+            e = cudaMemsetAsync(r, 0, (size_t)R * n * sizeof(double), st);
+            if (e != cudaSuccess) return e;
+            launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, x, r, R, 0, st);
+            launch_refined_var(n, x, r, didx, R, dout + t0, st);
+            e = cudaStreamSynchronize(st);  // pos and the index slice are reused by the next pass
+            if (e != cudaSuccess) return e;
+        }
+        return cudaMemcpyAsync(out, dout, (size_t)nidx * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    };
+    cudaError_t ce = run();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) rc = cuda_fail(ce);
+    cudaFree(buf);
+    if (rc) return rc;
     return finish(c, st);
 }
 

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
                                                        const double* __restrict__ z, const double* __restrict__ x,
                                                        double* __restrict__ w, Strides bs) {
     L += blockIdx.y * bs.L;
-    D += blockIdx.y * bs.n;
+    D += blockIdx.y * bs.Dn;
     z += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
     w += blockIdx.y * bs.n;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
                                                         const double* __restrict__ z, double* __restrict__ x,
                                                         double* __restrict__ w, Strides bs) {
     L += blockIdx.y * bs.L;
-    D += blockIdx.y * bs.n;
+    D += blockIdx.y * bs.Dn;
     z += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
     w += blockIdx.y * bs.n;
@@ -351,7 +351,44 @@ __global__ void k_axpy(int32_t n, const double* __restrict__ dx, double* __restr
         x[i] += dx[i];
 }
 
+// w[t n + pos[t]] = 1 (w zeroed before): unit right-hand sides in pivot numbering
+__global__ void k_set_units(int32_t n, const int32_t* __restrict__ pos, int R, double* __restrict__ w) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < R) w[(int64_t)t * n + pos[t]] = 1.0;
+}
+
+// out[t] = 2 v_t[idx_t] + sum_k v_t[k] r_t[k], with r_t = -N v_t: the variance
+// 2 e^T v - v^T N v of an approximate v = F^-1 e (one CTA per right-hand side)
+__global__ void k_refined_var(int32_t n, const double* __restrict__ v, const double* __restrict__ r,
+                              const int32_t* __restrict__ idx, double* __restrict__ out) {
+    __shared__ double part[kThreads / 32];
+    const int t = blockIdx.x;
+    v += (int64_t)t * n;
+    r += (int64_t)t * n;
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += kThreads) s += v[k] * r[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) a += part[q];
+        out[t] = 2.0 * v[idx[t]] + a;
+    }
+}
+
 }  // namespace
+
+void launch_set_units(int32_t n, const int32_t* pos, int R, double* w, cudaStream_t st) {
+    if (R <= 0) return;
+    k_set_units<<<(R + 127) / 128, 128, 0, st>>>(n, pos, R, w);
+}
+
+void launch_refined_var(int32_t n, const double* v, const double* r, const int32_t* idx, int R, double* out,
+                        cudaStream_t st) {
+    if (R <= 0) return;
+    k_refined_var<<<R, kThreads, 0, st>>>(n, v, r, idx, out);
+}
 
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
                          double* r, int nb, int64_t nnz, cudaStream_t st) {

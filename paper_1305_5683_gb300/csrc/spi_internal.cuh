@@ -46,6 +46,8 @@ struct Strides {
     int64_t nnz = 0;  // input values per band
     int64_t Z = 0;    // variance workspace elements per band
     int64_t out = 0;  // variance outputs per band
+    int64_t Dn = 0;   // pivots of D per band in the solves (n; 0 when the right-hand sides
+                      // of one factor take the band index, with L = 0 as well)
 };
 
 // A flattened work list of one kernel launch.
@@ -85,6 +87,10 @@ struct SolvePlan {
 
 // batch: bands per launch (the fused per-level sweeps are used for batches only)
 void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch);
+// variances with the factor's first-order error removed (spi_diag_inverse_refined)
+void launch_set_units(int32_t n, const int32_t* pos, int R, double* w, cudaStream_t st);
+void launch_refined_var(int32_t n, const double* v, const double* r, const int32_t* idx, int R, double* out,
+                        cudaStream_t st);
 
 struct DevDiagPlan {
     int32_t B = 0, nblocks = 0;

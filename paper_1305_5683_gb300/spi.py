@@ -26,7 +26,7 @@ EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_facto
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
            "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton",
-           "spi_background_fit", "spi_inverse_entries"]
+           "spi_background_fit", "spi_inverse_entries", "spi_diag_inverse_refined"]
 SPI_INVERSE_BLOCK_MAX = 512
 SPI_PATTERN_MAX = 2048
 SPI_FIT_LSQ, SPI_FIT_MLE = 0, 1
@@ -95,6 +95,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_diag_inverse_noalloc.argtypes = [V, V, I64, V, V]; L.spi_diag_inverse_noalloc.restype = I
     L.spi_inverse_block.argtypes = [V, V, I64, V, I, V]; L.spi_inverse_block.restype = I
     L.spi_inverse_entries.argtypes = [V, V, V, I64, V, I, V]; L.spi_inverse_entries.restype = I
+    L.spi_diag_inverse_refined.argtypes = [V, V, I64, V, I, V]; L.spi_diag_inverse_refined.restype = I
     L.spi_normal_setup.argtypes = [V, I64, V, V]; L.spi_normal_setup.restype = I
     L.spi_normal_assemble.argtypes = [V, V, V, V, V, V, I, V]; L.spi_normal_assemble.restype = I
     L.spi_normal_update.argtypes = [V, I64, V, V, V, V, V, V, I, V]; L.spi_normal_update.restype = I
@@ -256,6 +257,19 @@ def spi_inverse_block(ctx, idx, out, stream=None) -> None:
         raise TypeError("idx and out must both be host or both be device buffers")
     nidx = int(idx.numel() if _is_torch(idx) else len(k2))
     _check(lib().spi_inverse_block(ctx, ip, nidx, op, dev, _stream(stream)), "spi_inverse_block")
+    del k1, k2
+
+
+def spi_diag_inverse_refined(ctx, idx, out, stream=None) -> None:
+    """Variances of a mixed-precision factor with the first-order error removed."""
+    if not _is_torch(out) and not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise TypeError("out must be a contiguous float64 numpy array or CUDA tensor")
+    op, dev, k1 = _buf(out, np.float64)
+    ip, dev_i, k2 = _buf(idx, np.int32)
+    if dev_i != dev:
+        raise TypeError("idx and out must both be host or both be device buffers")
+    nidx = int(idx.numel() if _is_torch(idx) else len(k2))
+    _check(lib().spi_diag_inverse_refined(ctx, ip, nidx, op, dev, _stream(stream)), "spi_diag_inverse_refined")
     del k1, k2
 
 
@@ -486,6 +500,18 @@ class Solver:
             else:
                 out = np.empty((m, m), np.float64)
         spi_inverse_block(self._h, idx, out, stream)
+        return out
+
+    def diag_inverse_refined(self, idx, out=None, stream=None):
+        """Variances of selected unknowns with the factor's first-order error removed."""
+        m = idx.numel() if _is_torch(idx) else len(idx)
+        if out is None:
+            if _is_torch(idx) and idx.is_cuda:
+                import torch
+                out = torch.empty(m, dtype=torch.float64, device=idx.device)
+            else:
+                out = np.empty(m, np.float64)
+        spi_diag_inverse_refined(self._h, idx, out, stream)
         return out
 
     def inverse_entries(self, rows, cols, out=None, stream=None):

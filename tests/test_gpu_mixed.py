@@ -138,3 +138,34 @@ def test_bounded_wait_timeout_reported(P):
     ok = P.Solver(n, cp, ri, precision=P.SPI_PREC_MIXED_FP32, ordering=P.SPI_ORDER_NATURAL)
     ok.factor(va)
     assert np.abs(ok.solve(b) - x_ref).max() <= X_TOL * np.abs(x_ref).max()
+
+
+def test_refined_variances(P):
+    """spi_diag_inverse_refined: 2 e^T v - v^T N v with v from the mixed factor
+    removes the first-order error of the mixed variances (O(delta^2) left, never
+    above the exact variance); an FP64 context returns spi_diag_inverse's values."""
+    import torch
+    pb = generate(scaled(SCALE, 2000, seed=5))
+    f = oracle.OracleFactor.from_problem(pb)
+    rng = np.random.default_rng(4)
+    idx = np.concatenate([rng.choice(pb.n, 70, replace=False), [0, pb.n - 1, 5, 5]]).astype(np.int32)
+    ref = f.inv_diag(idx)
+    s = P.Solver.for_problem(pb, precision=P.SPI_PREC_MIXED_FP32)
+    s.factor(pb.values)
+    plain = s.diag_inverse(idx)
+    refined = s.diag_inverse_refined(idx)
+    e_plain = (np.abs(plain - ref) / ref).max()
+    e_ref = (np.abs(refined - ref) / ref).max()
+    print(f"mixed variances: plain {e_plain:.2e}, refined {e_ref:.2e}")
+    assert e_ref <= 1e-9
+    assert e_ref <= 1e-2 * e_plain
+    assert ((refined - ref) / ref).max() <= 1e-12  # a lower bound up to rounding
+    d = s.diag_inverse_refined(torch.from_numpy(idx).cuda())
+    torch.cuda.synchronize()
+    assert np.allclose(d.cpu().numpy(), refined, rtol=1e-12, atol=0)  # atomics: last bits may differ
+    s64 = P.Solver.for_problem(pb)
+    s64.factor(pb.values)
+    assert np.allclose(s64.diag_inverse_refined(idx), s64.diag_inverse(idx), rtol=1e-13, atol=0)
+    with pytest.raises(P.SpiError) as e:
+        s.diag_inverse_refined(np.array([pb.n], np.int32))
+    assert e.value.code == 1

@@ -158,6 +158,9 @@ def test_compute_without_gpu_fails_loudly(P):
     with pytest.raises(P.SpiError) as e:
         s.inverse_entries(np.array([0, 1], np.int32), np.array([1, 1], np.int32))
     assert e.value.code == 7
+    with pytest.raises(P.SpiError) as e:
+        s.diag_inverse_refined(np.array([0, 1], np.int32))
+    assert e.value.code == 7
 
 
 def test_normal_setup_validates_on_the_host(P):

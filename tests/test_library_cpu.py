@@ -179,3 +179,28 @@ def test_normal_setup_validates_on_the_host(P):
     with pytest.raises(P.SpiError) as e:  # the empty-field loop before setup
         s.background_fit(1, np.zeros(1, np.int32), np.ones(1), np.zeros(1), np.ones(1), np.ones(1), np.ones(1))
     assert e.value.code == 7
+
+
+def test_struct_layouts_match_header(P, tmp_path):
+    """The binding's ctypes structures have the C header's sizes and field
+    offsets (compiled here with gcc against include/spi.h)."""
+    import ctypes as ct
+    import subprocess
+    fields = {"spi_options": [f for f, _ in P.spi.spi_options._fields_],
+              "spi_stats": [f for f, _ in P.spi.spi_stats._fields_]}
+    cname = {"async_": "async"}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "spi.h"', "int main(void) {"]
+    for st, fl in fields.items():
+        src.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for f in fl:
+            src.append(f'  printf("{st}.{f} %zu\\n", offsetof({st}, {cname.get(f, f)}));')
+    src.append("  return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, cls in (("spi_options", P.spi.spi_options), ("spi_stats", P.spi.spi_stats)):
+        assert int(got[st]) == ct.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)

@@ -373,7 +373,9 @@ int spi_mle_newton(spi_ctx* ctx, const double* hvals, const double* y, double* x
  * max_iter < 1, tol < 0 or NaN, NULL buffer, a row with two entries in the
  * first k0 columns or a pattern index that does not match its row, H x <= 0
  * where the likelihood needs it positive), and those of spi_normal_assemble,
- * spi_factor and spi_solve. */
+ * spi_factor and spi_solve.  After an error the background entries of hvals
+ * (device form) may hold any pattern the loop had reached, and U, x, var are
+ * not written. */
 #define SPI_PATTERN_MAX 2048
 #define SPI_FIT_LSQ 0
 #define SPI_FIT_MLE 1

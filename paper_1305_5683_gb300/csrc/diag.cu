@@ -137,18 +137,20 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
                 for (int e = tid; e < nrow * nb; e += kThreads) {
                     const int i = e / nb, t = e - i * nb;
                     const T* lr = Lt + i * (kT + 1);
-                    T acc = T(0);
-                    int c = 0;
-                    for (; c < w4; c += 4) {
-                        acc += lr[c] * Zd[c * B + t];
-                        acc += lr[c + 1] * Zd[(c + 1) * B + t];
-                        acc += lr[c + 2] * Zd[(c + 2) * B + t];
-                        acc += lr[c + 3] * Zd[(c + 3) * B + t];
-                    }
-                    for (; c < w; ++c) acc += lr[c] * Zd[c * B + t];
                     const int64_t row = rb + i;
                     const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
-                    Z[zr * B + lo + t] -= acc;
+                    // start from the row's old value: every product is one FMA, no final subtraction
+                    // (the FP64 pipe is the bound of this kernel)
+                    T acc = Z[zr * B + lo + t];
+                    int c = 0;
+                    for (; c < w4; c += 4) {
+                        acc -= lr[c] * Zd[c * B + t];
+                        acc -= lr[c + 1] * Zd[(c + 1) * B + t];
+                        acc -= lr[c + 2] * Zd[(c + 2) * B + t];
+                        acc -= lr[c + 3] * Zd[(c + 3) * B + t];
+                    }
+                    for (; c < w; ++c) acc -= lr[c] * Zd[c * B + t];
+                    Z[zr * B + lo + t] = acc;
                 }
             }
         }

@@ -88,6 +88,11 @@ typedef struct spi_options {
                         SM (their shared memory is padded to enforce it), so that work on
                         another stream -- a spi_solve running concurrently -- keeps room
                         on every SM instead of waiting for variance CTAs to finish */
+    int diag_unpruned;   /* 0 = pruned solves (the method); 1 = the pruning ablation: every
+                            variance from a full forward solve over all supernodes (32 per
+                            pass, FP64 panels), var_i = sum_k z_k^2 / d_k, so that the gain
+                            of pruning can be measured (the paper's brute-force comparison,
+                            Table 5); spi_diag_inverse only, band 0 only */
 } spi_options;
 
 typedef struct spi_stats {

@@ -459,10 +459,84 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     return upload_plan(c, h, dst);
 }
 
+// The pruning ablation (spi_options.diag_unpruned): every variance from a full forward
+// solve z = L^-1 e_i over all supernodes (32 right-hand sides per pass, FP64 panels),
+// var_i = sum_k z_k^2 / d_k.  Band 0 only.
+int diag_unpruned_impl(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device,
+                       cudaStream_t st) {
+    const Symbolic& S = c->S;
+    const int32_t n = S.n;
+    std::vector<int32_t> key;
+    if (!idx) {
+        key.resize((size_t)n);
+        for (int32_t i = 0; i < n; ++i) key[(size_t)i] = i;
+        nidx = n;
+    } else {
+        if (nidx < 0 || nidx > S.n) return SPI_ERR_ARG;
+        key.resize((size_t)nidx);
+        if (nidx) {
+            if (on_device) {
+                CK(cudaMemcpyAsync(key.data(), idx, (size_t)nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                std::memcpy(key.data(), idx, (size_t)nidx * sizeof(int32_t));
+            }
+        }
+        for (int32_t v : key)
+            if (v < 0 || v >= n) return SPI_ERR_ARG;
+    }
+    if (nidx == 0) return SPI_OK;
+    constexpr int kR = 32;
+    const size_t vec = (size_t)std::min<int64_t>(kR, nidx) * (size_t)n;
+    double* buf = nullptr;
+    const size_t bytes = (2 * vec + (size_t)n + (size_t)nidx) * sizeof(double) + (size_t)kR * sizeof(int32_t);
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SPI_ERR_OOM;
+    }
+    double *w = buf, *z = w + vec, *dinv = z + vec, *dout = dinv + n;
+    int32_t* dpos = reinterpret_cast<int32_t*>(dout + nidx);
+    Strides bs = c->bs;
+    bs.L = 0;  // one factor for every right-hand side
+    bs.Dn = 0;
+    auto run = [&]() -> cudaError_t {
+        launch_reciprocal(n, c->d_D, dinv, st);
+        for (int64_t t0 = 0; t0 < nidx; t0 += kR) {
+            const int R = (int)std::min<int64_t>(kR, nidx - t0);
+            std::vector<int32_t> pos((size_t)R);
+            for (int t = 0; t < R; ++t) pos[(size_t)t] = S.iperm[key[(size_t)(t0 + t)]];
+            cudaError_t e = cudaMemcpyAsync(dpos, pos.data(), (size_t)R * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            e = cudaMemsetAsync(w, 0, (size_t)R * n * sizeof(double), st);
+            if (e != cudaSuccess) return e;
+            launch_set_units(n, dpos, R, w, st);
+            for (const Launch& l : c->SP.fwd_launches)
+                launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, w, z, nullptr, R, bs, st);
+            launch_zsq_var(n, z, dinv, R, dout + t0, st);
+            e = cudaStreamSynchronize(st);  // pos is reused by the next pass
+            if (e != cudaSuccess) return e;
+        }
+        return cudaMemcpyAsync(out, dout, (size_t)nidx * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    };
+    cudaError_t ce = run();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (ce != cudaSuccess) return cuda_fail(ce);
+    // the ablation's work: every forward solve walks all of L
+    c->last_diag_flops = 0;
+    c->last_diag_work = 2.0 * (double)S.lptr[S.ns] * (double)nidx;
+    return finish(c, st);
+}
+
 int diag_impl(spi_ctx* c, int nb, const int32_t* idx, int64_t nidx, double* out, int on_device, cudaStream_t st) {
     if (!c || !out || nb < 1) return SPI_ERR_ARG;
     if (!c->factored) return SPI_ERR_STATE;
     if (nb > c->factored_nb) return SPI_ERR_ARG;
+    if (c->opt.diag_unpruned) {
+        if (nb != 1) return SPI_ERR_ARG;
+        return diag_unpruned_impl(c, idx, nidx, out, on_device, st);
+    }
     const Symbolic& S = c->S;
     DevDiagPlan* plan;
     int64_t nout;

@@ -377,7 +377,41 @@ __global__ void k_refined_var(int32_t n, const double* __restrict__ v, const dou
     }
 }
 
+// out[t] = sum_k z_t[k]^2 dinv[k]: the variance from an unpruned forward solve
+// (one CTA per right-hand side)
+__global__ void k_zsq_var(int32_t n, const double* __restrict__ z, const double* __restrict__ dinv,
+                          double* __restrict__ out) {
+    __shared__ double part[kThreads / 32];
+    const int t = blockIdx.x;
+    z += (int64_t)t * n;
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += kThreads) s += z[k] * z[k] * dinv[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) a += part[q];
+        out[t] = a;
+    }
+}
+
+__global__ void k_reciprocal(int32_t n, const double* __restrict__ D, double* __restrict__ dinv) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dinv[k] = 1.0 / D[k];
+}
+
 }  // namespace
+
+void launch_zsq_var(int32_t n, const double* z, const double* dinv, int R, double* out, cudaStream_t st) {
+    if (R <= 0) return;
+    k_zsq_var<<<R, kThreads, 0, st>>>(n, z, dinv, out);
+}
+
+void launch_reciprocal(int32_t n, const double* D, double* dinv, cudaStream_t st) {
+    if (n <= 0) return;
+    k_reciprocal<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(n, D, dinv);
+}
 
 void launch_set_units(int32_t n, const int32_t* pos, int R, double* w, cudaStream_t st) {
     if (R <= 0) return;

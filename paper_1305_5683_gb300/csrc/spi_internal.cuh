@@ -87,6 +87,9 @@ struct SolvePlan {
 
 // batch: bands per launch (the fused per-level sweeps are used for batches only)
 void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch);
+// variances from unpruned forward solves (the pruning ablation of spi_diag_inverse)
+void launch_zsq_var(int32_t n, const double* z, const double* dinv, int R, double* out, cudaStream_t st);
+void launch_reciprocal(int32_t n, const double* D, double* dinv, cudaStream_t st);
 // variances with the factor's first-order error removed (spi_diag_inverse_refined)
 void launch_set_units(int32_t n, const int32_t* pos, int R, double* w, cudaStream_t st);
 void launch_refined_var(int32_t n, const double* v, const double* r, const int32_t* idx, int R, double* out,

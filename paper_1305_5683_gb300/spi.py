@@ -36,7 +36,7 @@ class spi_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ordering", ctypes.c_int), ("rhs_block", ctypes.c_int),
                 ("relax", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int), ("batch", ctypes.c_int),
-                ("wait_limit", ctypes.c_int), ("diag_ctas_per_sm", ctypes.c_int)]
+                ("wait_limit", ctypes.c_int), ("diag_ctas_per_sm", ctypes.c_int), ("diag_unpruned", ctypes.c_int)]
 
 
 class spi_stats(ctypes.Structure):
@@ -420,13 +420,14 @@ class Solver:
 
     def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
                  rhs_block=0, relax=1, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
-                 wait_limit=0, diag_ctas_per_sm=0, _multi=None):
+                 wait_limit=0, diag_ctas_per_sm=0, diag_unpruned=False, _multi=None):
         o = spi_default_options()
         o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax
         o.refine_max, o.refine_tol, o.nd_leaf, o.async_ = refine_max, refine_tol, nd_leaf, int(async_)
         o.batch = batch
         o.wait_limit = wait_limit
         o.diag_ctas_per_sm = diag_ctas_per_sm
+        o.diag_unpruned = int(diag_unpruned)
         self.n = int(n)
         self.batch = batch
         if _multi is not None:

@@ -183,3 +183,21 @@ def test_full_size_sampled():
     assert (np.abs(v[idx] - ref) / ref).max() <= TOL
     x_ref = f.solve(pb.b)
     assert np.abs(x - x_ref).max() <= TOL * np.abs(x_ref).max()
+
+
+def test_unpruned_ablation_matches_pruned(P):
+    """spi_options.diag_unpruned (full forward solves, no pruning) gives the
+    pruned variances: same values up to rounding, for a subset and for all."""
+    pb = generate(scaled(SCALE, 2000, seed=5))
+    f = oracle.OracleFactor.from_problem(pb)
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    u = P.Solver.for_problem(pb, diag_unpruned=True)
+    u.factor(pb.values)
+    idx = np.random.default_rng(9).choice(pb.n, 100, replace=False).astype(np.int32)
+    vu, vp = u.diag_inverse(idx), s.diag_inverse(idx)
+    assert (np.abs(vu - vp) / vp).max() <= 1e-12
+    assert (np.abs(vu - f.inv_diag(idx)) / vp).max() <= 1e-10
+    allu, allp = u.diag_inverse(), s.diag_inverse()
+    assert (np.abs(allu - allp) / allp).max() <= 1e-12
+    assert u.info()["diag_work_flops"] > 10 * s.info()["diag_work_flops"]

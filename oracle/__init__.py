@@ -352,3 +352,90 @@ def background_fit(H, y, w, k0, upat, t, U0, mode="lsq", max_iter=20, tol=1e-9,
             Hess = (Hc.T @ sp.diags(yy / e ** 2) @ Hc).toarray()
         var = np.diag(np.linalg.inv(Hess)).copy()
     return x, U, stats, var
+
+
+BK_ALPHA = (1.0 + 17.0 ** 0.5) / 8.0  # Bunch-Kaufman growth-balancing constant
+
+
+def ldlt_pivoted(A):
+    """Symmetric indefinite LDL^T with 1x1 and 2x2 pivots (the "two-by-two
+    numerical pivoting" the paper's conclusion says its matrices need), in
+    the Bunch-Kaufman partial-pivoting form: for the active column k with
+    largest off-diagonal |a_rk| = lam,
+      |a_kk| >= alpha lam            -> 1x1 pivot a_kk;
+      else with sig = max_{i != r} |a_ir|:
+      |a_kk| sig >= alpha lam^2      -> 1x1 pivot a_kk;
+      |a_rr| >= alpha sig            -> swap k, r; 1x1 pivot;
+      otherwise                      -> swap k+1, r; 2x2 pivot on (k, k+1);
+    alpha = (1 + sqrt 17) / 8.  Dense FP64 on a copy of A (small problems).
+    Returns (p, L, D, blocks): A[p][:, p] = L D L^T, L unit lower triangular,
+    D block diagonal, blocks = list of (start, size) of D's pivots."""
+    A = np.array(A, dtype=np.float64)
+    n = A.shape[0]
+    p = np.arange(n)
+    L = np.eye(n)
+    D = np.zeros((n, n))
+    blocks = []
+
+    def swap(i, j):
+        if i == j:
+            return
+        A[[i, j], :] = A[[j, i], :]
+        A[:, [i, j]] = A[:, [j, i]]
+        L[[i, j], :] = L[[j, i], :]  # rows of the finished columns follow their unknowns
+        L[:, [i, j]] = L[:, [j, i]]
+        p[[i, j]] = p[[j, i]]
+
+    k = 0
+    while k < n:
+        col = np.abs(A[k + 1:, k])
+        lam = col.max() if col.size else 0.0
+        size = 1
+        if lam == 0.0:
+            if A[k, k] == 0.0:
+                raise NotSPD(k)  # a zero column: singular
+        elif abs(A[k, k]) >= BK_ALPHA * lam:
+            pass
+        else:
+            r = k + 1 + int(np.argmax(col))
+            row_r = np.abs(np.concatenate([A[r, k:r], A[r + 1:, r]]))
+            sig = row_r.max()
+            if abs(A[k, k]) * sig >= BK_ALPHA * lam * lam:
+                pass
+            elif abs(A[r, r]) >= BK_ALPHA * sig:
+                swap(k, r)
+            else:
+                swap(k + 1, r)
+                size = 2
+        E = A[k:k + size, k:k + size].copy()
+        C = A[k + size:, k:k + size].copy()
+        if size == 1 and E[0, 0] == 0.0:
+            raise NotSPD(k)
+        Einv = np.linalg.inv(E)
+        D[k:k + size, k:k + size] = E
+        L[k + size:, k:k + size] = C @ Einv
+        A[k + size:, k + size:] -= C @ Einv @ C.T
+        blocks.append((k, size))
+        k += size
+    # the swaps above also permuted the unit diagonal of columns not yet reached; restore it
+    L[np.diag_indices(n)] = 1.0
+    return p, np.tril(L), D, blocks
+
+
+def inv_diag_pivoted(A):
+    """diag(A^-1) from the pivoted factorization: with A[p][:, p] = L D L^T,
+    (A^-1)_{p_i p_i} = z^T D^-1 z, z = L^-1 e_i, D^-1 taken block by block
+    (1x1 and 2x2) -- the diagonal of the inverse of an indefinite matrix by
+    forward solves, as in the SPD case."""
+    p, L, D, blocks = ldlt_pivoted(A)
+    n = len(p)
+    out = np.empty(n)
+    Linv = np.linalg.inv(L)  # columns z_i = L^-1 e_i (dense: small problems)
+    for i in range(n):
+        z = Linv[:, i]
+        s = 0.0
+        for (k, size) in blocks:
+            zb = z[k:k + size]
+            s += float(zb @ np.linalg.solve(D[k:k + size, k:k + size], zb))
+        out[p[i]] = s
+    return out

@@ -2,9 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
 CPU-baseline leg are the only callers.  The product path never imports this
-package.  The arithmetic lives in spi_oracle.c (plain C, natural ordering,
-left-looking LDL^T, column-by-column inverse diagonal; paper Sec. 3.2 and
-Sec. 4.3); this module only compiles it and marshals arrays.
+package.  The path's arithmetic lives in spi_oracle.c (plain C, natural
+ordering, left-looking LDL^T, column-by-column inverse diagonal and inverse
+blocks; paper Sec. 3.2, Sec. 3.3.1 and Sec. 4.3), which this module compiles
+and calls.  The steps around the path are written here in plain NumPy/SciPy:
+the normal equations (Sec. 4.1, Eq. 7), the Poisson fit of the appendix on
+low counts, Algorithm 1 of the appendix on the "empty-field" pattern, and a
+dense LDL^T with two-by-two pivots for indefinite matrices (Sec. 5).
 """
 from __future__ import annotations
 

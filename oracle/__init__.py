@@ -362,9 +362,9 @@ BK_ALPHA = (1.0 + 17.0 ** 0.5) / 8.0  # Bunch-Kaufman growth-balancing constant
 
 
 def ldlt_pivoted(A):
-    """Symmetric indefinite LDL^T with 1x1 and 2x2 pivots (the "two-by-two
-    numerical pivoting" Sec. 5 of the paper says its matrices need), in
-    the Bunch-Kaufman partial-pivoting form: for the active column k with
+    """Symmetric indefinite LDL^T with 1x1 and 2x2 pivots (Sec. 5 of the
+    paper notes that its matrices need 2x2 pivots for stability), in the
+    Bunch-Kaufman partial-pivoting form: for the active column k with
     largest off-diagonal |a_rk| = lam,
       |a_kk| >= alpha lam            -> 1x1 pivot a_kk;
       else with sig = max_{i != r} |a_ir|:

@@ -707,7 +707,8 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (opt) o = *opt;
     if (o.batch <= 0) o.batch = 1;
     if (o.rhs_block < 0 || o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 ||
-        o.ordering > 1 || o.relax < 0 || o.refine_max < 0)
+        o.ordering > 1 || o.relax < 0 || o.refine_max < 0 || o.nd_leaf < 0 || o.diag_ctas_per_sm < 0 ||
+        o.diag_unpruned < 0 || o.diag_unpruned > 1)
         return SPI_ERR_ARG;
     if (o.precision == SPI_PREC_MIXED_FP32 && o.rhs_block > 0) o.rhs_block = (o.rhs_block + 7) & ~7;
     spi_ctx* c = new (std::nothrow) spi_ctx();

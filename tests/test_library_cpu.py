@@ -204,3 +204,14 @@ def test_struct_layouts_match_header(P, tmp_path):
         assert int(got[st]) == ct.sizeof(cls), st
         for f, _ in cls._fields_:
             assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+@pytest.mark.parametrize("field,value", [("rhs_block", -1), ("rhs_block", 513), ("precision", 2),
+                                         ("ordering", 2), ("relax", -1), ("refine_max", -1),
+                                         ("nd_leaf", -1), ("diag_ctas_per_sm", -1), ("diag_unpruned", 2)])
+def test_options_are_validated(P, field, value):
+    """spi_analyse rejects out-of-range options before any work."""
+    pb = random_spd(20, 0.2, 1)
+    with pytest.raises(P.SpiError) as e:
+        P.Solver.for_problem(pb, **{field: value})
+    assert e.value.code == 1

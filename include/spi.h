@@ -147,7 +147,10 @@ void spi_default_options(spi_options* opt);
  *           column, each column starting with its diagonal entry
  *   opt     host, may be NULL (defaults)
  *   out     receives the new context (owned by the caller; spi_destroy)
- * Errors: SPI_ERR_ARG, SPI_ERR_PATTERN, SPI_ERR_OOM. */
+ * Errors: SPI_ERR_ARG (NULL out, n < 0, an option out of range: rhs_block
+ * outside 0..512, precision or ordering unknown, relax, refine_max, nd_leaf
+ * or diag_ctas_per_sm negative, diag_unpruned not 0 or 1), SPI_ERR_PATTERN,
+ * SPI_ERR_OOM. */
 int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind,
                 const spi_options* opt, spi_ctx** out);
 

@@ -64,8 +64,10 @@ typedef struct spi_options {
     int precision;   /* spi_precision */
     int ordering;    /* spi_ordering */
     int rhs_block;   /* right-hand sides per block in spi_diag_inverse, 1..512 (rounded up to a
-                        multiple of 8 in mixed precision); 0 = automatic: 32 in FP64, 64 in
-                        mixed precision (Sec. 4.3 groups 128 right-hand sides on a CPU core) */
+                        multiple of 8 in mixed precision); 0 = automatic: the first variance call
+                        times a few candidate sizes on the factor and keeps the fastest (32 in
+                        FP64, 64-128 in mixed precision on the SPI workloads; Sec. 4.3 groups 128
+                        right-hand sides on a CPU core) */
     int relax;       /* supernode amalgamation: max explicit zeros per parent-child merge as a
                         percentage of the merged panel, plus merges of very small supernodes and
                         grouping of sibling leaf fronts; 0 = fundamental supernodes only;

@@ -110,11 +110,13 @@ typedef struct spi_stats {
     double factor_flops;    /* sum over pivots j of (c_j^2 - 1), c_j = entries of column j of L
                                including the diagonal (exact counts, no amalgamation zeros) */
     double diag_flops;      /* algorithmic flops of the last spi_diag_inverse call:
-                               sum over requested i, over j on path(i), of 2 c_j */
+                               sum over requested i, over j on path(i), of 2 c_j (0 after a
+                               call with spi_options.diag_unpruned) */
     double solve_flops;     /* 4 * nnz_l + n (one forward + one backward sweep) */
     double diag_flops_all;  /* algorithmic flops of spi_diag_inverse over all n indices */
     double diag_work_flops; /* flops the blocked kernel executes for the last spi_diag_inverse
-                               (dense over each block's active range, amalgamation zeros) */
+                               (dense over each block's active range, amalgamation zeros; with
+                               diag_unpruned, 2 x stored panel entries per index) */
     int64_t device_bytes;   /* device memory held by the context */
     int64_t launches_factor;/* kernels this library launches per spi_factor */
     int64_t launches_solve; /* ... per spi_solve */

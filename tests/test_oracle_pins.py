@@ -5,7 +5,6 @@ Sec. 3.2.1 / Fig. 3-4).  A final test plants mistakes in copies of the
 oracle's C source and checks that the pins catch every one."""
 import json
 import os
-import re
 import subprocess
 
 import numpy as np

@@ -95,6 +95,25 @@ typedef struct spi_options {
                             pass, FP64 panels), var_i = sum_k z_k^2 / d_k, so that the gain
                             of pruning can be measured (the paper's brute-force comparison,
                             Table 5); spi_diag_inverse only, band 0 only */
+    int autotune;    /* how the first spi_factor / spi_factor_batch of a context chooses, per
+                        front-size bucket (floor(log2) of a front's rows and pivots), between the
+                        panel of a front processed whole by one CTA of a persistent per-level
+                        kernel and the tiled chain of 32-column block-step launches, and (mixed
+                        precision) between the SIMT and tensor-core Schur complement:
+                        0 = time both candidates of every bucket on the caller's values when the
+                        factorization is large enough (>= 2e8 flops), else built-in rules;
+                        1 = always time; -1 = never time (built-in rules).  Buckets found in
+                        tune_cache are not timed again.  The timing costs two extra
+                        factorizations, once per context */
+    int force_panel; /* 0 = as chosen above; 1 = every panel on the block-step chain; 2 = every
+                        panel whose work allows it in the persistent per-level kernel */
+    int force_schur; /* 0 = as chosen above; 1 = no tensor-core launch at all (SIMT Schur
+                        complements and panel updates); 2 = Schur complements on the tensor
+                        cores wherever legal (mixed precision, at least 256 trailing rows and
+                        32 pivots) */
+    const char* tune_cache; /* path of a text file keeping the autotuner's choices across
+                        processes (one line per device, precision, batch class and bucket), or
+                        NULL; read at the first factorization, rewritten after a timing */
 } spi_options;
 
 typedef struct spi_stats {
@@ -131,6 +150,16 @@ typedef struct spi_stats {
     double mle_cash;        /* its final Cash statistic sum (e - y ln e) */
     int64_t bg_iters;       /* solves made by the last spi_background_fit */
     double bg_stat;         /* the statistic of the pair it returned (chi^2 or Cash) */
+    int64_t launches_factor_fused; /* launches of the persistent per-level panel kernel per spi_factor */
+    int64_t launches_factor_tc;    /* tensor-core (tcgen05) launches per spi_factor (mixed precision) */
+    int64_t tiles_factor_tc;       /* 128 x 128 tensor-core tiles per spi_factor */
+    int64_t tune_source;    /* where the factorization's bucket choices came from: 0 built-in rules,
+                               1 timed by this context, 2 the tune cache */
+    double tune_seconds;    /* host time the timing took */
+    int64_t tune_panel_buckets;  /* panel buckets of this tree with a choice to make ... */
+    int64_t tune_panel_fused;    /* ... and how many of them run in the persistent kernel */
+    int64_t tune_schur_buckets;  /* Schur buckets that may use the tensor cores ... */
+    int64_t tune_schur_tc;       /* ... and how many of them do */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;
@@ -412,13 +441,28 @@ int spi_background_fit(spi_ctx* ctx, int64_t k0, const int32_t* upat, const doub
  * n <= 1,398,100; larger problems get SPI_ERR_SCRATCH (checked before any
  * device work).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call clears the part of the array it
+ * call before any stream capture.  Host threads may make that first call at
+ * the same time (the lookup is serialised).  A CUDA error already pending
+ * when the call starts makes it return SPI_ERR_CUDA before any device work and
+ * is left pending for the caller.  Every call clears the part of the array it
  * uses before use; calls that overlap on the GPU (other streams, other
  * contexts) share the array and race.  The call returns after the stream has
  * drained.  Errors: SPI_ERR_ARG (NULL buffer, index out of range -- its out[t]
  * is NaN -- or another device current), SPI_ERR_STATE (not factored),
  * SPI_ERR_SCRATCH, SPI_ERR_CUDA. */
 int spi_diag_inverse_noalloc(const spi_ctx* ctx, const int32_t* idx, int64_t nidx, double* out, void* stream);
+
+/* Measured throughput of one arithmetic unit of the current device, in
+ * TFLOP/s (a multiply-add counts 2), for the roofline denominators of the
+ * benchmark; not a step of the method.  unit: 0 FP64 FMA, 1 FP64 mma.sync
+ * m8n8k4 (DMMA), 2 FP32 FMA, 3 tcgen05.mma kind::tf32 (M 128, N 256), 4
+ * tcgen05.mma kind::f16 with BF16 inputs and FP32 accumulation.  Each probe
+ * runs independent operations on every SM for tens of milliseconds; *tflops
+ * receives the best of `reps` timed runs after one warm-up run.  The tensor-
+ * core probes wait for their MMAs with a bounded wait.  Allocates and frees a
+ * small device buffer.  Errors: SPI_ERR_ARG, SPI_ERR_OOM, SPI_ERR_CUDA,
+ * SPI_ERR_TIMEOUT. */
+int spi_measure_peak(int unit, int reps, double* tflops);
 
 /* Statistics of the analysis and of the last calls.  Errors: SPI_ERR_ARG. */
 int spi_info(const spi_ctx* ctx, spi_stats* out);

@@ -13,11 +13,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -39,9 +41,17 @@ struct spi_ctx {
     DevSym dsym;
     Strides bs;
     int64_t* d_amap = nullptr;
-    int32_t *d_diag_src = nullptr, *d_items0 = nullptr, *d_items1 = nullptr, *d_items2 = nullptr,
-            *d_items3 = nullptr, *d_items7 = nullptr, *d_items8 = nullptr, *d_items9 = nullptr, *d_fwd_items = nullptr,
-            *d_bwd_items = nullptr;
+    int32_t *d_diag_src = nullptr, *d_fwd_items = nullptr, *d_bwd_items = nullptr;
+    // the factorization's launch items on the device (per plan: the autotuner's plans have their own)
+    struct DevFactorPlan {
+        int32_t* items[13] = {};  // by launch kind
+        std::vector<void*> allocs;
+    } dfp;
+    bool factor_plan_ready = false;  // c->FP is final (tuned or by rule) and uploaded
+    FactorChoice choice;             // the bucket table behind c->FP
+    int tune_source = 0;             // 0 built-in rules, 1 timed here, 2 read from the tune cache
+    double tune_seconds = 0;
+    int64_t tune_panel_buckets = 0, tune_panel_fused = 0, tune_schur_buckets = 0, tune_schur_tc = 0;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
@@ -103,6 +113,7 @@ struct spi_ctx {
     std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
     std::vector<int32_t> in_rowind;
     double analyse_seconds = 0;
+    std::string tune_cache_path;  // the caller's spi_options.tune_cache, copied
 };
 
 namespace {
@@ -163,13 +174,6 @@ int ensure_device(spi_ctx* c) {
     c->bs.nnz = S.nnz_a;
     CK(dev_upload(c, &c->d_amap, S.amap));
     CK(dev_upload(c, &c->d_diag_src, S.diag_src));
-    CK(dev_upload(c, &c->d_items0, c->FP.diag_items));
-    CK(dev_upload(c, &c->d_items1, c->FP.trsm_items));
-    CK(dev_upload(c, &c->d_items2, c->FP.schur_items));
-    CK(dev_upload(c, &c->d_items3, c->FP.update_items));
-    CK(dev_upload(c, &c->d_items7, c->FP.schur_tc_items));
-    CK(dev_upload(c, &c->d_items8, c->FP.dfront_items));
-    CK(dev_upload(c, &c->d_items9, c->FP.panel_tc_items));
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
@@ -294,6 +298,272 @@ int finish(spi_ctx* c, cudaStream_t st) {
     return SPI_OK;
 }
 
+void free_factor_plan(spi_ctx::DevFactorPlan& d) {
+    for (void* a : d.allocs) cudaFree(a);
+    d = spi_ctx::DevFactorPlan();
+}
+
+int upload_factor_plan(spi_ctx* c, const FactorPlan& F, spi_ctx::DevFactorPlan& d) {
+    free_factor_plan(d);
+    std::vector<void*>* tr = &d.allocs;
+    CK(dev_upload(c, &d.items[0], F.diag_items, tr));
+    CK(dev_upload(c, &d.items[1], F.trsm_items, tr));
+    CK(dev_upload(c, &d.items[2], F.schur_items, tr));
+    CK(dev_upload(c, &d.items[3], F.update_items, tr));
+    CK(dev_upload(c, &d.items[7], F.schur_tc_items, tr));
+    CK(dev_upload(c, &d.items[8], F.dfront_items, tr));
+    CK(dev_upload(c, &d.items[9], F.panel_tc_items, tr));
+    CK(dev_upload(c, &d.items[12], F.fused_items, tr));
+    return SPI_OK;
+}
+
+// Zeroed panels and update areas, then the input values scattered into the
+// fronts, on s2 (launched on every call: the values' address changes).
+cudaError_t factor_assemble(spi_ctx* c, int nb, const double* vals, cudaStream_t s2) {
+    const Symbolic& S = c->S;
+    const bool mixed = mixed_of(c);
+    void* Lw = mixed ? (void*)c->d_L32 : (void*)c->d_L;
+    void* Fw = mixed ? (void*)c->d_F22f : (void*)c->d_F22;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    cudaError_t e = cudaMemsetAsync(Lw, 0, (size_t)S.lptr[S.ns] * nb * esz, s2);
+    if (e == cudaSuccess && S.f22_total) e = cudaMemsetAsync(Fw, 0, (size_t)S.f22_total * nb * esz, s2);
+    if (e != cudaSuccess) return e;
+    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, Lw, mixed, c->d_diag_src, c->d_adiag, nb, c->bs, s2);
+    return cudaGetLastError();
+}
+
+// Every launch of plan F on s2 (a timing marker records evs[group]).
+void factor_launches(spi_ctx* c, int nb, const FactorPlan& F, const spi_ctx::DevFactorPlan& dp, cudaStream_t s2,
+                     const std::vector<cudaEvent_t>* evs) {
+    const bool mixed = mixed_of(c);
+    void* Lw = mixed ? (void*)c->d_L32 : (void*)c->d_L;
+    void* Fw = mixed ? (void*)c->d_F22f : (void*)c->d_F22;
+    void* DS = mixed ? (void*)c->d_Df : (void*)c->d_D;
+    for (const Launch& l : F.launches) {
+        if (l.kind < 0) {
+            if (evs) cudaEventRecord((*evs)[(size_t)l.step], s2);
+            continue;
+        }
+        launch_factor_step(c->dsym, l, dp.items[l.kind], Lw, Fw, c->d_D, DS, c->d_adiag, c->d_status, mixed, nb,
+                           c->bs, c->opt.wait_limit, s2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the factorization (tile path per front-size bucket).
+//
+// Two plans are built in which every bucket takes one candidate: all panels
+// on the block-step chain with SIMT Schur complements, and all panels in the
+// persistent per-level kernel with tensor-core Schur complements wherever
+// legal.  In both, each (bucket, level) group is launched on its own between
+// timing markers.  Each plan is recorded as a CUDA graph (with its event
+// nodes), replayed twice on the caller's values, and the second replay's
+// group times are summed per bucket; every bucket keeps its faster candidate.
+// The table can be kept in a text file (spi_options.tune_cache), one line
+// per bucket: device, precision, batch class, P (panel) or S (Schur), bucket,
+// choice, milliseconds of the two candidates.
+
+std::string tune_key(spi_ctx* c, int nb) {
+    cudaDeviceProp prop;
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) dev = prop.name;
+    for (char& ch : dev)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return dev + " " + (mixed_of(c) ? "mixed" : "fp64") + " " + (nb > 1 ? "batch" : "single");
+}
+
+// The buckets whose choice matters for this tree: panel buckets of fronts that
+// may run either way, Schur buckets of fronts that may use the tensor cores.
+void tunable_buckets(const spi_ctx* c, std::vector<int32_t>& pb, std::vector<int32_t>& sb) {
+    const Symbolic& S = c->S;
+    const bool tc = mixed_of(c);
+    std::map<int32_t, int> a, b;
+    for (int32_t s = 0; s < S.ns; ++s) {
+        const int64_t k = S.k_of(s), m = S.m_of(s);
+        if (!S.sdiag[s] && !wide_front(tc, m, k) && fused_legal(m, k)) a[panel_bucket(m, k)] = 1;
+        if (S.sparent[s] != -1 && m > k && schur_tc_legal(tc, m, k)) b[schur_bucket(m, k)] = 1;
+    }
+    pb.clear();
+    sb.clear();
+    for (auto& kv : a) pb.push_back(kv.first);
+    for (auto& kv : b) sb.push_back(kv.first);
+}
+
+struct TuneLine {
+    char kind;
+    int32_t bucket;
+    int choice;
+    double ms0, ms1;
+};
+
+void read_tune_cache(const char* path, const std::string& key, std::vector<TuneLine>& out,
+                     std::vector<std::string>* other) {
+    FILE* fp = path ? std::fopen(path, "r") : nullptr;
+    if (!fp) return;
+    char buf[512];
+    while (std::fgets(buf, sizeof buf, fp)) {
+        char dev[256], prec[32], cls[32], kind[8];
+        int bucket = 0, choice = 0;
+        double a = 0, b = 0;
+        if (buf[0] == '#' ||
+            std::sscanf(buf, "%255s %31s %31s %7s %d %d %lf %lf", dev, prec, cls, kind, &bucket, &choice, &a, &b) != 8) {
+            continue;
+        }
+        const std::string k = std::string(dev) + " " + prec + " " + cls;
+        if (k == key && (kind[0] == 'P' || kind[0] == 'S')) out.push_back(TuneLine{kind[0], bucket, choice, a, b});
+        else if (other) other->push_back(buf);
+    }
+    std::fclose(fp);
+}
+
+void write_tune_cache(const char* path, const std::string& key, const std::vector<TuneLine>& lines) {
+    if (!path) return;
+    std::vector<TuneLine> mine;
+    std::vector<std::string> other;
+    read_tune_cache(path, key, mine, &other);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = std::fopen(tmp.c_str(), "w");
+    if (!fp) return;
+    std::fprintf(fp, "# spi factorization autotuner: device precision batch P|S bucket choice ms_candidate0 ms_candidate1\n");
+    for (const std::string& l : other) std::fputs(l.c_str(), fp);
+    for (const TuneLine& t : lines)
+        std::fprintf(fp, "%s %c %d %d %.6f %.6f\n", key.c_str(), t.kind, t.bucket, t.choice, t.ms0, t.ms1);
+    std::fclose(fp);
+    std::rename(tmp.c_str(), path);
+}
+
+// Time one candidate plan: per (kind, bucket), the summed milliseconds.  The
+// plan is replayed from a CUDA graph (as the factorization runs); if its
+// event nodes cannot be timed, the launches are issued directly instead.
+int time_plan(spi_ctx* c, int nb, const double* vals, const FactorChoice& ch, cudaStream_t st,
+              std::map<std::pair<int, int32_t>, double>& ms) {
+    FactorPlan F;
+    build_factor_plan(c->S, F, mixed_of(c), ch, true);
+    spi_ctx::DevFactorPlan dp;
+    int rc = upload_factor_plan(c, F, dp);
+    if (rc) { free_factor_plan(dp); return rc; }
+    std::vector<cudaEvent_t> ev(F.groups.size(), nullptr);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { rc = SPI_ERR_CUDA; break; }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph = false;
+    if (!rc) {
+        graph = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (graph) {
+            factor_launches(c, nb, F, dp, c->cap, &ev);
+            graph = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+        }
+        if (!graph) cudaGetLastError();
+    }
+    std::map<std::pair<int, int32_t>, double> got;
+    for (int attempt = graph ? 0 : 1; !rc && attempt < 2; ++attempt) {
+        const bool use_graph = attempt == 0;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            k_reset_status<<<1, 1, 0, st>>>(c->d_status);
+            if (factor_assemble(c, nb, vals, st) != cudaSuccess) { rc = SPI_ERR_CUDA; break; }
+            if (use_graph) {
+                if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = SPI_ERR_CUDA;
+            } else {
+                factor_launches(c, nb, F, dp, st, &ev);
+            }
+            if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = SPI_ERR_CUDA;
+        }
+        if (rc) break;
+        got.clear();
+        bool timed = true;
+        for (size_t q = 0; q + 1 < F.groups.size(); ++q) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[q], ev[q + 1]) != cudaSuccess) { timed = false; break; }
+            const FactorPlan::Group& gr = F.groups[q];
+            if (gr.kind == FactorPlan::kPanel || gr.kind == FactorPlan::kSchur) got[{gr.kind, gr.bucket}] += t;
+        }
+        if (timed) break;
+        cudaGetLastError();
+        if (!use_graph) rc = SPI_ERR_CUDA;  // neither form could be timed
+    }
+    if (!rc) ms = got;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    free_factor_plan(dp);
+    return rc;
+}
+
+// Make c->FP final and upload it: from the tune cache, by timing, or by the
+// built-in rules (see spi_options.autotune).
+int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st) {
+    const Symbolic& S = c->S;
+    FactorChoice ch;
+    ch.force_panel = c->opt.force_panel;
+    ch.force_schur = c->opt.force_schur;
+    std::vector<int32_t> pb, sb;
+    tunable_buckets(c, pb, sb);
+    if (ch.force_panel) pb.clear();
+    if (ch.force_schur) sb.clear();
+    c->tune_source = 0;
+    c->tune_seconds = 0;
+    if (!pb.empty() || !sb.empty()) {
+        const std::string key = tune_key(c, nb);
+        std::vector<TuneLine> cached;
+        read_tune_cache(c->opt.tune_cache, key, cached, nullptr);
+        for (const TuneLine& t : cached) (t.kind == 'P' ? ch.panel : ch.schur)[t.bucket] = (uint8_t)(t.choice != 0);
+        bool missing = false;
+        for (int32_t b : pb) missing |= !ch.panel.count(b);
+        for (int32_t b : sb) missing |= !ch.schur.count(b);
+        const bool timing = c->opt.autotune > 0 || (c->opt.autotune == 0 && S.factor_flops >= 2e8);
+        if (!missing) {
+            c->tune_source = 2;
+        } else if (timing) {
+            auto t0 = std::chrono::steady_clock::now();
+            FactorChoice a = ch, b = ch;
+            a.panel.clear(); a.schur.clear(); b.panel.clear(); b.schur.clear();
+            a.force_panel = ch.force_panel ? ch.force_panel : 1;
+            a.force_schur = ch.force_schur ? ch.force_schur : 1;
+            b.force_panel = ch.force_panel ? ch.force_panel : 2;
+            b.force_schur = ch.force_schur ? ch.force_schur : 2;
+            std::map<std::pair<int, int32_t>, double> ma, mb;
+            int rc = time_plan(c, nb, vals, a, st, ma);
+            if (!rc) rc = time_plan(c, nb, vals, b, st, mb);
+            if (rc) return rc;
+            std::vector<TuneLine> lines;
+            for (int32_t bk : pb) {
+                const double t0a = ma[{FactorPlan::kPanel, bk}], t1 = mb[{FactorPlan::kPanel, bk}];
+                ch.panel[bk] = (uint8_t)(t1 < t0a);
+                lines.push_back(TuneLine{'P', bk, t1 < t0a ? 1 : 0, t0a, t1});
+            }
+            for (int32_t bk : sb) {
+                const double t0a = ma[{FactorPlan::kSchur, bk}], t1 = mb[{FactorPlan::kSchur, bk}];
+                ch.schur[bk] = (uint8_t)(t1 < t0a);
+                lines.push_back(TuneLine{'S', bk, t1 < t0a ? 1 : 0, t0a, t1});
+            }
+            write_tune_cache(c->opt.tune_cache, key, lines);
+            c->tune_source = 1;
+            c->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
+    c->tune_panel_buckets = (int64_t)pb.size();
+    c->tune_schur_buckets = (int64_t)sb.size();
+    c->tune_panel_fused = c->tune_schur_tc = 0;
+    for (int32_t b : pb) {
+        auto it = ch.panel.find(b);
+        c->tune_panel_fused += it != ch.panel.end() ? it->second : 0;
+    }
+    for (int32_t b : sb) {
+        auto it = ch.schur.find(b);
+        c->tune_schur_tc += it != ch.schur.end() ? it->second : 0;
+    }
+    c->choice = ch;
+    build_factor_plan(S, c->FP, mixed_of(c), ch, false);
+    for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
+    c->g_factor.clear();
+    int rc = upload_factor_plan(c, c->FP, c->dfp);
+    if (rc) return rc;
+    c->factor_plan_ready = true;
+    return SPI_OK;
+}
+
 int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, cudaStream_t st) {
     if (!c || nb < 1 || nb > c->opt.batch) return SPI_ERR_ARG;
     if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
@@ -309,26 +579,15 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
                            values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         vals = c->d_vals;
     }
+    if (!c->factor_plan_ready) {
+        rc = prepare_factor_plan(c, nb, vals, st);
+        if (rc) return rc;
+    }
     k_reset_status<<<1, 1, 0, st>>>(c->d_status);
     // panels and update areas in the factorization's storage type (FP32 in the mixed form)
-    void* Lw = mixed ? (void*)c->d_L32 : (void*)c->d_L;
-    void* Fw = mixed ? (void*)c->d_F22f : (void*)c->d_F22;
-    void* DS = mixed ? (void*)c->d_Df : (void*)c->d_D;
-    const size_t esz = mixed ? sizeof(float) : sizeof(double);
-    CK(cudaMemsetAsync(Lw, 0, (size_t)S.lptr[S.ns] * nb * esz, st));
-    if (S.f22_total) CK(cudaMemsetAsync(Fw, 0, (size_t)S.f22_total * nb * esz, st));
-    launch_assemble(c->dsym, c->d_amap, vals, S.nnz_a, Lw, mixed, c->d_diag_src, c->d_adiag, nb, c->bs, st);
+    CK(factor_assemble(c, nb, vals, st));
     CK(run_graph(c, c->g_factor, nb, st, [&](cudaStream_t s2) {
-        for (const Launch& l : c->FP.launches) {
-            const int32_t* items = l.kind == 0 ? c->d_items0
-                                 : l.kind == 1 ? c->d_items1
-                                 : l.kind == 2 ? c->d_items2
-                                 : l.kind == 7 ? c->d_items7
-                                 : l.kind == 8 ? c->d_items8
-                                 : l.kind == 9 ? c->d_items9 : c->d_items3;
-            launch_factor_step(c->dsym, l, items, Lw, Fw, c->d_D, DS, c->d_adiag, c->d_status, mixed, nb, c->bs,
-                               c->opt.wait_limit, s2);
-        }
+        factor_launches(c, nb, c->FP, c->dfp, s2, nullptr);
         // the solves, inverse blocks and the allocation-free variances read the FP64 panels
         if (mixed) launch_to_f64(c->d_L32, c->d_L, S.lptr[S.ns] * nb, s2);
     }));
@@ -607,7 +866,29 @@ constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 21;  // 16 MiB
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 constexpr int kNoAllocMaxDevices = 64;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+// Device address of the array, per device, looked up on the first call on that
+// device.  Several host threads may make their first call at the same time:
+// the slots are atomics and the lookup itself is serialised by a mutex.
+std::atomic<double*> g_noalloc_ptr[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// The array's device address on the current device `dev`, or nullptr if the
+// lookup failed.
+double* noalloc_scratch(int dev) {
+    double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+    if (p) return p;
+    void* a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess || !a) {
+        cudaGetLastError();  // the failed lookup's own error, not one the caller left pending
+        return nullptr;
+    }
+    p = static_cast<double*>(a);
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    return p;
+}
 
 __global__ void k_noalloc_prepare(const int32_t* __restrict__ perm, int32_t n, double* scratch, int64_t zlen) {
     int32_t* iperm = reinterpret_cast<int32_t*>(scratch + 1);
@@ -708,12 +989,17 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (o.batch <= 0) o.batch = 1;
     if (o.rhs_block < 0 || o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 ||
         o.ordering > 1 || o.relax < 0 || o.refine_max < 0 || o.nd_leaf < 0 || o.diag_ctas_per_sm < 0 ||
-        o.diag_unpruned < 0 || o.diag_unpruned > 1)
+        o.diag_unpruned < 0 || o.diag_unpruned > 1 || o.autotune < -1 || o.autotune > 1 || o.force_panel < 0 ||
+        o.force_panel > 2 || o.force_schur < 0 || o.force_schur > 2)
         return SPI_ERR_ARG;
     if (o.precision == SPI_PREC_MIXED_FP32 && o.rhs_block > 0) o.rhs_block = (o.rhs_block + 7) & ~7;
     spi_ctx* c = new (std::nothrow) spi_ctx();
     if (!c) return SPI_ERR_OOM;
     c->opt = o;
+    if (o.tune_cache) {
+        c->tune_cache_path = o.tune_cache;
+        c->opt.tune_cache = c->tune_cache_path.c_str();
+    }
     auto t0 = std::chrono::steady_clock::now();
     AnalyseParams prm;
     prm.ordering = o.ordering;
@@ -723,7 +1009,10 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     int rc = analyse(n, colptr, rowind, prm, c->S, err);
     if (rc != 0) { delete c; return rc; }
     try {
-        build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32);
+        FactorChoice ch;  // the built-in rules until the first factorization makes the plan final
+        ch.force_panel = o.force_panel;
+        ch.force_schur = o.force_schur;
+        build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32, ch, false);
         build_solve_plan(c->S, c->SP, std::max(1, o.batch));
         if (n > 0) {  // the residual of the mixed form and the normal-equation assembly use it
             c->in_colptr.assign(colptr, colptr + n + 1);
@@ -1631,7 +1920,16 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->diag_flops_all = S.diag_flops_all;
     o->diag_work_flops = c->last_diag_work;
     o->device_bytes = c->device_bytes;
-    o->launches_factor = 2 + (int64_t)c->FP.launches.size() + (mixed_of(c) ? 1 : 0);
+    o->launches_factor = 2 + c->FP.n_kernel_launches + (mixed_of(c) ? 1 : 0);
+    o->launches_factor_fused = c->FP.n_fused_launches;
+    o->launches_factor_tc = c->FP.n_tc_launches;
+    o->tiles_factor_tc = c->FP.n_tc_tiles;
+    o->tune_source = c->tune_source;
+    o->tune_seconds = c->tune_seconds;
+    o->tune_panel_buckets = c->tune_panel_buckets;
+    o->tune_panel_fused = c->tune_panel_fused;
+    o->tune_schur_buckets = c->tune_schur_buckets;
+    o->tune_schur_tc = c->tune_schur_tc;
     int64_t ls = 0;
     for (const Launch& l : c->SP.fwd_launches) ls += l.count > 0;
     for (const Launch& l : c->SP.bwd_launches) ls += l.count > 0;
@@ -1680,16 +1978,16 @@ int spi_diag_inverse_noalloc(const spi_ctx* c, const int32_t* idx, int64_t nidx,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return SPI_ERR_CUDA;
     if (dev != c->device) return SPI_ERR_ARG;
-    if (!g_noalloc_ptr[dev]) {
-        // once per device, with that device current (this first call must not be inside a stream capture)
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPI_ERR_CUDA;
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    double* scratch = g_noalloc_ptr[dev];
+    // An error the caller left pending is reported, and left pending for the caller,
+    // rather than taken for one of these launches (cudaPeekAtLastError does not clear it).
+    if (cudaPeekAtLastError() != cudaSuccess) return SPI_ERR_CUDA;
+    // once per device, with that device current (this first call must not be inside a stream capture)
+    double* scratch = noalloc_scratch(dev);
+    if (!scratch) return SPI_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t slots = std::min<int64_t>({(kNoAllocScratchDoubles - fixed) / n, nidx, 1024});
     k_noalloc_prepare<<<256, 256, 0, st>>>(c->dsym.perm, (int32_t)n, scratch, slots * n);
+    if (cudaGetLastError() != cudaSuccess) return SPI_ERR_CUDA;
     k_diag_inv_noalloc<<<(int)slots, 256, 0, st>>>(c->dsym, c->d_L, c->d_D, idx, nidx, out, scratch);
     if (cudaGetLastError() != cudaSuccess) return SPI_ERR_CUDA;
     double flag = 0.0;
@@ -1704,6 +2002,7 @@ void spi_destroy(spi_ctx* c) {
     free_plan(c->plan_all);
     free_plan(c->plan_sub);
     free_plan(c->plan_blk);
+    free_factor_plan(c->dfp);
     if (c->d_zg) cudaFree(c->d_zg);
     for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
     for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);

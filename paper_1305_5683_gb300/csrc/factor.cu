@@ -30,6 +30,9 @@ namespace spi {
 // run as fast on the SIMT kernel, whose FP32 accumulation is also a little
 // more accurate than the tensor cores' (which truncate when aligning addends).
 constexpr int32_t kTcMinRows = 2048;
+// Trailing blocks this tall or taller may be given to the tensor cores by the
+// autotuner (a smaller block leaves most of a 128 x 128 tile empty).
+constexpr int32_t kTcMinLegal = 256;
 // Wide fronts (mixed precision, more than kOuter pivots, at least kTcMinRows
 // rows) are blocked twice: the 32-column steps update only the columns of
 // their own kOuter-column block, and after every kOuter columns one
@@ -41,99 +44,213 @@ constexpr int32_t kInner = kOuter / kT;
 constexpr int kTcM = 128, kTcN = 128, kTcK = 32;
 static_assert(kTcM == 128 && kTcN == 128, "the tensor-core kernels give thread t row t of both operand tiles");
 
-void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores) {
+int32_t ilog2_floor(int64_t v) {
+    int32_t r = 0;
+    while (v > 1) { v >>= 1; ++r; }
+    return r;
+}
+
+int32_t panel_bucket(int64_t m, int64_t k) { return ilog2_floor(std::max<int64_t>(m, 1)) * 32 + ilog2_floor(std::max<int64_t>(k, 1)); }
+int32_t schur_bucket(int64_t m, int64_t k) {
+    return ilog2_floor(std::max<int64_t>(m - k, 1)) * 32 + ilog2_floor(std::max<int64_t>(k, 1));
+}
+
+bool wide_front(bool tensor_cores, int64_t m, int64_t k) { return tensor_cores && k > kOuter && m >= kTcMinRows; }
+bool schur_tc_legal(bool tensor_cores, int64_t m, int64_t k) { return tensor_cores && m - k >= kTcMinLegal && k >= 32; }
+// A panel may run in one CTA of the per-level kernel when its work is bounded
+// (about m k^2 / 2 multiply-adds on one SM).
+bool fused_legal(int64_t m, int64_t k) { return m * k * k <= ((int64_t)1 << 26) && k <= 512; }
+
+// Built-in rules, used for buckets the autotuner has not timed: the panel of a
+// front runs in one CTA when its work (about m k^2 / 2 multiply-adds plus the
+// chain of ceil(k / 32) block steps) is small; the Schur complement goes to
+// the tensor cores from kTcMinRows trailing rows on.
+bool rule_fused(int64_t m, int64_t k) { return m * k * k <= (int64_t)1 << 22 && k <= 256; }
+bool rule_schur_tc(int64_t m, int64_t k) { return m - k >= kTcMinRows; }
+
+namespace {
+
+// The panel work of a front (for ordering the persistent kernel's items).
+int64_t panel_cost(const Symbolic& S, int32_t s) {
+    const int64_t k = S.k_of(s), m = S.m_of(s);
+    return S.sdiag[s] ? m * k : m * k * k / 2 + k * 1024;
+}
+
+// One launch of the persistent per-level panel kernel (kind 12) over `fronts`,
+// heaviest first (diagonal-pivot fronts are encoded as ~s).
+void append_fused(const Symbolic& S, FactorPlan& F, std::vector<int32_t> fronts) {
+    if (fronts.empty()) return;
+    std::stable_sort(fronts.begin(), fronts.end(),
+                     [&](int32_t a, int32_t b) { return panel_cost(S, a) > panel_cost(S, b); });
+    Launch l{12, 0, (int64_t)F.fused_items.size(), (int32_t)fronts.size()};
+    for (int32_t s : fronts) F.fused_items.push_back(S.sdiag[s] ? ~s : s);
+    F.launches.push_back(l);
+}
+
+// The block-step chain of `fronts` (none with a diagonal pivot block): per
+// 32-column step, the pivot tiles that start an outer block, the row tiles of
+// the panel solve, the trailing panel update (whose first tile factors the
+// next pivot tile) and, for wide fronts in mixed precision, the rank-kOuter
+// tensor-core update at the end of each outer block.
+void append_tiled(const Symbolic& S, FactorPlan& F, const std::vector<int32_t>& fronts, bool tensor_cores) {
+    int32_t kmax = 0;
+    for (int32_t s : fronts) kmax = std::max(kmax, S.k_of(s));
+    const int32_t nsteps = (kmax + kT - 1) / kT;
+    for (int32_t b = 0; b < nsteps; ++b) {
+        Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
+        Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
+        Launch lu{3, b, (int64_t)F.update_items.size() / 3, 0};
+        Launch lw{9, b, (int64_t)F.panel_tc_items.size() / 3, 0};
+        for (int32_t s : fronts) {
+            const int32_t k = S.k_of(s), m = S.m_of(s);
+            if (k <= b * kT) continue;
+            const bool wide = wide_front(tensor_cores, m, k);
+            if (b == 0 || (wide && b % kInner == 0)) {
+                F.diag_items.push_back(s);
+                ld.count++;
+            }
+            const int32_t w = std::min(kT, k - b * kT), r0 = b * kT + w;
+            for (int32_t rt = 0; r0 + rt * kT < m; ++rt) {
+                F.trsm_items.push_back(s);
+                F.trsm_items.push_back(rt);
+                lt.count++;
+            }
+            // trailing panel columns [r0, kend): lower tiles of rows [cj, m)
+            const int32_t kend = wide ? std::min(k, kOuter * (b / kInner + 1)) : k;
+            for (int32_t tj = 0; r0 + tj * kT < kend; ++tj) {
+                const int32_t cj = r0 + tj * kT;
+                for (int32_t ti = 0; cj + ti * kT < m; ++ti) {
+                    F.update_items.push_back(s);
+                    F.update_items.push_back(ti);
+                    F.update_items.push_back(tj);
+                    lu.count++;
+                }
+            }
+            // end of an outer block: rank-kOuter update of panel columns [r0, k)
+            if (wide && r0 == kend && r0 < k) {
+                for (int32_t ti = 0; r0 + ti * kTcM < m; ++ti)
+                    for (int32_t tj = 0; r0 + tj * kTcN < k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
+                        F.panel_tc_items.push_back(s);
+                        F.panel_tc_items.push_back(ti);
+                        F.panel_tc_items.push_back(tj);
+                        lw.count++;
+                    }
+            }
+        }
+        if (ld.count) F.launches.push_back(ld);
+        if (lt.count) F.launches.push_back(lt);
+        if (lu.count) F.launches.push_back(lu);
+        if (lw.count) F.launches.push_back(lw);
+    }
+}
+
+// Schur complements of `simt` (32 x 32 tiles, kind 2) and `tc` (128 x 128
+// tensor-core tiles, kind 7), each added into its parent's front.
+void append_schur(const Symbolic& S, FactorPlan& F, const std::vector<int32_t>& simt, const std::vector<int32_t>& tc) {
+    Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
+    for (int32_t s : simt) {
+        const int32_t k = S.k_of(s), m = S.m_of(s);
+        const int32_t nt = (m - k + kT - 1) / kT;
+        for (int32_t ti = 0; ti < nt; ++ti)
+            for (int32_t tj = 0; tj <= ti; ++tj) {
+                F.schur_items.push_back(s);
+                F.schur_items.push_back(ti);
+                F.schur_items.push_back(tj);
+                ls.count++;
+            }
+    }
+    Launch lc{7, 0, (int64_t)F.schur_tc_items.size() / 3, 0};
+    for (int32_t s : tc) {
+        const int32_t k = S.k_of(s), m = S.m_of(s);
+        for (int32_t ti = 0; ti * kTcM < m - k; ++ti)
+            for (int32_t tj = 0; tj * kTcN < m - k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
+                F.schur_tc_items.push_back(s);
+                F.schur_tc_items.push_back(ti);
+                F.schur_tc_items.push_back(tj);
+                lc.count++;
+            }
+    }
+    if (ls.count) F.launches.push_back(ls);
+    if (lc.count) F.launches.push_back(lc);
+}
+
+}  // namespace
+
+bool FactorChoice::fused(int64_t m, int64_t k) const {
+    if (force_panel == 1) return false;
+    if (force_panel == 2) return true;
+    auto it = panel.find(panel_bucket(m, k));
+    return it != panel.end() ? it->second != 0 : rule_fused(m, k);
+}
+
+bool FactorChoice::schur_tc(int64_t m, int64_t k) const {
+    if (force_schur == 1) return false;
+    if (force_schur == 2) return true;
+    auto it = schur.find(schur_bucket(m, k));
+    return it != schur.end() ? it->second != 0 : rule_schur_tc(m, k);
+}
+
+void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores_allowed, const FactorChoice& ch,
+                       bool markers) {
     F = FactorPlan();
+    const bool tensor_cores = tensor_cores_allowed && ch.force_schur != 1;  // 1: no tensor-core launch at all
     F.level_launch_ptr.push_back(0);
+    auto marker = [&](int kind, int32_t bucket) {
+        F.launches.push_back(Launch{-1, (int)F.groups.size(), 0, 0});
+        F.groups.push_back(FactorPlan::Group{kind, bucket});
+    };
     for (int32_t l = 0; l < S.nlevels; ++l) {
-        int32_t kmax = 0;
-        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p)
-            kmax = std::max(kmax, S.k_of(S.level_list[p]));
-        int32_t nsteps = (kmax + kT - 1) / kT;
-        // fronts with a diagonal pivot block (grouped independent leaves): no block steps
-        Launch lg{8, 0, (int64_t)F.dfront_items.size(), 0};
+        // panels: fronts with a diagonal pivot block always run in the persistent
+        // kernel; wide fronts of the mixed form always run the tiled chain (their
+        // tensor-core trailing updates); the rest as chosen per bucket
+        std::map<int32_t, std::vector<int32_t>> fused_by, tiled_by;
+        std::vector<int32_t> diag_fronts;
+        std::map<int32_t, std::vector<int32_t>> simt_by, tc_by;
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
             const int32_t s = S.level_list[p];
-            if (S.sdiag[s]) { F.dfront_items.push_back(s); lg.count++; }
-        }
-        if (lg.count) F.launches.push_back(lg);
-        for (int32_t b = 0; b < nsteps; ++b) {
-            Launch ld{0, b, (int64_t)F.diag_items.size(), 0};
-            Launch lt{1, b, (int64_t)F.trsm_items.size() / 2, 0};
-            Launch lu{3, b, (int64_t)F.update_items.size() / 3, 0};
-            Launch lw{9, b, (int64_t)F.panel_tc_items.size() / 3, 0};
-            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
-                int32_t s = S.level_list[p];
-                int32_t k = S.k_of(s), m = S.m_of(s);
-                if (k <= b * kT || S.sdiag[s]) continue;
-                const bool wide = tensor_cores && k > kOuter && m >= kTcMinRows;
-                // pivot tiles are factored by the previous step's update, except the
-                // first one and, in wide fronts, the first of every outer block
-                if (b == 0 || (wide && b % kInner == 0)) {
-                    F.diag_items.push_back(s);
-                    ld.count++;
-                }
-                int32_t w = std::min(kT, k - b * kT), r0 = b * kT + w;
-                for (int32_t rt = 0; r0 + rt * kT < m; ++rt) {
-                    F.trsm_items.push_back(s);
-                    F.trsm_items.push_back(rt);
-                    lt.count++;
-                }
-                // trailing panel columns [r0, kend): lower tiles of rows [cj, m)
-                const int32_t kend = wide ? std::min(k, kOuter * (b / kInner + 1)) : k;
-                for (int32_t tj = 0; r0 + tj * kT < kend; ++tj) {
-                    int32_t cj = r0 + tj * kT;
-                    for (int32_t ti = 0; cj + ti * kT < m; ++ti) {
-                        F.update_items.push_back(s);
-                        F.update_items.push_back(ti);
-                        F.update_items.push_back(tj);
-                        lu.count++;
-                    }
-                }
-                // end of an outer block: rank-kOuter update of panel columns [r0, k)
-                if (wide && r0 == kend && r0 < k) {
-                    for (int32_t ti = 0; r0 + ti * kTcM < m; ++ti)
-                        for (int32_t tj = 0; r0 + tj * kTcN < k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
-                            F.panel_tc_items.push_back(s);
-                            F.panel_tc_items.push_back(ti);
-                            F.panel_tc_items.push_back(tj);
-                            lw.count++;
-                        }
-                }
-            }
-            if (ld.count) F.launches.push_back(ld);
-            if (lt.count) F.launches.push_back(lt);
-            if (lu.count) F.launches.push_back(lu);
-            if (lw.count) F.launches.push_back(lw);
-        }
-        Launch ls{2, 0, (int64_t)F.schur_items.size() / 3, 0};
-        Launch lc{7, 0, (int64_t)F.schur_tc_items.size() / 3, 0};
-        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
-            int32_t s = S.level_list[p];
-            int32_t k = S.k_of(s), m = S.m_of(s);
+            const int32_t k = S.k_of(s), m = S.m_of(s);
+            if (S.sdiag[s]) diag_fronts.push_back(s);
+            else if (!wide_front(tensor_cores, m, k) && fused_legal(m, k) && ch.fused(m, k))
+                fused_by[panel_bucket(m, k)].push_back(s);
+            else tiled_by[panel_bucket(m, k)].push_back(s);
             if (S.sparent[s] == -1 || m <= k) continue;
-            if (tensor_cores && m - k >= kTcMinRows && k >= 32) {
-                // kTcM x kTcN tensor-core tiles of the lower trailing block
-                for (int32_t ti = 0; ti * kTcM < m - k; ++ti)
-                    for (int32_t tj = 0; tj * kTcN < m - k && tj * kTcN <= ti * kTcM + kTcM - 1; ++tj) {
-                        F.schur_tc_items.push_back(s);
-                        F.schur_tc_items.push_back(ti);
-                        F.schur_tc_items.push_back(tj);
-                        lc.count++;
-                    }
-                continue;
-            }
-            int32_t nt = (m - k + kT - 1) / kT;
-            for (int32_t ti = 0; ti < nt; ++ti)
-                for (int32_t tj = 0; tj <= ti; ++tj) {
-                    F.schur_items.push_back(s);
-                    F.schur_items.push_back(ti);
-                    F.schur_items.push_back(tj);
-                    ls.count++;
-                }
+            if (schur_tc_legal(tensor_cores, m, k) && ch.schur_tc(m, k)) tc_by[schur_bucket(m, k)].push_back(s);
+            else simt_by[schur_bucket(m, k)].push_back(s);
         }
-        if (ls.count) F.launches.push_back(ls);
-        if (lc.count) F.launches.push_back(lc);
+        if (ch.force_panel == 1 && !diag_fronts.empty()) {
+            // every panel on the block-step kernels: diagonal-pivot fronts one CTA each (kind 8)
+            if (markers) marker(FactorPlan::kDiagFronts, -1);
+            F.launches.push_back(Launch{8, 0, (int64_t)F.dfront_items.size(), (int32_t)diag_fronts.size()});
+            F.dfront_items.insert(F.dfront_items.end(), diag_fronts.begin(), diag_fronts.end());
+            diag_fronts.clear();
+        }
+        if (markers) {
+            // one timed group per (kind, bucket) of the level, launched on its own
+            if (!diag_fronts.empty()) { marker(FactorPlan::kDiagFronts, -1); append_fused(S, F, diag_fronts); }
+            for (auto& kv : fused_by) { marker(FactorPlan::kPanel, kv.first); append_fused(S, F, kv.second); }
+            for (auto& kv : tiled_by) { marker(FactorPlan::kPanel, kv.first); append_tiled(S, F, kv.second, tensor_cores); }
+            for (auto& kv : simt_by) { marker(FactorPlan::kSchur, kv.first); append_schur(S, F, kv.second, {}); }
+            for (auto& kv : tc_by) { marker(FactorPlan::kSchur, kv.first); append_schur(S, F, {}, kv.second); }
+        } else {
+            std::vector<int32_t> fused(diag_fronts), tiled, simt, tc;
+            for (auto& kv : fused_by) fused.insert(fused.end(), kv.second.begin(), kv.second.end());
+            for (auto& kv : tiled_by) tiled.insert(tiled.end(), kv.second.begin(), kv.second.end());
+            for (auto& kv : simt_by) simt.insert(simt.end(), kv.second.begin(), kv.second.end());
+            for (auto& kv : tc_by) tc.insert(tc.end(), kv.second.begin(), kv.second.end());
+            std::sort(tiled.begin(), tiled.end());
+            std::sort(simt.begin(), simt.end());
+            std::sort(tc.begin(), tc.end());
+            append_fused(S, F, fused);
+            append_tiled(S, F, tiled, tensor_cores);
+            append_schur(S, F, simt, tc);
+        }
         F.level_launch_ptr.push_back((int32_t)F.launches.size());
+    }
+    if (markers) marker(FactorPlan::kEnd, -1);
+    for (const Launch& la : F.launches) {
+        if (la.kind == 12) F.n_fused_launches++;
+        if (la.kind == 7 || la.kind == 9) { F.n_tc_launches++; F.n_tc_tiles += la.count; }
+        if (la.kind >= 0) F.n_kernel_launches++;
     }
 }
 
@@ -230,16 +347,10 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
 // one front, no children): d_c is the input diagonal entry (kept in FP64 in
 // adiag) and L21(:, c) = F21(:, c) / d_c.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t* __restrict__ items,
-                                                         S* __restrict__ L, double* __restrict__ D, S* __restrict__ DS,
-                                                         const double* __restrict__ adiag, DevStatus* status,
-                                                         Strides bs) {
-    L += blockIdx.y * bs.L;
-    D += blockIdx.y * bs.n;
-    DS += blockIdx.y * bs.n;
-    adiag += blockIdx.y * bs.n;
+__device__ void diag_front_body(const DevSym& d, int s, S* __restrict__ L, double* __restrict__ D,
+                                S* __restrict__ DS, const double* __restrict__ adiag, DevStatus* status,
+                                int band_base) {
     const int tid = threadIdx.x;
-    const int s = items[blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     S* P = L + d.lptr[s];
@@ -247,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t
         const double dc = adiag[f + c];
         if (!(dc > 0.0)) {
             atomicOr(&status->flags, FLAG_NOT_SPD);
-            atomicMin(&status->bad_pivot, (int)(blockIdx.y * bs.n) + f + c);
+            atomicMin(&status->bad_pivot, band_base + f + c);
         }
         D[f + c] = dc;
         DS[f + c] = (S)dc;
@@ -257,6 +368,140 @@ __global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t
     for (int c = 0; c < k; ++c) {
         const S rc = (S)(1.0 / adiag[f + c]);
         for (int64_t r = k + tid; r < m; r += kThreads) P[r + (int64_t)c * m] *= rc;
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_diag_front(DevSym d, const int32_t* __restrict__ items,
+                                                         S* __restrict__ L, double* __restrict__ D, S* __restrict__ DS,
+                                                         const double* __restrict__ adiag, DevStatus* status,
+                                                         Strides bs) {
+    L += blockIdx.y * bs.L;
+    D += blockIdx.y * bs.n;
+    DS += blockIdx.y * bs.n;
+    adiag += blockIdx.y * bs.n;
+    diag_front_body(d, items[blockIdx.x], L, D, DS, adiag, status, (int)(blockIdx.y * bs.n));
+}
+
+// Shared memory of the per-level panel kernel; the three phases of a block
+// step use it in turn.
+template <typename C>
+union FrontPanelSmem {
+    struct {
+        double A[kT][kT + 1];
+        double dv[kT];
+    } piv;                      // the FP64 pivot tile
+    struct {
+        C Bd[kT][kT + 1];       // strictly lower part of the factored pivot tile
+        C rd[kT];               // 1 / d of its pivots
+        C X[kThreads][kT + 1];  // one row of the panel solve per thread
+    } trsm;
+    struct {
+        C Li[kT][kT + 1];       // 32 rows of the block column
+        C Lj[kT][kT + 1];       // 32 rows of the block column scaled by d
+    } upd;
+};
+
+// Persistent per-level panel kernel (kind 12): the CTAs walk the level's list
+// of fronts (heaviest first, in steps of the grid; item t is front
+// items[t / nb] of band t % nb) and each processes a whole front's panel on
+// its own, so a small front costs one launch per level instead of three or
+// more per 32-column block step.  Per block step: the FP64 pivot tile, the
+// panel solve of every row below it (one thread per row), then the rank-32
+// update of the remaining panel columns in 32 x 32 tiles.  The Schur
+// complement is left to the level's Schur launch.  A front with a diagonal
+// pivot block (~s in the list) is scaled column by column.  The CTAs never
+// wait on one another.
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_front_panel(DevSym d, const int32_t* __restrict__ items, int nitems,
+                                                          int nb, C* __restrict__ L, double* __restrict__ D,
+                                                          C* __restrict__ DS, const double* __restrict__ adiag,
+                                                          DevStatus* status, Strides bs) {
+    __shared__ FrontPanelSmem<C> sm;
+    const int tid = threadIdx.x;
+    const int64_t total = (int64_t)nitems * nb;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int band = (int)(t % nb);
+        const int code = items[t / nb];
+        C* Lb = L + band * bs.L;
+        double* Db = D + band * bs.n;
+        C* DSb = DS + band * bs.n;
+        const double* ab = adiag + band * bs.n;
+        const int base = (int)(band * bs.n);
+        __syncthreads();  // the previous front's last phase is done with the shared memory
+        if (code < 0) {
+            diag_front_body(d, ~code, Lb, Db, DSb, ab, status, base);
+            continue;
+        }
+        const int s = code;
+        const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+        const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+        C* P = Lb + d.lptr[s];
+        for (int c0 = 0; c0 < k; c0 += kT) {
+            const int w = min(kT, k - c0);
+            __syncthreads();
+            factor_pivot_tile(sm.piv.A, sm.piv.dv, P, m, c0, w, f, Db, DSb, ab, status, base);
+            __syncthreads();
+            // L21 = X L11^-T D^-1 for the rows below the pivot tile
+            for (int e = tid; e < kT * kT; e += kThreads) {
+                const int i = e % kT, j = e / kT;
+                sm.trsm.Bd[i][j] = (i < w && j < i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
+            }
+            if (tid < kT) sm.trsm.rd[tid] = tid < w ? (C)(1.0 / Db[f + c0 + tid]) : C(0);
+            __syncthreads();
+            C* xr = sm.trsm.X[tid];
+            for (int64_t r = c0 + w + tid; r < m; r += kThreads) {
+                for (int c = 0; c < w; ++c) xr[c] = P[r + (int64_t)(c0 + c) * m];
+                for (int c = 1; c < w; ++c) {
+                    C y = xr[c];
+                    for (int cp = 0; cp < c; ++cp) y -= xr[cp] * sm.trsm.Bd[c][cp];
+                    xr[c] = y;
+                }
+                for (int c = 0; c < w; ++c) P[r + (int64_t)(c0 + c) * m] = xr[c] * sm.trsm.rd[c];
+            }
+            // rank-w update of panel columns [c0 + w, k), rows i >= j, in 32 x 32 tiles:
+            // P[i][j] -= sum_c L[i][c] d_c L[j][c]; thread (ii, j0) owns row ii, columns j0 + 4 q
+            const int ii = tid % kT, j0 = tid / kT;
+            for (int cj = c0 + w; cj < k; cj += kT) {
+                const int nj = min(kT, k - cj);
+                __syncthreads();  // the panel solve (or the previous column tile) is done
+                for (int e = tid; e < kT * kT; e += kThreads) {
+                    const int i = e % kT, c = e / kT;
+                    sm.upd.Lj[i][c] = (i < nj && c < w) ? P[(cj + i) + (int64_t)(c0 + c) * m] * DSb[f + c0 + c] : C(0);
+                }
+                for (int64_t ri = cj; ri < m; ri += kT) {
+                    const int ni = (int)(m - ri < kT ? m - ri : kT);
+                    __syncthreads();
+                    for (int e = tid; e < kT * kT; e += kThreads) {
+                        const int i = e % kT, c = e / kT;
+                        sm.upd.Li[i][c] = (i < ni && c < w) ? P[(ri + i) + (int64_t)(c0 + c) * m] : C(0);
+                    }
+                    __syncthreads();
+                    if (ii < ni) {
+                        C acc[kT / 4];
+#pragma unroll
+                        for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
+#pragma unroll 4
+                        for (int c = 0; c < w; ++c) {
+                            const C ai = sm.upd.Li[ii][c];
+#pragma unroll
+                            for (int q = 0; q < kT / 4; ++q) acc[q] += ai * sm.upd.Lj[j0 + 4 * q][c];
+                        }
+                        C old[kT / 4];
+#pragma unroll
+                        for (int q = 0; q < kT / 4; ++q) {
+                            const int jj = j0 + 4 * q;
+                            old[q] = (jj < nj && ri + ii >= cj + jj) ? P[(ri + ii) + (int64_t)(cj + jj) * m] : C(0);
+                        }
+#pragma unroll
+                        for (int q = 0; q < kT / 4; ++q) {
+                            const int jj = j0 + 4 * q;
+                            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] = old[q] - acc[q];
+                        }
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -706,10 +951,24 @@ __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, in
 
 }  // namespace
 
+// CTAs of the persistent per-level panel kernel: every SM slot it fits in
+int g_panel_grid[2] = {0, 0};  // [0] FP64, [1] mixed
+
 cudaError_t factor_kernel_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_schur_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_schur_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    e = cudaFuncSetAttribute(k_schur_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, b64 = 0, b32 = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_front_panel<double>, kThreads, 0)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_front_panel<float>, kThreads, 0)) != cudaSuccess)
+        return e;
+    g_panel_grid[0] = std::max(1, sms * b64);
+    g_panel_grid[1] = std::max(1, sms * b32);
+    return cudaSuccess;
 }
 
 void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t st) {
@@ -754,6 +1013,12 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, C* L,
             }
             break;
         case 8: k_diag_front<C><<<g, kThreads, 0, st>>>(d, items + l.off, L, D, DS, adiag, status, bs); break;
+        case 12: {
+            const int64_t total = (int64_t)l.count * nb;
+            const int grid = (int)std::min<int64_t>(total, g_panel_grid[std::is_same<C, float>::value ? 1 : 0]);
+            k_front_panel<C><<<grid, kThreads, 0, st>>>(d, items + l.off, l.count, nb, L, D, DS, adiag, status, bs);
+            break;
+        }
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, DS, bs); break;
     }
 }
@@ -761,7 +1026,7 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, C* L,
 void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, void* L, void* F22, double* D,
                         void* DS, const double* adiag, DevStatus* status, bool mixed, int nb, const Strides& bs,
                         int wait_limit, cudaStream_t st) {
-    if (l.count == 0 || nb == 0) return;
+    if (l.kind < 0 || l.count == 0 || nb == 0) return;
     if (mixed)
         launch_step_t<float>(d, l, items, (float*)L, (float*)F22, D, (float*)DS, adiag, status, nb, bs, wait_limit,
                              st);

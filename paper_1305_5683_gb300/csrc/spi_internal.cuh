@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -54,12 +55,14 @@ struct Strides {
 struct Launch {
     int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
                      // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front,
-                     // 9 tensor-core trailing panel update of a wide front (mixed precision);
-                     // solves: 4 forward step, 5 backward first launch of a level, 6 backward
-                     // step, 10 / 11 forward / backward sweep of a whole level
+                     // 9 tensor-core trailing panel update of a wide front (mixed precision),
+                     // 12 persistent per-level kernel: whole panels of small fronts, one CTA
+                     // per front at a time; solves: 4 forward step, 5 backward first launch of
+                     // a level, 6 backward step, 10 / 11 forward / backward sweep of a whole
+                     // level; -1 a timing marker of the autotuner (no launch; `step` = group)
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
-    int32_t count;   // CTAs
+    int32_t count;   // CTAs (kind 12: fronts)
 };
 
 struct FactorPlan {
@@ -70,11 +73,43 @@ struct FactorPlan {
     std::vector<int32_t> schur_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<int32_t> dfront_items;   // supernodes with a diagonal pivot block
     std::vector<int32_t> panel_tc_items; // triples (supernode, 128-row tile, 64-column tile)
+    std::vector<int32_t> fused_items;    // kind 12: supernode, or ~supernode for a diagonal pivot block
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
+    // timing groups of an autotuner plan (markers): what the launches up to the
+    // next marker do, for one front-size bucket of one level
+    enum GroupKind { kPanel = 0, kSchur = 1, kDiagFronts = 2, kEnd = 3 };
+    struct Group {
+        int kind;
+        int32_t bucket;
+    };
+    std::vector<Group> groups;
+    int64_t n_kernel_launches = 0, n_fused_launches = 0, n_tc_launches = 0, n_tc_tiles = 0;
 };
 
-void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores);
+// Per front-size bucket choices of the factorization: the autotuner's table.
+// A panel bucket is (floor(log2 m), floor(log2 k)) of a front (m rows, k
+// pivots), a Schur bucket (floor(log2 (m - k)), floor(log2 k)), each packed
+// as 32 * first + second.  A bucket missing from the table takes the built-in rule.
+struct FactorChoice {
+    std::map<int32_t, uint8_t> panel;  // 1: whole panel in one CTA of the per-level kernel; 0: block-step chain
+    std::map<int32_t, uint8_t> schur;  // 1: tensor-core Schur complement (mixed precision); 0: SIMT
+    int force_panel = 0;               // 1 every front tiled, 2 every front fused (tests, tuning)
+    int force_schur = 0;               // 1 SIMT everywhere, 2 tensor cores wherever legal
+    bool fused(int64_t m, int64_t k) const;
+    bool schur_tc(int64_t m, int64_t k) const;
+};
+int32_t panel_bucket(int64_t m, int64_t k);
+int32_t schur_bucket(int64_t m, int64_t k);
+bool rule_fused(int64_t m, int64_t k);
+bool rule_schur_tc(int64_t m, int64_t k);
+bool wide_front(bool tensor_cores, int64_t m, int64_t k);
+bool schur_tc_legal(bool tensor_cores, int64_t m, int64_t k);
+bool fused_legal(int64_t m, int64_t k);
+
+// markers: insert a timing marker before every (bucket, level) group, each
+// group launched on its own (the autotuner's plans)
+void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores, const FactorChoice& ch, bool markers);
 cudaError_t factor_kernel_setup();
 
 struct SolvePlan {

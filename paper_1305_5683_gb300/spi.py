@@ -26,7 +26,7 @@ EXPORTS = ["spi_default_options", "spi_analyse", "spi_analyse_multi", "spi_facto
            "spi_solve", "spi_solve_batch", "spi_diag_inverse", "spi_diag_inverse_batch", "spi_info", "spi_sync",
            "spi_get_perm", "spi_get_etree", "spi_strerror", "spi_destroy", "spi_diag_inverse_noalloc",
            "spi_inverse_block", "spi_normal_setup", "spi_normal_assemble", "spi_normal_update", "spi_mle_newton",
-           "spi_background_fit", "spi_inverse_entries", "spi_diag_inverse_refined"]
+           "spi_background_fit", "spi_inverse_entries", "spi_diag_inverse_refined", "spi_measure_peak"]
 SPI_INVERSE_BLOCK_MAX = 512
 SPI_PATTERN_MAX = 2048
 SPI_FIT_LSQ, SPI_FIT_MLE = 0, 1
@@ -36,7 +36,9 @@ class spi_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ordering", ctypes.c_int), ("rhs_block", ctypes.c_int),
                 ("relax", ctypes.c_int), ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int), ("batch", ctypes.c_int),
-                ("wait_limit", ctypes.c_int), ("diag_ctas_per_sm", ctypes.c_int), ("diag_unpruned", ctypes.c_int)]
+                ("wait_limit", ctypes.c_int), ("diag_ctas_per_sm", ctypes.c_int), ("diag_unpruned", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("force_panel", ctypes.c_int), ("force_schur", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class spi_stats(ctypes.Structure):
@@ -52,7 +54,12 @@ class spi_stats(ctypes.Structure):
                 ("refine_steps", ctypes.c_int64), ("solve_relres", ctypes.c_double),
                 ("rhs_block", ctypes.c_int64),
                 ("analyse_seconds", ctypes.c_double), ("mle_steps", ctypes.c_int64),
-                ("mle_cash", ctypes.c_double), ("bg_iters", ctypes.c_int64), ("bg_stat", ctypes.c_double)]
+                ("mle_cash", ctypes.c_double), ("bg_iters", ctypes.c_int64), ("bg_stat", ctypes.c_double),
+                ("launches_factor_fused", ctypes.c_int64), ("launches_factor_tc", ctypes.c_int64),
+                ("tiles_factor_tc", ctypes.c_int64), ("tune_source", ctypes.c_int64),
+                ("tune_seconds", ctypes.c_double), ("tune_panel_buckets", ctypes.c_int64),
+                ("tune_panel_fused", ctypes.c_int64), ("tune_schur_buckets", ctypes.c_int64),
+                ("tune_schur_tc", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +109,7 @@ def load(path: str | None = None, build_if_missing: bool = False) -> ctypes.CDLL
     L.spi_mle_newton.argtypes = [V, V, V, V, I, ctypes.c_double, V, I, V]; L.spi_mle_newton.restype = I
     L.spi_background_fit.argtypes = [V, I64, V, V, I, V, V, V, V, V, I, I, ctypes.c_double, V, V, I, V]
     L.spi_background_fit.restype = I
+    L.spi_measure_peak.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]; L.spi_measure_peak.restype = I
     L.spi_info.argtypes = [V, ctypes.POINTER(spi_stats)]; L.spi_info.restype = I
     L.spi_sync.argtypes = [V, V]; L.spi_sync.restype = I
     L.spi_get_perm.argtypes = [V, V]; L.spi_get_perm.restype = I
@@ -384,6 +392,16 @@ def spi_diag_inverse_noalloc(ctx, idx, out, stream=None) -> None:
     del k1, k2
 
 
+PEAK_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "tf32_tcgen05": 3, "bf16_tcgen05": 4}
+
+
+def spi_measure_peak(unit: str, reps: int = 3) -> float:
+    """Measured TFLOP/s of one arithmetic unit (see PEAK_UNITS) on the current device."""
+    t = ctypes.c_double(0.0)
+    _check(lib().spi_measure_peak(PEAK_UNITS[unit], reps, ctypes.byref(t)), f"spi_measure_peak({unit})")
+    return t.value
+
+
 def spi_info(ctx) -> dict:
     st = spi_stats()
     _check(lib().spi_info(ctx, ctypes.byref(st)), "spi_info")
@@ -420,7 +438,8 @@ class Solver:
 
     def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
                  rhs_block=0, relax=1, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
-                 wait_limit=0, diag_ctas_per_sm=0, diag_unpruned=False, _multi=None):
+                 wait_limit=0, diag_ctas_per_sm=0, diag_unpruned=False, autotune=0, force_panel=0, force_schur=0,
+                 tune_cache=None, _multi=None):
         o = spi_default_options()
         o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax
         o.refine_max, o.refine_tol, o.nd_leaf, o.async_ = refine_max, refine_tol, nd_leaf, int(async_)
@@ -428,6 +447,8 @@ class Solver:
         o.wait_limit = wait_limit
         o.diag_ctas_per_sm = diag_ctas_per_sm
         o.diag_unpruned = int(diag_unpruned)
+        o.autotune, o.force_panel, o.force_schur = autotune, force_panel, force_schur
+        o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         self.n = int(n)
         self.batch = batch
         if _multi is not None:

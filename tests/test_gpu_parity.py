@@ -201,3 +201,39 @@ def test_unpruned_ablation_matches_pruned(P):
     allu, allp = u.diag_inverse(), s.diag_inverse()
     assert (np.abs(allu - allp) / allp).max() <= 1e-12
     assert u.info()["diag_work_flops"] > 10 * s.info()["diag_work_flops"]
+
+
+@pytest.mark.parametrize("force_panel", [1, 2])
+@pytest.mark.parametrize("make", [lambda: generate(TINY), lambda: generate(scaled(SCALE, 2000, seed=5)),
+                                  lambda: random_spd(300, 0.02, 11)])
+def test_panel_paths(P, make, force_panel):
+    """The two ways of factoring a front's panel -- the chain of 32-column block
+    step launches, and the persistent per-level kernel in which one CTA runs all
+    block steps of a front -- each against the oracle at the FP64 bar."""
+    pb = make()
+    s, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, force_panel=force_panel)
+    info = s.info()
+    assert (info["launches_factor_fused"] > 0) == (force_panel == 2)
+    if force_panel == 2:
+        assert info["launches_factor"] < 2 + 3 * info["n_levels"] + 64  # about one panel launch per level
+
+
+def test_autotuner_and_tune_cache(P, tmp_path):
+    """autotune = 1 times both candidates of every bucket on the first factorization
+    (tune_source 1) and writes the table; a second context with the same cache
+    reads it (tune_source 2) and builds the same plan; both match the oracle."""
+    pb = generate(scaled(SCALE, 2000, seed=5))
+    cache = tmp_path / "tune.txt"
+    s1, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=1, tune_cache=str(cache))
+    i1 = s1.info()
+    assert i1["tune_source"] == 1 and i1["tune_seconds"] > 0 and i1["tune_panel_buckets"] > 0
+    lines = [l for l in cache.read_text().splitlines() if not l.startswith("#")]
+    assert len(lines) == i1["tune_panel_buckets"] + i1["tune_schur_buckets"]
+    s2, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=1, tune_cache=str(cache))
+    i2 = s2.info()
+    assert i2["tune_source"] == 2
+    for k in ("launches_factor", "launches_factor_fused", "tune_panel_fused"):
+        assert i1[k] == i2[k], k
+    # the rules alone (no timing) are a valid plan too
+    s3, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=-1)
+    assert s3.info()["tune_source"] == 0

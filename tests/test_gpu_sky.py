@@ -45,6 +45,7 @@ def test_sky_mixed_with_tensor_core_fronts(P):
     s.factor(pb.values)
     info = s.info()
     assert info["max_front"] >= 2048
+    assert info["launches_factor_tc"] > 0 and info["tiles_factor_tc"] > 0  # the tcgen05 path ran
     x = s.solve(pb.b)
     v = s.diag_inverse(pb.sky_columns)
     ex = np.abs(x - x_ref).max() / np.abs(x_ref).max()
@@ -52,4 +53,4 @@ def test_sky_mixed_with_tensor_core_fronts(P):
     print(f"sky mixed n={pb.n} sky={pb.n_sky} max_front={info['max_front']} x_err={ex:.2e} var_err={ev:.2e}")
     assert s.info()["solve_relres"] <= 1e-13
     assert ex <= 1e-8
-    assert ev <= 1e-4
+    assert ev <= 3e-5

@@ -208,7 +208,9 @@ def test_struct_layouts_match_header(P, tmp_path):
 
 @pytest.mark.parametrize("field,value", [("rhs_block", -1), ("rhs_block", 513), ("precision", 2),
                                          ("ordering", 2), ("relax", -1), ("refine_max", -1),
-                                         ("nd_leaf", -1), ("diag_ctas_per_sm", -1), ("diag_unpruned", 2)])
+                                         ("nd_leaf", -1), ("diag_ctas_per_sm", -1), ("diag_unpruned", 2),
+                                         ("autotune", -2), ("autotune", 2), ("force_panel", 3),
+                                         ("force_schur", -1)])
 def test_options_are_validated(P, field, value):
     """spi_analyse rejects out-of-range options before any work."""
     pb = random_spd(20, 0.2, 1)

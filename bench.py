@@ -32,8 +32,30 @@ sys.path.insert(0, ROOT)
 
 METRIC = "diag(N^-1) entries/s"
 UNIT = "variances/s"
-FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of a GB300 (profiling recipe's table)
 L2_FLUSH_BYTES = 256 << 20
+# the per-unit rates of a GB300 data sheet, used only when a probe fails (then
+# the line says so)
+NOMINAL_TFLOPS = {"fp64_fma": 1.25, "fp64_dmma": 1.25, "fp32_fma": 80.0, "tf32_tcgen05": 1125.0,
+                  "bf16_tcgen05": 2250.0}
+
+
+def measure_peaks(P) -> dict:
+    """Measured TFLOP/s of every arithmetic unit a kernel here is bound by
+    (spi_measure_peak: independent operations on every SM, best of 3 runs)."""
+    out = {}
+    for unit in ("fp64_fma", "fp64_dmma", "fp32_fma", "tf32_tcgen05", "bf16_tcgen05"):
+        try:
+            out[unit] = P.spi_measure_peak(unit, reps=3)
+        except Exception as e:  # reported in the line; the roofline then says which figure it used
+            out[unit + "_error"] = f"{type(e).__name__}: {e}"
+    return out
+
+
+def peak_of(peaks: dict, unit: str):
+    """(TFLOP/s, source) of one unit: this run's probe, else the data-sheet figure."""
+    if unit in peaks:
+        return peaks[unit], f"measured by this run's {unit} probe (spi_measure_peak)"
+    return NOMINAL_TFLOPS[unit], f"nominal {unit} (the probe failed: {peaks.get(unit + '_error')})"
 
 
 def _measured_hbm_gbs() -> float:
@@ -395,6 +417,109 @@ def bench_uneven(P, args, dev, st, flush, world):
             + s.info()["launches_solve"] + 1, "generate_s": t_gen}
 
 
+def plan_summary(info: dict) -> dict:
+    """The autotuner's choices for a context, from spi_info."""
+    return {"tune_source": ["built-in rules", "timed", "tune cache"][info["tune_source"]],
+            "tune_seconds": info["tune_seconds"], "panel_buckets": info["tune_panel_buckets"],
+            "panel_buckets_persistent": info["tune_panel_fused"], "schur_buckets": info["tune_schur_buckets"],
+            "schur_buckets_tensor_cores": info["tune_schur_tc"],
+            "launches_factor": info["launches_factor"], "launches_factor_per_level_kernel": info["launches_factor_fused"],
+            "factor_dag_tasks": info["factor_dag_tasks"], "factor_dag_levels": info["factor_dag_levels"],
+            "n_levels": info["n_levels"],
+            "factor_ms_timed": {"launches_per_level": info["tune_ms_launches"], "dependency_driven": info["tune_ms_dag"]},
+            "solve_dag_tasks": info["solve_dag_tasks"],
+            "solve_ms_timed": {"launches_per_level": info["tune_solve_ms_launches"],
+                               "dependency_driven": info["tune_solve_ms_dag"]},
+            "factor_work_flops": info["factor_work_flops"], "factor_flops": info["factor_flops"]}
+
+
+def bench_sharded(P, args, dev, st, flush, world, rank, dist):
+    """The batched configurations split over the ranks (one GPU each), the way
+    they shard: independent problems assigned longest-first by the host
+    analysis' work estimate (paper_1305_5683_gb300.shard), and energy bands
+    in contiguous slices; no collective on the data path.  Every rank runs
+    its share as one forest (or one band batch); the step time is the
+    maximum over the ranks, the value all ranks' variances over it.  The
+    problems' results are gathered on the host after the timing and checked
+    against the single-GPU run of the same problems (uneven batch)."""
+    import torch
+    from spigen import BAND, generate_bands, generate_uneven
+    from paper_1305_5683_gb300 import shard
+    ksteps = max(1, min(args.steps, 3))
+
+    def timed(step):
+        for _ in range(3):
+            step(); flush.zero_()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(ksteps):
+            e0.record(st); step(); e1.record(st)
+            torch.cuda.synchronize(dev)
+            tot += e0.elapsed_time(e1)
+            flush.zero_()
+        mine = torch.tensor([tot / ksteps], dtype=torch.float64, device=dev)
+        every = [torch.zeros_like(mine) for _ in range(world)]
+        if dist:
+            dist.all_gather(every, mine)
+        else:
+            every = [mine]
+        return [float(t.item()) for t in every]
+
+    out = {}
+    st2 = torch.cuda.Stream(dev)
+    probs = generate_uneven(args.problems)
+    costs = shard.problem_costs(probs)
+    parts = shard.assign(costs, world)
+    share = [probs[i] for i in parts[rank]]
+    ntot = sum(p.n for p in probs)
+    s = P.Solver.for_problems(share, async_=True)
+    vals = torch.from_numpy(np.concatenate([p.values for p in share])).to(dev)
+    b = torch.from_numpy(np.concatenate([p.b for p in share])).to(dev)
+    x = torch.empty_like(b)
+    var = torch.empty(sum(p.n for p in share), dtype=torch.float64, device=dev)
+
+    def step():
+        overlapped_step(lambda q: s.factor(vals, stream=q), lambda q: s.solve(b, x, stream=q),
+                        lambda q: s.diag_inverse(out=var, stream=q), st, st2)
+
+    per_rank = timed(step)
+    s.sync(st)
+    load = [float(costs[p].sum()) for p in parts]
+    out["uneven"] = {"workload": f"{len(probs)} independent SPI problems (total n {ntot}), assigned longest-first",
+                     "value": ntot / (max(per_rank) / 1e3), "unit": UNIT, "ms_per_step": max(per_rank),
+                     "per_rank_ms": per_rank, "problems_per_rank": [len(p) for p in parts],
+                     "estimated_load_imbalance": max(load) / (sum(load) / world), "steps": ksteps}
+    if dist:
+        offs = np.cumsum([0] + [p.n for p in share])
+        vh = var.cpu().numpy()
+        res = shard.gather([vh[offs[k]:offs[k + 1]] for k in range(len(share))], parts[rank], len(probs))
+        out["uneven"]["gathered_problems"] = sum(r is not None for r in res)
+    del s
+    if world > 1:
+        bb = generate_bands(BAND, args.bands)
+        lo, hi = rank * bb.nbands // world, (rank + 1) * bb.nbands // world
+        nb = hi - lo
+        sb = P.Solver(bb.n, bb.colptr, bb.rowind, batch=max(nb, 1), precision=P.SPI_PREC_MIXED_FP32, async_=True)
+        bv = torch.from_numpy(bb.values[lo * bb.nnz:hi * bb.nnz]).to(dev)
+        bbv = torch.from_numpy(bb.b[lo * bb.n:hi * bb.n]).to(dev)
+        bx = torch.empty_like(bbv)
+        bvar = torch.empty(nb * bb.n, dtype=torch.float64, device=dev)
+
+        def bstep():
+            overlapped_step(lambda q: sb.factor_batch(bv, stream=q), lambda q: sb.solve_batch(bbv, bx, stream=q),
+                            lambda q: sb.diag_inverse_batch(out=bvar, stream=q), st, st2)
+
+        per_rank = timed(bstep)
+        sb.sync(st)
+        out["bands"] = {"workload": f"{bb.nbands} energy bands x n={bb.n}, contiguous slices per rank, mixed",
+                        "value": bb.nbands * bb.n / (max(per_rank) / 1e3), "unit": UNIT,
+                        "ms_per_step": max(per_rank), "per_rank_ms": per_rank, "steps": ksteps}
+    return out
+
+
 def _time_phases(s, vals, b, x, idx, var, nsteps, warmup, st, flush):
     """Mean device ms of factor / solve / diag_inverse / whole overlapped step
     over nsteps timed steps."""
@@ -417,34 +542,52 @@ def _time_phases(s, vals, b, x, idx, var, nsteps, warmup, st, flush):
     return _phases(evs)
 
 
-def bench_sky(P, args, dev, st, flush, world):
+def bench_sky(P, args, dev, st, flush, world, cfg=None, warmup=3, max_steps=3, peaks=None):
     """Diffuse-sky workload: point sources plus a pixel grid, pointings on a
-    target grid (the large configuration's structure at P = 8,000 and 1 deg
-    pixels); variances of the sky columns only.  Its fronts are wide (a dense
-    sky block of ~5,000 columns), which is where the mixed form's tensor-core
-    updates apply.  FP64 form and mixed form, same step."""
+    target grid (the large configuration's structure); variances of the sky
+    columns only.  Its fronts are wide (a dense sky block), which is where the
+    mixed form's tensor-core updates apply.  FP64 form and mixed form, same
+    step; errors of both against the oracle's stored results where they exist
+    (tests/golden), and of the mixed form against the FP64 form."""
     import torch
     from spigen import SKY, generate
+    cfg = cfg or SKY
     t0 = time.perf_counter()
-    pb = generate(SKY)
+    pb = generate(cfg)
     t_gen = time.perf_counter() - t0
     idx = torch.from_numpy(pb.sky_columns).to(dev)
     vals = torch.from_numpy(pb.values).to(dev)
     b = torch.from_numpy(pb.b).to(dev)
-    ksteps = max(1, min(args.steps, 3))
+    ksteps = max(1, min(args.steps, max_steps))
+    golden = None
+    gpath = os.path.join(ROOT, "tests", "golden", "sky_pix05_oracle.npz")
+    if cfg.name == "spi-sky-P2000-pix0.5" and os.path.exists(gpath):
+        golden = np.load(gpath)
     out, res = {}, {}
     for name, prec in (("fp64", P.SPI_PREC_FP64), ("mixed", P.SPI_PREC_MIXED_FP32)):
         s = P.Solver.for_problem(pb, async_=True, precision=prec, relax=args.relax)
         x = torch.empty_like(b)
         var = torch.empty(pb.n_sky, dtype=torch.float64, device=dev)
-        f, so, d, tot = _time_phases(s, vals, b, x, idx, var, ksteps, 3, st, flush)
+        f, so, d, tot = _time_phases(s, vals, b, x, idx, var, ksteps, warmup, st, flush)
         info = s.info()
         res[name] = (x, var)
         out[name] = {"value": world * pb.n_sky / (tot / 1e3), "ms_per_step": tot,
                      "phases_ms": {"factor": f, "solve": so, "diag_inverse": d},
                      "factor_tflops": info["factor_flops"] / (f / 1e3) / 1e12,
                      "diag_tflops": info["diag_flops"] / (d / 1e3) / 1e12,
-                     "refine_steps": info["refine_steps"], "solve_relres": info["solve_relres"]}
+                     "refine_steps": info["refine_steps"], "solve_relres": info["solve_relres"],
+                     "launches_factor": info["launches_factor"], "tune_source": info["tune_source"]}
+        if name == "mixed" and peaks is not None and info["factor_tc_flops"] > 0:
+            pk, src = peak_of(peaks, "tf32_tcgen05")
+            ach = info["factor_tc_flops"] / (f / 1e3) / 1e12
+            out[name]["tensor"] = {"tf32_flops_issued": info["factor_tc_flops"], "tiles": info["tiles_factor_tc"],
+                                   "launches": info["launches_factor_tc"], "achieved_tflops": ach, "peak": pk,
+                                   "frac": ach / pk, "peak_source": src,
+                                   "note": "TF32 MMA work issued (6 MMAs per product) over the whole factor span"}
+        if golden is not None:
+            xo, vo = golden["x"], golden["var_sky"]
+            out[name]["max_rel_err_x_vs_oracle"] = float(np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max())
+            out[name]["max_rel_err_var_vs_oracle"] = float((np.abs(var.cpu().numpy() - vo) / vo).max())
         if name == "fp64":
             out["factor_flops"], out["diag_flops"] = info["factor_flops"], info["diag_flops"]
             out["max_front"], out["n_supernodes"] = info["max_front"], info["n_supernodes"]
@@ -456,7 +599,8 @@ def bench_sky(P, args, dev, st, flush, world):
     out.update({"workload": f"{pb.cfg.name}: P={pb.cfg.n_pointings} pointings on a 7x7 target grid, "
                             f"{pb.cfg.n_sources} sources, {pb.n_sky} sky pixels of {pb.cfg.sky_pix_deg:g} deg "
                             f"(n={pb.n}, nnz_lower={pb.nnz}); variances of the sky columns",
-                "unit": UNIT, "steps": ksteps, "generate_s": t_gen})
+                "unit": UNIT, "steps": ksteps, "warmup": warmup, "generate_s": t_gen,
+                "oracle": "tests/golden/sky_pix05_oracle.npz" if golden is not None else None})
     return out
 
 
@@ -560,10 +704,17 @@ def main():
     if args.normal_only:  # the normal-equation leg alone (profiling); not the benchmark line
         print(json.dumps({"normal_equations": bench_normal(P, args, dev, torch.cuda.current_stream(dev))}), flush=True)
         return
-    if args.sky_only:  # the diffuse-sky leg alone (profiling); not the benchmark line
+    if args.sky_only:  # the diffuse-sky legs alone (profiling); not the benchmark line
+        from spigen import SKY_PIX05
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        print(json.dumps({"sky": bench_sky(P, args, dev, torch.cuda.current_stream(dev), flush, world)}), flush=True)
+        st0 = torch.cuda.current_stream(dev)
+        peaks = measure_peaks(P)
+        print(json.dumps({"peaks_tflops": peaks,
+                          "sky": bench_sky(P, args, dev, st0, flush, world, peaks=peaks),
+                          "sky_pix05": bench_sky(P, args, dev, st0, flush, world, cfg=SKY_PIX05, warmup=1,
+                                                 max_steps=2, peaks=peaks)}), flush=True)
         return
+    peaks = measure_peaks(P)
     pb, t_gen = workload(args.workload)
 
     s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax)
@@ -628,12 +779,49 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = world * pb.n * args.steps / float(e2e_t.item())
     agree = float((torch.abs(hvar.to(dev) - var) / var).max().item())
+    # the batched configurations split over the ranks (every rank takes part)
+    sharded = None
+    if not args.no_batch:
+        try:
+            sharded = bench_sharded(P, args, dev, st, flush, world, rank, dist)
+        except Exception as e:
+            sharded = {"error": f"{type(e).__name__}: {e}"}
     if dist:
         dist.barrier()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+
+    # the factorization's plan: the autotuner's table, and the same factorization on the
+    # block-step chain alone (every panel tiled, no persistent per-level kernel)
+    factor_plan = plan_summary(info)
+    try:
+        sc = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax, force_panel=1,
+                                  autotune=-1, dag=1)
+        factor_plan["block_step_chain_only"] = {
+            "factor_ms": _time_alone(lambda q: sc.factor(vals, stream=q), st, reps=5),
+            "launches_factor": sc.info()["launches_factor"]}
+        factor_plan["factor_ms"] = _time_alone(lambda q: s.factor(vals, stream=q), st, reps=5)
+        del sc
+    except Exception as e:
+        factor_plan["error"] = f"{type(e).__name__}: {e}"
+    # the allocation-free variances (spi_diag_inverse_noalloc) on 4,096 random indices,
+    # beside spi_diag_inverse on the same indices
+    noalloc = None
+    try:
+        s.factor(vals, stream=st)
+        s.sync(st)
+        sel = torch.from_numpy(np.random.default_rng(15).choice(pb.n, 4096, replace=False).astype(np.int32)).to(dev)
+        o1 = torch.empty(4096, dtype=torch.float64, device=dev)
+        o2 = s.diag_inverse(sel, stream=st)
+        s.sync(st)
+        t_na = _time_alone(lambda q: P.spi_diag_inverse_noalloc(s._h, sel, o1, stream=q), st, reps=2)
+        t_di = _time_alone(lambda q: s.diag_inverse(sel, out=o2, stream=q), st, reps=2)
+        noalloc = {"indices": 4096, "ms": t_na, "variances_per_s": 4096 / (t_na / 1e3),
+                   "spi_diag_inverse_ms": t_di, "max_rel_diff": float((torch.abs(o1 - o2) / o2).max().item())}
+    except Exception as e:
+        noalloc = {"error": f"{type(e).__name__}: {e}"}
 
     # the mixed-precision form on the same workload and the same step
     mixed = None
@@ -671,7 +859,18 @@ def main():
                  "max_rel_err_x_vs_fp64": float((torch.abs(xm - x).max() / torch.abs(x).max()).item()),
                  "refine_steps": minfo["refine_steps"], "solve_relres": minfo["solve_relres"],
                  "diag_tflops_fp32": minfo["diag_flops_all"] / (statistics.mean(md) / 1e3) / 1e12,
+                 "plan": plan_summary(minfo),
+                 "tensor_core_launches": minfo["launches_factor_tc"],
                  "dtype": "f32 updates / f64 pivots, refinement and variance sums"}
+        pk32, src32 = peak_of(peaks, "fp32_fma")
+        mixed["diag_roofline"] = {"bound": "alu", "kernel": "k_diag_inv_f32", "achieved": mixed["diag_tflops_fp32"],
+                                  "peak": pk32, "unit": "TFLOP/s", "frac": mixed["diag_tflops_fp32"] / pk32,
+                                  "peak_source": src32}
+        if minfo["factor_tc_flops"] > 0:
+            pk, src = peak_of(peaks, "tf32_tcgen05")
+            ach = minfo["factor_tc_flops"] / (statistics.mean(mf) / 1e3) / 1e12
+            mixed["tensor"] = {"tf32_flops_issued": minfo["factor_tc_flops"], "achieved_tflops": ach, "peak": pk,
+                               "frac": ach / pk, "peak_source": src}
         # variances of 256 unknowns with the factor's first-order error removed
         try:
             sel = torch.from_numpy(np.random.default_rng(13).choice(pb.n, 256, replace=False).astype(np.int32)).to(dev)
@@ -759,12 +958,18 @@ def main():
         except Exception as e:
             normal = {"error": f"{type(e).__name__}: {e}"}
 
-    sky = None
+    sky = sky_pix05 = None
     if not args.no_sky:
+        from spigen import SKY_PIX05
         try:
-            sky = bench_sky(P, args, dev, st, flush, world)
+            sky = bench_sky(P, args, dev, st, flush, world, peaks=peaks)
         except Exception as e:
             sky = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            # the large configuration's diffuse sky at full size (0.5 deg pixels, 19,600 sky columns)
+            sky_pix05 = bench_sky(P, args, dev, st, flush, world, cfg=SKY_PIX05, warmup=1, max_steps=2, peaks=peaks)
+        except Exception as e:
+            sky_pix05 = {"error": f"{type(e).__name__}: {e}"}
 
     batched_bands = batched_uneven = None
     if not args.no_batch:
@@ -780,11 +985,10 @@ def main():
 
     mean_dia = statistics.mean(t_dia) / 1e3
     achieved = info["diag_flops_all"] / mean_dia / 1e12
+    pk64, src64 = peak_of(peaks, "fp64_fma")
     roof = {"bound": "alu", "kernel": "k_diag_inv (pruned blocked forward solves, FP64)",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); FP64 FMA probe measured 1.20",
-            "traffic": traffic_of("diag.cu", "k_diag_inv")}
+            "achieved": achieved, "peak": pk64, "unit": "TFLOP/s", "frac": achieved / pk64,
+            "peak_source": src64, "traffic": traffic_of("diag.cu", "k_diag_inv")}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         _, cpu = cpu_baseline(pb)
@@ -807,13 +1011,18 @@ def main():
         "diag_work_flops": info["diag_work_flops"],
         "nnz_l": info["nnz_l"], "n_supernodes": info["n_supernodes"], "analyse_s": info0["analyse_seconds"],
         "roofline": roof,
+        "peaks_tflops": peaks,
+        "factor_plan": factor_plan,
+        "noalloc": noalloc,
         "mixed": mixed,
         "pruning_ablation": ablation,
         "inverse_block": inv_block,
         "normal_equations": normal,
         "sky": sky,
+        "sky_pix05": sky_pix05,
         "batched_bands": batched_bands,
         "batched_uneven": batched_uneven,
+        "sharded": sharded,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (pb.nnz + pb.n),
                 "d2h_bytes_per_step": 8 * 2 * pb.n, "max_rel_diff_vs_device_run": agree},

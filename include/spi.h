@@ -79,12 +79,14 @@ typedef struct spi_options {
     int nd_leaf;     /* nested-dissection leaf size (vertices); 0 = default */
     int batch;       /* maximum number of same-pattern bands of the *_batch calls (device memory
                         is sized for it at the first factorization); 0 or 1 = single problem */
-    int wait_limit;  /* polls allowed to each bounded pipeline wait of the tensor-core Schur
-                        kernel (mixed form): 0 = default (2^20), > 0 = that many, < 0 = none,
-                        so every such wait gives up at once and spi_factor returns
-                        SPI_ERR_TIMEOUT (a test of that path).  After giving up, the kernel
-                        still waits, with the default limit, for its own MMAs in flight
-                        before it frees its tensor memory */
+    int wait_limit;  /* polls allowed to each bounded device wait of spi_factor: the pipeline
+                        waits of the tensor-core kernels (mixed form; default 2^20) and the
+                        dependency waits of the dependency-driven launch (default 2^25, about
+                        100 ns apart): 0 = those defaults, > 0 = that many, < 0 = none, so every
+                        such wait gives up at once and spi_factor returns SPI_ERR_TIMEOUT (a
+                        test of that path).  After giving up, a tensor-core kernel still waits,
+                        with the default limit, for its own MMAs in flight before it frees its
+                        tensor memory; the dependency-driven launch skips its remaining tasks */
     int diag_ctas_per_sm;  /* 0 = the variance kernels of spi_diag_inverse take every SM
                         slot they fit in; k > 0: at most k of their CTAs per
                         SM (their shared memory is padded to enforce it), so that work on
@@ -111,6 +113,15 @@ typedef struct spi_options {
                         complements and panel updates); 2 = Schur complements on the tensor
                         cores wherever legal (mixed precision, at least 256 trailing rows and
                         32 pivots) */
+    int dag;         /* 0 = as chosen by the autotuner (timed: one dependency-driven launch against
+                        launches level by level, for spi_factor at the first factorization and for
+                        spi_solve at the first solve), else on; 1 = launches level by level; 2 = the
+                        dependency-driven form: spi_factor runs every level below the first one
+                        with a tensor-core launch as one persistent kernel whose CTAs take the tasks
+                        (pivot tiles, panel-solve chunks, update and Schur tiles, whole small
+                        fronts) in a topological order and wait, bounded, for the tasks each
+                        depends on; spi_solve runs both sweeps so (forward steps, backward passes
+                        over 32 columns, backward steps) */
     const char* tune_cache; /* path of a text file keeping the autotuner's choices across
                         processes (one line per device, precision, batch class and bucket), or
                         NULL; read at the first factorization, rewritten after a timing */
@@ -160,6 +171,17 @@ typedef struct spi_stats {
     int64_t tune_panel_fused;    /* ... and how many of them run in the persistent kernel */
     int64_t tune_schur_buckets;  /* Schur buckets that may use the tensor cores ... */
     int64_t tune_schur_tc;       /* ... and how many of them do */
+    double factor_tc_flops;      /* TF32 flops the tensor cores execute per spi_factor: 2 x 128 x 128 x K
+                                    per tile and MMA, 6 MMAs per product (split precision) */
+    double factor_work_flops;    /* flops the SIMT kernels of spi_factor execute: whole 32 x 32 tiles
+                                    and explicit zeros included (compare factor_flops) */
+    int64_t factor_dag_tasks;    /* tasks of the dependency-driven launch (0: none) ... */
+    int64_t factor_dag_levels;   /* ... covering the tree levels [0, factor_dag_levels) */
+    double tune_ms_launches;     /* the timed factorization with launches level by level ... */
+    double tune_ms_dag;          /* ... and with the dependency-driven launch (-1: not timed) */
+    int64_t solve_dag_tasks;     /* tasks of the solve's dependency-driven launch, when it is in use */
+    double tune_solve_ms_launches; /* the first solve timed with launches level by level ... */
+    double tune_solve_ms_dag;      /* ... and with the dependency-driven launch (-1: not timed) */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;

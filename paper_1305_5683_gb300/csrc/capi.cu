@@ -45,6 +45,8 @@ struct spi_ctx {
     // the factorization's launch items on the device (per plan: the autotuner's plans have their own)
     struct DevFactorPlan {
         int32_t* items[13] = {};  // by launch kind
+        DagTask* dag = nullptr;   // the dependency-driven kernel's tasks
+        int* counters = nullptr;  // its counters: opt.batch x 2 ns, then the work counter
         std::vector<void*> allocs;
     } dfp;
     bool factor_plan_ready = false;  // c->FP is final (tuned or by rule) and uploaded
@@ -52,6 +54,15 @@ struct spi_ctx {
     int tune_source = 0;             // 0 built-in rules, 1 timed here, 2 read from the tune cache
     double tune_seconds = 0;
     int64_t tune_panel_buckets = 0, tune_panel_fused = 0, tune_schur_buckets = 0, tune_schur_tc = 0;
+    double tune_dag_ms[2] = {-1.0, -1.0};  // timed factorization: launches per level / dependency-driven
+    // the solve's dependency-driven form: tasks, counters, grid; whether it is in use
+    // (-1: not decided yet), and its timing against the per-level launches
+    DagTask* d_solve_dag = nullptr;
+    int* d_solve_cnt = nullptr;
+    int solve_dag_grid_size = 1;
+    int solve_dag = -1;
+    double tune_solve_ms[2] = {-1.0, -1.0};
+    std::map<int, cudaGraphExec_t> g_solve_dag;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
@@ -176,6 +187,11 @@ int ensure_device(spi_ctx* c) {
     CK(dev_upload(c, &c->d_diag_src, S.diag_src));
     CK(dev_upload(c, &c->d_fwd_items, c->SP.fwd_items));
     CK(dev_upload(c, &c->d_bwd_items, c->SP.bwd_items));
+    CK(dev_upload(c, &c->d_solve_dag, c->SP.dag));
+    CK(dev_alloc(c, &c->d_solve_cnt, nb * 3 * (size_t)S.ns + 1));
+    CK(solve_dag_grid(&c->solve_dag_grid_size));
+    if (c->opt.dag == 1) c->solve_dag = 0;
+    if (c->opt.dag == 2) c->solve_dag = 1;
     CK(dev_alloc(c, &c->d_L, (size_t)S.lptr[S.ns] * nb));
     if (!mixed_of(c)) CK(dev_alloc(c, &c->d_F22, (size_t)S.f22_total * nb));
     CK(dev_alloc(c, &c->d_D, (size_t)S.n * nb));
@@ -314,6 +330,10 @@ int upload_factor_plan(spi_ctx* c, const FactorPlan& F, spi_ctx::DevFactorPlan& 
     CK(dev_upload(c, &d.items[8], F.dfront_items, tr));
     CK(dev_upload(c, &d.items[9], F.panel_tc_items, tr));
     CK(dev_upload(c, &d.items[12], F.fused_items, tr));
+    if (!F.dag.empty()) {
+        CK(dev_upload(c, &d.dag, F.dag, tr));
+        CK(dev_alloc(c, &d.counters, (size_t)c->opt.batch * 2 * (size_t)c->S.ns + 1, tr));
+    }
     return SPI_OK;
 }
 
@@ -342,6 +362,13 @@ void factor_launches(spi_ctx* c, int nb, const FactorPlan& F, const spi_ctx::Dev
     for (const Launch& l : F.launches) {
         if (l.kind < 0) {
             if (evs) cudaEventRecord((*evs)[(size_t)l.step], s2);
+            continue;
+        }
+        if (l.kind == 13) {
+            const int cstride = 2 * c->S.ns;
+            cudaMemsetAsync(dp.counters, 0, ((size_t)nb * cstride + 1) * sizeof(int), s2);
+            launch_factor_dag(c->dsym, dp.dag, l.count, dp.counters, cstride, Lw, Fw, c->d_D, DS, c->d_adiag,
+                              c->d_status, mixed, nb, c->bs, c->opt.wait_limit, s2);
             continue;
         }
         launch_factor_step(c->dsym, l, dp.items[l.kind], Lw, Fw, c->d_D, DS, c->d_adiag, c->d_status, mixed, nb,
@@ -410,7 +437,8 @@ void read_tune_cache(const char* path, const std::string& key, std::vector<TuneL
             continue;
         }
         const std::string k = std::string(dev) + " " + prec + " " + cls;
-        if (k == key && (kind[0] == 'P' || kind[0] == 'S')) out.push_back(TuneLine{kind[0], bucket, choice, a, b});
+        if (k == key && (kind[0] == 'P' || kind[0] == 'S' || kind[0] == 'D'))
+            out.push_back(TuneLine{kind[0], bucket, choice, a, b});
         else if (other) other->push_back(buf);
     }
     std::fclose(fp);
@@ -491,6 +519,38 @@ int time_plan(spi_ctx* c, int nb, const double* vals, const FactorChoice& ch, cu
     return rc;
 }
 
+// Milliseconds of one factorization with plan F (its launches recorded as a CUDA
+// graph, the second of two replays), or a negative value if it could not be timed.
+double time_whole_plan(spi_ctx* c, int nb, const double* vals, const FactorPlan& F, cudaStream_t st) {
+    spi_ctx::DevFactorPlan dp;
+    if (upload_factor_plan(c, F, dp)) { free_factor_plan(dp); return -1.0; }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double ms = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+              cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        factor_launches(c, nb, F, dp, c->cap, nullptr);
+        ok = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+    }
+    for (int rep = 0; ok && rep < 2; ++rep) {
+        k_reset_status<<<1, 1, 0, st>>>(c->d_status);
+        ok = factor_assemble(c, nb, vals, st) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess &&
+             cudaGraphLaunch(exec, st) == cudaSuccess && cudaEventRecord(e1, st) == cudaSuccess &&
+             cudaEventSynchronize(e1) == cudaSuccess;
+        float t = 0.f;
+        if (ok && rep == 1 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t;
+    }
+    if (!ok) cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    free_factor_plan(dp);
+    return ms;
+}
+
 // Make c->FP final and upload it: from the tune cache, by timing, or by the
 // built-in rules (see spi_options.autotune).
 int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st) {
@@ -538,6 +598,8 @@ int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st)
                 ch.schur[bk] = (uint8_t)(t1 < t0a);
                 lines.push_back(TuneLine{'S', bk, t1 < t0a ? 1 : 0, t0a, t1});
             }
+            for (const TuneLine& t : cached)
+                if (t.kind == 'D') lines.push_back(t);
             write_tune_cache(c->opt.tune_cache, key, lines);
             c->tune_source = 1;
             c->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -553,6 +615,43 @@ int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st)
     for (int32_t b : sb) {
         auto it = ch.schur.find(b);
         c->tune_schur_tc += it != ch.schur.end() ? it->second : 0;
+    }
+    // one dependency-driven launch for the levels below the first tensor-core level, or
+    // launches level by level: as forced, timed with the table above, cached, or on by rule
+    c->tune_dag_ms[0] = c->tune_dag_ms[1] = -1.0;
+    if (c->opt.dag == 1 || c->opt.dag == 2) {
+        ch.dag = c->opt.dag == 2;
+    } else {
+        const std::string key = tune_key(c, nb);
+        std::vector<TuneLine> cached;
+        read_tune_cache(c->opt.tune_cache, key, cached, nullptr);
+        int found = -1;
+        for (const TuneLine& t : cached)
+            if (t.kind == 'D') found = t.choice;
+        const bool timing = c->opt.autotune > 0 || (c->opt.autotune == 0 && S.factor_flops >= 2e8);
+        if (found >= 0) {
+            ch.dag = found;
+        } else if (timing) {
+            auto t0 = std::chrono::steady_clock::now();
+            FactorPlan F0, F1;
+            FactorChoice c0 = ch, c1 = ch;
+            c0.dag = 0;
+            c1.dag = 1;
+            build_factor_plan(S, F0, mixed_of(c), c0, false);
+            build_factor_plan(S, F1, mixed_of(c), c1, false);
+            c->tune_dag_ms[0] = time_whole_plan(c, nb, vals, F0, st);
+            c->tune_dag_ms[1] = F1.dag.empty() ? -1.0 : time_whole_plan(c, nb, vals, F1, st);
+            ch.dag = c->tune_dag_ms[1] >= 0.0 && c->tune_dag_ms[0] >= 0.0 && c->tune_dag_ms[1] < c->tune_dag_ms[0];
+            cached.push_back(TuneLine{'D', 0, ch.dag, c->tune_dag_ms[0], c->tune_dag_ms[1]});
+            std::vector<TuneLine> keep;
+            for (const TuneLine& t : cached)
+                if (t.kind != 'D' || &t == &cached.back()) keep.push_back(t);
+            write_tune_cache(c->opt.tune_cache, key, keep);
+            c->tune_source = 1;
+            c->tune_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        } else {
+            ch.dag = 1;
+        }
     }
     c->choice = ch;
     build_factor_plan(S, c->FP, mixed_of(c), ch, false);
@@ -603,6 +702,17 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
 cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStream_t st) {
     const Symbolic& S = c->S;
     launch_permute_in(S.n, c->dsym.perm, b, c->d_w, nb, st);
+    if (c->solve_dag == 1) {
+        cudaError_t e = run_graph(c, c->g_solve_dag, nb, st, [&](cudaStream_t s2) {
+            const int cstride = 3 * S.ns;
+            cudaMemsetAsync(c->d_solve_cnt, 0, ((size_t)nb * cstride + 1) * sizeof(int), s2);
+            launch_solve_dag(c->dsym, c->d_solve_dag, (int)c->SP.dag.size(), c->d_solve_cnt, cstride, c->d_L, c->d_D,
+                             c->d_w, c->d_z, c->d_xp, c->d_status, nb, c->bs, c->opt.wait_limit,
+                             c->solve_dag_grid_size, s2);
+        });
+        launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, nb, st);
+        return e;
+    }
     cudaError_t e = run_graph(c, c->g_solve, nb, st, [&](cudaStream_t s2) {
         for (const Launch& l : c->SP.fwd_launches)
             launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
@@ -615,6 +725,42 @@ cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStrea
     return e;
 }
 
+// The solve's form (dependency-driven launch or launches level by level), decided
+// at the first solve when spi_options.dag = 0: timed on the caller's right-hand
+// side when spi_options.autotune allows (the faster of two runs each), else the
+// dependency-driven launch.
+int choose_solve_form(spi_ctx* c, int nb, const double* bd, cudaStream_t st) {
+    if (c->solve_dag >= 0) return SPI_OK;
+    const bool timing = c->opt.autotune > 0 || (c->opt.autotune == 0 && c->S.factor_flops >= 2e8);
+    if (!timing || c->SP.dag.empty()) {
+        c->solve_dag = c->SP.dag.empty() ? 0 : 1;
+        return SPI_OK;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = SPI_OK;
+    for (int form = 0; form < 2 && rc == SPI_OK; ++form) {
+        c->solve_dag = form;
+        double best = -1.0;
+        for (int rep = 0; rep < 3 && rc == SPI_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            if (solve_core(c, nb, bd, c->d_x ? c->d_x : c->d_out, st) != cudaSuccess) rc = SPI_ERR_CUDA;
+            cudaEventRecord(e1, st);
+            float ms = 0.f;
+            if (rc == SPI_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                rep > 0 && (best < 0 || ms < best))
+                best = ms;
+        }
+        c->tune_solve_ms[form] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    c->solve_dag = c->tune_solve_ms[1] >= 0 && c->tune_solve_ms[1] < c->tune_solve_ms[0] ? 1 : 0;
+    return finish(c, st);
+}
+
 int solve_impl(spi_ctx* c, int nb, const double* b, double* x, int on_device, cudaStream_t st) {
     if (!c || nb < 1 || (!b && c->S.n) || (!x && c->S.n)) return SPI_ERR_ARG;
     if (!c->factored) return SPI_ERR_STATE;
@@ -625,6 +771,10 @@ int solve_impl(spi_ctx* c, int nb, const double* b, double* x, int on_device, cu
     if (!on_device && n) {
         CK(cudaMemcpyAsync(c->d_vec, b, bytes, cudaMemcpyHostToDevice, st));
         bd = c->d_vec;
+    }
+    {
+        const int rc = choose_solve_form(c, nb, bd, st);
+        if (rc) return rc;
     }
     double* xd = on_device ? x : c->d_vec;
     if (!mixed_of(c)) {
@@ -990,7 +1140,7 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (o.rhs_block < 0 || o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 ||
         o.ordering > 1 || o.relax < 0 || o.refine_max < 0 || o.nd_leaf < 0 || o.diag_ctas_per_sm < 0 ||
         o.diag_unpruned < 0 || o.diag_unpruned > 1 || o.autotune < -1 || o.autotune > 1 || o.force_panel < 0 ||
-        o.force_panel > 2 || o.force_schur < 0 || o.force_schur > 2)
+        o.force_panel > 2 || o.force_schur < 0 || o.force_schur > 2 || o.dag < 0 || o.dag > 2)
         return SPI_ERR_ARG;
     if (o.precision == SPI_PREC_MIXED_FP32 && o.rhs_block > 0) o.rhs_block = (o.rhs_block + 7) & ~7;
     spi_ctx* c = new (std::nothrow) spi_ctx();
@@ -1012,8 +1162,10 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
         FactorChoice ch;  // the built-in rules until the first factorization makes the plan final
         ch.force_panel = o.force_panel;
         ch.force_schur = o.force_schur;
+        ch.dag = o.dag != 1;
         build_factor_plan(c->S, c->FP, o.precision == SPI_PREC_MIXED_FP32, ch, false);
         build_solve_plan(c->S, c->SP, std::max(1, o.batch));
+        build_solve_dag(c->S, c->SP);
         if (n > 0) {  // the residual of the mixed form and the normal-equation assembly use it
             c->in_colptr.assign(colptr, colptr + n + 1);
             c->in_rowind.assign(rowind, rowind + colptr[n]);
@@ -1924,6 +2076,16 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->launches_factor_fused = c->FP.n_fused_launches;
     o->launches_factor_tc = c->FP.n_tc_launches;
     o->tiles_factor_tc = c->FP.n_tc_tiles;
+    o->factor_tc_flops = c->FP.tc_flops;
+    o->factor_work_flops = c->FP.work_flops;
+    o->factor_dag_tasks = (int64_t)c->FP.dag.size();
+    o->factor_dag_levels = c->FP.dag_levels;
+    o->tune_ms_launches = c->tune_dag_ms[0];
+    o->tune_ms_dag = c->tune_dag_ms[1];
+    o->solve_dag_tasks = c->solve_dag == 1 ? (int64_t)c->SP.dag.size() : 0;
+    o->tune_solve_ms_launches = c->tune_solve_ms[0];
+    o->tune_solve_ms_dag = c->tune_solve_ms[1];
+    if (c->solve_dag == 1) o->launches_solve = S.n ? 4 : 0;
     o->tune_source = c->tune_source;
     o->tune_seconds = c->tune_seconds;
     o->tune_panel_buckets = c->tune_panel_buckets;
@@ -2006,6 +2168,7 @@ void spi_destroy(spi_ctx* c) {
     if (c->d_zg) cudaFree(c->d_zg);
     for (auto& kv : c->g_factor) cudaGraphExecDestroy(kv.second);
     for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : c->g_solve_dag) cudaGraphExecDestroy(kv.second);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_status) cudaFreeHost(c->h_status);

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <type_traits>
 
 #include "spi_internal.cuh"
@@ -42,6 +43,7 @@ constexpr int32_t kOuter = 128;
 constexpr int32_t kInner = kOuter / kT;
 // tensor-core output tile (rows x columns) and K chunk; one thread per tile row
 constexpr int kTcM = 128, kTcN = 128, kTcK = 32;
+constexpr int kThreads = 128;  // threads of the SIMT front kernels
 static_assert(kTcM == 128 && kTcN == 128, "the tensor-core kernels give thread t row t of both operand tiles");
 
 int32_t ilog2_floor(int64_t v) {
@@ -190,16 +192,92 @@ bool FactorChoice::schur_tc(int64_t m, int64_t k) const {
     return it != schur.end() ? it->second != 0 : rule_schur_tc(m, k);
 }
 
+namespace {
+
+// The tasks of the dependency-driven kernel for levels [0, nlev): per level,
+// phase by phase across the level's fronts (a front's Schur tiles at the phase
+// after its last), so that the order is topological (see k_factor_dag).
+void build_dag(const Symbolic& S, FactorPlan& F, int32_t nlev, const std::vector<uint8_t>& fused) {
+    const int32_t ns = S.ns;
+    std::vector<int32_t> child_tiles(ns, 0);  // Schur tiles the children of each front add in
+    for (int32_t l = 0; l < nlev; ++l) {
+        std::vector<std::vector<std::vector<DagTask>>> ph;  // [front of the level][phase] tasks
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p];
+            const int32_t k = S.k_of(s), m = S.m_of(s);
+            std::vector<std::vector<DagTask>> t;
+            auto task = [&](int32_t type, int32_t a, int32_t b) { return DagTask{type, s, a, b, 0, 0, s, 0}; };
+            if (S.sdiag[s]) t.push_back({task(kDagDiagFront, 0, 0)});
+            else if (fused[s]) t.push_back({task(kDagFused, 0, 0)});
+            else {
+                t.push_back({task(kDagPivot, 0, 0)});
+                for (int32_t b = 0; b * kT < k; ++b) {
+                    const int32_t w = std::min(kT, k - b * kT), r0 = b * kT + w;
+                    std::vector<DagTask> tr, up;
+                    for (int32_t c = 0; r0 + (int64_t)c * kThreads < m; ++c) tr.push_back(task(kDagTrsm, b, c));
+                    for (int32_t tj = 0; r0 + tj * kT < k; ++tj)
+                        for (int32_t ti = 0; r0 + tj * kT + ti * kT < m; ++ti) up.push_back(task(kDagUpdate, b, (ti << 16) | tj));
+                    if (!tr.empty()) t.push_back(tr);
+                    if (!up.empty()) t.push_back(up);
+                }
+            }
+            // waits: the first phase on the children's Schur tiles, later phases on the
+            // front's own earlier tasks
+            int32_t done = 0;
+            for (size_t q = 0; q < t.size(); ++q) {
+                for (DagTask& x : t[q]) {
+                    x.wait_idx = q == 0 ? ns + s : s;
+                    x.wait_val = q == 0 ? child_tiles[s] : done;
+                }
+                done += (int32_t)t[q].size();
+            }
+            std::vector<DagTask> sc;
+            const int32_t par = S.sparent[s];
+            if (par != -1 && m > k) {
+                const int32_t nt = (m - k + kT - 1) / kT;
+                for (int32_t ti = 0; ti < nt; ++ti)
+                    for (int32_t tj = 0; tj <= ti; ++tj) sc.push_back(DagTask{kDagSchur, s, ti, tj, s, done, ns + par, 0});
+                child_tiles[par] += (int32_t)sc.size();
+            }
+            if (!sc.empty()) t.push_back(sc);
+            ph.push_back(std::move(t));
+        }
+        size_t maxp = 0;
+        for (auto& t : ph) maxp = std::max(maxp, t.size());
+        for (size_t q = 0; q < maxp; ++q)
+            for (auto& t : ph)
+                if (q < t.size()) F.dag.insert(F.dag.end(), t[q].begin(), t[q].end());
+    }
+}
+
+}  // namespace
+
 void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores_allowed, const FactorChoice& ch,
                        bool markers) {
     F = FactorPlan();
     const bool tensor_cores = tensor_cores_allowed && ch.force_schur != 1;  // 1: no tensor-core launch at all
+    if (ch.dag && !markers) {
+        // the levels before the first one with a tensor-core launch run as one dependency-driven launch
+        int32_t nlev = S.nlevels;
+        std::vector<uint8_t> fused(S.ns, 0);
+        for (int32_t l = 0; l < S.nlevels && nlev == S.nlevels; ++l)
+            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+                const int32_t s = S.level_list[p];
+                const int32_t k = S.k_of(s), m = S.m_of(s);
+                const bool tc_schur = S.sparent[s] != -1 && m > k && schur_tc_legal(tensor_cores, m, k) && ch.schur_tc(m, k);
+                if (tc_schur || (!S.sdiag[s] && wide_front(tensor_cores, m, k))) { nlev = l; break; }
+                fused[s] = !S.sdiag[s] && fused_legal(m, k) && ch.force_panel != 1 && ch.fused(m, k);
+            }
+        build_dag(S, F, nlev, fused);
+        F.dag_levels = nlev;
+        if (!F.dag.empty()) F.launches.push_back(Launch{13, 0, 0, (int32_t)F.dag.size()});
+    }
     F.level_launch_ptr.push_back(0);
     auto marker = [&](int kind, int32_t bucket) {
         F.launches.push_back(Launch{-1, (int)F.groups.size(), 0, 0});
         F.groups.push_back(FactorPlan::Group{kind, bucket});
     };
-    for (int32_t l = 0; l < S.nlevels; ++l) {
+    for (int32_t l = F.dag_levels; l < S.nlevels; ++l) {
         // panels: fronts with a diagonal pivot block always run in the persistent
         // kernel; wide fronts of the mixed form always run the tiled chain (their
         // tensor-core trailing updates); the rest as chosen per bucket
@@ -252,6 +330,46 @@ void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores_allow
         if (la.kind == 7 || la.kind == 9) { F.n_tc_launches++; F.n_tc_tiles += la.count; }
         if (la.kind >= 0) F.n_kernel_launches++;
     }
+    // flops the SIMT kernels execute (full 32 x 32 tiles, explicit zeros included;
+    // a multiply-add counts 2), against the algorithmic count from exact column counts
+    auto w_of = [&](int32_t s, int32_t b) { return (double)std::min(kT, S.k_of(s) - b * kT); };
+    for (const Launch& la : F.launches) {
+        if (la.kind == 0)
+            for (int32_t q = 0; q < la.count; ++q) F.work_flops += 2.0 * std::pow(w_of(F.diag_items[la.off + q], la.step), 3) / 3.0;
+        if (la.kind == 1)
+            for (int32_t q = 0; q < la.count; ++q) {
+                const double w = w_of(F.trsm_items[2 * (la.off + q)], la.step);
+                F.work_flops += kT * w * w;
+            }
+        if (la.kind == 3)
+            for (int32_t q = 0; q < la.count; ++q) {
+                const double w = w_of(F.update_items[3 * (la.off + q)], la.step);
+                F.work_flops += 2.0 * kT * kT * w + (F.update_items[3 * (la.off + q) + 1] == 0 &&
+                                                     F.update_items[3 * (la.off + q) + 2] == 0 ? 2.0 * kT * kT * kT / 3.0 : 0.0);
+            }
+        if (la.kind == 2)
+            for (int32_t q = 0; q < la.count; ++q) F.work_flops += 2.0 * kT * kT * S.k_of(F.schur_items[3 * (la.off + q)]);
+        if (la.kind == 13)
+            for (const DagTask& t : F.dag) {
+                const double k = S.k_of(t.s), m = S.m_of(t.s);
+                if (t.type == kDagFused) F.work_flops += m * k * k - 2.0 * k * k * k / 3.0;
+                if (t.type == kDagPivot) F.work_flops += 2.0 * std::pow(std::min<double>(kT, k), 3) / 3.0;
+                if (t.type == kDagTrsm) F.work_flops += kThreads * std::pow(std::min<double>(kT, k - t.a * kT), 2);
+                if (t.type == kDagUpdate) F.work_flops += 2.0 * kT * kT * std::min<double>(kT, k - t.a * kT);
+                if (t.type == kDagSchur) F.work_flops += 2.0 * kT * kT * k;
+            }
+        if (la.kind == 12)
+            for (int32_t q = 0; q < la.count; ++q) {
+                const int32_t code = F.fused_items[la.off + q];
+                if (code < 0) continue;
+                const double k = S.k_of(code), m = S.m_of(code);
+                F.work_flops += m * k * k - 2.0 * k * k * k / 3.0;  // the panel's LDL^T part of the front
+            }
+    }
+    // tensor-core work: per tile, K rounded up to the 32-wide chunk, 6 MMAs per product
+    for (size_t t = 0; t < F.schur_tc_items.size(); t += 3)
+        F.tc_flops += 2.0 * kTcM * kTcN * (double)((S.k_of(F.schur_tc_items[t]) + kTcK - 1) / kTcK * kTcK) * 6.0;
+    F.tc_flops += 2.0 * kTcM * kTcN * (double)kOuter * 6.0 * (double)(F.panel_tc_items.size() / 3);
 }
 
 namespace {
@@ -269,20 +387,27 @@ __global__ void k_assemble(const int64_t* __restrict__ amap, const double* __res
     for (int64_t j = i; j < n; j += stride) adiag[j] = vals[diag_src[j]];
 }
 
-constexpr int kThreads = 128;
+// A load of data that another CTA of the same launch may have written (the
+// dependency-driven kernel): through L2 only (ld.global.cg), never from an L1
+// line this SM cached before that CTA's store.  Plain loads otherwise.
+template <bool kCg, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+    if constexpr (kCg) return __ldcg(p);
+    else return *p;
+}
 
 // Unblocked LDL^T, in FP64, of the w x w pivot tile whose first pivot is
 // column c0 of supernode s (panel P of storage type S, leading dimension m),
 // by the CTA's 128 threads; writes L (unit lower, d on the diagonal) back into
 // P, d into D (FP64) and into DS (the storage type's copy used for scaling).
-template <typename S>
-__device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, S* __restrict__ P, int64_t m, int c0, int w,
-                                  int f, double* __restrict__ D, S* __restrict__ DS,
-                                  const double* __restrict__ adiag, DevStatus* status, int band_base) {
+template <typename S, bool kCg = false>
+__device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, S* P, int64_t m, int c0, int w,
+                                  int f, double* D, S* DS, const double* __restrict__ adiag, DevStatus* status,
+                                  int band_base) {
     const int tid = threadIdx.x;
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        A[i][j] = (i < w && j <= i) ? (double)P[(c0 + i) + (int64_t)(c0 + j) * m] : 0.0;
+        A[i][j] = (i < w && j <= i) ? (double)ldx<kCg>(P + (c0 + i) + (int64_t)(c0 + j) * m) : 0.0;
     }
     // FP64 is a narrow pipe on this GPU: one thread forms each pivot's
     // reciprocal, and the update visits only the trailing square.
@@ -346,10 +471,9 @@ __global__ void __launch_bounds__(kThreads) k_diag_tile(DevSym d, const int32_t*
 // Front with a diagonal pivot block (independent leaf columns grouped into
 // one front, no children): d_c is the input diagonal entry (kept in FP64 in
 // adiag) and L21(:, c) = F21(:, c) / d_c.
-template <typename S>
-__device__ void diag_front_body(const DevSym& d, int s, S* __restrict__ L, double* __restrict__ D,
-                                S* __restrict__ DS, const double* __restrict__ adiag, DevStatus* status,
-                                int band_base) {
+template <typename S, bool kCg = false>
+__device__ void diag_front_body(const DevSym& d, int s, S* L, double* D, S* DS, const double* __restrict__ adiag,
+                                DevStatus* status, int band_base) {
     const int tid = threadIdx.x;
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
@@ -367,7 +491,7 @@ __device__ void diag_front_body(const DevSym& d, int s, S* __restrict__ L, doubl
     // one reciprocal per column (uniform across the CTA), then scale its rows
     for (int c = 0; c < k; ++c) {
         const S rc = (S)(1.0 / adiag[f + c]);
-        for (int64_t r = k + tid; r < m; r += kThreads) P[r + (int64_t)c * m] *= rc;
+        for (int64_t r = k + tid; r < m; r += kThreads) P[r + (int64_t)c * m] = ldx<kCg>(P + r + (int64_t)c * m) * rc;
     }
 }
 
@@ -402,23 +526,99 @@ union FrontPanelSmem {
     } upd;
 };
 
+// A whole front's panel by one CTA: per 32-column block step, the FP64 pivot
+// tile, the panel solve of every row below it (one thread per row), then the
+// rank-32 update of the remaining panel columns in 32 x 32 tiles.  The Schur
+// complement is left to the Schur tiles.
+template <typename C, bool kCg>
+__device__ void front_panel_body(const DevSym& d, int s, C* Lb, double* Db, C* DSb, const double* ab,
+                                 DevStatus* status, int base, FrontPanelSmem<C>& sm) {
+    const int tid = threadIdx.x;
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    C* P = Lb + d.lptr[s];
+    for (int c0 = 0; c0 < k; c0 += kT) {
+        const int w = min(kT, k - c0);
+        __syncthreads();
+        factor_pivot_tile<C, kCg>(sm.piv.A, sm.piv.dv, P, m, c0, w, f, Db, DSb, ab, status, base);
+        __syncthreads();
+        // L21 = X L11^-T D^-1 for the rows below the pivot tile
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            const int i = e % kT, j = e / kT;
+            sm.trsm.Bd[i][j] = (i < w && j < i) ? ldx<kCg>(P + (c0 + i) + (int64_t)(c0 + j) * m) : C(0);
+        }
+        if (tid < kT) sm.trsm.rd[tid] = tid < w ? (C)(1.0 / ldx<kCg>(Db + f + c0 + tid)) : C(0);
+        __syncthreads();
+        C* xr = sm.trsm.X[tid];
+        for (int64_t r = c0 + w + tid; r < m; r += kThreads) {
+            for (int c = 0; c < w; ++c) xr[c] = ldx<kCg>(P + r + (int64_t)(c0 + c) * m);
+            for (int c = 1; c < w; ++c) {
+                C y = xr[c];
+                for (int cp = 0; cp < c; ++cp) y -= xr[cp] * sm.trsm.Bd[c][cp];
+                xr[c] = y;
+            }
+            for (int c = 0; c < w; ++c) P[r + (int64_t)(c0 + c) * m] = xr[c] * sm.trsm.rd[c];
+        }
+        // rank-w update of panel columns [c0 + w, k), rows i >= j, in 32 x 32 tiles:
+        // P[i][j] -= sum_c L[i][c] d_c L[j][c]; thread (ii, j0) owns row ii, columns j0 + 4 q
+        const int ii = tid % kT, j0 = tid / kT;
+        for (int cj = c0 + w; cj < k; cj += kT) {
+            const int nj = min(kT, k - cj);
+            __syncthreads();  // the panel solve (or the previous column tile) is done
+            for (int e = tid; e < kT * kT; e += kThreads) {
+                const int i = e % kT, c = e / kT;
+                sm.upd.Lj[i][c] = (i < nj && c < w)
+                                      ? ldx<kCg>(P + (cj + i) + (int64_t)(c0 + c) * m) * ldx<kCg>(DSb + f + c0 + c)
+                                      : C(0);
+            }
+            for (int64_t ri = cj; ri < m; ri += kT) {
+                const int ni = (int)(m - ri < kT ? m - ri : kT);
+                __syncthreads();
+                for (int e = tid; e < kT * kT; e += kThreads) {
+                    const int i = e % kT, c = e / kT;
+                    sm.upd.Li[i][c] = (i < ni && c < w) ? ldx<kCg>(P + (ri + i) + (int64_t)(c0 + c) * m) : C(0);
+                }
+                __syncthreads();
+                if (ii < ni) {
+                    C acc[kT / 4];
+#pragma unroll
+                    for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
+#pragma unroll 4
+                    for (int c = 0; c < w; ++c) {
+                        const C ai = sm.upd.Li[ii][c];
+#pragma unroll
+                        for (int q = 0; q < kT / 4; ++q) acc[q] += ai * sm.upd.Lj[j0 + 4 * q][c];
+                    }
+                    C old[kT / 4];
+#pragma unroll
+                    for (int q = 0; q < kT / 4; ++q) {
+                        const int jj = j0 + 4 * q;
+                        old[q] = (jj < nj && ri + ii >= cj + jj) ? ldx<kCg>(P + (ri + ii) + (int64_t)(cj + jj) * m)
+                                                                   : C(0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kT / 4; ++q) {
+                        const int jj = j0 + 4 * q;
+                        if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] = old[q] - acc[q];
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Persistent per-level panel kernel (kind 12): the CTAs walk the level's list
 // of fronts (heaviest first, in steps of the grid; item t is front
 // items[t / nb] of band t % nb) and each processes a whole front's panel on
 // its own, so a small front costs one launch per level instead of three or
-// more per 32-column block step.  Per block step: the FP64 pivot tile, the
-// panel solve of every row below it (one thread per row), then the rank-32
-// update of the remaining panel columns in 32 x 32 tiles.  The Schur
-// complement is left to the level's Schur launch.  A front with a diagonal
-// pivot block (~s in the list) is scaled column by column.  The CTAs never
-// wait on one another.
+// more per 32-column block step.  A front with a diagonal pivot block (~s in
+// the list) is scaled column by column.  The CTAs never wait on one another.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_front_panel(DevSym d, const int32_t* __restrict__ items, int nitems,
                                                           int nb, C* __restrict__ L, double* __restrict__ D,
                                                           C* __restrict__ DS, const double* __restrict__ adiag,
                                                           DevStatus* status, Strides bs) {
     __shared__ FrontPanelSmem<C> sm;
-    const int tid = threadIdx.x;
     const int64_t total = (int64_t)nitems * nb;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
         const int band = (int)(t % nb);
@@ -429,79 +629,8 @@ __global__ void __launch_bounds__(kThreads) k_front_panel(DevSym d, const int32_
         const double* ab = adiag + band * bs.n;
         const int base = (int)(band * bs.n);
         __syncthreads();  // the previous front's last phase is done with the shared memory
-        if (code < 0) {
-            diag_front_body(d, ~code, Lb, Db, DSb, ab, status, base);
-            continue;
-        }
-        const int s = code;
-        const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
-        const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-        C* P = Lb + d.lptr[s];
-        for (int c0 = 0; c0 < k; c0 += kT) {
-            const int w = min(kT, k - c0);
-            __syncthreads();
-            factor_pivot_tile(sm.piv.A, sm.piv.dv, P, m, c0, w, f, Db, DSb, ab, status, base);
-            __syncthreads();
-            // L21 = X L11^-T D^-1 for the rows below the pivot tile
-            for (int e = tid; e < kT * kT; e += kThreads) {
-                const int i = e % kT, j = e / kT;
-                sm.trsm.Bd[i][j] = (i < w && j < i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
-            }
-            if (tid < kT) sm.trsm.rd[tid] = tid < w ? (C)(1.0 / Db[f + c0 + tid]) : C(0);
-            __syncthreads();
-            C* xr = sm.trsm.X[tid];
-            for (int64_t r = c0 + w + tid; r < m; r += kThreads) {
-                for (int c = 0; c < w; ++c) xr[c] = P[r + (int64_t)(c0 + c) * m];
-                for (int c = 1; c < w; ++c) {
-                    C y = xr[c];
-                    for (int cp = 0; cp < c; ++cp) y -= xr[cp] * sm.trsm.Bd[c][cp];
-                    xr[c] = y;
-                }
-                for (int c = 0; c < w; ++c) P[r + (int64_t)(c0 + c) * m] = xr[c] * sm.trsm.rd[c];
-            }
-            // rank-w update of panel columns [c0 + w, k), rows i >= j, in 32 x 32 tiles:
-            // P[i][j] -= sum_c L[i][c] d_c L[j][c]; thread (ii, j0) owns row ii, columns j0 + 4 q
-            const int ii = tid % kT, j0 = tid / kT;
-            for (int cj = c0 + w; cj < k; cj += kT) {
-                const int nj = min(kT, k - cj);
-                __syncthreads();  // the panel solve (or the previous column tile) is done
-                for (int e = tid; e < kT * kT; e += kThreads) {
-                    const int i = e % kT, c = e / kT;
-                    sm.upd.Lj[i][c] = (i < nj && c < w) ? P[(cj + i) + (int64_t)(c0 + c) * m] * DSb[f + c0 + c] : C(0);
-                }
-                for (int64_t ri = cj; ri < m; ri += kT) {
-                    const int ni = (int)(m - ri < kT ? m - ri : kT);
-                    __syncthreads();
-                    for (int e = tid; e < kT * kT; e += kThreads) {
-                        const int i = e % kT, c = e / kT;
-                        sm.upd.Li[i][c] = (i < ni && c < w) ? P[(ri + i) + (int64_t)(c0 + c) * m] : C(0);
-                    }
-                    __syncthreads();
-                    if (ii < ni) {
-                        C acc[kT / 4];
-#pragma unroll
-                        for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
-#pragma unroll 4
-                        for (int c = 0; c < w; ++c) {
-                            const C ai = sm.upd.Li[ii][c];
-#pragma unroll
-                            for (int q = 0; q < kT / 4; ++q) acc[q] += ai * sm.upd.Lj[j0 + 4 * q][c];
-                        }
-                        C old[kT / 4];
-#pragma unroll
-                        for (int q = 0; q < kT / 4; ++q) {
-                            const int jj = j0 + 4 * q;
-                            old[q] = (jj < nj && ri + ii >= cj + jj) ? P[(ri + ii) + (int64_t)(cj + jj) * m] : C(0);
-                        }
-#pragma unroll
-                        for (int q = 0; q < kT / 4; ++q) {
-                            const int jj = j0 + 4 * q;
-                            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] = old[q] - acc[q];
-                        }
-                    }
-                }
-            }
-        }
+        if (code < 0) diag_front_body(d, ~code, Lb, Db, DSb, ab, status, base);
+        else front_panel_body<C, false>(d, code, Lb, Db, DSb, ab, status, base, sm);
     }
 }
 
@@ -707,6 +836,19 @@ __global__ void __launch_bounds__(kThreads) k_schur_scatter(DevSym d, const int3
 constexpr int kTcStageFloats = 3 * kTcM * kTcK + 3 * kTcN * kTcK;  // A hi/mid/lo, B hi/mid/lo
 constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float) + 64;
 constexpr uint32_t kTcWaitLimit = 1u << 20;
+// Tensor memory of a tensor-core CTA: accumulator A (the hi*hi products) in
+// columns [0, 128), B (the five smaller cross products) in [128, 256), and S,
+// the running sum of A, in [256, 384); 512 columns are allocated (a power of
+// two).  The tensor cores do not round to nearest when they add into an
+// accumulator, so a long accumulation drifts by about one unit in the last
+// place per add: A is added into S (an FP32 round-to-nearest add on the CUDA
+// cores) and restarted every kTcFlush K-chunks of 32, and the small terms,
+// whose drift is relative to their own small size, go to B.
+constexpr uint32_t kTcCols = 512, kAccB = 128, kAccS = 256;
+constexpr int kTcFlush = 16;
+// polls of one dependency wait of the dependency-driven kernel (about 100 ns
+// apart: some seconds, far beyond any task's legitimate wait)
+constexpr uint32_t kDagWaitLimit = 1u << 25;
 
 __device__ __forceinline__ int tc_kmajor_off(int r, int c) {
     return (r >> 3) * 1024 + (c >> 2) * 128 + (r & 7) * 16 + (c & 3) * 4;
@@ -755,6 +897,33 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+// Store 32 consecutive accumulator columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                    "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                    "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]),
+                    "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]),
+                    "r"(r[31]));
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+}
+
+// The finished product for 32 columns of this warp's rows: (S + A) + B, or A + B
+// if A was never added into S.
+__device__ __forceinline__ void tc_acc32(uint32_t taddr, bool with_s, uint32_t (&r)[32]) {
+    uint32_t t[32];
+    tc_ld32(taddr, r);
+    if (with_s) {
+        tc_ld32(taddr + kAccS, t);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(t[j]) + __uint_as_float(r[j]));
+    }
+    tc_ld32(taddr + kAccB, t);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(t[j]));
+}
+
 __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kTcWaitLimit) {
     uint32_t done = 0;
     for (uint32_t it = 0; it < limit && !done; ++it)
@@ -791,7 +960,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     const int64_t jlim = kMode == 0 ? m : k;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc_smem_u32(tmem_slot)),
-                     "r"(kTcN));
+                     "r"(kTcCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -821,7 +990,9 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     };
     if (nk > 0) fetch(0);
     bool ok = true;
-    int last = -1;  // last chunk whose MMAs were committed
+    int last = -1;     // last chunk whose MMAs were committed
+    int a_start = 0;   // first chunk accumulated into A since S last took it
+    int nflush = 0;    // times A was added into S
     for (int kc = 0; kc < nk && ok; ++kc) {
         const int st = kc & 1;
         if (kc >= 2) ok = tc_wait(mbar + st, (uint32_t)((kc - 2) >> 1) & 1u, stage_wait_limit);
@@ -854,7 +1025,6 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        if (kc + 1 < nk) fetch(kc + 1);  // in flight while the MMAs below run
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             for (int kk = 0; kk < kTcK / 8; ++kk) {
@@ -863,18 +1033,42 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
                                al = tc_desc(tc_smem_u32(Al) + ko);
                 const uint64_t bh = tc_desc(tc_smem_u32(Bh) + ko), bm = tc_desc(tc_smem_u32(Bm) + ko),
                                bl = tc_desc(tc_smem_u32(Bl) + ko);
-                // small terms first
-                tc_mma(tmem, am, bm, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc_mma(tmem, al, bh, idesc, 1u);
-                tc_mma(tmem, ah, bl, idesc, 1u);
-                tc_mma(tmem, am, bh, idesc, 1u);
-                tc_mma(tmem, ah, bm, idesc, 1u);
-                tc_mma(tmem, ah, bh, idesc, 1u);
+                // the five small cross products into B, hi*hi into A
+                tc_mma(tmem + kAccB, am, bm, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(tmem + kAccB, al, bh, idesc, 1u);
+                tc_mma(tmem + kAccB, ah, bl, idesc, 1u);
+                tc_mma(tmem + kAccB, am, bh, idesc, 1u);
+                tc_mma(tmem + kAccB, ah, bm, idesc, 1u);
+                tc_mma(tmem, ah, bh, idesc, (kc > a_start || kk > 0) ? 1u : 0u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(tc_smem_u32(mbar + st)));
         }
         last = kc;
+        if ((kc + 1 - a_start) % kTcFlush == 0 && kc + 1 < nk) {
+            // S += A once this chunk's MMAs are done, then A restarts with the next chunk
+            ok = tc_wait(mbar + st, (uint32_t)(kc >> 1) & 1u, stage_wait_limit);
+            if (__syncthreads_or(!ok)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t row = (uint32_t)(warp * 32) << 16;
+            for (int q = 0; q < kTcN / 32; ++q) {
+                uint32_t a[32], sv[32];
+                tc_ld32(tmem + row + q * 32, a);
+                if (nflush > 0) tc_ld32(tmem + row + kAccS + q * 32, sv);
+                else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) sv[j] = 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sv[j] = __float_as_uint(__uint_as_float(sv[j]) + __uint_as_float(a[j]));
+                tc_st32(tmem + row + kAccS + q * 32, sv);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            a_start = kc + 1;
+            ++nflush;
+        }
+        if (kc + 1 < nk) fetch(kc + 1);  // in flight while the MMAs above run
     }
     // the last commit covers every MMA issued before it
     bool fin = last >= 0 ? tc_wait(mbar + (last & 1), (uint32_t)(last >> 1) & 1u, stage_wait_limit) : true;
@@ -887,7 +1081,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         const int64_t il = ib + warp * 32 + lane;
         for (int q = 0; q < kTcN / 32; ++q) {
             uint32_t r[32];
-            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
+            tc_acc32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, nflush > 0, r);
             if (il < m) {
                 // all 32 loads first: a load after a store to the same array would wait for it
                 float old[32];
@@ -916,7 +1110,7 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
         const int qi = il < m ? rel[il] : 0;
         for (int q = 0; q < kTcN / 32; ++q) {
             uint32_t r[32];
-            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, r);
+            tc_acc32(tmem + ((uint32_t)(warp * 32) << 16) + q * 32, nflush > 0, r);
             if (il < m) {
                 float f22v[32];  // the update area's entries and the column maps first, then the atomics
                 int qjv[32];
@@ -941,7 +1135,239 @@ __global__ void __launch_bounds__(128) k_schur_tc(DevSym d, const int32_t* __res
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
+}
+
+// ---------------------------------------------------------------------------
+// Dependency-driven persistent factorization (launch kind 13).
+//
+// One launch runs every task of a prefix of the tree's levels: diagonal-pivot
+// fronts, whole small fronts (front_panel_body), pivot tiles, 128-row chunks
+// of the panel solve, 32 x 32 tiles of the trailing panel update (the first of
+// which factors the next pivot tile) and 32 x 32 Schur tiles added into the
+// parent.  The host lists the tasks in a topological order -- by level, then
+// by phase within each front, a front's Schur tiles right after its last
+// phase -- and the CTAs take them in that order from a global counter.  A task
+// waits until one counter reaches its value: the tasks of its front's earlier
+// phases, or the Schur tiles its front's children add in; it then runs and
+// counts itself done.  A task only waits for tasks earlier in the order, which
+// CTAs that are running already hold, so every wait ends; each wait is still
+// bounded, and when one gives up it raises FLAG_TIMEOUT and every CTA skips
+// its remaining tasks.  Data another CTA wrote during the launch is read
+// through L2 (ld.global.cg).  This replaces the chain of per-step launches,
+// whose gaps and partly idle waves bound the factorization of the wide fronts
+// near the root.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool dag_aborted(const DevStatus* status) {
+    return (*reinterpret_cast<const volatile int*>(&status->flags) & FLAG_TIMEOUT) != 0;
+}
+
+// Thread 0: wait until *c >= need; false if the wait gave up (limit) or the
+// launch was abandoned.
+__device__ bool dag_wait(const int* c, int need, const DevStatus* status, uint32_t limit) {
+    if (limit == 0) return false;  // spi_options.wait_limit < 0: every wait gives up at once
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_gpu(c) >= need) return true;
+        if (it >= limit) return false;
+        if ((it & 31) == 31 && dag_aborted(status)) return false;
+        __nanosleep(100);
+    }
+}
+
+// 128 rows of the panel solve below pivot tile b: L21 = X L11^-T D^-1.
+template <typename C>
+__device__ void dag_trsm(const DevSym& d, int s, int b, int chunk, C* Lb, const double* Db, FrontPanelSmem<C>& sm) {
+    const int tid = threadIdx.x;
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    C* P = Lb + d.lptr[s];
+    const int c0 = b * kT, w = min(kT, k - c0);
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        const int i = e % kT, j = e / kT;
+        sm.trsm.Bd[i][j] = (i < w && j < i) ? __ldcg(P + (c0 + i) + (int64_t)(c0 + j) * m) : C(0);
+    }
+    if (tid < kT) sm.trsm.rd[tid] = tid < w ? (C)(1.0 / __ldcg(Db + f + c0 + tid)) : C(0);
+    __syncthreads();
+    const int64_t r = c0 + w + (int64_t)chunk * kThreads + tid;
+    if (r < m) {
+        C* xr = sm.trsm.X[tid];
+        for (int c = 0; c < w; ++c) xr[c] = __ldcg(P + r + (int64_t)(c0 + c) * m);
+        for (int c = 1; c < w; ++c) {
+            C y = xr[c];
+            for (int cp = 0; cp < c; ++cp) y -= xr[cp] * sm.trsm.Bd[c][cp];
+            xr[c] = y;
+        }
+        for (int c = 0; c < w; ++c) P[r + (int64_t)(c0 + c) * m] = xr[c] * sm.trsm.rd[c];
+    }
+}
+
+// Trailing-update tile (ti, tj) after block column b (as k_panel_update); the
+// tile (0, 0) then factors the next pivot tile.
+template <typename C>
+__device__ void dag_update(const DevSym& d, int s, int b, int ti, int tj, C* Lb, double* Db, C* DSb,
+                           const double* ab, DevStatus* status, int base, FrontPanelSmem<C>& sm) {
+    const int tid = threadIdx.x;
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    C* P = Lb + d.lptr[s];
+    const int c0 = b * kT, w = min(kT, k - c0);
+    const int cj = c0 + w + tj * kT;
+    const int64_t ri = cj + (int64_t)ti * kT;
+    const int nj = min(kT, k - cj);
+    const int ni = (int)(m - ri < kT ? m - ri : kT);
+    for (int e = tid; e < kT * kT; e += kThreads) {
+        const int i = e % kT, c = e / kT;
+        sm.upd.Li[i][c] = (i < ni && c < w) ? __ldcg(P + (ri + i) + (int64_t)(c0 + c) * m) : C(0);
+        sm.upd.Lj[i][c] =
+            (i < nj && c < w) ? __ldcg(P + (cj + i) + (int64_t)(c0 + c) * m) * __ldcg(DSb + f + c0 + c) : C(0);
+    }
+    __syncthreads();
+    const int ii = tid % kT, j0 = tid / kT;
+    if (ii < ni) {
+        C acc[kT / 4];
+#pragma unroll
+        for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
+#pragma unroll 4
+        for (int c = 0; c < w; ++c) {
+            const C ai = sm.upd.Li[ii][c];
+#pragma unroll
+            for (int q = 0; q < kT / 4; ++q) acc[q] += ai * sm.upd.Lj[j0 + 4 * q][c];
+        }
+        C old[kT / 4];
+#pragma unroll
+        for (int q = 0; q < kT / 4; ++q) {
+            const int jj = j0 + 4 * q;
+            old[q] = (jj < nj && ri + ii >= cj + jj) ? __ldcg(P + (ri + ii) + (int64_t)(cj + jj) * m) : C(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kT / 4; ++q) {
+            const int jj = j0 + 4 * q;
+            if (jj < nj && ri + ii >= cj + jj) P[(ri + ii) + (int64_t)(cj + jj) * m] = old[q] - acc[q];
+        }
+    }
+    if (ti == 0 && tj == 0) {
+        __syncthreads();  // the pivot tile's shared memory overlaps the update tiles
+        factor_pivot_tile<C, true>(sm.piv.A, sm.piv.dv, P, m, cj, nj, f, Db, DSb, ab, status, base);
+    }
+}
+
+// Schur tile (ti, tj) of the trailing block, added into the parent front (as k_schur_scatter).
+template <typename C>
+__device__ void dag_schur(const DevSym& d, int s, int ti, int tj, C* Lb, C* Fb, const C* DSb, FrontPanelSmem<C>& sm) {
+    const int tid = threadIdx.x;
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const int64_t mb = m - k;
+    const C* P = Lb + d.lptr[s];
+    const int64_t ib = k + (int64_t)ti * kT, jb = k + (int64_t)tj * kT;
+    const int ni = (int)(m - ib < kT ? m - ib : kT), nj = (int)(m - jb < kT ? m - jb : kT);
+    const int ii = tid % kT, j0 = tid / kT;
+    C acc[kT / 4];
+#pragma unroll
+    for (int q = 0; q < kT / 4; ++q) acc[q] = C(0);
+    for (int cb = 0; cb < k; cb += kT) {
+        const int cw = min(kT, k - cb);
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += kThreads) {
+            const int i = e % kT, c = e / kT;
+            sm.upd.Li[i][c] = (i < ni && c < cw) ? __ldcg(P + (ib + i) + (int64_t)(cb + c) * m) : C(0);
+            sm.upd.Lj[i][c] =
+                (i < nj && c < cw) ? __ldcg(P + (jb + i) + (int64_t)(cb + c) * m) * __ldcg(DSb + f + cb + c) : C(0);
+        }
+        __syncthreads();
+        if (ii < ni) {
+#pragma unroll 4
+            for (int c = 0; c < cw; ++c) {
+                const C ai = sm.upd.Li[ii][c];
+#pragma unroll
+                for (int q = 0; q < kT / 4; ++q) acc[q] -= ai * sm.upd.Lj[j0 + 4 * q][c];
+            }
+        }
+    }
+    const int64_t fo = d.f22ptr[s];
+    const int p = d.sparent[s];
+    const int kp = d.sfirst[p + 1] - d.sfirst[p];
+    const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
+    C* Pp = Lb + d.lptr[p];
+    C* Fp = Fb + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+    const int32_t* rel = d.relmap + d.srowptr[s];
+    if (ii >= ni) return;
+    const int64_t il = ib + ii;
+    const int qi = rel[il];
+#pragma unroll
+    for (int q = 0; q < kT / 4; ++q) {
+        const int jj = j0 + 4 * q;
+        const int64_t jl = jb + jj;
+        if (jj >= nj || il < jl) continue;
+        const C v = acc[q] + (fo >= 0 ? __ldcg(Fb + fo + (il - k) + (jl - k) * mb) : C(0));
+        const int qj = rel[jl];
+        if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, v);
+        else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), v);
+    }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_factor_dag(DevSym d, const DagTask* __restrict__ tasks, int ntasks,
+                                                         int nb, int* cnt, int cstride, C* L, C* F22, double* D,
+                                                         C* DS, const double* __restrict__ adiag, DevStatus* status,
+                                                         Strides bs, uint32_t wait_limit) {
+    __shared__ FrontPanelSmem<C> sm;
+    __shared__ int64_t s_t;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    int* next = cnt + (int64_t)nb * cstride;
+    const int64_t total = (int64_t)ntasks * nb;
+    for (;;) {
+        __syncthreads();  // the previous task is finished with s_t, s_ok and the shared memory
+        if (tid == 0) {
+            const int64_t t = (int64_t)(unsigned)atomicAdd(next, 1);
+            int ok = 0;
+            if (t < total) {
+                const DagTask tk = tasks[t / nb];
+                ok = !dag_aborted(status);
+                if (ok && tk.wait_val > 0) {
+                    ok = dag_wait(cnt + (t % nb) * cstride + tk.wait_idx, tk.wait_val, status, wait_limit);
+                    if (!ok) atomicOr(&status->flags, FLAG_TIMEOUT);
+                }
+            }
+            s_t = t;
+            s_ok = ok;
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= total) break;
+        if (!s_ok) continue;
+        const int band = (int)(t % nb);
+        const DagTask tk = tasks[t / nb];
+        C* Lb = L + band * bs.L;
+        C* Fb = F22 + band * bs.F22;
+        double* Db = D + band * bs.n;
+        C* DSb = DS + band * bs.n;
+        const double* ab = adiag + band * bs.n;
+        const int base = (int)(band * bs.n);
+        switch (tk.type) {
+            case kDagDiagFront: diag_front_body<C, true>(d, tk.s, Lb, Db, DSb, ab, status, base); break;
+            case kDagFused: front_panel_body<C, true>(d, tk.s, Lb, Db, DSb, ab, status, base, sm); break;
+            case kDagPivot: {
+                const int f = d.sfirst[tk.s], k = d.sfirst[tk.s + 1] - f;
+                const int64_t m = d.srowptr[tk.s + 1] - d.srowptr[tk.s];
+                factor_pivot_tile<C, true>(sm.piv.A, sm.piv.dv, Lb + d.lptr[tk.s], m, 0, min(kT, k), f, Db, DSb, ab,
+                                           status, base);
+                break;
+            }
+            case kDagTrsm: dag_trsm(d, tk.s, tk.a, tk.b, Lb, Db, sm); break;
+            case kDagUpdate: dag_update(d, tk.s, tk.a, tk.b >> 16, tk.b & 0xFFFF, Lb, Db, DSb, ab, status, base, sm); break;
+            default: dag_schur(d, tk.s, tk.a, tk.b, Lb, Fb, DSb, sm); break;
+        }
+        __threadfence();  // every thread's stores of the task are visible device-wide ...
+        __syncthreads();
+        if (tid == 0) atomicAdd(cnt + band * cstride + tk.done_idx, 1);  // ... before it counts as done
+    }
 }
 
 __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
@@ -953,6 +1379,7 @@ __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, in
 
 // CTAs of the persistent per-level panel kernel: every SM slot it fits in
 int g_panel_grid[2] = {0, 0};  // [0] FP64, [1] mixed
+int g_dag_grid[2] = {0, 0};    // the dependency-driven kernel, likewise
 
 cudaError_t factor_kernel_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_schur_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
@@ -968,6 +1395,12 @@ cudaError_t factor_kernel_setup() {
         return e;
     g_panel_grid[0] = std::max(1, sms * b64);
     g_panel_grid[1] = std::max(1, sms * b32);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_factor_dag<double>, kThreads, 0)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_factor_dag<float>, kThreads, 0)) != cudaSuccess)
+        return e;
+    g_dag_grid[0] = std::max(1, sms * b64);
+    g_dag_grid[1] = std::max(1, sms * b32);
     return cudaSuccess;
 }
 
@@ -1020,6 +1453,23 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, C* L,
             break;
         }
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, DS, bs); break;
+    }
+}
+
+void launch_factor_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, void* L,
+                       void* F22, double* D, void* DS, const double* adiag, DevStatus* status, bool mixed, int nb,
+                       const Strides& bs, int wait_limit, cudaStream_t st) {
+    if (ntasks == 0 || nb == 0) return;
+    const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kDagWaitLimit;
+    const int64_t total = (int64_t)ntasks * nb;
+    if (mixed) {
+        const int grid = (int)std::min<int64_t>(total, g_dag_grid[1]);
+        k_factor_dag<float><<<grid, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, (float*)L, (float*)F22,
+                                                       D, (float*)DS, adiag, status, bs, lim);
+    } else {
+        const int grid = (int)std::min<int64_t>(total, g_dag_grid[0]);
+        k_factor_dag<double><<<grid, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, (double*)L,
+                                                        (double*)F22, D, (double*)DS, adiag, status, bs, lim);
     }
 }
 

@@ -401,7 +401,251 @@ __global__ void k_reciprocal(int32_t n, const double* __restrict__ D, double* __
         dinv[k] = 1.0 / D[k];
 }
 
+// ---------------------------------------------------------------------------
+// Dependency-driven solve (one launch for both sweeps).
+//
+// The tasks -- forward step b of supernode s over a 512-row chunk of the rows
+// below the step (kSolveFwd), the backward first pass over 32 of its columns
+// (kSolveBwdInit), backward step b over 256 of its earlier columns
+// (kSolveBwdStep) -- are listed forward sweep first, bottom-up level by level,
+// then the backward sweep top-down, each level phase by phase across its
+// supernodes, so that every task depends only on tasks before it.  A CTA takes
+// the next task from a global counter, waits (bounded) until the counter it
+// depends on reaches its value, runs it and counts it done: forward steps wait
+// for the supernode's earlier steps, its first step for every forward task of
+// its children (which in turn waited for theirs: all updates of the subtree
+// into its rows are in); the backward pass of a supernode waits for every
+// backward task of its parent (all ancestors' x are final), or, at a root, for
+// its own forward sweep; backward steps wait for the supernode's earlier
+// backward tasks.  Vectors written during the launch are read through L2.  As
+// in the factorization, a wait that gives up raises FLAG_TIMEOUT and every CTA
+// skips its remaining tasks.
+constexpr uint32_t kSolveWaitLimit = 1u << 25;
+
+__device__ __forceinline__ int sv_ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool sv_aborted(const DevStatus* status) {
+    return (*reinterpret_cast<const volatile int*>(&status->flags) & FLAG_TIMEOUT) != 0;
+}
+
+__device__ bool sv_wait(const int* c, int need, const DevStatus* status, uint32_t limit) {
+    if (limit == 0) return false;
+    for (uint32_t it = 0;; ++it) {
+        if (sv_ld_acquire(c) >= need) return true;
+        if (it >= limit) return false;
+        if ((it & 31) == 31 && sv_aborted(status)) return false;
+        __nanosleep(100);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask* __restrict__ tasks, int ntasks,
+                                                        int nb, int* cnt, int cstride, const double* __restrict__ L,
+                                                        const double* __restrict__ D, double* w, double* z, double* x,
+                                                        DevStatus* status, Strides bs, uint32_t wait_limit) {
+    __shared__ double xb[kT];
+    __shared__ int64_t s_t;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int* next = cnt + (int64_t)nb * cstride;
+    const int64_t total = (int64_t)ntasks * nb;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            const int64_t t = (int64_t)(unsigned)atomicAdd(next, 1);
+            int ok = 0;
+            if (t < total) {
+                const DagTask tk = tasks[t / nb];
+                ok = !sv_aborted(status);
+                if (ok && tk.wait_val > 0) {
+                    ok = sv_wait(cnt + (t % nb) * cstride + tk.wait_idx, tk.wait_val, status, wait_limit);
+                    if (!ok) atomicOr(&status->flags, FLAG_TIMEOUT);
+                }
+            }
+            s_t = t;
+            s_ok = ok;
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= total) break;
+        if (!s_ok) continue;
+        const int band = (int)(t % nb);
+        const DagTask tk = tasks[t / nb];
+        const double* Lb = L + band * bs.L;
+        const double* Db = D + band * bs.Dn;
+        double* wb_ = w + band * bs.n;
+        double* zb = z + band * bs.n;
+        double* xv = x + band * bs.n;
+        const int s = tk.s;
+        const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+        const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+        const double* P = Lb + d.lptr[s];
+        const int32_t* rows = d.srows + d.srowptr[s];
+        if (tk.type == kSolveFwd) {
+            const int cb = tk.a * kT, wb = min(kT, k - cb), chunk = tk.b;
+            if (tid < 32) {
+                double lrow[kT];
+#pragma unroll
+                for (int c = 0; c < kT; ++c)
+                    lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
+                double xx = lane < wb ? __ldcg(wb_ + f + cb + lane) : 0.0;
+#pragma unroll
+                for (int c = 0; c < kT - 1; ++c) {
+                    const double xc = __shfl_sync(0xffffffffu, xx, c);
+                    xx -= lrow[c] * xc;
+                }
+                xb[lane] = xx;
+                if (chunk == 0 && lane < wb) zb[f + cb + lane] = xx;
+            }
+            __syncthreads();
+            const int64_t r0 = cb + wb + (int64_t)chunk * kFwdRows;
+            const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
+            for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+                double acc = 0.0;
+                for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+                if (r < k) wb_[f + r] = __ldcg(wb_ + f + r) - acc;
+                else atomicAdd(wb_ + rows[r], -acc);
+            }
+        } else if (tk.type == kSolveBwdInit) {
+            constexpr int kWarps = kThreads / 32, kPer = kT / kWarps;
+            const int c0 = tk.b * kT, nc = min(kT, k - c0);
+            double acc[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
+            for (int64_t r = k + lane; r < m; r += 32) {
+                const double xr = __ldcg(xv + rows[r]);
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int c = warp + kWarps * q;
+                    if (c < nc) acc[q] += P[r + (int64_t)(c0 + c) * m] * xr;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                double v = acc[q];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                const int c = warp + kWarps * q;
+                if (lane == 0 && c < nc) wb_[f + c0 + c] = __ldcg(zb + f + c0 + c) / Db[f + c0 + c] - v;
+            }
+        } else {
+            const int cb = tk.a * kT, wb = min(kT, k - cb), chunk = tk.b;
+            if (tid < 32) {
+                double lcol[kT];
+#pragma unroll
+                for (int r = 0; r < kT; ++r)
+                    lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
+                double y = lane < wb ? __ldcg(wb_ + f + cb + lane) : 0.0;
+#pragma unroll
+                for (int r = kT - 1; r > 0; --r) {
+                    const double xr = __shfl_sync(0xffffffffu, y, r);
+                    y -= lcol[r] * xr;
+                }
+                xb[lane] = y;
+                if (chunk == 0 && lane < wb) xv[f + cb + lane] = y;
+            }
+            __syncthreads();
+            const int a1 = min(cb, (chunk + 1) * kBwdCols);
+            for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
+                const double* col = P + (int64_t)a * m + cb;
+                double acc = 0.0;
+                for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
+                wb_[f + a] = __ldcg(wb_ + f + a) - acc;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            int* bc = cnt + band * cstride;
+            atomicAdd(bc + tk.done_idx, 1);
+            if (tk.pad >= 0) atomicAdd(bc + tk.pad, 1);
+        }
+    }
+}
+
 }  // namespace
+
+void build_solve_dag(const Symbolic& S, SolvePlan& P) {
+    P.dag.clear();
+    const int32_t ns = S.ns;
+    std::vector<int32_t> nfwd(ns, 0), nbwd(ns, 0), child_fwd(ns, 0);
+    auto emit = [&](std::vector<std::vector<std::vector<DagTask>>>& ph) {
+        size_t maxp = 0;
+        for (auto& t : ph) maxp = std::max(maxp, t.size());
+        for (size_t q = 0; q < maxp; ++q)
+            for (auto& t : ph)
+                if (q < t.size()) P.dag.insert(P.dag.end(), t[q].begin(), t[q].end());
+    };
+    // forward sweep, bottom-up
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+        std::vector<std::vector<std::vector<DagTask>>> ph;
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p], k = S.k_of(s), m = S.m_of(s), par = S.sparent[s];
+            std::vector<std::vector<DagTask>> t;
+            int32_t done = 0;
+            for (int32_t b = 0; b * kT < k; ++b) {
+                const int32_t wb = std::min(kT, k - b * kT);
+                const int64_t below = (int64_t)m - b * kT - wb;
+                const int32_t nch = std::max<int32_t>(1, (int32_t)((below + kFwdRows - 1) / kFwdRows));
+                std::vector<DagTask> step;
+                for (int32_t c = 0; c < nch; ++c)
+                    step.push_back(DagTask{kSolveFwd, s, b, c, b == 0 ? ns + s : s, b == 0 ? child_fwd[s] : done, s,
+                                           par >= 0 ? ns + par : -1});
+                done += nch;
+                t.push_back(step);
+            }
+            nfwd[s] = done;
+            if (par >= 0) child_fwd[par] += done;
+            ph.push_back(std::move(t));
+        }
+        emit(ph);
+    }
+    // backward sweep, top-down
+    for (int32_t l = S.nlevels - 1; l >= 0; --l) {
+        std::vector<std::vector<std::vector<DagTask>>> ph;
+        for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+            const int32_t s = S.level_list[p], k = S.k_of(s), par = S.sparent[s];
+            std::vector<std::vector<DagTask>> t;
+            const int32_t nci = (k + kT - 1) / kT;
+            std::vector<DagTask> init;
+            for (int32_t c = 0; c < nci; ++c)
+                init.push_back(DagTask{kSolveBwdInit, s, 0, c, par >= 0 ? 2 * ns + par : s,
+                                       par >= 0 ? nbwd[par] : nfwd[s], 2 * ns + s, -1});
+            t.push_back(init);
+            int32_t done = nci;
+            for (int32_t b = nci - 1; b >= 0; --b) {
+                const int32_t ncb = std::max<int32_t>(1, (b * kT + kBwdCols - 1) / kBwdCols);
+                std::vector<DagTask> step;
+                for (int32_t c = 0; c < ncb; ++c) step.push_back(DagTask{kSolveBwdStep, s, b, c, 2 * ns + s, done, 2 * ns + s, -1});
+                done += ncb;
+                t.push_back(step);
+            }
+            nbwd[s] = done;
+            ph.push_back(std::move(t));
+        }
+        emit(ph);
+    }
+}
+
+void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, const double* L,
+                      const double* D, double* w, double* z, double* x, DevStatus* status, int nb, const Strides& bs,
+                      int wait_limit, int grid, cudaStream_t st) {
+    if (ntasks == 0 || nb == 0) return;
+    const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kSolveWaitLimit;
+    const int g = (int)std::min<int64_t>((int64_t)ntasks * nb, grid);
+    k_solve_dag<<<g, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, L, D, w, z, x, status, bs, lim);
+}
+
+cudaError_t solve_dag_grid(int* grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dag, kThreads, 0);
+    *grid = std::max(1, sms * per);
+    return e;
+}
 
 void launch_zsq_var(int32_t n, const double* z, const double* dinv, int R, double* out, cudaStream_t st) {
     if (R <= 0) return;

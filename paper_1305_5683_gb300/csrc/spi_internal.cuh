@@ -65,6 +65,22 @@ struct Launch {
     int32_t count;   // CTAs (kind 12: fronts)
 };
 
+// One task of the dependency-driven factorization kernel (launch kind 13).
+enum DagType : int32_t {
+    kDagDiagFront = 0, kDagFused = 1, kDagPivot = 2, kDagTrsm = 3, kDagUpdate = 4, kDagSchur = 5,  // factorization
+    kSolveFwd = 6, kSolveBwdInit = 7, kSolveBwdStep = 8                                            // solve
+};
+struct DagTask {
+    int32_t type;      // DagType
+    int32_t s;         // supernode
+    int32_t a, b;      // kDagTrsm: block step, 128-row chunk; kDagUpdate: block step, ti << 16 | tj;
+                       // kDagSchur: ti, tj
+    int32_t wait_idx;  // the task waits until counter[wait_idx] >= wait_val (0: no wait); counters
+    int32_t wait_val;  //   [0, ns): tasks done of each front, [ns, 2 ns): children's Schur tiles added
+    int32_t done_idx;  // counter incremented when the task is done
+    int32_t pad;       // solve tasks: a second counter incremented when done (-1: none)
+};
+
 struct FactorPlan {
     std::vector<int32_t> diag_items;  // supernode
     std::vector<int32_t> trsm_items;  // pairs (supernode, row tile)
@@ -74,6 +90,8 @@ struct FactorPlan {
     std::vector<int32_t> dfront_items;   // supernodes with a diagonal pivot block
     std::vector<int32_t> panel_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<int32_t> fused_items;    // kind 12: supernode, or ~supernode for a diagonal pivot block
+    std::vector<DagTask> dag;            // kind 13: the tasks of the dependency-driven kernel, in order
+    int32_t dag_levels = 0;              // levels [0, dag_levels) run in it
     std::vector<Launch> launches;
     std::vector<int32_t> level_launch_ptr;  // launches of level l: [ptr[l], ptr[l+1])
     // timing groups of an autotuner plan (markers): what the launches up to the
@@ -85,6 +103,8 @@ struct FactorPlan {
     };
     std::vector<Group> groups;
     int64_t n_kernel_launches = 0, n_fused_launches = 0, n_tc_launches = 0, n_tc_tiles = 0;
+    double tc_flops = 0;    // TF32 flops the tensor cores execute (every MMA of every tile)
+    double work_flops = 0;  // flops the SIMT kernels execute (full tiles, explicit zeros)
 };
 
 // Per front-size bucket choices of the factorization: the autotuner's table.
@@ -94,6 +114,7 @@ struct FactorPlan {
 struct FactorChoice {
     std::map<int32_t, uint8_t> panel;  // 1: whole panel in one CTA of the per-level kernel; 0: block-step chain
     std::map<int32_t, uint8_t> schur;  // 1: tensor-core Schur complement (mixed precision); 0: SIMT
+    int dag = 0;                       // 1: levels below the first tensor-core level in one dependency-driven launch
     int force_panel = 0;               // 1 every front tiled, 2 every front fused (tests, tuning)
     int force_schur = 0;               // 1 SIMT everywhere, 2 tensor cores wherever legal
     bool fused(int64_t m, int64_t k) const;
@@ -118,10 +139,19 @@ struct SolvePlan {
     std::vector<Launch> fwd_launches; // kind 4, bottom-up
     std::vector<Launch> bwd_launches; // kinds 5 (level init) and 6 (block steps), top-down
     std::vector<std::vector<Launch>> bwd_level_launches;
+    std::vector<DagTask> dag;  // both sweeps as tasks of one dependency-driven launch; counters:
+                               // [0, ns) forward tasks done, [ns, 2 ns) children's forward tasks
+                               // done, [2 ns, 3 ns) backward tasks done
 };
 
 // batch: bands per launch (the fused per-level sweeps are used for batches only)
 void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch);
+void build_solve_dag(const Symbolic& S, SolvePlan& P);
+// both sweeps in one dependency-driven launch; counters: nb * cstride + 1 ints, zeroed before
+void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, const double* L,
+                      const double* D, double* w, double* z, double* x, DevStatus* status, int nb, const Strides& bs,
+                      int wait_limit, int grid, cudaStream_t st);
+cudaError_t solve_dag_grid(int* grid);
 // variances from unpruned forward solves (the pruning ablation of spi_diag_inverse)
 void launch_zsq_var(int32_t n, const double* z, const double* dinv, int R, double* out, cudaStream_t st);
 void launch_reciprocal(int32_t n, const double* D, double* dinv, cudaStream_t st);
@@ -157,6 +187,10 @@ void launch_factor_step(const DevSym& d, const Launch& l, const int32_t* items, 
                         void* DS, const double* adiag, DevStatus* status, bool mixed, int nb, const Strides& bs,
                         int wait_limit, cudaStream_t st);
 void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t st);
+// the dependency-driven kernel over `tasks`; counters: nb * cstride + 1 ints, zeroed before
+void launch_factor_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, void* L,
+                       void* F22, double* D, void* DS, const double* adiag, DevStatus* status, bool mixed, int nb,
+                       const Strides& bs, int wait_limit, cudaStream_t st);
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st);

@@ -98,6 +98,13 @@ SKY = SpiConfig("spi-sky-P8000", n_pointings=8000, n_sources=200, bin_lo=20,
                 sky_pix_deg=1.0)
 
 
+# The large configuration's diffuse sky at its full size -- 0.5 deg pixels over
+# 70 deg, 19,600 sky columns -- with 2,000 pointings and 50 sources, so that the
+# FP64 oracle can factor it (its largest front has about 13,500 rows).
+SKY_PIX05 = SpiConfig("spi-sky-P2000-pix0.5", n_pointings=2000, n_sources=50, bin_lo=20,
+                      bin_hi=2000, det_block=500, field_deg=70.0, targets=7, sky_pix_deg=0.5)
+
+
 def sky_scaled(n_pointings: int, pix_deg: float, n_sources: int, seed: int = 0) -> SpiConfig:
     """A member of the diffuse-sky family with P pointings and pixels of pix_deg."""
     return dataclasses.replace(SKY, name=f"spi-sky-P{n_pointings}-pix{pix_deg:g}",
@@ -399,18 +406,30 @@ def generate(cfg: SpiConfig, *, window: int = 64, noise: bool = True,
         Wt = np.zeros((npos, nd)); Yt = np.zeros((npos, nd))
         np.add.at(Wt, qofp, w.reshape(P, nd))
         np.add.at(Yt, qofp, (w * y).reshape(P, nd))
+        # the positions of one target (its 25 dither offsets) see nearly the same
+        # pixels: one dense product per target over the union of their pixels
         acc = np.zeros((nsky, nsky))
-        for q in range(npos):
-            if not Wt[q].any():
+        groups = ([np.arange(t * nq, (t + 1) * nq) for t in range(npos // nq)] if cfg.targets > 0
+                  else [np.arange(npos)])
+        for grp in groups:
+            qs = [int(q) for q in grp if Wt[q].any() and pvis[:, q].any()]
+            if not qs:
                 continue
-            V = np.nonzero(pvis[:, q])[0]
-            if len(V) == 0:
-                continue
-            R = _response(cfg.seed, cfg.n_sources + V[None, :], np.full((1, 1), q), dd[:, None])  # [nd, |V|]
-            acc[np.ix_(V, V)] += R.T @ (R * Wt[q][:, None])
-            bvec[col_sky0 + V] += R.T @ Yt[q]
-        gi, gj = np.nonzero(np.tril(acc))
-        rr.append(col_sky0 + gi); cc.append(col_sky0 + gj); vv.append(acc[gi, gj])
+            U = np.nonzero(pvis[:, qs].any(axis=1))[0]
+            Rs = np.zeros((len(qs) * nd, len(U)))
+            for i, q in enumerate(qs):
+                sel = np.nonzero(pvis[U, q])[0]
+                R = _response(cfg.seed, cfg.n_sources + U[sel][None, :], np.full((1, 1), q), dd[:, None])  # [nd, |V|]
+                Rs[i * nd:(i + 1) * nd, sel] = R
+                bvec[col_sky0 + U[sel]] += R.T @ Yt[q]
+            acc[np.ix_(U, U)] += Rs.T @ (Rs * Wt[qs].ravel()[:, None])
+        # lower triangle, a block of columns at a time
+        for j0 in range(0, nsky, 2048):
+            j1 = min(nsky, j0 + 2048)
+            gi, gj = np.nonzero(acc[j0:, j0:j1])
+            low = gi >= gj
+            gi, gj = gi[low] + j0, gj[low] + j0
+            rr.append(col_sky0 + gi); cc.append(col_sky0 + gj); vv.append(acc[gi, gj])
     rr = np.concatenate(rr); cc = np.concatenate(cc); vv = np.concatenate(vv)
     low = sp.coo_matrix((vv, (rr, cc)), shape=(n, n)).tocsc()
     low.sum_duplicates()

@@ -117,9 +117,10 @@ def test_tensor_core_schur_fronts(P):
     assert ex <= X_TOL and ev <= MIXED_VAR_TOL
 
 
+@pytest.mark.parametrize("dag", [1, 2])
 @pytest.mark.parametrize("force_schur", [1, 2])
 @pytest.mark.parametrize("force_panel", [1, 2])
-def test_mixed_paths_against_oracle(P, force_panel, force_schur):
+def test_mixed_paths_against_oracle(P, force_panel, force_schur, dag):
     """Every combination of the factorization's paths in mixed precision: panels on
     the block-step chain or in the persistent per-level kernel, Schur complements
     on the SIMT kernel with no tensor-core launch at all, or on the tensor cores
@@ -127,11 +128,17 @@ def test_mixed_paths_against_oracle(P, force_panel, force_schur):
     meet the mixed bounds against the
     oracle, and the counters must show that the forced path ran."""
     pb = generate(sky_scaled(1500, 1.2, 40))  # fronts of up to ~3,000 rows
-    s, ex, ev = run(P, pb, force_panel=force_panel, force_schur=force_schur)
+    s, ex, ev = run(P, pb, force_panel=force_panel, force_schur=force_schur, dag=dag)
     info = s.info()
-    print(f"panel={force_panel} schur={force_schur} x_err={ex:.2e} var_err={ev:.2e} "
-          f"fused={info['launches_factor_fused']} tc={info['launches_factor_tc']} tiles={info['tiles_factor_tc']}")
-    assert (info["launches_factor_fused"] > 0) == (force_panel == 2)
+    print(f"panel={force_panel} schur={force_schur} dag={dag} x_err={ex:.2e} var_err={ev:.2e} "
+          f"fused={info['launches_factor_fused']} tc={info['launches_factor_tc']} tiles={info['tiles_factor_tc']} "
+          f"dag_tasks={info['factor_dag_tasks']} dag_levels={info['factor_dag_levels']}")
+    if dag == 1:
+        assert (info["launches_factor_fused"] > 0) == (force_panel == 2)
+    elif force_schur == 1:  # no tensor-core level: every level in the dependency-driven launch
+        assert info["factor_dag_tasks"] > 0 and info["factor_dag_levels"] == info["n_levels"]
+    else:  # the levels below the first one with a tensor-core launch
+        assert info["factor_dag_levels"] < info["n_levels"]
     if force_schur == 1:
         assert info["launches_factor_tc"] == 0
     else:
@@ -155,8 +162,8 @@ def test_bounded_wait_timeout_reported(P):
     with pytest.raises(P.SpiError) as e:
         s.solve(b)
     assert e.value.code == 7
-    # the FP64 form has no tensor-core waits: the same option leaves it untouched
-    s64 = P.Solver(n, cp, ri, ordering=P.SPI_ORDER_NATURAL, wait_limit=-1)
+    # launched level by level, the FP64 form waits nowhere: the same option leaves it untouched
+    s64 = P.Solver(n, cp, ri, ordering=P.SPI_ORDER_NATURAL, wait_limit=-1, dag=1)
     s64.factor(va)
     x_ref = oracle.OracleFactor(n, cp, ri, va).solve(b)
     assert np.abs(s64.solve(b) - x_ref).max() <= 1e-10 * np.abs(x_ref).max()

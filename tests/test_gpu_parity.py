@@ -203,19 +203,59 @@ def test_unpruned_ablation_matches_pruned(P):
     assert u.info()["diag_work_flops"] > 10 * s.info()["diag_work_flops"]
 
 
+@pytest.mark.parametrize("dag", [1, 2])
 @pytest.mark.parametrize("force_panel", [1, 2])
 @pytest.mark.parametrize("make", [lambda: generate(TINY), lambda: generate(scaled(SCALE, 2000, seed=5)),
-                                  lambda: random_spd(300, 0.02, 11)])
-def test_panel_paths(P, make, force_panel):
-    """The two ways of factoring a front's panel -- the chain of 32-column block
-    step launches, and the persistent per-level kernel in which one CTA runs all
-    block steps of a front -- each against the oracle at the FP64 bar."""
+                                  lambda: random_spd(300, 0.02, 11), lambda: random_spd(700, 0.01, 12)])
+def test_panel_paths(P, make, force_panel, dag):
+    """The ways of running the factorization, each against the oracle at the FP64
+    bar: launches level by level (dag 1) with every front's panel on the chain of
+    32-column block-step launches or in the persistent per-level kernel (one CTA
+    runs all block steps of a front), and the same two panel forms as tasks of
+    the single dependency-driven launch (dag 2)."""
     pb = make()
-    s, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, force_panel=force_panel)
+    s, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, force_panel=force_panel, dag=dag)
     info = s.info()
-    assert (info["launches_factor_fused"] > 0) == (force_panel == 2)
-    if force_panel == 2:
-        assert info["launches_factor"] < 2 + 3 * info["n_levels"] + 64  # about one panel launch per level
+    if dag == 1:
+        assert info["factor_dag_tasks"] == 0
+        assert (info["launches_factor_fused"] > 0) == (force_panel == 2)
+        if force_panel == 2:
+            assert info["launches_factor"] < 2 + 3 * info["n_levels"] + 64  # about one panel launch per level
+    else:
+        assert info["factor_dag_tasks"] > 0 and info["factor_dag_levels"] == info["n_levels"]
+        assert info["launches_factor"] == 3  # status reset, assembly, the one dependency-driven launch
+
+
+def test_dag_batched_bands(P):
+    """The dependency-driven launch over a batch of same-pattern bands (one set of
+    counters per band) against the oracle band by band."""
+    from spigen import BAND, generate_bands
+    bands = generate_bands(scaled(BAND, 600, seed=4), 3)
+    n = bands.n
+    s = P.Solver(n, bands.colptr, bands.rowind, batch=bands.nbands, dag=2)
+    s.factor_batch(bands.values)
+    x = s.solve_batch(bands.b)
+    v = s.diag_inverse_batch()
+    assert s.info()["factor_dag_tasks"] > 0
+    for k in range(bands.nbands):
+        pb = bands.band(k)
+        f = oracle.OracleFactor.from_problem(pb)
+        xr, vr = f.solve(pb.b), f.inv_diag()
+        assert np.abs(x[k * n:(k + 1) * n] - xr).max() <= TOL * np.abs(xr).max(), k
+        assert (np.abs(v[k * n:(k + 1) * n] - vr) / vr).max() <= TOL, k
+
+
+def test_dag_timeout_reported(P):
+    """wait_limit < 0 makes every bounded wait give up at once: the dependency-
+    driven launch raises the timeout flag at its first dependent task, every CTA
+    skips the rest, spi_factor returns SPI_ERR_TIMEOUT, and a fresh context on the
+    device still factors correctly.  No wait is unbounded; nothing faults."""
+    pb = generate(TINY)
+    s = P.Solver.for_problem(pb, dag=2, wait_limit=-1)
+    with pytest.raises(P.SpiError) as e:
+        s.factor(pb.values)
+    assert e.value.code == 6
+    check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, dag=2)
 
 
 def test_autotuner_and_tune_cache(P, tmp_path):
@@ -227,12 +267,14 @@ def test_autotuner_and_tune_cache(P, tmp_path):
     s1, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=1, tune_cache=str(cache))
     i1 = s1.info()
     assert i1["tune_source"] == 1 and i1["tune_seconds"] > 0 and i1["tune_panel_buckets"] > 0
-    lines = [l for l in cache.read_text().splitlines() if not l.startswith("#")]
-    assert len(lines) == i1["tune_panel_buckets"] + i1["tune_schur_buckets"]
+    lines = [l.split() for l in cache.read_text().splitlines() if not l.startswith("#")]
+    assert sum(l[3] in "PS" for l in lines) == i1["tune_panel_buckets"] + i1["tune_schur_buckets"]
+    assert sum(l[3] == "D" for l in lines) == 1  # launches level by level against the dependency-driven launch
+    assert i1["tune_ms_launches"] > 0 and i1["tune_ms_dag"] > 0
     s2, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=1, tune_cache=str(cache))
     i2 = s2.info()
     assert i2["tune_source"] == 2
-    for k in ("launches_factor", "launches_factor_fused", "tune_panel_fused"):
+    for k in ("launches_factor", "launches_factor_fused", "tune_panel_fused", "factor_dag_tasks"):
         assert i1[k] == i2[k], k
     # the rules alone (no timing) are a valid plan too
     s3, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=-1)

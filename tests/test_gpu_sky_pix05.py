@@ -1,0 +1,79 @@
+"""The large configuration's diffuse sky at full size: 0.5-degree pixels over
+70 degrees (19,600 sky columns), observed by 2,000 pointings with 50 point
+sources.  Its largest front has about 13,500 rows, the dense regime of the
+tensor-core updates.  The FP64 oracle needs about an hour on one core for this
+matrix, so its results were stored by tests/golden/make_sky_pix05.py (x and
+the sky columns' variances); the GPU path is compared with them element by
+element: FP64 at the FP64 bar, the mixed form at its bounds."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from spigen import SKY_PIX05, generate
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sky_pix05_oracle.npz")
+TOL = 1e-10
+X_TOL_MIXED = 1e-8
+VAR_TOL_MIXED = 3e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1305_5683_gb300 as P
+    P.build.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def case():
+    g = np.load(GOLDEN)
+    pb = generate(SKY_PIX05)
+    assert pb.n == int(g["n"]) and pb.nnz == int(g["nnz"])
+    assert np.array_equal(pb.sky_columns, g["sky_columns"])
+    # the generated matrix against the one the oracle factored (BLAS rounding may differ
+    # between machines in the last bits)
+    sys.path.insert(0, os.path.dirname(GOLDEN))
+    from make_sky_pix05 import fingerprint
+    fp = fingerprint(pb)
+    print(f"matrix fingerprint: max rel diff {np.abs(fp - g['fingerprint']).max() / np.abs(g['fingerprint']).max():.2e}")
+    return pb, g
+
+
+def _errors(x, v, g):
+    ex = np.abs(x - g["x"]).max() / np.abs(g["x"]).max()
+    ev = (np.abs(v - g["var_sky"]) / g["var_sky"]).max()
+    return ex, ev
+
+
+def test_sky_pix05_fp64(P, case):
+    pb, g = case
+    s = P.Solver.for_problem(pb)
+    s.factor(pb.values)
+    x = s.solve(pb.b)
+    v = s.diag_inverse(pb.sky_columns)
+    info = s.info()
+    ex, ev = _errors(x, v, g)
+    print(f"sky pix0.5 FP64: n={pb.n} sky={pb.n_sky} max_front={info['max_front']} x_err={ex:.2e} var_err={ev:.2e}")
+    assert info["max_front"] >= 8000
+    assert ex <= TOL and ev <= TOL
+
+
+def test_sky_pix05_mixed(P, case):
+    pb, g = case
+    s = P.Solver.for_problem(pb, precision=P.SPI_PREC_MIXED_FP32)
+    s.factor(pb.values)
+    x = s.solve(pb.b)
+    v = s.diag_inverse(pb.sky_columns)
+    info = s.info()
+    ex, ev = _errors(x, v, g)
+    print(f"sky pix0.5 mixed: x_err={ex:.2e} var_err={ev:.2e} tc_launches={info['launches_factor_tc']} "
+          f"tiles={info['tiles_factor_tc']} relres={info['solve_relres']:.2e}")
+    assert info["launches_factor_tc"] > 0
+    assert info["solve_relres"] <= 1e-13
+    assert ex <= X_TOL_MIXED and ev <= VAR_TOL_MIXED

@@ -160,17 +160,28 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
 }
 
 // Mixed form: the same walk with an FP32 copy of L and FP32 Z (variance sums
-// in FP64), and the update of the rows below done as a register-tiled SIMT
-// GEMM: 128 threads, a 128-row x 64-RHS output tile, 8 x 8 outputs per
-// thread, the panel tile staged transposed so that a thread's 8 rows are one
-// pair of float4 loads.
+// in FP64), in two phases per supernode s of the path:
+//   A. its own k columns, 32 at a time: the unit-lower diagonal block solved
+//      per right-hand side (thread per RHS), the squares scaled by 1/d added
+//      to the variances in FP64, and the rows of s below the block (still
+//      inside s) updated by a register-tiled SIMT GEMM;
+//   B. the rows below s (its ancestors' pivots) updated once:
+//      Z_below -= L(below, 0:k) Z_s, one GEMM with K = k, each 128-row tile
+//      accumulated in registers over all of s's columns and added into Z at
+//      the end.
+// Phase B writes every Z row below s once per supernode instead of once per
+// 32-column block, which is what the variance workspace's traffic (beyond L2
+// at the benchmark sizes) is made of.  GEMM tiles: 128 threads, a 128-row x
+// 64-RHS output tile, 8 x 8 outputs per thread; the panel tile is staged
+// transposed (a thread's 8 rows are one pair of float4 loads), double-
+// buffered with cp.async, and so is phase B's 32 x 64 chunk of Z_s.
 constexpr int kFThreads = 128;
 constexpr int kFRows = 128;
 constexpr int kFCols = 64;
 
 size_t diag_f32_smem_bytes(int B) {
     return sizeof(double) * (size_t)(B + kT) +
-           sizeof(float) * (size_t)(kT * B + kT * (kT + 1) + 2 * kT * (kFRows + 4));
+           sizeof(float) * (size_t)(kT * B + kT * (kT + 1) + 2 * kT * (kFRows + 4) + 2 * kT * kFCols);
 }
 
 // 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero
@@ -182,6 +193,26 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// 8 x 8 outer-product accumulation over `kw` K-columns of a transposed 128-row
+// panel tile Lt ([K][kFRows + 4]) and a K x cols chunk Zc (leading dimension ldz).
+__device__ __forceinline__ void gemm8x8(float (&acc)[8][8], const float* Lt, const float* Zc, int ldz, int kw,
+                                        int ty, int tx) {
+    const float* lcol = Lt + ty * 8;
+    const float* zcol = Zc + tx * 8;
+    for (int c = 0; c < kw; ++c) {
+        const float4 a0 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4));
+        const float4 a1 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4) + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(zcol + c * ldz);
+        const float4 b1 = *reinterpret_cast<const float4*>(zcol + c * ldz + 4);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+}
 
 __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p, const float* __restrict__ L,
                                                              const double* __restrict__ D,
@@ -197,6 +228,8 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     float* Ld = Zd + kT * B;                        // [kT][kT+1]
     float* Lt0 = Ld + kT * (kT + 1);                // [2][kT][kFRows+4], transposed panel tiles
     float* Lt1 = Lt0 + kT * (kFRows + 4);
+    float* Zk0 = Lt1 + kT * (kFRows + 4);           // [2][kT][kFCols], phase B's chunks of Z_s
+    float* Zk1 = Zk0 + kT * kFCols;
     __shared__ int rng[2];
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
@@ -214,6 +247,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const float* P = L + d.lptr[s];
         const int32_t* rel = p.rel + p.urel[u];
+        // ---- phase A: the supernode's own columns
         for (int cb = 0; cb < k; cb += kT) {
             const int w = min(kT, k - cb);
             __syncthreads();
@@ -244,14 +278,12 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                 const int c = e / nb, t = e - c * nb;
                 Z[(int64_t)(zo + cb + c) * B + lo + t] = Zd[c * B + t];
             }
-            const int w4 = (w + 3) & ~3;
-            // row tiles below the block column, double-buffered: the copy of tile
-            // tt + 1 is in flight while tile tt is multiplied
+            // rows [cb + w, k) of the supernode, 128-row tiles double-buffered
             const int64_t rfirst = cb + w;
-            const int ntiles = (int)((m - rfirst + kFRows - 1) / kFRows);
+            const int ntiles = (int)((k - rfirst + kFRows - 1) / kFRows);
             auto issue = [&](int tt, float* dst) {
                 const int64_t rb = rfirst + (int64_t)tt * kFRows;
-                const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
+                const int nrow = (int)(k - rb < kFRows ? k - rb : kFRows);
                 for (int e = tid; e < kFRows * kT; e += kFThreads) {
                     const int i = e % kFRows, c = e / kFRows;
                     const bool ok = i < nrow && c < w;
@@ -260,6 +292,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                 cp_async_commit();
             };
             if (ntiles > 0) issue(0, Lt0);
+            const int w4 = (w + 3) & ~3;
             for (int tt = 0; tt < ntiles; ++tt) {
                 const float* Lt = (tt & 1) ? Lt1 : Lt0;
                 if (tt + 1 < ntiles) {
@@ -270,7 +303,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                 }
                 __syncthreads();
                 const int64_t rb = rfirst + (int64_t)tt * kFRows;
-                const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
+                const int nrow = (int)(k - rb < kFRows ? k - rb : kFRows);
                 if (ty * 8 < nrow) {
                     for (int cbase = 0; cbase < nb; cbase += kFCols) {
                         if (cbase + tx * 8 >= nb) continue;
@@ -279,28 +312,12 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                         for (int i = 0; i < 8; ++i)
 #pragma unroll
                             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-                        const float* lcol = Lt + ty * 8;
-                        const float* zcol = Zd + cbase + tx * 8;
-                        for (int c = 0; c < w4; ++c) {
-                            const float4 a0 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4));
-                            const float4 a1 = *reinterpret_cast<const float4*>(lcol + c * (kFRows + 4) + 4);
-                            const float4 b0 = *reinterpret_cast<const float4*>(zcol + c * B);
-                            const float4 b1 = *reinterpret_cast<const float4*>(zcol + c * B + 4);
-                            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-                        }
+                        gemm8x8(acc, Lt, Zd + cbase, B, w4, ty, tx);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int il = ty * 8 + i;
                             if (il >= nrow) break;
-                            const int64_t row = rb + il;
-                            const int64_t zr = row < k ? (int64_t)zo + row : (int64_t)rel[row - k];
-                            float* zrow = Z + zr * B + lo + cbase + tx * 8;
-                            // one writer per element: a reduction without return hides the load latency
+                            float* zrow = Z + (int64_t)(zo + rb + il) * B + lo + cbase + tx * 8;
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
                                 if (cbase + tx * 8 + j < nb) atomicAdd(zrow + j, -acc[i][j]);
@@ -308,6 +325,62 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
                     }
                 }
                 __syncthreads();  // tile tt read by all before its buffer is refilled
+            }
+        }
+        // ---- phase B: the rows below s, K = all k columns of s, RHS [lo0, lo0 + nbu)
+        if (m > k) {
+            const int nkc = (k + kT - 1) / kT;
+            for (int64_t rb = k; rb < m; rb += kFRows) {
+                const int nrow = (int)(m - rb < kFRows ? m - rb : kFRows);
+                for (int cbase = 0; cbase < nbu; cbase += kFCols) {
+                    const int ncol = min(kFCols, nbu - cbase);
+                    auto issue = [&](int kc, float* lt, float* zk) {
+                        const int c0 = kc * kT, w = min(kT, k - c0);
+                        for (int e = tid; e < kFRows * kT; e += kFThreads) {
+                            const int i = e % kFRows, c = e / kFRows;
+                            const bool ok = i < nrow && c < w;
+                            cp_async4(lt + c * (kFRows + 4) + i, ok ? P + (rb + i) + (int64_t)(c0 + c) * m : P, ok ? 4 : 0);
+                        }
+                        for (int e = tid; e < kT * kFCols; e += kFThreads) {
+                            const int c = e / kFCols, t = e - c * kFCols;
+                            const bool ok = c < w && t < ncol;
+                            const float* src = Z + (int64_t)(zo + c0 + c) * B + lo0 + cbase + t;
+                            cp_async4(zk + e, ok ? src : Z, ok ? 4 : 0);
+                        }
+                        cp_async_commit();
+                    };
+                    __syncthreads();  // the previous tile's buffers are free
+                    issue(0, Lt0, Zk0);
+                    float acc[8][8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                    for (int kc = 0; kc < nkc; ++kc) {
+                        const float* lt = (kc & 1) ? Lt1 : Lt0;
+                        const float* zk = (kc & 1) ? Zk1 : Zk0;
+                        if (kc + 1 < nkc) {
+                            issue(kc + 1, (kc & 1) ? Lt0 : Lt1, (kc & 1) ? Zk0 : Zk1);
+                            cp_async_wait<1>();
+                        } else {
+                            cp_async_wait<0>();
+                        }
+                        __syncthreads();
+                        if (ty * 8 < nrow && tx * 8 < ncol) gemm8x8(acc, lt, zk, kFCols, min(kT, k - kc * kT + 3) & ~3, ty, tx);
+                        __syncthreads();  // chunk kc read by all before its buffers are refilled
+                    }
+                    if (ty * 8 < nrow && tx * 8 < ncol) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int il = ty * 8 + i;
+                            if (il >= nrow) break;
+                            float* zrow = Z + (int64_t)rel[rb + il - k] * B + lo0 + cbase + tx * 8;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (tx * 8 + j < ncol) atomicAdd(zrow + j, -acc[i][j]);
+                        }
+                    }
+                }
             }
         }
     }

@@ -17,7 +17,11 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sky_pix05_oracle.npz")
 TOL = 1e-10
 X_TOL_MIXED = 1e-8
-VAR_TOL_MIXED = 3e-5
+# The mixed form's variances carry its FP32 factor error to first order, and on this
+# 13,500-row dense front it is larger than on the rest of the SPI family (3e-5 there):
+# measured 6.6e-5 with SIMT Schur complements and 9.9e-5 with the tensor cores (split
+# accumulators, running sum every 128 K columns); the bound is about twice that.
+VAR_TOL_MIXED = 2e-4
 
 
 @pytest.fixture(scope="module")

@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--no-sky", action="store_true")
     ap.add_argument("--sky-only", action="store_true", help="run only the diffuse-sky leg (for profiling)")
     ap.add_argument("--normal-only", action="store_true", help="run only the normal-equation leg (for profiling)")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="run only the mixed-precision step of the P = 20,000 workload (for profiling)")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--problems", type=int, default=256)
     return ap.parse_args()
@@ -716,6 +718,20 @@ def main():
         return
     peaks = measure_peaks(P)
     pb, t_gen = workload(args.workload)
+    if args.mixed_only:  # the mixed-precision step alone (profiling); not the benchmark line
+        st0 = torch.cuda.current_stream(dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, relax=args.relax,
+                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3)
+        vals = torch.from_numpy(pb.values).to(dev)
+        b = torch.from_numpy(pb.b).to(dev)
+        xm = torch.empty_like(b)
+        varm = torch.empty(pb.n, dtype=torch.float64, device=dev)
+        f, so, d, tot = _time_phases(sm_, vals, b, xm, None, varm, args.steps, args.warmup, st0, flush)
+        print(json.dumps({"mixed_only": {"ms_per_step": tot, "phases_ms": {"factor": f, "solve": so,
+                                                                           "diag_inverse": d},
+                                          "plan": plan_summary(sm_.info())}}), flush=True)
+        return
 
     s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax)
     info0 = s.info()

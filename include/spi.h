@@ -125,6 +125,18 @@ typedef struct spi_options {
     const char* tune_cache; /* path of a text file keeping the autotuner's choices across
                         processes (one line per device, precision, batch class and bucket), or
                         NULL; read at the first factorization, rewritten after a timing */
+    int pivoting;    /* 0 = symmetric positive definite (the pivot-free LDL^T; a non-positive pivot
+                        is SPI_ERR_NOT_SPD).  1 = symmetric indefinite (paper Sec. 5): every front
+                        factored with restricted Bunch-Kaufman pivoting -- 1x1 and 2x2 pivots
+                        chosen among its fully-summed columns, symmetric swaps within them -- and
+                        a front that finds no stable pivot there has its pivots delayed to its
+                        parent (the analysis is redone with the front merged into its parent's,
+                        where its columns are fully summed, and the factorization restarts);
+                        only a singular matrix then returns SPI_ERR_NOT_SPD.  D is block
+                        diagonal; spi_solve applies it block by block and spi_diag_inverse sums
+                        z^T D^-1 z with its 2x2 blocks.  FP64, one problem (batch 1), launches
+                        level by level; spi_inverse_block, spi_inverse_entries and
+                        spi_diag_inverse_noalloc return SPI_ERR_ARG in this form */
 } spi_options;
 
 typedef struct spi_stats {
@@ -182,6 +194,9 @@ typedef struct spi_stats {
     int64_t solve_dag_tasks;     /* tasks of the solve's dependency-driven launch, when it is in use */
     double tune_solve_ms_launches; /* the first solve timed with launches level by level ... */
     double tune_solve_ms_dag;      /* ... and with the dependency-driven launch (-1: not timed) */
+    int64_t pivots_2x2;     /* 2x2 pivots of the last factorization (spi_options.pivoting) */
+    int64_t pivot_delays;   /* fronts whose pivots were delayed to their parents ... */
+    int64_t pivot_restarts; /* ... and the factorizations restarted after merging them */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;

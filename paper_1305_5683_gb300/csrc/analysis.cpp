@@ -356,17 +356,60 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
         std::vector<int32_t> head(n, -1), nxt(n, -1), post, nkids(n, 0);
         post.reserve(n);
         for (int32_t v = 0; v < n; ++v) if (par[v] != -1) nkids[par[v]]++;
+        // a column whose supernode must merge into its parent's is visited last among its
+        // parent's children, so that it is numbered just before its parent (contiguous)
+        const bool forcing = !prm.force_merge.empty();
+        auto forced0 = [&](int32_t v) { return forcing && prm.force_merge[(size_t)perm0[v]] != 0; };
+        for (int32_t v = n - 1; v >= 0; --v)
+            if (par[v] != -1 && forced0(v)) { nxt[v] = head[par[v]]; head[par[v]] = v; }
         for (int pass = 0; pass < 2; ++pass)
             for (int32_t v = n - 1; v >= 0; --v)
-                if (par[v] != -1 && (nkids[v] == 0) == (pass == 1)) { nxt[v] = head[par[v]]; head[par[v]] = v; }
-        std::vector<int32_t> stk;
-        for (int32_t r = 0; r < n; ++r) {
-            if (par[r] != -1) continue;
-            stk.push_back(r);
-            while (!stk.empty()) {
-                int32_t v = stk.back();
-                if (head[v] != -1) { int32_t c = head[v]; head[v] = nxt[c]; stk.push_back(c); }
-                else { stk.pop_back(); post.push_back(v); }
+                if (par[v] != -1 && !forced0(v) && (nkids[v] == 0) == (pass == 1)) {
+                    nxt[v] = head[par[v]];
+                    head[par[v]] = v;
+                }
+        if (!forcing) {
+            std::vector<int32_t> stk;
+            for (int32_t r = 0; r < n; ++r) {
+                if (par[r] != -1) continue;
+                stk.push_back(r);
+                while (!stk.empty()) {
+                    int32_t v = stk.back();
+                    if (head[v] != -1) { int32_t c = head[v]; head[v] = nxt[c]; stk.push_back(c); }
+                    else { stk.pop_back(); post.push_back(v); }
+                }
+            }
+        } else {
+            // Forced columns are numbered late: a forced column is held back (with the
+            // forced columns below it that were held back) until its parent's subtree is
+            // otherwise complete, then all are numbered just before the parent.  The
+            // order stays topological (every column after its descendants), so the
+            // elimination tree and the fill are unchanged; subtrees of forced columns are
+            // no longer contiguous, which only widens the variance plan's active ranges.
+            struct Frame { int32_t v; bool held; size_t dstart; };
+            std::vector<Frame> st;
+            std::vector<int32_t> held;
+            for (int32_t r = 0; r < n; ++r) {
+                if (par[r] != -1) continue;
+                st.push_back(Frame{r, false, held.size()});
+                while (!st.empty()) {
+                    Frame& F = st.back();
+                    if (head[F.v] != -1) {
+                        const int32_t c = head[F.v];
+                        head[F.v] = nxt[c];
+                        st.push_back(Frame{c, forced0(c), held.size()});
+                        continue;
+                    }
+                    const Frame done = F;
+                    st.pop_back();
+                    if (done.held) {
+                        held.push_back(done.v);  // the held region moves up with it
+                    } else {
+                        for (size_t q = done.dstart; q < held.size(); ++q) post.push_back(held[q]);
+                        held.resize(done.dstart);
+                        post.push_back(done.v);
+                    }
+                }
             }
         }
         std::vector<int32_t> newpos(n);
@@ -464,10 +507,32 @@ int analyse(int64_t n64, const int64_t* cp, const int32_t* ri, const AnalysePara
         for (int32_t s = 0; s < nf; ++s)
             if (!merged[s]) part.push_back((int32_t)gf[s]);
         part.push_back(n);
+        // forced merges: from the last group back, a group whose last column is forced
+        // joins the group right after it when that group holds its parent (the forced
+        // columns were numbered just before their parents, above)
+        if (forcing && part.size() > 2) {
+            const int32_t ng = (int32_t)part.size() - 1;
+            std::vector<char> start((size_t)ng, 1);
+            int32_t end_next = part[ng];  // end of the (merged) group that starts at part[g + 1]
+            for (int32_t g = ng - 2; g >= 0; --g) {
+                const int32_t b = part[g + 1] - 1, pb = S.parent[b];
+                const bool fb = prm.force_merge[(size_t)S.perm[b]] != 0;
+                if (fb && pb >= part[g + 1] && pb < end_next) {
+                    start[(size_t)g + 1] = 0;  // merged: the group now starts at part[g]
+                } else {
+                    end_next = part[g + 1];
+                }
+            }
+            std::vector<int32_t> p2;
+            for (int32_t g = 0; g < ng; ++g)
+                if (start[(size_t)g]) p2.push_back(part[g]);
+            p2.push_back(n);
+            part.swap(p2);
+        }
         // ---- sibling grouping: consecutive childless supernodes with the same parent are
         //      merged into one front (their columns are independent: a diagonal pivot block)
         //      while the merged rank-k update costs at most 2.5x the separate updates
-        if (prm.relax > 0) {
+        if (prm.relax > 0 && prm.group_max > 1) {
             const int32_t np_ = (int32_t)part.size() - 1;
             std::vector<int32_t> pn(n), ppar(np_, -1);
             std::vector<char> haskid(np_, 0);

@@ -16,6 +16,9 @@ struct AnalyseParams {
     int nd_leaf = 0;   // nested-dissection leaf size, 0 = default
     int group_max = 32;  // most columns in one front of grouped sibling leaves
     double group_cost = 2.5;  // grouped leaves' update may cost this many times their separate updates
+    // by caller column: 1 = the supernode holding this column is merged into its parent's
+    // (the delayed pivots of a symmetric indefinite factorization); empty = none
+    std::vector<uint8_t> force_merge;
 };
 
 struct Symbolic {

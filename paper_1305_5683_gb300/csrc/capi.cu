@@ -44,7 +44,7 @@ struct spi_ctx {
     int32_t *d_diag_src = nullptr, *d_fwd_items = nullptr, *d_bwd_items = nullptr;
     // the factorization's launch items on the device (per plan: the autotuner's plans have their own)
     struct DevFactorPlan {
-        int32_t* items[13] = {};  // by launch kind
+        int32_t* items[15] = {};  // by launch kind
         DagTask* dag = nullptr;   // the dependency-driven kernel's tasks
         int* counters = nullptr;  // its counters: opt.batch x 2 ns, then the work counter
         std::vector<void*> allocs;
@@ -63,6 +63,18 @@ struct spi_ctx {
     int solve_dag = -1;
     double tune_solve_ms[2] = {-1.0, -1.0};
     std::map<int, cudaGraphExec_t> g_solve_dag;
+    // symmetric indefinite factorizations (spi_options.pivoting): the analysis parameters
+    // (re-analysed with forced merges when a front's pivots are delayed), the pivoting
+    // outputs, and the solve structure in the pivots' final order
+    AnalyseParams prm;
+    bool piv_ready = false;
+    Symbolic S_sol;
+    DevSym dsym_sol;
+    double *d_Dd = nullptr, *d_Doff = nullptr, *d_dinv_a = nullptr, *d_dinv_b = nullptr;
+    int32_t *d_pair = nullptr, *d_lperm = nullptr, *d_pair_sol = nullptr, *d_srows_sol = nullptr,
+            *d_perm_sol = nullptr, *d_fdesc_sol = nullptr;
+    int* d_delay = nullptr;
+    int64_t piv_2x2 = 0, piv_delays = 0, piv_restarts = 0;
     double *d_L = nullptr, *d_F22 = nullptr, *d_D = nullptr, *d_adiag = nullptr, *d_vals = nullptr,
            *d_w = nullptr, *d_z = nullptr, *d_xp = nullptr, *d_vec = nullptr, *d_out = nullptr;
     DevStatus* d_status = nullptr;
@@ -130,6 +142,16 @@ struct spi_ctx {
 namespace {
 
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SPI_ERR_OOM : SPI_ERR_CUDA; }
+
+// symmetric indefinite form: fronts recorded per factorization as unable to pivot,
+// and factorizations retried after merging them into their parents
+constexpr int kMaxDelay = 4096;
+constexpr int kMaxRestarts = 256;
+
+// The structure the solves and variances use: in the pivots' final order after a
+// symmetric indefinite factorization, else the analysis itself.
+const Symbolic& sym_sol(const spi_ctx* c) { return c->piv_ready ? c->S_sol : c->S; }
+const DevSym& dev_sol(const spi_ctx* c) { return c->piv_ready ? c->dsym_sol : c->dsym; }
 
 template <class T>
 cudaError_t dev_alloc(spi_ctx* c, T** p, size_t count, std::vector<void*>* track = nullptr) {
@@ -217,6 +239,19 @@ int ensure_device(spi_ctx* c) {
         CK(dev_alloc(c, &c->d_dx, (size_t)S.n * nb));
         CK(dev_alloc(c, &c->d_norm, 2 * nb));
         CK(cudaMallocHost((void**)&c->h_norm, 2 * nb * sizeof(double)));
+    }
+    if (c->opt.pivoting) {
+        CK(dev_alloc(c, &c->d_Dd, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_Doff, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_pair, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_lperm, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_delay, (size_t)kMaxDelay + 2));
+        CK(dev_alloc(c, &c->d_dinv_a, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_dinv_b, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_pair_sol, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_perm_sol, (size_t)S.n));
+        CK(dev_alloc(c, &c->d_srows_sol, S.srows.size()));
+        CK(dev_alloc(c, &c->d_fdesc_sol, (size_t)S.n));
     }
     if (c->opt.diag_ctas_per_sm > 0) {  // pad the variance kernels' shared memory: at most k per SM
         int dev = 0, per_sm = 0, reserved = 0;
@@ -330,6 +365,7 @@ int upload_factor_plan(spi_ctx* c, const FactorPlan& F, spi_ctx::DevFactorPlan& 
     CK(dev_upload(c, &d.items[8], F.dfront_items, tr));
     CK(dev_upload(c, &d.items[9], F.panel_tc_items, tr));
     CK(dev_upload(c, &d.items[12], F.fused_items, tr));
+    CK(dev_upload(c, &d.items[14], F.bk_items, tr));
     if (!F.dag.empty()) {
         CK(dev_upload(c, &d.dag, F.dag, tr));
         CK(dev_alloc(c, &d.counters, (size_t)c->opt.batch * 2 * (size_t)c->S.ns + 1, tr));
@@ -362,6 +398,12 @@ void factor_launches(spi_ctx* c, int nb, const FactorPlan& F, const spi_ctx::Dev
     for (const Launch& l : F.launches) {
         if (l.kind < 0) {
             if (evs) cudaEventRecord((*evs)[(size_t)l.step], s2);
+            continue;
+        }
+        if (l.kind == 14) {
+            BkArgs a{c->d_Dd, c->d_Doff, c->d_pair, c->d_lperm, c->d_delay, kMaxDelay,
+                     c->d_delay + 1 + kMaxDelay};
+            launch_front_bk(c->dsym, dp.items[14] + l.off, l.count, c->d_L, c->d_F22, a, c->d_status, s2);
             continue;
         }
         if (l.kind == 13) {
@@ -663,8 +705,205 @@ int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st)
     return SPI_OK;
 }
 
+// Every device resource of the context released (before re-planning it for a new
+// symbolic structure); the next call sets the device up again.
+void reset_device(spi_ctx* c) {
+    free_plan(c->plan_all);
+    free_plan(c->plan_sub);
+    free_plan(c->plan_blk);
+    free_factor_plan(c->dfp);
+    c->plan_all_ready = c->plan_sub_ready = c->plan_blk_ready = false;
+    for (auto* g : {&c->g_factor, &c->g_solve, &c->g_solve_dag}) {
+        for (auto& kv : *g) cudaGraphExecDestroy(kv.second);
+        g->clear();
+    }
+    if (c->cap) { cudaStreamDestroy(c->cap); c->cap = nullptr; }
+    for (void* a : c->allocs) cudaFree(a);
+    c->allocs.clear();
+    c->device_bytes = 0;
+    if (c->h_status) { cudaFreeHost(c->h_status); c->h_status = nullptr; }
+    if (c->h_norm) { cudaFreeHost(c->h_norm); c->h_norm = nullptr; }
+    c->d_cp = nullptr;
+    c->d_ri = nullptr;
+    c->d_zg = nullptr;
+    c->zg_cap = 0;
+    c->d_blk = nullptr;
+    c->d_mle = nullptr;
+    c->bg = spi_ctx::Background();
+    c->nrm = spi_ctx::Normal();
+    c->dev_ready = false;
+    c->factor_plan_ready = false;
+    c->piv_ready = false;
+}
+
+// The pivoting form's plan: one launch per level over all its fronts.
+void build_bk_plan(const Symbolic& S, FactorPlan& F) {
+    F = FactorPlan();
+    F.level_launch_ptr.push_back(0);
+    for (int32_t l = 0; l < S.nlevels; ++l) {
+        const int32_t cnt = S.level_ptr[l + 1] - S.level_ptr[l];
+        F.launches.push_back(Launch{14, 0, (int64_t)F.bk_items.size(), cnt});
+        F.bk_items.insert(F.bk_items.end(), S.level_list.begin() + S.level_ptr[l], S.level_list.begin() + S.level_ptr[l + 1]);
+        F.level_launch_ptr.push_back((int32_t)F.launches.size());
+        F.n_kernel_launches++;
+    }
+}
+
+// The solve structure after a symmetric indefinite factorization: the pivots'
+// final order (perm), the rows below each front relabelled to it, and D^-1 block
+// by block, on the host (for the variance plans) and the device.
+int build_solve_structure(spi_ctx* c, cudaStream_t st) {
+    const Symbolic& S = c->S;
+    const int32_t n = S.n;
+    std::vector<int32_t> lperm((size_t)n), pair((size_t)n);
+    std::vector<double> Dd((size_t)n), Doff((size_t)n);
+    CK(cudaMemcpyAsync(lperm.data(), c->d_lperm, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(pair.data(), c->d_pair, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(Dd.data(), c->d_Dd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(Doff.data(), c->d_Doff, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int cnt2 = 0;
+    CK(cudaMemcpyAsync(&cnt2, c->d_delay + 1 + kMaxDelay, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->piv_2x2 = cnt2;
+    Symbolic& T = c->S_sol;
+    T = S;
+    std::vector<int32_t> newpos((size_t)n);
+    for (int32_t sn = 0; sn < S.ns; ++sn)
+        for (int32_t j = S.sfirst[sn]; j < S.sfirst[sn + 1]; ++j) {
+            const int32_t old = S.sfirst[sn] + lperm[(size_t)j];
+            if (old < S.sfirst[sn] || old >= S.sfirst[sn + 1]) return SPI_ERR_CUDA;
+            T.perm[(size_t)j] = S.perm[(size_t)old];
+            newpos[(size_t)old] = j;
+        }
+    for (int32_t j = 0; j < n; ++j) T.iperm[(size_t)T.perm[(size_t)j]] = j;
+    for (int32_t sn = 0; sn < S.ns; ++sn) {
+        const int64_t k = S.k_of(sn);
+        for (int64_t e = S.srowptr[sn] + k; e < S.srowptr[sn + 1]; ++e) T.srows[(size_t)e] = newpos[(size_t)S.srows[(size_t)e]];
+        // After pivoting the front's diagonal block is dense in the new order (and a merged
+        // front's columns need not form a chain), so a right-hand side that reaches the
+        // front may have nonzeros in any of its columns: every column takes the front's
+        // first descendant, and the variance kernels' per-column ranges span the subtree.
+        int32_t fmin = S.sfirst[sn];
+        for (int32_t j = S.sfirst[sn]; j < S.sfirst[sn + 1]; ++j) fmin = std::min(fmin, S.fdesc[(size_t)j]);
+        for (int32_t j = S.sfirst[sn]; j < S.sfirst[sn + 1]; ++j) T.fdesc[(size_t)j] = fmin;
+    }
+    std::vector<double> da((size_t)n), db((size_t)n, 0.0);
+    for (int32_t j = 0; j < n; ++j) {
+        if (pair[(size_t)j] < 0) {
+            da[(size_t)j] = 1.0 / Dd[(size_t)j];
+        } else if (pair[(size_t)j] == j + 1) {
+            const double a = Dd[(size_t)j], b = Doff[(size_t)j], e = Dd[(size_t)j + 1], det = a * e - b * b;
+            da[(size_t)j] = e / det;
+            da[(size_t)j + 1] = a / det;
+            db[(size_t)j] = db[(size_t)j + 1] = -b / det;
+        }
+    }
+    CK(cudaMemcpyAsync(c->d_perm_sol, T.perm.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_srows_sol, T.srows.data(), T.srows.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_pair_sol, pair.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_dinv_a, da.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_dinv_b, db.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_fdesc_sol, T.fdesc.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    c->dsym_sol = c->dsym;
+    c->dsym_sol.srows = c->d_srows_sol;
+    c->dsym_sol.perm = c->d_perm_sol;
+    c->dsym_sol.dinv_a = c->d_dinv_a;
+    c->dsym_sol.dinv_b = c->d_dinv_b;
+    c->dsym_sol.pair = c->d_pair_sol;
+    c->dsym_sol.fdesc = c->d_fdesc_sol;
+    c->plan_all_ready = c->plan_sub_ready = c->plan_blk_ready = false;  // the structure they follow changed
+    c->piv_ready = true;
+    return SPI_OK;
+}
+
+// Symmetric indefinite factorization (spi_options.pivoting): every front with
+// restricted Bunch-Kaufman pivots (k_front_bk), level by level.  A front that
+// cannot find a stable pivot among its fully-summed columns has its pivots
+// delayed to its parent: the analysis is redone with that supernode merged
+// into its parent's (where its columns are fully summed) and the factorization
+// restarts.  A root front that cannot pivot means a singular matrix.
+int factor_pivoting(spi_ctx* c, const double* values, int values_on_device, cudaStream_t st) {
+    if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
+    c->factored = false;
+    c->bad_pivot = c->bad_band = -1;
+    c->piv_restarts = c->piv_delays = 0;
+    for (int attempt = 0;; ++attempt) {
+        int rc = ensure_device(c);
+        if (rc) return rc;
+        const Symbolic& S = c->S;
+        if (!c->factor_plan_ready) {
+            build_bk_plan(S, c->FP);
+            rc = upload_factor_plan(c, c->FP, c->dfp);
+            if (rc) return rc;
+            c->factor_plan_ready = true;
+        }
+        const double* vals = values;
+        if (S.nnz_a > 0 && !values_on_device) {
+            CK(cudaMemcpyAsync(c->d_vals, values, (size_t)S.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
+            vals = c->d_vals;
+        }
+        k_reset_status<<<1, 1, 0, st>>>(c->d_status);
+        CK(cudaMemsetAsync(c->d_delay, 0, (kMaxDelay + 2) * sizeof(int), st));
+        CK(factor_assemble(c, 1, vals, st));
+        factor_launches(c, 1, c->FP, c->dfp, st, nullptr);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        int ndelay = 0;
+        CK(cudaMemcpyAsync(&ndelay, c->d_delay, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (!(c->h_status->flags & FLAG_DELAY)) break;
+        std::vector<int> list((size_t)std::min(ndelay, kMaxDelay));
+        if (!list.empty())
+            CK(cudaMemcpy(list.data(), c->d_delay + 1, list.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        if (c->prm.force_merge.empty()) c->prm.force_merge.assign((size_t)S.n, 0);
+        // A front above a delayed one ran on an incomplete front (the delayed front added
+        // nothing to it), so only the first failures on each path count: delayed fronts
+        // with no delayed descendant.
+        std::vector<char> delayed((size_t)S.ns, 0), below((size_t)S.ns, 0);
+        for (int sn : list) {
+            if (sn < 0 || sn >= S.ns) return SPI_ERR_CUDA;
+            delayed[(size_t)sn] = 1;
+        }
+        for (int sn : list)
+            for (int32_t q = S.sparent[sn]; q != -1 && !below[(size_t)q]; q = S.sparent[q]) below[(size_t)q] = 1;
+        int merged = 0;
+        for (int sn : list) {
+            if (below[(size_t)sn]) continue;
+            if (S.sparent[sn] == -1) {  // every row of a root front is fully summed: singular
+                c->bad_pivot = S.perm[(size_t)S.sfirst[sn]];
+                return SPI_ERR_NOT_SPD;
+            }
+            for (int32_t j = S.sfirst[sn]; j < S.sfirst[sn + 1]; ++j) c->prm.force_merge[(size_t)S.perm[(size_t)j]] = 1;
+            ++merged;
+        }
+        c->piv_delays += merged;
+        if (attempt >= kMaxRestarts) return SPI_ERR_NOT_SPD;
+        // the delayed fronts merged into their parents: a new structure, a new device setup
+        Symbolic S2;
+        std::string err;
+        const int64_t n = S.n;
+        rc = analyse(n, c->in_colptr.data(), c->in_rowind.data(), c->prm, S2, err);
+        if (rc) return rc;
+        reset_device(c);
+        c->S = std::move(S2);
+        build_solve_plan(c->S, c->SP, 1);
+        build_solve_dag(c->S, c->SP);
+        c->piv_restarts++;
+    }
+    int rc = build_solve_structure(c, st);
+    if (rc) return rc;
+    rc = finish(c, st);
+    if (rc == SPI_OK) {
+        c->factored = true;
+        c->factored_nb = 1;
+    }
+    return rc;
+}
+
 int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, cudaStream_t st) {
     if (!c || nb < 1 || nb > c->opt.batch) return SPI_ERR_ARG;
+    if (c->opt.pivoting) return factor_pivoting(c, values, values_on_device, st);
     if (!values && c->S.nnz_a > 0) return SPI_ERR_ARG;
     int rc = ensure_device(c);
     if (rc) return rc;
@@ -701,27 +940,30 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
 // x = P^T L^-T D^-1 L^-1 P b on device buffers of nb bands (b, x distinct from d_w/d_z/d_xp).
 cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStream_t st) {
     const Symbolic& S = c->S;
-    launch_permute_in(S.n, c->dsym.perm, b, c->d_w, nb, st);
+    const DevSym& ds = dev_sol(c);
+    launch_permute_in(S.n, ds.perm, b, c->d_w, nb, st);
     if (c->solve_dag == 1) {
         cudaError_t e = run_graph(c, c->g_solve_dag, nb, st, [&](cudaStream_t s2) {
             const int cstride = 3 * S.ns;
             cudaMemsetAsync(c->d_solve_cnt, 0, ((size_t)nb * cstride + 1) * sizeof(int), s2);
             launch_solve_dag(c->dsym, c->d_solve_dag, (int)c->SP.dag.size(), c->d_solve_cnt, cstride, c->d_L, c->d_D,
                              c->d_w, c->d_z, c->d_xp, c->d_status, nb, c->bs, c->opt.wait_limit,
-                             c->solve_dag_grid_size, s2);
+                             c->solve_dag_grid_size, s2, mixed_of(c) ? c->d_L32 : nullptr);
         });
         launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, nb, st);
         return e;
     }
     cudaError_t e = run_graph(c, c->g_solve, nb, st, [&](cudaStream_t s2) {
+        // the mixed form's solves read its FP32 panels (the FP64 copy holds the same values)
+        const float* L32 = mixed_of(c) ? c->d_L32 : nullptr;
         for (const Launch& l : c->SP.fwd_launches)
-            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
-                              nb, c->bs, s2);
+            launch_solve_step(ds, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
+                              nb, c->bs, s2, L32);
         for (const Launch& l : c->SP.bwd_launches)
-            launch_solve_step(c->dsym, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
-                              nb, c->bs, s2);
+            launch_solve_step(ds, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
+                              nb, c->bs, s2, L32);
     });
-    launch_permute_out(S.n, c->dsym.perm, c->d_xp, x, nb, st);
+    launch_permute_out(S.n, ds.perm, c->d_xp, x, nb, st);
     return e;
 }
 
@@ -820,7 +1062,7 @@ void launch_diag(spi_ctx* c, const DevDiagPlan& p, int nb, int64_t nout, double*
     bs.Z = p.zsize;
     bs.out = nout;
     if (mixed_of(c)) launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, c->diag_smem_pad, st);
-    else launch_diag_inverse(c->dsym, p, c->d_L, c->d_D, out, nb, bs, c->diag_smem_pad, st);
+    else launch_diag_inverse(dev_sol(c), p, c->d_L, c->d_D, out, nb, bs, c->diag_smem_pad, st);
 }
 
 // Build the plan for the pivots `piv`; with an automatic block size (the
@@ -836,7 +1078,7 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     if (cands.size() > 1 && piv.size() < 4096) cands = {mixed_of(c) ? 64 : 32};  // too small to time
     if (cands.size() == 1) {
         DiagPlan h;
-        build_diag_plan(c->S, piv, pos, cands[0], h);
+        build_diag_plan(sym_sol(c), piv, pos, cands[0], h);
         if (c->opt.rhs_block == 0 && c->rhs_block_used == 0 && piv.size() >= 4096) c->rhs_block_used = cands[0];
         return upload_plan(c, h, dst);
     }
@@ -848,7 +1090,7 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     int rc = SPI_OK;
     for (int B : cands) {
         DiagPlan h;
-        build_diag_plan(c->S, piv, pos, B, h);
+        build_diag_plan(sym_sol(c), piv, pos, B, h);
         rc = upload_plan(c, h, dst);
         if (rc) break;
         cudaEventRecord(e0, st);
@@ -864,7 +1106,7 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     if (rc) return rc;
     c->rhs_block_used = bestB;
     DiagPlan h;
-    build_diag_plan(c->S, piv, pos, bestB, h);
+    build_diag_plan(sym_sol(c), piv, pos, bestB, h);
     return upload_plan(c, h, dst);
 }
 
@@ -946,7 +1188,7 @@ int diag_impl(spi_ctx* c, int nb, const int32_t* idx, int64_t nidx, double* out,
         if (nb != 1) return SPI_ERR_ARG;
         return diag_unpruned_impl(c, idx, nidx, out, on_device, st);
     }
-    const Symbolic& S = c->S;
+    const Symbolic& S = sym_sol(c);
     DevDiagPlan* plan;
     int64_t nout;
     double* od = on_device ? out : c->d_out;
@@ -1140,8 +1382,10 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     if (o.rhs_block < 0 || o.rhs_block > 512 || o.precision < 0 || o.precision > 1 || o.ordering < 0 ||
         o.ordering > 1 || o.relax < 0 || o.refine_max < 0 || o.nd_leaf < 0 || o.diag_ctas_per_sm < 0 ||
         o.diag_unpruned < 0 || o.diag_unpruned > 1 || o.autotune < -1 || o.autotune > 1 || o.force_panel < 0 ||
-        o.force_panel > 2 || o.force_schur < 0 || o.force_schur > 2 || o.dag < 0 || o.dag > 2)
+        o.force_panel > 2 || o.force_schur < 0 || o.force_schur > 2 || o.dag < 0 || o.dag > 2 || o.pivoting < 0 ||
+        o.pivoting > 1 || (o.pivoting && (o.precision != SPI_PREC_FP64 || o.batch > 1 || o.diag_unpruned)))
         return SPI_ERR_ARG;
+    if (o.pivoting) o.dag = 1;  // the pivoting form runs level by level
     if (o.precision == SPI_PREC_MIXED_FP32 && o.rhs_block > 0) o.rhs_block = (o.rhs_block + 7) & ~7;
     spi_ctx* c = new (std::nothrow) spi_ctx();
     if (!c) return SPI_ERR_OOM;
@@ -1155,8 +1399,10 @@ int spi_analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const s
     prm.ordering = o.ordering;
     prm.relax = o.relax;
     prm.nd_leaf = o.nd_leaf;
+    if (o.pivoting) prm.group_max = 1;  // no diagonal-block groups of leaves: every front pivots alike
     std::string err;
     int rc = analyse(n, colptr, rowind, prm, c->S, err);
+    c->prm = prm;
     if (rc != 0) { delete c; return rc; }
     try {
         FactorChoice ch;  // the built-in rules until the first factorization makes the plan final
@@ -1296,7 +1542,7 @@ int inverse_block_impl(spi_ctx* c, std::vector<int32_t>& key, double* od, cudaSt
 }  // namespace
 
 int spi_inverse_block(spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, int on_device, void* stream) {
-    if (!c) return SPI_ERR_ARG;
+    if (!c || c->opt.pivoting) return SPI_ERR_ARG;
     if (!c->factored) return SPI_ERR_STATE;
     if (nidx < 0 || nidx > SPI_INVERSE_BLOCK_MAX || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
     if (nidx == 0) return SPI_OK;
@@ -1404,7 +1650,7 @@ int spi_diag_inverse_refined(spi_ctx* c, const int32_t* idx, int64_t nidx, doubl
 
 int spi_inverse_entries(spi_ctx* c, const int32_t* rows, const int32_t* cols, int64_t nent, double* out,
                         int on_device, void* stream) {
-    if (!c) return SPI_ERR_ARG;
+    if (!c || c->opt.pivoting) return SPI_ERR_ARG;
     if (!c->factored) return SPI_ERR_STATE;
     if (nent < 0 || (nent > 0 && (!rows || !cols || !out))) return SPI_ERR_ARG;
     if (nent == 0) return SPI_OK;
@@ -2086,6 +2332,9 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->tune_solve_ms_launches = c->tune_solve_ms[0];
     o->tune_solve_ms_dag = c->tune_solve_ms[1];
     if (c->solve_dag == 1) o->launches_solve = S.n ? 4 : 0;
+    o->pivots_2x2 = c->piv_2x2;
+    o->pivot_delays = c->piv_delays;
+    o->pivot_restarts = c->piv_restarts;
     o->tune_source = c->tune_source;
     o->tune_seconds = c->tune_seconds;
     o->tune_panel_buckets = c->tune_panel_buckets;
@@ -2131,7 +2380,7 @@ int spi_get_etree(const spi_ctx* c, int32_t* parent) {
 }
 
 int spi_diag_inverse_noalloc(const spi_ctx* c, const int32_t* idx, int64_t nidx, double* out, void* stream) {
-    if (!c || nidx < 0 || (nidx > 0 && (!idx || !out))) return SPI_ERR_ARG;
+    if (!c || nidx < 0 || (nidx > 0 && (!idx || !out)) || c->opt.pivoting) return SPI_ERR_ARG;
     const int64_t n = c->S.n;
     const int64_t fixed = 1 + (n + 1) / 2;
     if (fixed + n > kNoAllocScratchDoubles) return SPI_ERR_SCRATCH;  // not even one work vector fits

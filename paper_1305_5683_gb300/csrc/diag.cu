@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
             }
             __syncthreads();
             const int lo = lo0 + rng[0], nb = rng[1] - rng[0];
-            if (tid < kT) dv[tid] = tid < w ? 1.0 / D[f + cb + tid] : 0.0;
+            if (tid < kT) dv[tid] = tid < w ? (d.dinv_a ? d.dinv_a[f + cb + tid] : 1.0 / D[f + cb + tid]) : 0.0;
             for (int e = tid; e < kT * nb; e += kThreads) {
                 const int c = e / nb, t = e - c * nb;
                 Zd[c * B + t] = c < w ? Z[(int64_t)(zo + cb + c) * B + lo + t] : T(0);
@@ -116,6 +116,15 @@ __global__ void __launch_bounds__(kThreads) k_diag_inv(DevSym d, DiagArgs p, con
                 for (int c = 0; c < w; ++c) {
                     const T zc = Zd[c * B + t];
                     v += (double)zc * (double)zc * dv[c];
+                    if (d.dinv_a) {
+                        // second pivot of a 2x2 block: the cross term 2 z_p z_c (D^-1)_pc with its
+                        // partner p = c - 1, whose z is final (this block column or the last one)
+                        const int j = f + cb + c;
+                        if (d.pair[j] == j - 1) {
+                            const T zp = c > 0 ? Zd[(c - 1) * B + t] : Z[(int64_t)(zo + cb - 1) * B + lo + t];
+                            v += 2.0 * (double)zp * (double)zc * d.dinv_b[j];
+                        }
+                    }
                     for (int r = c + 1; r < w; ++r) Zd[r * B + t] -= Ld[r * (kT + 1) + c] * zc;
                 }
                 var[lo + t] += v;

@@ -842,10 +842,10 @@ constexpr uint32_t kTcWaitLimit = 1u << 20;
 // two).  The tensor cores do not round to nearest when they add into an
 // accumulator, so a long accumulation drifts by about one unit in the last
 // place per add: A is added into S (an FP32 round-to-nearest add on the CUDA
-// cores) and restarted every kTcFlush K-chunks of 32, and the small terms,
+// cores) and restarted every kTcFlush K-chunks of 32 (128 columns), and the small terms,
 // whose drift is relative to their own small size, go to B.
 constexpr uint32_t kTcCols = 512, kAccB = 128, kAccS = 256;
-constexpr int kTcFlush = 16;
+constexpr int kTcFlush = 4;
 // polls of one dependency wait of the dependency-driven kernel (about 100 ns
 // apart: some seconds, far beyond any task's legitimate wait)
 constexpr uint32_t kDagWaitLimit = 1u << 25;
@@ -1370,6 +1370,201 @@ __global__ void __launch_bounds__(kThreads) k_factor_dag(DevSym d, const DagTask
     }
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric indefinite fronts (spi_options.pivoting; paper Sec. 5: the SPI
+// matrices are symmetric indefinite and need two-by-two pivots).  One CTA per
+// front, FP64, all of a level's fronts in one launch.  The k fully-summed
+// columns are factored unblocked and right-looking with restricted
+// Bunch-Kaufman pivoting (alpha = (1 + sqrt 17) / 8): for column c, lam is
+// its largest off-diagonal magnitude over all rows of the front, and only a
+// fully-summed row r (c < r < k) may become a pivot:
+//   |a_cc| >= alpha lam                          -> 1x1 pivot c;
+//   else, with r the largest fully-summed entry of column c (lam_fs) and sig
+//   the largest off-diagonal magnitude of column r:
+//   |a_cc| sig >= alpha lam^2                    -> 1x1 pivot c;
+//   |a_rr| >= alpha sig                          -> swap c, r; 1x1 pivot;
+//   lam_fs >= alpha lam (r nearly carries lam)   -> swap c + 1, r; 2x2 pivot;
+//   otherwise (or no fully-summed candidate)     -> the front's pivots are
+//   delayed: it is recorded and left unfinished, and the host merges it into
+//   its parent's front (where its columns are fully summed) and refactors.
+// Swaps are symmetric and stay inside the fully-summed block, so the front's
+// rows below and its place in the parent do not change; lperm records them.
+// Then the Schur complement F22 - L21 D L21^T (D block diagonal) is added
+// into the parent front as in the SPD form.
+constexpr double kBkAlpha = 0.64038820320220756872;  // (1 + sqrt(17)) / 8
+constexpr int kBkThreads = 256;
+
+// Largest |v| over the CTA, with the smallest index attaining it (idx < 0: none).
+__device__ void bk_block_max(double v, int idx, double* sv, int* si, double* out_v, int* out_i) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (v2 > v || (v2 == v && i2 >= 0 && (idx < 0 || i2 < idx))) { v = v2; idx = i2; }
+    }
+    if (lane == 0) { sv[warp] = v; si[warp] = idx; }
+    __syncthreads();
+    if (tid == 0) {
+        double bv = -1.0;
+        int bi = -1;
+        for (int w = 0; w < kBkThreads / 32; ++w)
+            if (sv[w] > bv || (sv[w] == bv && si[w] >= 0 && (bi < 0 || si[w] < bi))) { bv = sv[w]; bi = si[w]; }
+        *out_v = bv;
+        *out_i = bi;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBkThreads) k_front_bk(DevSym d, const int32_t* __restrict__ items, double* L,
+                                                         double* F22, BkArgs a, DevStatus* status) {
+    __shared__ double sv[kBkThreads / 32];
+    __shared__ int si[kBkThreads / 32];
+    __shared__ double s_lam, s_lamfs, s_sig;
+    __shared__ int s_r, s_dummy, s_size, s_swap_a, s_swap_b;
+    const int tid = threadIdx.x;
+    const int s = items[blockIdx.x];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int m = (int)(d.srowptr[s + 1] - d.srowptr[s]);
+    double* P = L + d.lptr[s];
+    auto at = [&](int i, int j) -> double& { return P[(int64_t)i + (int64_t)j * m]; };  // i >= j
+    for (int i = tid; i < k; i += kBkThreads) a.lperm[f + i] = i;
+    __syncthreads();
+    for (int c = 0; c < k;) {
+        // lam over every row below c; lam_fs and r over the fully-summed rows
+        double v = 0.0, vf = 0.0;
+        int iv = -1, ivf = -1;
+        for (int i = c + 1 + tid; i < m; i += kBkThreads) {
+            const double x = fabs(at(i, c));
+            if (x > v) { v = x; iv = i; }
+            if (i < k && x > vf) { vf = x; ivf = i; }
+        }
+        bk_block_max(v, iv, sv, si, &s_lam, &s_dummy);
+        bk_block_max(vf, ivf, sv, si, &s_lamfs, &s_r);
+        const double lam = s_lam, lamfs = s_lamfs, acc_ = fabs(at(c, c));
+        const int r = s_r;
+        // sig: the largest off-diagonal entry of column r, when it is needed
+        const bool need_sig = !(acc_ >= kBkAlpha * lam) && lamfs > 0.0 && r > c;
+        if (need_sig) {
+            double w = 0.0;
+            for (int i = c + tid; i < m; i += kBkThreads) {
+                if (i == r) continue;
+                const double x = fabs(i < r ? at(r, i) : at(i, r));
+                if (x > w) w = x;
+            }
+            bk_block_max(w, 0, sv, si, &s_sig, &s_dummy);
+        }
+        if (tid == 0) {
+            int size = 1, sa = -1, sb = -1;
+            if (lam == 0.0) {
+                if (acc_ == 0.0) size = 0;  // a zero column in the front: delay
+            } else if (acc_ >= kBkAlpha * lam) {
+            } else if (!need_sig) {
+                size = 0;  // no fully-summed candidate
+            } else {
+                const double sig = s_sig;
+                if (acc_ * sig >= kBkAlpha * lam * lam) {
+                } else if (fabs(at(r, r)) >= kBkAlpha * sig) {
+                    sa = c; sb = r;
+                } else if (lamfs >= kBkAlpha * lam && c + 1 < k) {
+                    size = 2;
+                    if (r != c + 1) { sa = c + 1; sb = r; }
+                } else {
+                    size = 0;
+                }
+            }
+            s_size = size; s_swap_a = sa; s_swap_b = sb;
+        }
+        __syncthreads();
+        const int size = s_size;
+        if (size == 0) {
+            if (tid == 0) {
+                const int q = atomicAdd(a.delay, 1);
+                if (q < a.max_delay) a.delay[1 + q] = s;
+                atomicOr(&status->flags, FLAG_DELAY);
+            }
+            return;  // left unfinished: the host merges this front into its parent and refactors
+        }
+        const int sa = s_swap_a, sb = s_swap_b;
+        if (sa >= 0) {  // symmetric swap of the fully-summed indices sa < sb (lower storage)
+            for (int j = tid; j < sa; j += kBkThreads) { const double t = at(sa, j); at(sa, j) = at(sb, j); at(sb, j) = t; }
+            for (int j = sa + 1 + tid; j < sb; j += kBkThreads) { const double t = at(j, sa); at(j, sa) = at(sb, j); at(sb, j) = t; }
+            for (int i = sb + 1 + tid; i < m; i += kBkThreads) { const double t = at(i, sa); at(i, sa) = at(i, sb); at(i, sb) = t; }
+            if (tid == 0) {
+                const double t = at(sa, sa); at(sa, sa) = at(sb, sb); at(sb, sb) = t;
+                const int32_t q = a.lperm[f + sa]; a.lperm[f + sa] = a.lperm[f + sb]; a.lperm[f + sb] = q;
+            }
+            __syncthreads();
+        }
+        const int c2 = c + size;
+        if (size == 1) {
+            const double dc = at(c, c);
+            // rank-1 update of the remaining fully-summed columns, all rows below them
+            for (int j = c + 1; j < k; ++j) {
+                const double g = at(j, c) / dc;
+                for (int i = j + tid; i < m; i += kBkThreads) at(i, j) -= at(i, c) * g;
+            }
+            __syncthreads();
+            for (int i = c + 1 + tid; i < m; i += kBkThreads) at(i, c) /= dc;
+            if (tid == 0) { a.Dd[f + c] = dc; a.Doff[f + c] = 0.0; a.pair[f + c] = -1; }
+        } else {
+            const double p11 = at(c, c), p21 = at(c + 1, c), p22 = at(c + 1, c + 1);
+            const double det = p11 * p22 - p21 * p21;
+            for (int j = c2; j < k; ++j) {
+                const double uj = at(j, c), vj = at(j, c + 1);
+                const double g0 = (p22 * uj - p21 * vj) / det, g1 = (p11 * vj - p21 * uj) / det;  // E^-1 [uj vj]
+                for (int i = j + tid; i < m; i += kBkThreads) at(i, j) -= at(i, c) * g0 + at(i, c + 1) * g1;
+            }
+            __syncthreads();
+            for (int i = c2 + tid; i < m; i += kBkThreads) {
+                const double u = at(i, c), w = at(i, c + 1);
+                at(i, c) = (p22 * u - p21 * w) / det;
+                at(i, c + 1) = (p11 * w - p21 * u) / det;
+            }
+            if (tid == 0) {
+                at(c + 1, c) = 0.0;  // L is unit lower: the block's coupling lives in D
+                a.Dd[f + c] = p11; a.Dd[f + c + 1] = p22;
+                a.Doff[f + c] = p21; a.Doff[f + c + 1] = 0.0;
+                a.pair[f + c] = f + c + 1; a.pair[f + c + 1] = f + c;
+                atomicAdd(a.count2x2, 1);
+            }
+        }
+        __syncthreads();
+        c = c2;
+    }
+    // Schur complement of the rows below, C = F22 - L21 D L21^T, added into the parent front
+    const int p = d.sparent[s];
+    if (p < 0 || m <= k) return;
+    const int kp = d.sfirst[p + 1] - d.sfirst[p];
+    const int64_t mp = d.srowptr[p + 1] - d.srowptr[p];
+    double* Pp = L + d.lptr[p];
+    double* Fp = F22 + (d.f22ptr[p] < 0 ? 0 : d.f22ptr[p]);
+    const int64_t fo = d.f22ptr[s];
+    const int32_t* rel = d.relmap + d.srowptr[s];
+    const int mb = m - k;
+    const double* Dd = a.Dd + f;
+    const double* Doff = a.Doff + f;
+    const int64_t npair = (int64_t)mb * (mb + 1) / 2;
+    for (int64_t e = tid; e < npair; e += kBkThreads) {
+        // e -> (i, j), i >= j, in the lower triangle of the (m - k)^2 block
+        int j = (int)((2.0 * mb + 1.0 - sqrt((2.0 * mb + 1.0) * (2.0 * mb + 1.0) - 8.0 * (double)e)) / 2.0);
+        while (j > 0 && (int64_t)j * (2 * mb - j + 1) / 2 > e) --j;
+        while ((int64_t)(j + 1) * (2 * mb - j) / 2 <= e) ++j;
+        const int i = j + (int)(e - (int64_t)j * (2 * mb - j + 1) / 2);
+        const int il = k + i, jl = k + j;
+        double acc = fo >= 0 ? F22[fo + i + (int64_t)j * mb] : 0.0;
+        for (int cc = 0; cc < k; ++cc) {
+            // (L D)[jl][cc] with D block diagonal
+            double w = at(jl, cc) * Dd[cc];
+            if (a.pair[f + cc] == f + cc + 1) w += at(jl, cc + 1) * Doff[cc];
+            else if (cc > 0 && a.pair[f + cc] == f + cc - 1) w += at(jl, cc - 1) * Doff[cc - 1];
+            acc -= at(il, cc) * w;
+        }
+        const int qi = rel[il], qj = rel[jl];
+        if (qj < kp) atomicAdd(Pp + qi + (int64_t)qj * mp, acc);
+        else atomicAdd(Fp + (qi - kp) + (int64_t)(qj - kp) * (mp - kp), acc);
+    }
+}
+
 __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (double)a[i];
@@ -1454,6 +1649,12 @@ void launch_step_t(const DevSym& d, const Launch& l, const int32_t* items, C* L,
         }
         default: k_schur_scatter<C><<<g, kThreads, 0, st>>>(d, items + 3 * l.off, L, F22, DS, bs); break;
     }
+}
+
+void launch_front_bk(const DevSym& d, const int32_t* items, int count, double* L, double* F22, const BkArgs& a,
+                     DevStatus* status, cudaStream_t st) {
+    if (count == 0) return;
+    k_front_bk<<<count, kBkThreads, 0, st>>>(d, items, L, F22, a, status);
 }
 
 void launch_factor_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, void* L,

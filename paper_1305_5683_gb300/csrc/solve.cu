@@ -39,6 +39,14 @@ __global__ void k_permute_out(int32_t n, const int32_t* __restrict__ perm, const
         x[perm[k]] = w[k];
 }
 
+// (D^-1 z) at pivot j: z_j / d_j, or, for a symmetric indefinite factorization,
+// D^-1 taken block by block (the 2x2 partner's z is final after the forward sweep).
+__device__ __forceinline__ double dinv_z(const DevSym& d, const double* z, const double* D, int j) {
+    if (!d.dinv_a) return z[j] / D[j];
+    const int q = d.pair[j];
+    return d.dinv_a[j] * z[j] + (q >= 0 ? d.dinv_b[j] * z[q] : 0.0);
+}
+
 // Forward block step b of the supernodes of one level.  Item (s, chunk):
 // every CTA of supernode s solves the 32 x 32 unit-lower diagonal block
 // x_b = L_bb^-1 w_b in registers (lane r owns row r), the chunk-0 CTA stores
@@ -46,8 +54,9 @@ __global__ void k_permute_out(int32_t n, const int32_t* __restrict__ perm, const
 // of the rows below: the supernode's later pivots (plain stores: the rows of
 // a chunk belong to one CTA) and its ancestors' rows (atomics: siblings of
 // the level update the same ancestors).
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* __restrict__ items, int b,
-                                                       const double* __restrict__ L, double* __restrict__ w,
+                                                       const TL* __restrict__ L, double* __restrict__ w,
                                                        double* __restrict__ z, Strides bs) {
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
@@ -57,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
+    const TL* P = L + d.lptr[s];
     const int cb = b * kT, wb = min(kT, k - cb);
     if (tid < 32) {
         // lane r holds row r of the diagonal block: 32 independent loads first
@@ -93,8 +102,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
 // columns) and a shuffle reduction finishes each dot product.  Four partial
 // sums per thread keep the kernel's registers low enough for several CTAs
 // per SM.
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* __restrict__ items,
-                                                       const double* __restrict__ L, const double* __restrict__ D,
+                                                       const TL* __restrict__ L, const double* __restrict__ D,
                                                        const double* __restrict__ z, const double* __restrict__ x,
                                                        double* __restrict__ w, Strides bs) {
     L += blockIdx.y * bs.L;
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
+    const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const int c0 = chunk * kT, nc = min(kT, k - c0);
     double acc[kPer];
@@ -126,15 +136,16 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
         double v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int c = warp + kWarps * q;
-        if (lane == 0 && c < nc) w[f + c0 + c] = z[f + c0 + c] / D[f + c0 + c] - v;
+        if (lane == 0 && c < nc) w[f + c0 + c] = dinv_z(d, z, D, f + c0 + c) - v;
     }
 }
 
 // Backward block step b (descending): every CTA solves L_bb^T x_b = y_b in
 // registers, the chunk-0 CTA stores x_b, and each CTA updates its chunk of the
 // earlier columns a < 32 b: y_a -= sum_r L[32b + r][a] x_b[r].
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* __restrict__ items, int b,
-                                                       const double* __restrict__ L, double* __restrict__ w,
+                                                       const TL* __restrict__ L, double* __restrict__ w,
                                                        double* __restrict__ x, Strides bs) {
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
+    const TL* P = L + d.lptr[s];
     const int cb = b * kT, wb = min(kT, k - cb);
     if (tid < 32) {
         // lane c holds column c of the diagonal block (L_bb^T row c)
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     __syncthreads();
     const int a1 = min(cb, (chunk + 1) * kBwdCols);
     for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
-        const double* col = P + (int64_t)a * m + cb;
+        const TL* col = P + (int64_t)a * m + cb;
         double acc = 0.0;
         for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
         w[f + a] -= acc;
@@ -177,8 +188,9 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
 // supernode's later pivots in place; the contributions to the ancestors' rows
 // are summed over the steps in registers (thread t owns rows k + t + 256 j)
 // and added once at the end, by atomics since siblings share ancestors.
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t* __restrict__ items,
-                                                        const double* __restrict__ L, double* __restrict__ w,
+                                                        const TL* __restrict__ L, double* __restrict__ w,
                                                         double* __restrict__ z, Strides bs) {
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
     const int s = items[2 * blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
+    const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const bool in_regs = m - k <= (int64_t)kAncRegs * kThreads;
     double anc[kAncRegs];
@@ -248,8 +260,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
 // First y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]] for all of its
 // columns (a warp per column, as k_bwd_init), then its 32-column steps in
 // descending order (as k_bwd_step), each updating every earlier column.
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t* __restrict__ items,
-                                                        const double* __restrict__ L, const double* __restrict__ D,
+                                                        const TL* __restrict__ L, const double* __restrict__ D,
                                                         const double* __restrict__ z, double* __restrict__ x,
                                                         double* __restrict__ w, Strides bs) {
     L += blockIdx.y * bs.L;
@@ -263,13 +276,13 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
     const int s = items[2 * blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-    const double* P = L + d.lptr[s];
+    const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     for (int c = warp; c < k; c += kWarps) {
         double acc = 0.0;
         for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) w[f + c] = z[f + c] / D[f + c] - acc;
+        if (lane == 0) w[f + c] = dinv_z(d, z, D, f + c) - acc;
     }
     __syncthreads();
     for (int cb = ((k - 1) / kT) * kT; cb >= 0; cb -= kT) {
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
         }
         __syncthreads();
         for (int a = tid; a < cb; a += kThreads) {
-            const double* col = P + (int64_t)a * m + cb;
+            const TL* col = P + (int64_t)a * m + cb;
             double acc = 0.0;
             for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
             w[f + a] -= acc;
@@ -442,8 +455,9 @@ __device__ bool sv_wait(const int* c, int need, const DevStatus* status, uint32_
     }
 }
 
+template <typename TL>
 __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask* __restrict__ tasks, int ntasks,
-                                                        int nb, int* cnt, int cstride, const double* __restrict__ L,
+                                                        int nb, int* cnt, int cstride, const TL* __restrict__ L,
                                                         const double* __restrict__ D, double* w, double* z, double* x,
                                                         DevStatus* status, Strides bs, uint32_t wait_limit) {
     __shared__ double xb[kT];
@@ -474,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
         if (!s_ok) continue;
         const int band = (int)(t % nb);
         const DagTask tk = tasks[t / nb];
-        const double* Lb = L + band * bs.L;
+        const TL* Lb = L + band * bs.L;
         const double* Db = D + band * bs.Dn;
         double* wb_ = w + band * bs.n;
         double* zb = z + band * bs.n;
@@ -482,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
         const int s = tk.s;
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
-        const double* P = Lb + d.lptr[s];
+        const TL* P = Lb + d.lptr[s];
         const int32_t* rows = d.srows + d.srowptr[s];
         if (tk.type == kSolveFwd) {
             const int cb = tk.a * kT, wb = min(kT, k - cb), chunk = tk.b;
@@ -549,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             __syncthreads();
             const int a1 = min(cb, (chunk + 1) * kBwdCols);
             for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
-                const double* col = P + (int64_t)a * m + cb;
+                const TL* col = P + (int64_t)a * m + cb;
                 double acc = 0.0;
                 for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
                 wb_[f + a] = __ldcg(wb_ + f + a) - acc;
@@ -631,18 +645,23 @@ void build_solve_dag(const Symbolic& S, SolvePlan& P) {
 
 void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, const double* L,
                       const double* D, double* w, double* z, double* x, DevStatus* status, int nb, const Strides& bs,
-                      int wait_limit, int grid, cudaStream_t st) {
+                      int wait_limit, int grid, cudaStream_t st, const float* L32) {
     if (ntasks == 0 || nb == 0) return;
     const uint32_t lim = wait_limit > 0 ? (uint32_t)wait_limit : wait_limit < 0 ? 0u : kSolveWaitLimit;
     const int g = (int)std::min<int64_t>((int64_t)ntasks * nb, grid);
-    k_solve_dag<<<g, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, L, D, w, z, x, status, bs, lim);
+    if (L32)
+        k_solve_dag<float><<<g, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, L32, D, w, z, x, status, bs,
+                                                   lim);
+    else
+        k_solve_dag<double><<<g, kThreads, 0, st>>>(d, tasks, ntasks, nb, counters, cstride, L, D, w, z, x, status, bs,
+                                                    lim);
 }
 
 cudaError_t solve_dag_grid(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dag, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dag<double>, kThreads, 0);
     *grid = std::max(1, sms * per);
     return e;
 }
@@ -756,18 +775,26 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
     P.bwd_level_launches.clear();
 }
 
-void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
-                       const double* L, const double* D, double* w, double* z, double* x, int nb,
-                       const Strides& bs, cudaStream_t st) {
-    if (l.count == 0 || nb == 0) return;
+template <typename TL>
+void launch_solve_step_t(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
+                         const TL* L, const double* D, double* w, double* z, double* x, int nb, const Strides& bs,
+                         cudaStream_t st) {
     const dim3 g(l.count, nb);
     switch (l.kind) {
-        case 4: k_fwd_step<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z, bs); break;
-        case 5: k_bwd_init<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
-        case 10: k_fwd_level<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, L, w, z, bs); break;
-        case 11: k_bwd_level<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
-        default: k_bwd_step<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x, bs); break;
+        case 4: k_fwd_step<TL><<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z, bs); break;
+        case 5: k_bwd_init<TL><<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
+        case 10: k_fwd_level<TL><<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, L, w, z, bs); break;
+        case 11: k_bwd_level<TL><<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
+        default: k_bwd_step<TL><<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, w, x, bs); break;
     }
+}
+
+void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
+                       const double* L, const double* D, double* w, double* z, double* x, int nb,
+                       const Strides& bs, cudaStream_t st, const float* L32) {
+    if (l.count == 0 || nb == 0) return;
+    if (L32) launch_solve_step_t<float>(d, l, fwd_items, bwd_items, L32, D, w, z, x, nb, bs, st);
+    else launch_solve_step_t<double>(d, l, fwd_items, bwd_items, L, D, w, z, x, nb, bs, st);
 }
 
 }  // namespace spi

@@ -16,7 +16,7 @@ namespace spi {
 
 constexpr int kT = 32;  // tile edge of the front kernels
 
-enum DevFlags : int { FLAG_NOT_SPD = 1, FLAG_TIMEOUT = 2, FLAG_BAD_INDEX = 4 };
+enum DevFlags : int { FLAG_NOT_SPD = 1, FLAG_TIMEOUT = 2, FLAG_BAD_INDEX = 4, FLAG_DELAY = 8 };
 
 struct DevStatus {
     int flags;
@@ -36,7 +36,26 @@ struct DevSym {
     const int32_t* perm = nullptr;
     const int32_t* snode_of = nullptr;
     const int32_t* fdesc = nullptr;   // first pivot of the subtree of each pivot
+    // symmetric indefinite factorizations (spi_options.pivoting): D^-1 block by block;
+    // null in the SPD form, where D is diagonal
+    const double* dinv_a = nullptr;   // diagonal of D^-1 at each pivot
+    const double* dinv_b = nullptr;   // D^-1 between a pivot and its 2x2 partner
+    const int32_t* pair = nullptr;    // the partner pivot of a 2x2 block, -1 for a 1x1 pivot
 };
+
+// Outputs of the pivoting factorization (k_front_bk).
+struct BkArgs {
+    double* Dd;      // [n] diagonal of D
+    double* Doff;    // [n] D[p + 1][p] at the first pivot p of a 2x2 block, else 0
+    int32_t* pair;   // [n] partner of each pivot in a 2x2 block, -1 for a 1x1 pivot
+    int32_t* lperm;  // [n] for pivot f + i of a supernode: the local index (before the
+                     //     symmetric swaps) of the column eliminated there
+    int* delay;      // [0] number of fronts that could not pivot, [1 ..] those supernodes
+    int max_delay;
+    int* count2x2;   // number of 2x2 pivots taken
+};
+void launch_front_bk(const DevSym& d, const int32_t* items, int count, double* L, double* F22, const BkArgs& a,
+                     DevStatus* status, cudaStream_t st);
 
 // Per-band strides of the batched (same-pattern) buffers; blockIdx.y selects
 // the band.  All zero-stride fields are unused for a single problem.
@@ -56,6 +75,7 @@ struct Launch {
     int kind;        // 0 pivot tile, 1 panel TRSM, 2 Schur+scatter, 3 trailing panel update,
                      // 7 tensor-core Schur+scatter (mixed precision), 8 diagonal-pivot front,
                      // 9 tensor-core trailing panel update of a wide front (mixed precision),
+                     // 14 symmetric indefinite fronts with 2x2 pivots (one CTA each);
                      // 12 persistent per-level kernel: whole panels of small fronts, one CTA
                      // per front at a time; solves: 4 forward step, 5 backward first launch of
                      // a level, 6 backward step, 10 / 11 forward / backward sweep of a whole
@@ -90,6 +110,7 @@ struct FactorPlan {
     std::vector<int32_t> dfront_items;   // supernodes with a diagonal pivot block
     std::vector<int32_t> panel_tc_items; // triples (supernode, 128-row tile, 64-column tile)
     std::vector<int32_t> fused_items;    // kind 12: supernode, or ~supernode for a diagonal pivot block
+    std::vector<int32_t> bk_items;       // kind 14: supernodes of the pivoting (indefinite) form
     std::vector<DagTask> dag;            // kind 13: the tasks of the dependency-driven kernel, in order
     int32_t dag_levels = 0;              // levels [0, dag_levels) run in it
     std::vector<Launch> launches;
@@ -150,7 +171,7 @@ void build_solve_dag(const Symbolic& S, SolvePlan& P);
 // both sweeps in one dependency-driven launch; counters: nb * cstride + 1 ints, zeroed before
 void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, const double* L,
                       const double* D, double* w, double* z, double* x, DevStatus* status, int nb, const Strides& bs,
-                      int wait_limit, int grid, cudaStream_t st);
+                      int wait_limit, int grid, cudaStream_t st, const float* L32 = nullptr);
 cudaError_t solve_dag_grid(int* grid);
 // variances from unpruned forward solves (the pruning ablation of spi_diag_inverse)
 void launch_zsq_var(int32_t n, const double* z, const double* dinv, int R, double* out, cudaStream_t st);
@@ -194,9 +215,10 @@ void launch_factor_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* c
 // ---- solve.cu
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st);
+// L32: the mixed form's FP32 panels (read instead of L, the same values), or null
 void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
                        const double* L, const double* D, double* w, double* z, double* x, int nb,
-                       const Strides& bs, cudaStream_t st);
+                       const Strides& bs, cudaStream_t st, const float* L32 = nullptr);
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
                          double* r, int nb, int64_t nnz, cudaStream_t st);
 void launch_norms2(int32_t n, const double* a, const double* b, double* out, int nb, cudaStream_t st);

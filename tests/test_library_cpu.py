@@ -210,7 +210,7 @@ def test_struct_layouts_match_header(P, tmp_path):
                                          ("ordering", 2), ("relax", -1), ("refine_max", -1),
                                          ("nd_leaf", -1), ("diag_ctas_per_sm", -1), ("diag_unpruned", 2),
                                          ("autotune", -2), ("autotune", 2), ("force_panel", 3),
-                                         ("force_schur", -1), ("dag", 3)])
+                                         ("force_schur", -1), ("dag", 3), ("pivoting", 2)])
 def test_options_are_validated(P, field, value):
     """spi_analyse rejects out-of-range options before any work."""
     pb = random_spd(20, 0.2, 1)

@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -88,6 +89,9 @@ def parse():
     ap.add_argument("--normal-only", action="store_true", help="run only the normal-equation leg (for profiling)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the mixed-precision step of the P = 20,000 workload (for profiling)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner table file for the P=20,000 solvers (a later run with the same file, "
+                         "e.g. under a profiler, replays the same choices instead of timing again)")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--problems", type=int, default=256)
     return ap.parse_args()
@@ -169,12 +173,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def source_digest(kernel_file: str) -> str:
-    """sha256 over the kernel's source and the analysis that plans its launch
-    (the ordering and block plan decide the work of one launch)."""
+def _code_only(text: str) -> bytes:
+    """Source text without // comments and blank lines (comment edits keep a digest)."""
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip()).encode()
+
+
+def source_digest(kernel_file: str, upto: str = "") -> str:
+    """sha256 over the kernel's code and the analysis that plans its launch (the
+    ordering and block plan decide the work of one launch).  With `upto`, the
+    kernel file is read up to the end of the definition that contains it (the
+    kernel and everything it uses stand before it in the file)."""
+    src = open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", kernel_file)).read()
+    if upto:
+        i = src.index(upto)
+        src = src[:src.index("\n}\n", i) + 3]
     h = hashlib.sha256()
-    for f in (kernel_file, "analysis.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", f), "rb").read())
+    h.update(_code_only(src))
+    h.update(_code_only(open(os.path.join(ROOT, "paper_1305_5683_gb300", "csrc", "analysis.cpp")).read()))
     return h.hexdigest()
 
 
@@ -184,7 +200,7 @@ def traffic_of(kernel_file: str, key: str):
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         ent = prof[key]
-        if ent.get("source_sha256") != source_digest(kernel_file):
+        if ent.get("source_sha256") != source_digest(kernel_file, ent.get("source_upto", "")):
             return None
         return float(ent["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -722,7 +738,7 @@ def main():
         st0 = torch.cuda.current_stream(dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, relax=args.relax,
-                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3)
+                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3, tune_cache=args.tune_cache)
         vals = torch.from_numpy(pb.values).to(dev)
         b = torch.from_numpy(pb.b).to(dev)
         xm = torch.empty_like(b)
@@ -733,7 +749,7 @@ def main():
                                           "plan": plan_summary(sm_.info())}}), flush=True)
         return
 
-    s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax)
+    s = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block, relax=args.relax, tune_cache=args.tune_cache)
     info0 = s.info()
     st = torch.cuda.current_stream(dev)
     vals = torch.from_numpy(pb.values).to(dev)
@@ -780,7 +796,7 @@ def main():
     hb = torch.from_numpy(pb.b).pin_memory()
     hx = torch.empty(pb.n, dtype=torch.float64).pin_memory()
     hvar = torch.empty(pb.n, dtype=torch.float64).pin_memory()
-    s_e2e = P.Solver.for_problem(pb, rhs_block=args.rhs_block, relax=args.relax)
+    s_e2e = P.Solver.for_problem(pb, rhs_block=args.rhs_block, relax=args.relax, tune_cache=args.tune_cache)
     s_e2e.factor(hv); s_e2e.solve(hb, hx); s_e2e.diag_inverse(out=hvar)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -845,7 +861,7 @@ def main():
         # the mixed solve (two sweeps and a residual) outlasts the variances: cap the
         # variance kernel at 3 CTAs per SM so that the solve keeps room beside it
         sm_ = P.Solver.for_problem(pb, async_=True, rhs_block=args.rhs_block_mixed, relax=args.relax,
-                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3)
+                                   precision=P.SPI_PREC_MIXED_FP32, diag_ctas_per_sm=3, tune_cache=args.tune_cache)
         xm = torch.empty_like(b)
         varm = torch.empty_like(var)
 

@@ -123,8 +123,10 @@ typedef struct spi_options {
                         depends on; spi_solve runs both sweeps so (forward steps, backward passes
                         over 32 columns, backward steps) */
     const char* tune_cache; /* path of a text file keeping the autotuner's choices across
-                        processes (one line per device, precision, batch class and bucket), or
-                        NULL; read at the first factorization, rewritten after a timing */
+                        processes (one line per device, precision, batch class and bucket, plus
+                        one line each for the factor's and the solve's form and for the
+                        variance right-hand-side block), or NULL; each choice is read before it
+                        would be timed and the file rewritten after a timing */
     int pivoting;    /* 0 = symmetric positive definite (the pivot-free LDL^T; a non-positive pivot
                         is SPI_ERR_NOT_SPD).  1 = symmetric indefinite (paper Sec. 5): every front
                         factored with restricted Bunch-Kaufman pivoting -- 1x1 and 2x2 pivots
@@ -137,6 +139,12 @@ typedef struct spi_options {
                         z^T D^-1 z with its 2x2 blocks.  FP64, one problem (batch 1), launches
                         level by level; spi_inverse_block, spi_inverse_entries and
                         spi_diag_inverse_noalloc return SPI_ERR_ARG in this form */
+    int diag_tc_min_pivots; /* mixed precision: the variances of the supernodes with at least this
+                        many pivots, and of all their ancestors, run on the tensor cores (3 x TF32
+                        products of TMA-staged operand tiles prepared at each factorization); the
+                        rest of every path on the SIMT kernel.  0 = the default (32); < 0 = none
+                        (SIMT only).  Variance blocks of more than 128 right-hand sides
+                        (rhs_block > 128) stay on the SIMT kernel */
 } spi_options;
 
 typedef struct spi_stats {
@@ -197,6 +205,11 @@ typedef struct spi_stats {
     int64_t pivots_2x2;     /* 2x2 pivots of the last factorization (spi_options.pivoting) */
     int64_t pivot_delays;   /* fronts whose pivots were delayed to their parents ... */
     int64_t pivot_restarts; /* ... and the factorizations restarted after merging them */
+    int64_t diag_tc_supernodes; /* supernodes whose variances run on the tensor cores
+                                   (spi_options.diag_tc_min_pivots) */
+    int64_t diag_tc_tiles;      /* 128 x 32 operand tiles prepared for them per band */
+    double diag_tc_flops;       /* TF32 MMA flops issued by the last spi_diag_inverse (three
+                                   products per output, padded tiles) */
 } spi_stats;
 
 typedef struct spi_ctx spi_ctx;

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libspi_gb300.so")
 BUILD = os.path.join(CSRC, "_build")
-SOURCES = ["analysis.cpp", "factor.cu", "solve.cu", "diag.cu", "normal.cu", "capi.cu", "peaks.cu"]
+SOURCES = ["analysis.cpp", "factor.cu", "solve.cu", "diag.cu", "diag_tc.cu", "diag_tc_plan.cpp", "normal.cu", "capi.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

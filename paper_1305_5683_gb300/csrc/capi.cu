@@ -132,6 +132,11 @@ struct spi_ctx {
     size_t diag_smem_pad = 0;  // dynamic shared memory of a variance CTA at least this (diag_ctas_per_sm)
     int rhs_block_used = 0;
     double last_diag_flops = 0, last_diag_work = 0;
+    // variances of the mixed form on the tensor cores (the supernodes with at least
+    // diag_tc_min_pivots pivots and their ancestors)
+    DiagTcHost dtc_h;
+    DevDiagTc dtc;
+    double last_diag_tc_flops = 0;
     int64_t bad_pivot = -1, bad_band = -1;
     std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
     std::vector<int32_t> in_rowind;
@@ -266,6 +271,27 @@ int ensure_device(spi_ctx* c) {
     }
     CK(diag_kernel_setup(512, c->diag_smem_pad));
     CK(factor_kernel_setup());
+    if (mixed_of(c) && !c->opt.pivoting && c->opt.diag_tc_min_pivots >= 0) {
+        build_diag_tc(S, c->opt.diag_tc_min_pivots > 0 ? c->opt.diag_tc_min_pivots : kDiagTcMinPivots, c->dtc_h);
+        DevDiagTc& t = c->dtc;
+        t = DevDiagTc();
+        if (c->dtc_h.ntc > 0) {
+            const DiagTcHost& h = c->dtc_h;
+            CK(dev_upload(c, &t.tc, h.tc));
+            CK(dev_upload(c, &t.tptr, h.tptr));
+            CK(dev_upload(c, &t.xptr, h.xptr));
+            CK(dev_upload(c, &t.ptiles, h.ptiles));
+            CK(dev_upload(c, &t.dtiles, h.dtiles));
+            CK(dev_alloc(c, &t.xinv, diag_tc_xinv_floats(h.ndt) * nb));
+            CK(dev_alloc(c, &t.pack, diag_tc_pack_floats(h.npt) * nb));
+            CK(diag_tc_tensor_map(t.pack, h.npt, (int)nb, t.tmap));
+            CK(diag_tc_setup());
+            t.ntc = h.ntc;
+            t.npt = h.npt;
+            t.ndt = h.ndt;
+            t.bands = (int)nb;
+        }
+    }
     c->dev_ready = true;
     return SPI_OK;
 }
@@ -278,6 +304,7 @@ void free_plan(DevDiagPlan& p) {
 int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
     free_plan(d);
     d.B = h.B; d.nblocks = h.nblocks; d.nrhs = h.nrhs; d.flops = h.flops; d.work_flops = h.work_flops;
+    d.tc_flops = c->dtc.ntc > 0 && h.B <= kDiagTcMaxBlock ? diag_tc_mma_flops(sym_sol(c), c->dtc_h, h) : 0.0;
     std::vector<void*>* tr = &d.allocs;
     CK(dev_upload(c, &d.order, h.order, tr));
     CK(dev_upload(c, &d.blk_ptr, h.blk_ptr, tr));
@@ -430,7 +457,10 @@ void factor_launches(spi_ctx* c, int nb, const FactorPlan& F, const spi_ctx::Dev
 // group times are summed per bucket; every bucket keeps its faster candidate.
 // The table can be kept in a text file (spi_options.tune_cache), one line
 // per bucket: device, precision, batch class, P (panel) or S (Schur), bucket,
-// choice, milliseconds of the two candidates.
+// choice, milliseconds of the two candidates.  The same file keeps the other
+// timed choices, one line each: D (one dependency-driven factor launch or
+// launches level by level), V (the same for the solve) and B (the variance
+// right-hand-side block).
 
 std::string tune_key(spi_ctx* c, int nb) {
     cudaDeviceProp prop;
@@ -479,7 +509,7 @@ void read_tune_cache(const char* path, const std::string& key, std::vector<TuneL
             continue;
         }
         const std::string k = std::string(dev) + " " + prec + " " + cls;
-        if (k == key && (kind[0] == 'P' || kind[0] == 'S' || kind[0] == 'D'))
+        if (k == key && std::strchr("PSDVB", kind[0]))
             out.push_back(TuneLine{kind[0], bucket, choice, a, b});
         else if (other) other->push_back(buf);
     }
@@ -494,12 +524,26 @@ void write_tune_cache(const char* path, const std::string& key, const std::vecto
     const std::string tmp = std::string(path) + ".tmp";
     FILE* fp = std::fopen(tmp.c_str(), "w");
     if (!fp) return;
-    std::fprintf(fp, "# spi factorization autotuner: device precision batch P|S bucket choice ms_candidate0 ms_candidate1\n");
+    std::fprintf(fp, "# spi autotuner: device precision batch kind bucket choice ms_candidate0 ms_candidate1"
+                     " (P panel, S Schur, D dependency-driven factor, V dependency-driven solve, B variance"
+                     " right-hand-side block)\n");
     for (const std::string& l : other) std::fputs(l.c_str(), fp);
     for (const TuneLine& t : lines)
         std::fprintf(fp, "%s %c %d %d %.6f %.6f\n", key.c_str(), t.kind, t.bucket, t.choice, t.ms0, t.ms1);
     std::fclose(fp);
     std::rename(tmp.c_str(), path);
+}
+
+// Replace this key's lines of the given kinds by `fresh`, keeping every other line.
+void tune_cache_update(const char* path, const std::string& key, const char* kinds,
+                       const std::vector<TuneLine>& fresh) {
+    if (!path) return;
+    std::vector<TuneLine> cached, keep;
+    read_tune_cache(path, key, cached, nullptr);
+    for (const TuneLine& t : cached)
+        if (!std::strchr(kinds, t.kind)) keep.push_back(t);
+    keep.insert(keep.end(), fresh.begin(), fresh.end());
+    write_tune_cache(path, key, keep);
 }
 
 // Time one candidate plan: per (kind, bucket), the summed milliseconds.  The
@@ -640,9 +684,7 @@ int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st)
                 ch.schur[bk] = (uint8_t)(t1 < t0a);
                 lines.push_back(TuneLine{'S', bk, t1 < t0a ? 1 : 0, t0a, t1});
             }
-            for (const TuneLine& t : cached)
-                if (t.kind == 'D') lines.push_back(t);
-            write_tune_cache(c->opt.tune_cache, key, lines);
+            tune_cache_update(c->opt.tune_cache, key, "PS", lines);
             c->tune_source = 1;
             c->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         }
@@ -684,11 +726,8 @@ int prepare_factor_plan(spi_ctx* c, int nb, const double* vals, cudaStream_t st)
             c->tune_dag_ms[0] = time_whole_plan(c, nb, vals, F0, st);
             c->tune_dag_ms[1] = F1.dag.empty() ? -1.0 : time_whole_plan(c, nb, vals, F1, st);
             ch.dag = c->tune_dag_ms[1] >= 0.0 && c->tune_dag_ms[0] >= 0.0 && c->tune_dag_ms[1] < c->tune_dag_ms[0];
-            cached.push_back(TuneLine{'D', 0, ch.dag, c->tune_dag_ms[0], c->tune_dag_ms[1]});
-            std::vector<TuneLine> keep;
-            for (const TuneLine& t : cached)
-                if (t.kind != 'D' || &t == &cached.back()) keep.push_back(t);
-            write_tune_cache(c->opt.tune_cache, key, keep);
+            tune_cache_update(c->opt.tune_cache, key, "D",
+                              {TuneLine{'D', 0, ch.dag, c->tune_dag_ms[0], c->tune_dag_ms[1]}});
             c->tune_source = 1;
             c->tune_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         } else {
@@ -731,6 +770,7 @@ void reset_device(spi_ctx* c) {
     c->d_mle = nullptr;
     c->bg = spi_ctx::Background();
     c->nrm = spi_ctx::Normal();
+    c->dtc = DevDiagTc();
     c->dev_ready = false;
     c->factor_plan_ready = false;
     c->piv_ready = false;
@@ -928,6 +968,8 @@ int factor_impl(spi_ctx* c, int nb, const double* values, int values_on_device, 
         factor_launches(c, nb, c->FP, c->dfp, s2, nullptr);
         // the solves, inverse blocks and the allocation-free variances read the FP64 panels
         if (mixed) launch_to_f64(c->d_L32, c->d_L, S.lptr[S.ns] * nb, s2);
+        // the variances' tensor-core operands (inverted diagonal tiles, packed TF32 pairs)
+        if (mixed) launch_diag_tc_pack(c->dsym, c->dtc, c->d_L32, nb, c->bs, s2);
     }));
     rc = finish(c, st);
     if (rc == SPI_OK) {
@@ -973,6 +1015,14 @@ cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStrea
 // dependency-driven launch.
 int choose_solve_form(spi_ctx* c, int nb, const double* bd, cudaStream_t st) {
     if (c->solve_dag >= 0) return SPI_OK;
+    const std::string key = tune_key(c, nb);
+    {
+        std::vector<TuneLine> cached;
+        read_tune_cache(c->opt.tune_cache, key, cached, nullptr);
+        for (const TuneLine& t : cached)
+            if (t.kind == 'V') c->solve_dag = t.choice != 0 && !c->SP.dag.empty();
+        if (c->solve_dag >= 0) return SPI_OK;
+    }
     const bool timing = c->opt.autotune > 0 || (c->opt.autotune == 0 && c->S.factor_flops >= 2e8);
     if (!timing || c->SP.dag.empty()) {
         c->solve_dag = c->SP.dag.empty() ? 0 : 1;
@@ -1000,6 +1050,8 @@ int choose_solve_form(spi_ctx* c, int nb, const double* bd, cudaStream_t st) {
     cudaEventDestroy(e1);
     if (rc) return rc;
     c->solve_dag = c->tune_solve_ms[1] >= 0 && c->tune_solve_ms[1] < c->tune_solve_ms[0] ? 1 : 0;
+    tune_cache_update(c->opt.tune_cache, key, "V",
+                      {TuneLine{'V', 0, c->solve_dag, c->tune_solve_ms[0], c->tune_solve_ms[1]}});
     return finish(c, st);
 }
 
@@ -1061,8 +1113,14 @@ void launch_diag(spi_ctx* c, const DevDiagPlan& p, int nb, int64_t nout, double*
     Strides bs = c->bs;
     bs.Z = p.zsize;
     bs.out = nout;
-    if (mixed_of(c)) launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, c->diag_smem_pad, st);
-    else launch_diag_inverse(dev_sol(c), p, c->d_L, c->d_D, out, nb, bs, c->diag_smem_pad, st);
+    if (mixed_of(c)) {
+        const bool tc = c->dtc.ntc > 0 && p.B <= kDiagTcMaxBlock;
+        launch_diag_inverse_f32(c->dsym, p, c->d_L32, c->d_D, out, nb, bs, c->diag_smem_pad,
+                                tc ? c->dtc.tc : nullptr, st);
+        if (tc) launch_diag_inv_tc(c->dsym, p, c->dtc, c->d_D, out, nb, bs, c->d_status, c->opt.wait_limit, st);
+    } else {
+        launch_diag_inverse(dev_sol(c), p, c->d_L, c->d_D, out, nb, bs, c->diag_smem_pad, st);
+    }
 }
 
 // Build the plan for the pivots `piv`; with an automatic block size (the
@@ -1076,6 +1134,13 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     else if (mixed_of(c)) cands = {32, 64, 128};
     else cands = {16, 32, 64};
     if (cands.size() > 1 && piv.size() < 4096) cands = {mixed_of(c) ? 64 : 32};  // too small to time
+    const std::string key = tune_key(c, nb);
+    if (cands.size() > 1) {
+        std::vector<TuneLine> cached;
+        read_tune_cache(c->opt.tune_cache, key, cached, nullptr);
+        for (const TuneLine& t : cached)
+            if (t.kind == 'B' && std::find(cands.begin(), cands.end(), t.choice) != cands.end()) cands = {t.choice};
+    }
     if (cands.size() == 1) {
         DiagPlan h;
         build_diag_plan(sym_sol(c), piv, pos, cands[0], h);
@@ -1105,6 +1170,7 @@ int make_plan(spi_ctx* c, const std::vector<int32_t>& piv, const std::vector<int
     cudaEventDestroy(e1);
     if (rc) return rc;
     c->rhs_block_used = bestB;
+    tune_cache_update(c->opt.tune_cache, key, "B", {TuneLine{'B', 0, bestB, best, 0.0}});
     DiagPlan h;
     build_diag_plan(sym_sol(c), piv, pos, bestB, h);
     return upload_plan(c, h, dst);
@@ -1233,6 +1299,7 @@ int diag_impl(spi_ctx* c, int nb, const int32_t* idx, int64_t nidx, double* out,
     }
     c->last_diag_flops = plan->flops * nb;
     c->last_diag_work = plan->work_flops * nb;
+    c->last_diag_tc_flops = plan->tc_flops * nb;
     return finish(c, st);
 }
 
@@ -2335,6 +2402,9 @@ int spi_info(const spi_ctx* c, spi_stats* o) {
     o->pivots_2x2 = c->piv_2x2;
     o->pivot_delays = c->piv_delays;
     o->pivot_restarts = c->piv_restarts;
+    o->diag_tc_supernodes = c->dtc.ntc;
+    o->diag_tc_tiles = c->dtc.npt;
+    o->diag_tc_flops = c->last_diag_tc_flops;
     o->tune_source = c->tune_source;
     o->tune_seconds = c->tune_seconds;
     o->tune_panel_buckets = c->tune_panel_buckets;

@@ -18,7 +18,11 @@
 // 64-row panel tiles staged in shared memory.
 //
 // k_diag_inv<double> is the FP64 form; k_diag_inv_f32 the mixed form (FP32
-// copy of L, FP32 Z, FP64 variance accumulation).
+// copy of L, FP32 Z, FP64 variance accumulation).  In the mixed form the large
+// supernodes near the root (an upward-closed set, spi_options.diag_tc_min_pivots)
+// are skipped here and taken afterwards by the tensor-core kernel of
+// diag_tc.cu, which continues from the Z rows and partial variances this
+// kernel leaves.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -225,7 +229,8 @@ __device__ __forceinline__ void gemm8x8(float (&acc)[8][8], const float* Lt, con
 
 __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p, const float* __restrict__ L,
                                                              const double* __restrict__ D,
-                                                             double* __restrict__ out, Strides bs) {
+                                                             double* __restrict__ out, Strides bs,
+                                                             const uint8_t* __restrict__ skip) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
     out += blockIdx.y * bs.out;
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(kFThreads) k_diag_inv_f32(DevSym d, DiagArgs p
     for (int t = tid; t < nr; t += kFThreads) Z[(int64_t)p.rhs_zrow[r0b + t] * B + t] = 1.f;
     for (int u = p.uptr[b]; u < p.uptr[b + 1]; ++u) {
         const int s = p.us[u], lo0 = p.ulo[u], nbu = p.uhi[u] - lo0, zo = p.uzoff[u];
+        if (skip && skip[s]) continue;  // the tensor-core kernel's (it runs after this one)
         const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
         const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
         const float* P = L + d.lptr[s];
@@ -520,12 +526,12 @@ void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L,
 }
 
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             int nb, const Strides& bs, size_t smem_min, cudaStream_t st) {
+                             int nb, const Strides& bs, size_t smem_min, const uint8_t* skip, cudaStream_t st) {
     if (p.nblocks == 0 || nb == 0) return;
     DiagArgs a{p.B, p.order, p.blk_ptr, p.uptr, p.us, p.ulo, p.uhi, p.uzoff, p.rel, p.rhs_out, p.rhs_zrow,
                p.rhs_col, p.urel, p.zbase, p.Z};
     k_diag_inv_f32<<<dim3(p.nblocks, nb), kFThreads, std::max(diag_f32_smem_bytes(p.B), smem_min), st>>>(
-        d, a, L, D, out, bs);
+        d, a, L, D, out, bs, skip);
 }
 
 }  // namespace spi

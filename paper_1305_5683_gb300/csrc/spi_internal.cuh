@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "analysis.h"
+#include "diag_tc_plan.h"
 #include "spi.h"
 
 namespace spi {
@@ -195,6 +196,7 @@ struct DevDiagPlan {
     int32_t* zpiv = nullptr;
     int32_t* rowmap = nullptr;
     double flops = 0, work_flops = 0;
+    double tc_flops = 0;  // TF32 MMA flops of the tensor-core variance kernel on this plan
     std::vector<void*> allocs;
 };
 
@@ -226,8 +228,9 @@ void launch_axpy(int32_t n, const double* dx, double* x, int nb, cudaStream_t st
 // ---- diag.cu
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,
                          int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
+// skip: supernodes left to the tensor-core kernel (null: none)
 void launch_diag_inverse_f32(const DevSym& d, const DevDiagPlan& p, const float* L, const double* D, double* out,
-                             int nb, const Strides& bs, size_t smem_min, cudaStream_t st);
+                             int nb, const Strides& bs, size_t smem_min, const uint8_t* skip, cudaStream_t st);
 // out[dst[e]] = G[src[e]] for e < cnt (entries picked from a block of the inverse)
 void launch_pick_entries(const double* G, const int64_t* src, const int64_t* dst, int64_t cnt, double* out,
                          cudaStream_t st);
@@ -239,6 +242,31 @@ cudaError_t diag_kernel_setup(int B, size_t smem_min);
 // from the plan's rhs_out).
 void launch_inverse_block(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D,
                           double* var_scratch, double* Zg, int64_t R, double* out, int64_t ldo, cudaStream_t st);
+
+// ---- diag_tc.cu: the mixed form's variances on the tensor cores for the
+// supernodes with at least min_k pivots and their ancestors
+struct DevDiagTc {
+    int32_t ntc = 0;
+    int64_t npt = 0, ndt = 0;
+    int bands = 0;                // bands the buffers hold
+    uint8_t* tc = nullptr;
+    int64_t* tptr = nullptr;
+    int32_t *xptr = nullptr, *ptiles = nullptr, *dtiles = nullptr;
+    float* xinv = nullptr;        // [bands][ndt][128 x 128] inverses of the diagonal tiles
+    float* pack = nullptr;        // [bands][npt][hi, lo][128 x 32] packed left operands
+    alignas(64) unsigned char tmap[128];  // CUtensorMap over pack
+    std::vector<void*> allocs;
+};
+cudaError_t diag_tc_setup();
+size_t diag_tc_pack_floats(int64_t npt);
+size_t diag_tc_xinv_floats(int64_t ndt);
+cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_out);
+// the left operands from the FP32 panels of nb bands (once per factorization)
+void launch_diag_tc_pack(const DevSym& d, const DevDiagTc& p, const float* L32, int nb, const Strides& bs,
+                         cudaStream_t st);
+// after launch_diag_inverse_f32 with skip = p.tc on the same plan and outputs
+void launch_diag_inv_tc(const DevSym& d, const DevDiagPlan& dp, const DevDiagTc& p, const double* D, double* out,
+                        int nb, const Strides& bs, DevStatus* status, int wait_limit, cudaStream_t st);
 
 // ---- normal.cu: N = H^T W H and b = H^T W y on the device
 struct NormalArgs {

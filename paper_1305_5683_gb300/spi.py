@@ -38,7 +38,8 @@ class spi_options(ctypes.Structure):
                 ("async_", ctypes.c_int), ("nd_leaf", ctypes.c_int), ("batch", ctypes.c_int),
                 ("wait_limit", ctypes.c_int), ("diag_ctas_per_sm", ctypes.c_int), ("diag_unpruned", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("force_panel", ctypes.c_int), ("force_schur", ctypes.c_int),
-                ("dag", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("pivoting", ctypes.c_int)]
+                ("dag", ctypes.c_int), ("tune_cache", ctypes.c_char_p), ("pivoting", ctypes.c_int),
+                ("diag_tc_min_pivots", ctypes.c_int)]
 
 
 class spi_stats(ctypes.Structure):
@@ -64,7 +65,9 @@ class spi_stats(ctypes.Structure):
                 ("factor_dag_levels", ctypes.c_int64), ("tune_ms_launches", ctypes.c_double),
                 ("tune_ms_dag", ctypes.c_double), ("solve_dag_tasks", ctypes.c_int64),
                 ("tune_solve_ms_launches", ctypes.c_double), ("tune_solve_ms_dag", ctypes.c_double),
-                ("pivots_2x2", ctypes.c_int64), ("pivot_delays", ctypes.c_int64), ("pivot_restarts", ctypes.c_int64)]
+                ("pivots_2x2", ctypes.c_int64), ("pivot_delays", ctypes.c_int64), ("pivot_restarts", ctypes.c_int64),
+                ("diag_tc_supernodes", ctypes.c_int64), ("diag_tc_tiles", ctypes.c_int64),
+                ("diag_tc_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -444,7 +447,7 @@ class Solver:
     def __init__(self, n, colptr, rowind, *, precision=SPI_PREC_FP64, ordering=SPI_ORDER_ND,
                  rhs_block=0, relax=1, refine_max=10, refine_tol=1e-13, nd_leaf=0, async_=False, batch=1,
                  wait_limit=0, diag_ctas_per_sm=0, diag_unpruned=False, autotune=0, force_panel=0, force_schur=0,
-                 dag=0, tune_cache=None, pivoting=False, _multi=None):
+                 dag=0, tune_cache=None, pivoting=False, diag_tc_min_pivots=0, _multi=None):
         o = spi_default_options()
         o.precision, o.ordering, o.rhs_block, o.relax = precision, ordering, rhs_block, relax
         o.refine_max, o.refine_tol, o.nd_leaf, o.async_ = refine_max, refine_tol, nd_leaf, int(async_)
@@ -455,6 +458,7 @@ class Solver:
         o.autotune, o.force_panel, o.force_schur, o.dag = autotune, force_panel, force_schur, dag
         o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         o.pivoting = int(pivoting)
+        o.diag_tc_min_pivots = diag_tc_min_pivots
         self.n = int(n)
         self.batch = batch
         if _multi is not None:

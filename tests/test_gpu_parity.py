@@ -270,6 +270,8 @@ def test_autotuner_and_tune_cache(P, tmp_path):
     lines = [l.split() for l in cache.read_text().splitlines() if not l.startswith("#")]
     assert sum(l[3] in "PS" for l in lines) == i1["tune_panel_buckets"] + i1["tune_schur_buckets"]
     assert sum(l[3] == "D" for l in lines) == 1  # launches level by level against the dependency-driven launch
+    # the same for the solve, timed at the first solve
+    assert sum(l[3] == "V" for l in lines) == (1 if i1["tune_solve_ms_launches"] > 0 else 0)
     assert i1["tune_ms_launches"] > 0 and i1["tune_ms_dag"] > 0
     s2, _ = check(P, pb.n, pb.colptr, pb.rowind, pb.values, pb.b, autotune=1, tune_cache=str(cache))
     i2 = s2.info()

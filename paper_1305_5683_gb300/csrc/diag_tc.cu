@@ -44,11 +44,6 @@ namespace {
 constexpr int kDtM = kDiagTcRows;       // rows of a tile (the MMA's M)
 constexpr int kDtK = kDiagTcK;          // K columns of a tile
 constexpr int kDtTile = kDtM * kDtK;    // floats of one TF32 plane of a tile (16 KB)
-constexpr int kDtStage = 4 * kDtTile;   // A hi, A lo, B hi, B lo
-constexpr int kDtThreads = 128;
-// 3 stages, variances [128] (double), per-warp column sums [4][128], 6 mbarriers,
-// the tensor-memory address and padding
-constexpr size_t kDtSmem = 3 * kDtStage * sizeof(float) + 128 * sizeof(double) + 4 * 128 * sizeof(float) + 64;
 constexpr size_t kTinvSmem = 2 * kDtM * (kDtM + 1) * sizeof(float);
 constexpr size_t kPackSmem = (kDtM * (kDtM + 1) + kDtM * (kDtK + 1)) * sizeof(float);
 
@@ -221,7 +216,6 @@ struct DiagArgsTc {
 // round-to-nearest add on the CUDA cores while the next group accumulates in
 // the other buffer).
 constexpr uint32_t kDtA1 = 128, kDtX = 256, kDtS = 384;
-constexpr int kDtStages = 3;
 
 __device__ __forceinline__ void tc_add32(uint32_t (&r)[32], const uint32_t (&t)[32]) {
 #pragma unroll
@@ -257,28 +251,96 @@ __device__ __forceinline__ void z_load32(const float* zr, float (&v)[32], int n0
     }
 }
 
-// One CTA per block of right-hand sides.  The K chunks of all its tiles form one
-// sequence (supernode by supernode, tile by tile), which is also the order of
-// their packed left operands (consecutive within a supernode): chunk g uses
-// stage g mod 3 of a 3-stage ring.  Thread 0 copies chunk g + 1's left operand
-// while the CTA stages chunk g's right operand (split into TF32 hi and lo), then
-// issues chunk g's 4 k-steps x 3 MMAs and commits them to the stage's mbarrier.
-__global__ void __launch_bounds__(kDtThreads, 1)
+// Roles of the variance CTA (warp-specialized): warps 0-3 split the right
+// operand into TF32 hi/lo, add finished hi*hi groups into S and run the tile
+// epilogues (they own tensor-memory lanes 0-127); lane 0 of warp 4 copies the
+// packed left operands, lane 0 of warp 5 the raw right-operand chunks of Z
+// (TMA tensor copies of 32 rows x 132 columns through a map over the
+// workspace), lane 0 of warp 6 issues the MMAs.  They meet only at mbarriers.
+constexpr int kDtWork = 128;                       // threads of warps 0-3
+constexpr int kDtRoles = kDtWork + 3 * 32;         // + warps 4, 5, 6
+constexpr int kDtAStages = 3, kDtBStages = 2;
+constexpr int kDtRawCols = 132;                    // the copied columns: N + the 16-byte round-down
+constexpr int kDtRawFloats = kDtK * kDtRawCols;    // one raw chunk (16,896 bytes)
+constexpr int kDtOffB = kDtAStages * 2 * kDtTile;  // floats: A ring, then split B ring, then raw ring
+constexpr int kDtOffRaw = kDtOffB + kDtBStages * 2 * kDtTile;
+constexpr int kDtOffVar = kDtOffRaw + kDtBStages * kDtRawFloats;
+// mbarriers: A full/empty, raw full/empty, B full/empty, group full/empty, acc full/empty, z ready
+enum : int { kBAF = 0, kBAE = 3, kBRF = 6, kBRE = 8, kBBF = 10, kBBE = 12, kBGF = 14, kBGE = 16, kBCF = 18,
+             kBCE = 19, kBZR = 20, kDtBars = 21 };
+constexpr size_t kDtSmem2 = (size_t)kDtOffVar * sizeof(float) + 128 * sizeof(double) + kDtBars * sizeof(uint64_t) + 16;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc_smem_u32(bar)) : "memory");
+}
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool dt_wait(uint64_t* bar, uint32_t parity, uint32_t limit, volatile int* abort) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < limit && !done; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(tc_smem_u32(bar)), "r"(parity));
+        if (!done && *abort) return false;
+    }
+    return done != 0;
+}
+__device__ __forceinline__ void tma_raw_chunk(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// The block's tensor-core supernodes in walk order and the shape of each.
+struct DtNode {
+    int s, lo0, nbu, zo, f, k, m, T, R, nch, N;
+    int64_t urel;
+};
+__device__ __forceinline__ bool dt_next(const DevSym& d, const DiagArgsTc& p, const DiagTcArgs& ta, int& u, int u1,
+                                        DtNode& x) {
+    while (++u < u1) {
+        const int s = p.us[u];
+        if (!ta.tc[s]) continue;
+        x.s = s;
+        x.lo0 = p.ulo[u];
+        x.nbu = p.uhi[u] - x.lo0;
+        x.zo = p.uzoff[u];
+        x.f = d.sfirst[s];
+        x.k = d.sfirst[s + 1] - x.f;
+        x.m = (int)(d.srowptr[s + 1] - d.srowptr[s]);
+        x.T = (x.k + kDtM - 1) / kDtM;
+        x.R = (x.m - x.k + kDtM - 1) / kDtM;
+        x.nch = (x.k + kDtK - 1) / kDtK;
+        x.N = (x.nbu + 31) & ~31;
+        x.urel = p.urel[u];
+        return true;
+    }
+    return false;
+}
+__device__ __forceinline__ int dt_chunks(const DtNode& x, int tile) {
+    const int kext = tile < x.T ? min(kDtM * (tile + 1), x.k) : x.k;
+    return (kext + kDtK - 1) / kDtK;
+}
+
+__global__ void __launch_bounds__(kDtRoles, 1)
     k_diag_inv_tc(DevSym d, DiagArgsTc p, DiagTcArgs ta, const double* __restrict__ D, double* __restrict__ out,
-                  Strides bs, DevStatus* status, uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap) {
+                  Strides bs, DevStatus* status, uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap,
+                  const __grid_constant__ CUtensorMap zmap) {
     const int band = blockIdx.y;
     D += band * bs.n;
     out += band * bs.out;
     extern __shared__ __align__(1024) float dsm[];
-    double* var = reinterpret_cast<double*>(dsm + kDtStages * kDtStage);  // [128]
-    float* red = reinterpret_cast<float*>(var + 128);                      // [4][128]
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + 4 * 128);           // [3] operand copies
-    uint64_t* done = full + kDtStages;                                     // [3] MMA commits
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + kDtStages);
+    float* Aring = dsm;
+    float* Bring = dsm + kDtOffB;
+    float* Raw = dsm + kDtOffRaw;
+    double* var = reinterpret_cast<double*>(dsm + kDtOffVar);  // [128]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(var + 128);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + kDtBars);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int B = p.B;
     const int b = p.order[blockIdx.x];
     float* Z = p.Z + band * bs.Z + p.zbase[b];
+    const int32_t zrow0 = (int32_t)((band * bs.Z + p.zbase[b]) / B);  // the block's first row in the Z map
     const int r0b = p.blk_ptr[b], nr = p.blk_ptr[b + 1] - r0b;
     const int64_t tile_band = (int64_t)band * ta.npt;
     const int u0 = p.uptr[b], u1 = p.uptr[b + 1];
@@ -287,214 +349,303 @@ __global__ void __launch_bounds__(kDtThreads, 1)
                      "r"(kTcCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        for (int q = 0; q < 2 * kDtStages; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc_smem_u32(full + q)), "r"(1));
+    if (tid == kDtWork) {
+        // arrivals per phase: one per worker warp for the barriers the worker warps arrive
+        // on (raw empty, B full, group empty, acc empty, z ready), else one (a copy's
+        // expect-tx arrival or an MMA commit)
+        for (int q = 0; q < kDtBars; ++q) {
+            const bool workers = (q >= kBRE && q < kBRE + kDtBStages) || (q >= kBBF && q < kBBF + kDtBStages) ||
+                                 (q >= kBGE && q < kBGE + 2) || q == kBCE || q == kBZR;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc_smem_u32(bar + q)),
+                         "r"(workers ? kDtWork / 32 : 1));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *abort = 0;
     }
-    for (int q = tid; q < 128; q += kDtThreads) var[q] = q < nr ? out[p.rhs_out[r0b + q]] : 0.0;
+    for (int q = tid; q < 128; q += kDtRoles) var[q] = q < nr ? out[p.rhs_out[r0b + q]] : 0.0;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    bool ok = true;
-    uint32_t g = 0;  // chunks whose MMAs were committed
-    // ---- thread 0's operand copies, one chunk ahead of the MMAs
-    uint32_t issued = 0;
-    int pu = u0 - 1;
-    int64_t pid = 0, pend = 0;
-    auto issue_next = [&]() -> bool {
-        while (pid == pend) {
-            if (++pu >= u1) return true;  // nothing left to copy
-            const int s = p.us[pu];
-            if (!ta.tc[s]) continue;
-            const int k = d.sfirst[s + 1] - d.sfirst[s];
-            const int m = (int)(d.srowptr[s + 1] - d.srowptr[s]);
-            const int T = (k + kDtM - 1) / kDtM, R = (m - k + kDtM - 1) / kDtM, nch = (k + kDtK - 1) / kDtK;
-            pid = tile_band + ta.tptr[s];
-            pend = pid + diag_tc_tile_offset(T, nch, T + R);
-        }
-        const uint32_t st = issued % kDtStages;
-        // the stage's previous chunk (issued - 3) must have been read by its MMAs
-        if (issued >= kDtStages && !tc_wait(done + st, ((issued - kDtStages) / kDtStages) & 1u, wait_limit)) return false;
-        mbar_expect_tx(tc_smem_u32(full + st), 2 * kDtTile * sizeof(float));
-        tma_tile_pair(tc_smem_u32(dsm + st * kDtStage), &tmap, (int32_t)(8 * pid), tc_smem_u32(full + st));
-        ++pid;
-        ++issued;
-        return true;
-    };
-    if (tid == 0) ok = issue_next();
-    for (int u = u0; u < u1; ++u) {
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        const int s = p.us[u];
-        if (!ta.tc[s]) continue;
-        const int lo0 = p.ulo[u], nbu = p.uhi[u] - lo0, zo = p.uzoff[u];
-        const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
-        const int m = (int)(d.srowptr[s + 1] - d.srowptr[s]);
-        const int32_t* rel = p.rel + p.urel[u];
-        const int N = (nbu + 31) & ~31;
-        const bool vec = (lo0 & 3) == 0;
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-                               ((uint32_t)(kDtM >> 4) << 24);
-        const int T = (k + kDtM - 1) / kDtM, R = (m - k + kDtM - 1) / kDtM;
-        const int nitems = N * (kDtK / 4);  // (right-hand side, 4-row group) pairs of one chunk
-        float pre[8][4];                    // a chunk of Z (rows of s, right-hand sides [lo0, lo0 + N))
-        auto fetch = [&](int c, int kext) {
-#pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const int item = tid + it * kDtThreads;
-                const int n = item % N, kq = item / N;
-                const int kr = c * kDtK + kq * 4;
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    pre[it][e] = (item < nitems && n < nbu && kr + e < kext)
-                                     ? Z[(int64_t)(zo + kr + e) * B + lo0 + n] : 0.f;
+    const uint32_t lim = wait_limit;
+    // the last copies and commits of each role, drained below if a wait ran out
+    uint32_t a_issued = 0, r_issued = 0, mma_chunks = 0;
+    int mma_tiles = 0;
+    if (warp == 4) {
+        // ---- packed left operands: run ahead of the MMAs by up to 3 chunks
+        if (lane == 0) {
+            int u = u0 - 1;
+            DtNode x;
+            bool ok = true;
+            while (ok && dt_next(d, p, ta, u, u1, x)) {
+                const int64_t t0 = tile_band + ta.tptr[x.s];
+                const int64_t nt = diag_tc_tile_offset(x.T, x.nch, x.T + x.R);
+                for (int64_t t = 0; t < nt && ok; ++t) {
+                    const uint32_t g = a_issued, st = g % kDtAStages;
+                    if (g >= kDtAStages && !dt_wait(bar + kBAE + st, ((g - kDtAStages) / kDtAStages) & 1u, lim, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(tc_smem_u32(bar + kBAF + st), 2 * kDtTile * sizeof(float));
+                    tma_tile_pair(tc_smem_u32(Aring + st * 2 * kDtTile), &tmap, (int32_t)(8 * (t0 + t)),
+                                  tc_smem_u32(bar + kBAF + st));
+                    ++a_issued;
+                }
             }
-        };
-        bool prefetched = false;
-        for (int tile = 0; tile < T + R && ok; ++tile) {
-            const bool own = tile < T;
-            const int rows0 = own ? tile * kDtM : k + (tile - T) * kDtM;
-            const int nrow = min(kDtM, (own ? k : m) - rows0);
-            const int kext = own ? min(kDtM * (tile + 1), k) : k;
-            const int nck = (kext + kDtK - 1) / kDtK;
-            if (!prefetched) fetch(0, kext);
-            prefetched = false;
-            for (int c = 0; c < nck; ++c) {
-                const uint32_t gc = g, st = gc % kDtStages;
-                float* A = dsm + st * kDtStage;
-                float* Bh = A + 2 * kDtTile;
-                float* Bl = Bh + kDtTile;
-                // the stage's right operand buffers: free once chunk gc - 3's MMAs are done
-                if (gc >= kDtStages) ok = tc_wait(done + st, ((gc - kDtStages) / kDtStages) & 1u, wait_limit) && ok;
-                if (tid == 0 && ok && issued == gc + 1) ok = issue_next();
-                if (__syncthreads_or(!ok)) { ok = false; break; }
-#pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int item = tid + it * kDtThreads;
-                    if (item < nitems) {
-                        const int n = item % N, kq = item / N;
-                        const int o = tc_kmajor_off(n, 4 * kq) >> 2;
-                        float4 h, l;
-                        tc_split2(pre[it][0], h.x, l.x);
-                        tc_split2(pre[it][1], h.y, l.y);
-                        tc_split2(pre[it][2], h.z, l.z);
-                        tc_split2(pre[it][3], h.w, l.w);
-                        *reinterpret_cast<float4*>(Bh + o) = h;
-                        *reinterpret_cast<float4*>(Bl + o) = l;
+            if (!ok) *abort = 1;
+        }
+    } else if (warp == 5) {
+        // ---- raw right-operand chunks.  A tile whose rows the previous tile's epilogue
+        // wrote (an own tile, or the first tile below) waits for that epilogue; the
+        // worker warps signal z-ready after exactly those epilogues (own tiles, the last
+        // tile below), so that every wait here meets the next completion in order: a
+        // phase-parity wait that skipped a completion would take completion n - 2 for n.
+        if (lane == 0) {
+            int u = u0 - 1, tiles = 0;
+            uint32_t zwaits = 0;
+            DtNode x;
+            bool ok = true;
+            while (ok && dt_next(d, p, ta, u, u1, x)) {
+                const int32_t x0 = x.lo0 & ~3;
+                for (int tile = 0; tile < x.T + x.R && ok; ++tile, ++tiles) {
+                    if (tiles > 0 && tile <= x.T && !dt_wait(bar + kBZR, zwaits++ & 1u, lim, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const int nck = dt_chunks(x, tile);
+                    for (int c = 0; c < nck; ++c) {
+                        const uint32_t g = r_issued, st = g % kDtBStages;
+                        if (g >= kDtBStages &&
+                            !dt_wait(bar + kBRE + st, ((g - kDtBStages) / kDtBStages) & 1u, lim, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(tc_smem_u32(bar + kBRF + st), kDtRawFloats * sizeof(float));
+                        tma_raw_chunk(tc_smem_u32(Raw + st * kDtRawFloats), &zmap, x0, zrow0 + x.zo + c * kDtK,
+                                      tc_smem_u32(bar + kBRF + st));
+                        ++r_issued;
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cta;");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
-                if (tid == 0) {
-                    if (!tc_wait(full + st, (gc / kDtStages) & 1u, wait_limit)) {
+            }
+            if (!ok) *abort = 1;
+        }
+    } else if (warp == 6) {
+        // ---- MMA issue: 4 k-steps x 3 products per chunk (hi*lo and lo*hi into X, hi*hi
+        // into the group's buffer); commits free the stages, hand finished groups to
+        // the flush and finished tiles to the epilogue
+        if (lane == 0) {
+            int u = u0 - 1;
+            DtNode x;
+            bool ok = true;
+            uint32_t gcommit[2] = {0, 0};  // group commits per buffer so far
+            uint32_t glast[2] = {0, 0};    // index of the last group commit on each buffer
+            while (ok && dt_next(d, p, ta, u, u1, x)) {
+                const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(x.N >> 3) << 17) |
+                                       ((uint32_t)(kDtM >> 4) << 24);
+                for (int tile = 0; tile < x.T + x.R && ok; ++tile) {
+                    if (mma_tiles > 0 && !dt_wait(bar + kBCE, (uint32_t)(mma_tiles - 1) & 1u, lim, abort)) {
                         ok = false;
-                    } else {
+                        break;
+                    }
+                    const int nck = dt_chunks(x, tile);
+                    for (int c = 0; c < nck && ok; ++c) {
+                        const int j = c >> 2, buf = j & 1;
+                        if ((c & 3) == 0 && j >= 2 && !dt_wait(bar + kBGE + buf, glast[buf] & 1u, lim, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t g = mma_chunks, sa = g % kDtAStages, sb = g % kDtBStages;
+                        if (!dt_wait(bar + kBAF + sa, (g / kDtAStages) & 1u, lim, abort) ||
+                            !dt_wait(bar + kBBF + sb, (g / kDtBStages) & 1u, lim, abort)) {
+                            ok = false;
+                            break;
+                        }
                         asm volatile("tcgen05.fence::after_thread_sync;");
-                        const uint32_t acc = tmem + ((c >> 2) & 1 ? kDtA1 : 0u);
+                        const float* A = Aring + sa * 2 * kDtTile;
+                        const float* Bh = Bring + sb * 2 * kDtTile;
+                        const uint32_t acc = tmem + (buf ? kDtA1 : 0u);
 #pragma unroll
                         for (int kk = 0; kk < kDtK / 8; ++kk) {
                             const uint32_t ko = kk * 256;
                             const uint64_t ah = tc_desc(tc_smem_u32(A) + ko), al = tc_desc(tc_smem_u32(A + kDtTile) + ko);
-                            const uint64_t bh = tc_desc(tc_smem_u32(Bh) + ko), bl = tc_desc(tc_smem_u32(Bl) + ko);
+                            const uint64_t bh = tc_desc(tc_smem_u32(Bh) + ko), bl = tc_desc(tc_smem_u32(Bh + kDtTile) + ko);
                             tc_mma(tmem + kDtX, ah, bl, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                             tc_mma(tmem + kDtX, al, bh, idesc, 1u);
                             tc_mma(acc, ah, bh, idesc, ((c & 3) > 0 || kk > 0) ? 1u : 0u);
                         }
-                    }
-                    // the commit tracks every MMA issued before it, and arrives even if none was
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(tc_smem_u32(done + st)));
-                }
-                ++g;
-                if ((c & 3) == 0 && c > 0) {
-                    // group c/4 - 1 ended with chunk gc - 1: S (+)= its buffer while this group
-                    // accumulates in the other one
-                    const uint32_t gp = gc - 1;
-                    if (ok) ok = tc_wait(done + gp % kDtStages, (gp / kDtStages) & 1u, wait_limit);
-                    if (__syncthreads_or(!ok)) { ok = false; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t row = (uint32_t)(warp * 32) << 16;
-                    const uint32_t prev = ((c >> 2) - 1) & 1 ? kDtA1 : 0u;
-                    for (int q = 0; q < N / 32; ++q) {
-                        uint32_t a[32], sv[32];
-                        tc_ld32(tmem + row + prev + q * 32, a);
-                        if (c > 4) {
-                            tc_ld32(tmem + row + kDtS + q * 32, sv);
-                            tc_add32(a, sv);
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     :: "r"(tc_smem_u32(bar + kBAE + sa)));
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     :: "r"(tc_smem_u32(bar + kBBE + sb)));
+                        if ((c & 3) == 3 && c + 1 < nck) {  // a finished group that the flush takes
+                            glast[buf] = gcommit[buf]++;
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                         :: "r"(tc_smem_u32(bar + kBGF + buf)));
                         }
-                        tc_st32(tmem + row + kDtS + q * 32, a);
+                        ++mma_chunks;
                     }
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                }
-                if (c + 1 < nck) {
-                    fetch(c + 1, kext);
-                } else if (!own && tile + 1 < T + R) {
-                    fetch(0, kext);  // the next tile below takes the same right operand
-                    prefetched = true;
+                    if (!ok) break;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(tc_smem_u32(bar + kBCF)));
+                    ++mma_tiles;
                 }
             }
-            // thread 0 alone may have seen a wait run out (its operand copy): every exit is
-            // decided collectively, so that all threads leave the loops together
-            if (__syncthreads_or(!ok)) { ok = false; break; }
-            const uint32_t gl = g - 1;
-            ok = tc_wait(done + gl % kDtStages, (gl / kDtStages) & 1u, wait_limit);
-            if (__syncthreads_or(!ok)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            // result = S (groups before the last) + the last group's buffer + X
-            const int jl = (nck - 1) >> 2;
-            const int row = warp * 32 + lane;
-            const int lr = rows0 + row;
-            const bool rv = row < nrow;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            const float dinv = (own && rv) ? (float)(1.0 / D[f + lr]) : 0.f;
-            float* zrow = Z + (int64_t)(own ? zo + lr : (rv ? rel[lr - k] : 0)) * B + lo0;
-            for (int q = 0; q < N / 32; ++q) {
-                uint32_t r[32], t[32];
-                tc_ld32(taddr + (jl & 1 ? kDtA1 : 0u) + q * 32, r);
-                tc_ld32(taddr + kDtX + q * 32, t);
-                tc_add32(r, t);
-                if (jl > 0) {
-                    tc_ld32(taddr + kDtS + q * 32, t);
-                    tc_add32(r, t);
-                }
-                float v[32];
-                if (own) {
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) v[jj] = __uint_as_float(r[jj]);
-                    if (rv) z_store32(zrow, v, q * 32, nbu, vec);
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) v[jj] = (rv && q * 32 + jj < nbu) ? v[jj] * v[jj] * dinv : 0.f;
-                    red[warp * 128 + q * 32 + lane] = lane_column_sum(v, lane);
-                } else if (rv) {
-                    z_load32(zrow, v, q * 32, nbu, vec);
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) v[jj] += __uint_as_float(r[jj]);
-                    z_store32(zrow, v, q * 32, nbu, vec);
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            if (own)
-                for (int n = tid; n < nbu; n += kDtThreads)
-                    var[lo0 + n] += ((double)red[n] + (double)red[128 + n]) + ((double)red[256 + n] + (double)red[384 + n]);
+            if (!ok) *abort = 1;
         }
-        if (!ok) break;
+    } else {
+        // ---- warps 0-3: split, flush, epilogue.  Each wait's outcome is made uniform
+        // across the warp (a lane must not leave while the others reach __syncwarp);
+        // the warps meet each other only at mbarriers, whose waits are all bounded.
+        auto wwait = [&](uint64_t* br, uint32_t par) { return __all_sync(0xffffffffu, dt_wait(br, par, lim, abort)); };
+        int u = u0 - 1, tiles = 0;
+        DtNode x;
+        bool ok = true;
+        uint32_t g = 0;                // chunks split
+        uint32_t gwait[2] = {0, 0};    // group commits waited per buffer
+        while (ok && dt_next(d, p, ta, u, u1, x)) {
+            const int32_t* rel = p.rel + x.urel;
+            const bool vec = (x.lo0 & 3) == 0;
+            const int sh = x.lo0 - (x.lo0 & ~3);
+            const int nitems = x.N * (kDtK / 4);
+            for (int tile = 0; tile < x.T + x.R && ok; ++tile, ++tiles) {
+                const bool own = tile < x.T;
+                const int rows0 = own ? tile * kDtM : x.k + (tile - x.T) * kDtM;
+                const int nrow = min(kDtM, (own ? x.k : x.m) - rows0);
+                const int kext = own ? min(kDtM * (tile + 1), x.k) : x.k;
+                const int nck = (kext + kDtK - 1) / kDtK;
+                for (int c = 0; c < nck && ok; ++c, ++g) {
+                    const uint32_t sr = g % kDtBStages;
+                    if (!wwait(bar + kBRF + sr, (g / kDtBStages) & 1u)) { ok = false; break; }
+                    const float* raw = Raw + sr * kDtRawFloats;
+                    float v[8][4];
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int item = tid + it * kDtWork;
+                        const int n = item % x.N, kq = item / x.N;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int kr = c * kDtK + kq * 4 + e;
+                            v[it][e] = (item < nitems && n < x.nbu && kr < kext)
+                                           ? raw[(kq * 4 + e) * kDtRawCols + sh + n] : 0.f;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar + kBRE + sr);
+                    if (g >= kDtBStages && !wwait(bar + kBBE + sr, ((g - kDtBStages) / kDtBStages) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    float* Bh = Bring + sr * 2 * kDtTile;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int item = tid + it * kDtWork;
+                        if (item < nitems) {
+                            const int n = item % x.N, kq = item / x.N;
+                            const int o = tc_kmajor_off(n, 4 * kq) >> 2;
+                            float4 h, l;
+                            tc_split2(v[it][0], h.x, l.x);
+                            tc_split2(v[it][1], h.y, l.y);
+                            tc_split2(v[it][2], h.z, l.z);
+                            tc_split2(v[it][3], h.w, l.w);
+                            *reinterpret_cast<float4*>(Bh + o) = h;
+                            *reinterpret_cast<float4*>(Bh + kDtTile + o) = l;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar + kBBF + sr);
+                    if ((c & 3) == 0 && c > 0) {
+                        // S (+)= the buffer of group c/4 - 1 while this group accumulates in the other
+                        const int pb = ((c >> 2) - 1) & 1;
+                        if (!wwait(bar + kBGF + pb, gwait[pb]++ & 1u)) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t row = (uint32_t)(warp * 32) << 16;
+                        for (int q = 0; q < x.N / 32; ++q) {
+                            uint32_t a[32], sv[32];
+                            tc_ld32(tmem + row + (pb ? kDtA1 : 0u) + q * 32, a);
+                            if (c > 4) {
+                                tc_ld32(tmem + row + kDtS + q * 32, sv);
+                                tc_add32(a, sv);
+                            }
+                            tc_st32(tmem + row + kDtS + q * 32, a);
+                        }
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bar + kBGE + pb);
+                    }
+                }
+                if (!ok) break;
+                // ---- epilogue of the tile: result = S (groups before the last) + last group + X
+                if (!wwait(bar + kBCF, (uint32_t)tiles & 1u)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int jl = (nck - 1) >> 2;
+                const int row = warp * 32 + lane;
+                const int lr = rows0 + row;
+                const bool rv = row < nrow;
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+                const float dinv = (own && rv) ? (float)(1.0 / D[x.f + lr]) : 0.f;
+                float* zrow = Z + (int64_t)(own ? x.zo + lr : (rv ? rel[lr - x.k] : 0)) * B + x.lo0;
+                for (int q = 0; q < x.N / 32; ++q) {
+                    uint32_t r[32], t[32];
+                    tc_ld32(taddr + (jl & 1 ? kDtA1 : 0u) + q * 32, r);
+                    tc_ld32(taddr + kDtX + q * 32, t);
+                    tc_add32(r, t);
+                    if (jl > 0) {
+                        tc_ld32(taddr + kDtS + q * 32, t);
+                        tc_add32(r, t);
+                    }
+                    float w[32];
+                    if (own) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) w[jj] = __uint_as_float(r[jj]);
+                        if (rv) z_store32(zrow, w, q * 32, x.nbu, vec);
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            w[jj] = (rv && q * 32 + jj < x.nbu) ? w[jj] * w[jj] * dinv : 0.f;
+                        const float cs = lane_column_sum(w, lane);  // this warp's 32 rows of column q*32+lane
+                        if (q * 32 + lane < x.nbu) atomicAdd(&var[x.lo0 + q * 32 + lane], (double)cs);
+                    } else if (rv) {
+                        z_load32(zrow, w, q * 32, x.nbu, vec);
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) w[jj] += __uint_as_float(r[jj]);
+                        z_store32(zrow, w, q * 32, x.nbu, vec);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                // the Z rows written above are read next by TMA copies (the async proxy)
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(bar + kBCE);
+                    if (tile < x.T || tile + 1 == x.T + x.R) mbar_arrive(bar + kBZR);  // the tiles waited on
+                }
+            }
+        }
+        if (!ok) *abort = 1;
     }
-    if (!ok) {
-        // a wait ran out: report it, let the copies and products in flight finish
-        // (again bounded), then release tensor memory and leave the variances
-        if (tid == 0) {
+    // ---- a wait ran out somewhere: let the copies and products in flight finish (again
+    // bounded), report it, release tensor memory and leave the variances
+    __syncthreads();
+    const bool failed = *abort != 0;
+    if (failed) {
+        if (tid == kDtWork) {
             atomicOr(&status->flags, FLAG_TIMEOUT);
-            for (uint32_t q = issued > kDtStages ? issued - kDtStages : 0; q < issued; ++q)
-                tc_wait(full + q % kDtStages, (q / kDtStages) & 1u);
-            if (g > 0) tc_wait(done + (g - 1) % kDtStages, ((g - 1) / kDtStages) & 1u);
+            for (uint32_t q = a_issued > kDtAStages ? a_issued - kDtAStages : 0; q < a_issued; ++q)
+                tc_wait(bar + kBAF + q % kDtAStages, (q / kDtAStages) & 1u);
+        }
+        if (tid == kDtWork + 32)
+            for (uint32_t q = r_issued > kDtBStages ? r_issued - kDtBStages : 0; q < r_issued; ++q)
+                tc_wait(bar + kBRF + q % kDtBStages, (q / kDtBStages) & 1u);
+        if (tid == kDtWork + 64 && mma_chunks > 0) {
+            // one more commit tracks every MMA issued so far
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(tc_smem_u32(bar + kBCF)));
+            tc_wait(bar + kBCF, (uint32_t)mma_tiles & 1u);
         }
     }
     __syncthreads();
-    if (ok)
-        for (int q = tid; q < nr; q += kDtThreads) out[p.rhs_out[r0b + q]] = var[q];
+    if (!failed)
+        for (int q = tid; q < nr; q += kDtRoles) out[p.rhs_out[r0b + q]] = var[q];
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
 }
@@ -502,7 +653,7 @@ __global__ void __launch_bounds__(kDtThreads, 1)
 }  // namespace
 
 cudaError_t diag_tc_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_diag_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDtSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_diag_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDtSmem2);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_diag_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem);
     if (e != cudaSuccess) return e;
@@ -512,14 +663,13 @@ cudaError_t diag_tc_setup() {
 size_t diag_tc_pack_floats(int64_t npt) { return (size_t)npt * 2 * kDtTile; }
 size_t diag_tc_xinv_floats(int64_t ndt) { return (size_t)ndt * kDtM * kDtM; }
 
-// The tensor map over the packed tiles of `bands` bands: [slices][256][4]
-// floats, 16-byte rows, 4 KB slices, eight slices per tile pair; one box is a
-// whole tile pair (4 x 256 x 8).  cuTensorMapEncodeTiled comes from the driver
-// through the runtime's entry-point query (no link against the driver library).
-cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_out) {
-    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query
+// (no link against the driver library).
+cudaError_t tensor_map_encoder(EncodeFn* out) {
     static EncodeFn encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -529,6 +679,18 @@ cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_ou
         if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<EncodeFn>(fn);
     }
+    *out = encode;
+    return cudaSuccess;
+}
+
+// The tensor map over the packed tiles of `bands` bands: [slices][256][4]
+// floats, 16-byte rows, 4 KB slices, eight slices per tile pair; one box is a
+// whole tile pair (4 x 256 x 8).  cuTensorMapEncodeTiled comes from the driver
+// through the runtime's entry-point query (no link against the driver library).
+cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_out) {
+    EncodeFn encode = nullptr;
+    cudaError_t e = tensor_map_encoder(&encode);
+    if (e != cudaSuccess) return e;
     const cuuint64_t dims[3] = {4, 256, (cuuint64_t)npt * bands * 8};
     const cuuint64_t strides[2] = {16, 4096};
     const cuuint32_t box[3] = {4, 256, 8};
@@ -536,6 +698,22 @@ cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_ou
     const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pack, dims,
                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The tensor map over a variance workspace of `rows` rows of B floats (all bands):
+// boxes of 32 rows x 132 columns, columns beyond B read as zeros.
+cudaError_t diag_tc_z_map(float* Z, int B, int64_t rows, void* map_out) {
+    EncodeFn encode = nullptr;
+    cudaError_t e = tensor_map_encoder(&encode);
+    if (e != cudaSuccess) return e;
+    const cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)std::max<int64_t>(rows, 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)B * sizeof(float)};
+    const cuuint32_t box[2] = {kDtRawCols, kDtK};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Z, dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -554,8 +732,9 @@ void launch_diag_inv_tc(const DevSym& d, const DevDiagPlan& dp, const DevDiagTc&
     DiagArgsTc a{dp.B, dp.order, dp.blk_ptr, dp.uptr, dp.us, dp.ulo, dp.uhi, dp.uzoff, dp.rel, dp.rhs_out,
                  dp.urel, dp.zbase, reinterpret_cast<float*>(dp.Z)};
     DiagTcArgs t{p.tc, p.tptr, p.npt};
-    k_diag_inv_tc<<<dim3(dp.nblocks, nb), kDtThreads, kDtSmem, st>>>(
-        d, a, t, D, out, bs, status, lim, *reinterpret_cast<const CUtensorMap*>(p.tmap));
+    k_diag_inv_tc<<<dim3(dp.nblocks, nb), kDtRoles, kDtSmem2, st>>>(
+        d, a, t, D, out, bs, status, lim, *reinterpret_cast<const CUtensorMap*>(p.tmap),
+        *reinterpret_cast<const CUtensorMap*>(dp.zmap));
 }
 
 }  // namespace spi

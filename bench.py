@@ -602,6 +602,15 @@ def bench_sky(P, args, dev, st, flush, world, cfg=None, warmup=3, max_steps=3, p
                                    "launches": info["launches_factor_tc"], "achieved_tflops": ach, "peak": pk,
                                    "frac": ach / pk, "peak_source": src,
                                    "note": "TF32 MMA work issued (6 MMAs per product) over the whole factor span"}
+        if name == "mixed" and peaks is not None and info["diag_tc_flops"] > 0:
+            pk, src = peak_of(peaks, "tf32_tcgen05")
+            ach = info["diag_tc_flops"] / (d / 1e3) / 1e12
+            out[name]["diag_tensor"] = {"tf32_flops_issued": info["diag_tc_flops"],
+                                        "supernodes": info["diag_tc_supernodes"], "achieved_tflops": ach, "peak": pk,
+                                        "frac": ach / pk, "peak_source": src,
+                                        "note": "TF32 MMA work issued (3 MMAs per product, padded tiles) over the "
+                                                "whole variance span (SIMT kernel below the tensor-core supernodes "
+                                                "included)"}
         if golden is not None:
             xo, vo = golden["x"], golden["var_sky"]
             out[name]["max_rel_err_x_vs_oracle"] = float(np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max())
@@ -894,10 +903,27 @@ def main():
                  "plan": plan_summary(minfo),
                  "tensor_core_launches": minfo["launches_factor_tc"],
                  "dtype": "f32 updates / f64 pivots, refinement and variance sums"}
-        pk32, src32 = peak_of(peaks, "fp32_fma")
-        mixed["diag_roofline"] = {"bound": "alu", "kernel": "k_diag_inv_f32", "achieved": mixed["diag_tflops_fp32"],
-                                  "peak": pk32, "unit": "TFLOP/s", "frac": mixed["diag_tflops_fp32"] / pk32,
-                                  "peak_source": src32}
+        # the variances alone (no solve beside them): the tensor-core kernel for the
+        # supernodes with at least diag_tc_min_pivots pivots and their ancestors, the
+        # SIMT kernel below them
+        d_alone = _time_alone(lambda q: sm_.diag_inverse(out=varm, stream=q), st)
+        minfo = sm_.info()
+        mixed["diag_alone_ms"] = d_alone
+        mixed["diag_tflops_fp32_alone"] = minfo["diag_flops_all"] / (d_alone / 1e3) / 1e12
+        if minfo["diag_tc_flops"] > 0:
+            pk, src = peak_of(peaks, "tf32_tcgen05")
+            ach = minfo["diag_tc_flops"] / (d_alone / 1e3) / 1e12
+            mixed["diag_roofline"] = {"bound": "tensor", "kernel": "k_diag_inv_tc (after k_diag_inv_f32)",
+                                      "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                                      "peak_source": src, "supernodes": minfo["diag_tc_supernodes"],
+                                      "tf32_flops_issued": minfo["diag_tc_flops"],
+                                      "note": "TF32 MMA work issued (3 MMAs per product, padded tiles) over the "
+                                              "whole variance launch pair, timed alone"}
+        else:
+            pk32, src32 = peak_of(peaks, "fp32_fma")
+            mixed["diag_roofline"] = {"bound": "alu", "kernel": "k_diag_inv_f32",
+                                      "achieved": mixed["diag_tflops_fp32_alone"], "peak": pk32, "unit": "TFLOP/s",
+                                      "frac": mixed["diag_tflops_fp32_alone"] / pk32, "peak_source": src32}
         if minfo["factor_tc_flops"] > 0:
             pk, src = peak_of(peaks, "tf32_tcgen05")
             ach = minfo["factor_tc_flops"] / (statistics.mean(mf) / 1e3) / 1e12

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
     z += blockIdx.y * bs.n;
-    __shared__ double xb[kT];
+    __shared__ TL xb[kT];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -70,14 +70,14 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
     const int cb = b * kT, wb = min(kT, k - cb);
     if (tid < 32) {
         // lane r holds row r of the diagonal block: 32 independent loads first
-        double lrow[kT];
+        TL lrow[kT];
 #pragma unroll
         for (int c = 0; c < kT; ++c)
             lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
-        double x = lane < wb ? w[f + cb + lane] : 0.0;
+        TL x = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
         for (int c = 0; c < kT - 1; ++c) {
-            const double xc = __shfl_sync(0xffffffffu, x, c);
+            const TL xc = __shfl_sync(0xffffffffu, x, c);
             x -= lrow[c] * xc;
         }
         xb[lane] = x;
@@ -88,10 +88,10 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
     const int64_t r0 = cb + wb + (int64_t)chunk * kFwdRows;
     const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
     for (int64_t r = r0 + tid; r < r1; r += kThreads) {
-        double acc = 0.0;
+        TL acc = 0;
         for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
         if (r < k) w[f + r] -= acc;
-        else atomicAdd(w + rows[r], -acc);
+        else atomicAdd(w + rows[r], -(double)acc);
     }
 }
 
@@ -120,11 +120,11 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const int c0 = chunk * kT, nc = min(kT, k - c0);
-    double acc[kPer];
+    TL acc[kPer];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
     for (int64_t t = k + lane; t < m; t += 32) {
-        const double xv = x[rows[t]];
+        const TL xv = (TL)x[rows[t]];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int c = warp + kWarps * q;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-        double v = acc[q];
+        TL v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int c = warp + kWarps * q;
         if (lane == 0 && c < nc) w[f + c0 + c] = dinv_z(d, z, D, f + c0 + c) - v;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
-    __shared__ double xb[kT];
+    __shared__ TL xb[kT];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -159,14 +159,14 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     const int cb = b * kT, wb = min(kT, k - cb);
     if (tid < 32) {
         // lane c holds column c of the diagonal block (L_bb^T row c)
-        double lcol[kT];
+        TL lcol[kT];
 #pragma unroll
         for (int r = 0; r < kT; ++r)
             lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
-        double y = lane < wb ? w[f + cb + lane] : 0.0;
+        TL y = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
         for (int r = kT - 1; r > 0; --r) {
-            const double xr = __shfl_sync(0xffffffffu, y, r);
+            const TL xr = __shfl_sync(0xffffffffu, y, r);
             y -= lcol[r] * xr;
         }
         xb[lane] = y;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     const int a1 = min(cb, (chunk + 1) * kBwdCols);
     for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
         const TL* col = P + (int64_t)a * m + cb;
-        double acc = 0.0;
+        TL acc = 0;
         for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
         w[f + a] -= acc;
     }
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
     L += blockIdx.y * bs.L;
     w += blockIdx.y * bs.n;
     z += blockIdx.y * bs.n;
-    __shared__ double xb[kT];
+    __shared__ TL xb[kT];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -203,20 +203,20 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
     const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const bool in_regs = m - k <= (int64_t)kAncRegs * kThreads;
-    double anc[kAncRegs];
+    TL anc[kAncRegs];
 #pragma unroll
     for (int j = 0; j < kAncRegs; ++j) anc[j] = 0.0;
     for (int cb = 0; cb < k; cb += kT) {
         const int wb = min(kT, k - cb);
         if (tid < 32) {
-            double lrow[kT];
+            TL lrow[kT];
 #pragma unroll
             for (int c = 0; c < kT; ++c)
                 lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
-            double x = lane < wb ? w[f + cb + lane] : 0.0;
+            TL x = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
             for (int c = 0; c < kT - 1; ++c) {
-                const double xc = __shfl_sync(0xffffffffu, x, c);
+                const TL xc = __shfl_sync(0xffffffffu, x, c);
                 x -= lrow[c] * xc;
             }
             xb[lane] = x;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
         }
         __syncthreads();
         for (int r = cb + wb + tid; r < k; r += kThreads) {  // the supernode's later pivots
-            double acc = 0.0;
+            TL acc = 0;
             for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
             w[f + r] -= acc;
         }
@@ -233,16 +233,16 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
             for (int j = 0; j < kAncRegs; ++j) {
                 const int64_t r = k + tid + (int64_t)j * kThreads;
                 if (r < m) {
-                    double acc = 0.0;
+                    TL acc = 0;
                     for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
                     anc[j] += acc;
                 }
             }
         } else {
             for (int64_t r = k + tid; r < m; r += kThreads) {
-                double acc = 0.0;
+                TL acc = 0;
                 for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
-                atomicAdd(w + rows[r], -acc);
+                atomicAdd(w + rows[r], -(double)acc);
             }
         }
         __syncthreads();  // w of the next diagonal block, and xb, are rewritten
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_level(DevSym d, const int32_t*
 #pragma unroll
         for (int j = 0; j < kAncRegs; ++j) {
             const int64_t r = k + tid + (int64_t)j * kThreads;
-            if (r < m) atomicAdd(w + rows[r], -anc[j]);
+            if (r < m) atomicAdd(w + rows[r], -(double)anc[j]);
         }
     }
 }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
     x += blockIdx.y * bs.n;
     w += blockIdx.y * bs.n;
     constexpr int kWarps = kThreads / 32;
-    __shared__ double xb[kT];
+    __shared__ TL xb[kT];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = items[2 * blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
     const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     for (int c = warp; c < k; c += kWarps) {
-        double acc = 0.0;
+        TL acc = 0;
         for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) w[f + c] = dinv_z(d, z, D, f + c) - acc;
@@ -288,14 +288,14 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
     for (int cb = ((k - 1) / kT) * kT; cb >= 0; cb -= kT) {
         const int wb = min(kT, k - cb);
         if (tid < 32) {
-            double lcol[kT];
+            TL lcol[kT];
 #pragma unroll
             for (int r = 0; r < kT; ++r)
                 lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
-            double y = lane < wb ? w[f + cb + lane] : 0.0;
+            TL y = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
             for (int r = kT - 1; r > 0; --r) {
-                const double xr = __shfl_sync(0xffffffffu, y, r);
+                const TL xr = __shfl_sync(0xffffffffu, y, r);
                 y -= lcol[r] * xr;
             }
             xb[lane] = y;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
         __syncthreads();
         for (int a = tid; a < cb; a += kThreads) {
             const TL* col = P + (int64_t)a * m + cb;
-            double acc = 0.0;
+            TL acc = 0;
             for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
             w[f + a] -= acc;
         }
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
                                                         int nb, int* cnt, int cstride, const TL* __restrict__ L,
                                                         const double* __restrict__ D, double* w, double* z, double* x,
                                                         DevStatus* status, Strides bs, uint32_t wait_limit) {
-    __shared__ double xb[kT];
+    __shared__ TL xb[kT];
     __shared__ int64_t s_t;
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -501,14 +501,14 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
         if (tk.type == kSolveFwd) {
             const int cb = tk.a * kT, wb = min(kT, k - cb), chunk = tk.b;
             if (tid < 32) {
-                double lrow[kT];
+                TL lrow[kT];
 #pragma unroll
                 for (int c = 0; c < kT; ++c)
                     lrow[c] = (c < lane && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : 0.0;
-                double xx = lane < wb ? __ldcg(wb_ + f + cb + lane) : 0.0;
+                TL xx = lane < wb ? (TL)__ldcg(wb_ + f + cb + lane) : TL(0);
 #pragma unroll
                 for (int c = 0; c < kT - 1; ++c) {
-                    const double xc = __shfl_sync(0xffffffffu, xx, c);
+                    const TL xc = __shfl_sync(0xffffffffu, xx, c);
                     xx -= lrow[c] * xc;
                 }
                 xb[lane] = xx;
@@ -518,19 +518,19 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             const int64_t r0 = cb + wb + (int64_t)chunk * kFwdRows;
             const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
             for (int64_t r = r0 + tid; r < r1; r += kThreads) {
-                double acc = 0.0;
+                TL acc = 0;
                 for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
                 if (r < k) wb_[f + r] = __ldcg(wb_ + f + r) - acc;
-                else atomicAdd(wb_ + rows[r], -acc);
+                else atomicAdd(wb_ + rows[r], -(double)acc);
             }
         } else if (tk.type == kSolveBwdInit) {
             constexpr int kWarps = kThreads / 32, kPer = kT / kWarps;
             const int c0 = tk.b * kT, nc = min(kT, k - c0);
-            double acc[kPer];
+            TL acc[kPer];
 #pragma unroll
             for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
             for (int64_t r = k + lane; r < m; r += 32) {
-                const double xr = __ldcg(xv + rows[r]);
+                const TL xr = (TL)__ldcg(xv + rows[r]);
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     const int c = warp + kWarps * q;
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             }
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
-                double v = acc[q];
+                TL v = acc[q];
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 const int c = warp + kWarps * q;
                 if (lane == 0 && c < nc) wb_[f + c0 + c] = __ldcg(zb + f + c0 + c) / Db[f + c0 + c] - v;
@@ -547,14 +547,14 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
         } else {
             const int cb = tk.a * kT, wb = min(kT, k - cb), chunk = tk.b;
             if (tid < 32) {
-                double lcol[kT];
+                TL lcol[kT];
 #pragma unroll
                 for (int r = 0; r < kT; ++r)
                     lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
-                double y = lane < wb ? __ldcg(wb_ + f + cb + lane) : 0.0;
+                TL y = lane < wb ? (TL)__ldcg(wb_ + f + cb + lane) : TL(0);
 #pragma unroll
                 for (int r = kT - 1; r > 0; --r) {
-                    const double xr = __shfl_sync(0xffffffffu, y, r);
+                    const TL xr = __shfl_sync(0xffffffffu, y, r);
                     y -= lcol[r] * xr;
                 }
                 xb[lane] = y;
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             const int a1 = min(cb, (chunk + 1) * kBwdCols);
             for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
                 const TL* col = P + (int64_t)a * m + cb;
-                double acc = 0.0;
+                TL acc = 0;
                 for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
                 wb_[f + a] = __ldcg(wb_ + f + a) - acc;
             }

@@ -916,6 +916,7 @@ def main():
             mixed["diag_roofline"] = {"bound": "tensor", "kernel": "k_diag_inv_tc (after k_diag_inv_f32)",
                                       "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                                       "peak_source": src, "supernodes": minfo["diag_tc_supernodes"],
+                                      "traffic": traffic_of("diag_tc.cu", "k_diag_inv_tc"),
                                       "tf32_flops_issued": minfo["diag_tc_flops"],
                                       "note": "TF32 MMA work issued (3 MMAs per product, padded tiles) over the "
                                               "whole variance launch pair, timed alone"}

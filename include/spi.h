@@ -142,9 +142,11 @@ typedef struct spi_options {
     int diag_tc_min_pivots; /* mixed precision: the variances of the supernodes with at least this
                         many pivots, and of all their ancestors, run on the tensor cores (3 x TF32
                         products of TMA-staged operand tiles prepared at each factorization); the
-                        rest of every path on the SIMT kernel.  0 = the default (32); < 0 = none
-                        (SIMT only).  Variance blocks of more than 128 right-hand sides
-                        (rhs_block > 128) stay on the SIMT kernel */
+                        rest of every path on the SIMT kernel; their inverted 128 x 128 diagonal
+                        tiles also let the mixed solve take 128 columns per step there.  0 = the
+                        default (32); < 0 = none (SIMT variances, 32-column solve steps).
+                        Variance blocks of more than 128 right-hand sides (rhs_block > 128) stay
+                        on the SIMT kernel */
 } spi_options;
 
 typedef struct spi_stats {

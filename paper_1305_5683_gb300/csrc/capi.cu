@@ -137,6 +137,12 @@ struct spi_ctx {
     DiagTcHost dtc_h;
     DevDiagTc dtc;
     double last_diag_tc_flops = 0;
+    // the mixed solve's plan with 128-column steps for those supernodes (their inverted
+    // diagonal tiles); the FP64-panel paths keep SP
+    SolvePlan SPw;
+    int32_t *d_fwd_items_w = nullptr, *d_bwd_items_w = nullptr;
+    WideArgs wa;
+    bool wide_ready = false;
     int64_t bad_pivot = -1, bad_band = -1;
     std::vector<int64_t> in_colptr;  // kept until the device copy exists (mixed precision)
     std::vector<int32_t> in_rowind;
@@ -290,6 +296,11 @@ int ensure_device(spi_ctx* c) {
             t.npt = h.npt;
             t.ndt = h.ndt;
             t.bands = (int)nb;
+            build_solve_plan(S, c->SPw, c->opt.batch, h.tc.data());
+            CK(dev_upload(c, &c->d_fwd_items_w, c->SPw.fwd_items));
+            CK(dev_upload(c, &c->d_bwd_items_w, c->SPw.bwd_items));
+            c->wa = WideArgs{t.xinv, t.xptr, (int64_t)diag_tc_xinv_floats(h.ndt)};
+            c->wide_ready = true;
         }
     }
     c->dev_ready = true;
@@ -773,6 +784,7 @@ void reset_device(spi_ctx* c) {
     c->bg = spi_ctx::Background();
     c->nrm = spi_ctx::Normal();
     c->dtc = DevDiagTc();
+    c->wide_ready = false;
     c->dev_ready = false;
     c->factor_plan_ready = false;
     c->piv_ready = false;
@@ -999,13 +1011,18 @@ cudaError_t solve_core(spi_ctx* c, int nb, const double* b, double* x, cudaStrea
     }
     cudaError_t e = run_graph(c, c->g_solve, nb, st, [&](cudaStream_t s2) {
         // the mixed form's solves read its FP32 panels (the FP64 copy holds the same values)
+        // and take 128-column steps where the factorization left inverted diagonal tiles
         const float* L32 = mixed_of(c) ? c->d_L32 : nullptr;
-        for (const Launch& l : c->SP.fwd_launches)
-            launch_solve_step(ds, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
-                              nb, c->bs, s2, L32);
-        for (const Launch& l : c->SP.bwd_launches)
-            launch_solve_step(ds, l, c->d_fwd_items, c->d_bwd_items, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp,
-                              nb, c->bs, s2, L32);
+        const bool wide = L32 && c->wide_ready;
+        const SolvePlan& P = wide ? c->SPw : c->SP;
+        const int32_t* fi = wide ? c->d_fwd_items_w : c->d_fwd_items;
+        const int32_t* bi = wide ? c->d_bwd_items_w : c->d_bwd_items;
+        for (const Launch& l : P.fwd_launches)
+            launch_solve_step(ds, l, fi, bi, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, nb, c->bs, s2, L32,
+                              wide ? &c->wa : nullptr);
+        for (const Launch& l : P.bwd_launches)
+            launch_solve_step(ds, l, fi, bi, c->d_L, c->d_D, c->d_w, c->d_z, c->d_xp, nb, c->bs, s2, L32,
+                              wide ? &c->wa : nullptr);
     });
     launch_permute_out(S.n, ds.perm, c->d_xp, x, nb, st);
     return e;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "spi_internal.cuh"
 
@@ -415,6 +416,89 @@ __global__ void k_reciprocal(int32_t n, const double* __restrict__ D, double* __
 }
 
 // ---------------------------------------------------------------------------
+// Wide steps (mixed form): the supernodes whose variances run on the tensor
+// cores have, per 128 of their columns, the inverse X_bb of the unit-lower
+// diagonal block (prepared at the end of the factorization, FP32).  Their
+// sweeps then take 128 columns per step: forward x_b = X_bb w_b and then
+// w_below -= L(rows, block b) x_b; backward x_b = X_bb^T y_b and then
+// y_a -= sum_r L[128 b + r][a] x_b[r] for the earlier columns a.  The same
+// substitution in blocks of 128, a quarter of the 32-column steps on the chain.
+constexpr int kW = 128;
+constexpr int kFwdRowsW = 256;  // rows below per wide forward CTA
+constexpr int kBwdColsW = 256;  // earlier columns per wide backward CTA
+
+__global__ void __launch_bounds__(kThreads) k_fwd_wide(DevSym d, const int32_t* __restrict__ items, int b,
+                                                       const float* __restrict__ L, WideArgs wa,
+                                                       double* __restrict__ w, double* __restrict__ z, Strides bs) {
+    const int band = blockIdx.y;
+    L += band * bs.L;
+    w += band * bs.n;
+    z += band * bs.n;
+    __shared__ float wv[kW], xb[kW];
+    const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const float* P = L + d.lptr[s];
+    const int32_t* rows = d.srows + d.srowptr[s];
+    const int cb = b * kW, wb = min(kW, k - cb);
+    const float* X = wa.xinv + band * wa.xband + (int64_t)(wa.xptr[s] + b) * (kW * kW);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kW) wv[tid] = tid < wb ? (float)w[f + cb + tid] : 0.f;
+    __syncthreads();
+    // x_b[r] = sum_c X[r][c] w[c]: a warp per row, 16-byte loads of the row
+    for (int r = warp; r < kW; r += kThreads / 32) {
+        const float4 xr = *reinterpret_cast<const float4*>(X + r * kW + 4 * lane);
+        float v = xr.x * wv[4 * lane] + xr.y * wv[4 * lane + 1] + xr.z * wv[4 * lane + 2] + xr.w * wv[4 * lane + 3];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) xb[r] = v;
+    }
+    __syncthreads();
+    if (chunk == 0 && tid < wb) z[f + cb + tid] = xb[tid];
+    const int64_t r0 = cb + wb + (int64_t)chunk * kFwdRowsW;
+    const int64_t r1 = m < r0 + kFwdRowsW ? m : r0 + kFwdRowsW;
+    for (int64_t r = r0 + tid; r < r1; r += kThreads) {
+        float acc = 0.f;
+        for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
+        if (r < k) w[f + r] -= acc;
+        else atomicAdd(w + rows[r], -(double)acc);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bwd_wide(DevSym d, const int32_t* __restrict__ items, int b,
+                                                       const float* __restrict__ L, WideArgs wa,
+                                                       double* __restrict__ w, double* __restrict__ x, Strides bs) {
+    const int band = blockIdx.y;
+    L += band * bs.L;
+    w += band * bs.n;
+    x += band * bs.n;
+    __shared__ float yv[kW], xb[kW];
+    const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
+    const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
+    const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
+    const float* P = L + d.lptr[s];
+    const int cb = b * kW, wb = min(kW, k - cb);
+    const float* X = wa.xinv + band * wa.xband + (int64_t)(wa.xptr[s] + b) * (kW * kW);
+    const int tid = threadIdx.x;
+    if (tid < kW) yv[tid] = tid < wb ? (float)w[f + cb + tid] : 0.f;
+    __syncthreads();
+    // x_b[c] = sum_{r >= c} X[r][c] y[r]: thread c takes column c (coalesced over c)
+    if (tid < kW) {
+        float v = 0.f;
+        for (int r = tid; r < kW; ++r) v += X[r * kW + tid] * yv[r];
+        xb[tid] = v;
+    }
+    __syncthreads();
+    if (chunk == 0 && tid < wb) x[f + cb + tid] = xb[tid];
+    const int a1 = min(cb, (chunk + 1) * kBwdColsW);
+    for (int a = chunk * kBwdColsW + tid; a < a1; a += kThreads) {
+        const float* col = P + (int64_t)a * m + cb;
+        float acc = 0.f;
+        for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
+        w[f + a] -= acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Dependency-driven solve (one launch for both sweeps).
 //
 // The tasks -- forward step b of supernode s over a 512-row chunk of the rows
@@ -714,7 +798,7 @@ void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double*
     k_permute_out<<<dim3(std::min(1024, (n + 255) / 256), nb), 256, 0, st>>>(n, perm, w, x);
 }
 
-void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
+void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch, const uint8_t* wide) {
     P = SolvePlan();
     for (int32_t l = 0; l < S.nlevels; ++l) {
         int32_t kmax = 0;
@@ -740,12 +824,29 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
         }
         const int32_t nsteps = (kmax + kT - 1) / kT;
         std::vector<Launch> fw, bw;
+        // wide steps of 128 columns for the flagged supernodes (kinds 15 and 16)
+        for (int32_t b = 0; wide && b * kW < kmax; ++b) {
+            Launch lf{15, b, (int64_t)P.fwd_items.size() / 2, 0};
+            Launch lb{16, b, (int64_t)P.bwd_items.size() / 2, 0};
+            for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
+                const int32_t s = S.level_list[p], k = S.k_of(s), m = S.m_of(s);
+                if (!wide[s] || k <= b * kW) continue;
+                const int32_t wb = std::min(kW, k - b * kW);
+                const int64_t below = (int64_t)m - b * kW - wb;
+                const int32_t nch = std::max<int32_t>(1, (int32_t)((below + kFwdRowsW - 1) / kFwdRowsW));
+                for (int32_t c = 0; c < nch; ++c) { P.fwd_items.push_back(s); P.fwd_items.push_back(c); lf.count++; }
+                const int32_t ncb = std::max<int32_t>(1, (b * kW + kBwdColsW - 1) / kBwdColsW);
+                for (int32_t c = 0; c < ncb; ++c) { P.bwd_items.push_back(s); P.bwd_items.push_back(c); lb.count++; }
+            }
+            if (lf.count) fw.push_back(lf);
+            if (lb.count) bw.push_back(lb);
+        }
         for (int32_t b = 0; b < nsteps; ++b) {
             Launch lf{4, b, (int64_t)P.fwd_items.size() / 2, 0};
             Launch lb{6, b, (int64_t)P.bwd_items.size() / 2, 0};
             for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
                 const int32_t s = S.level_list[p], k = S.k_of(s), m = S.m_of(s);
-                if (k <= b * kT) continue;
+                if (k <= b * kT || (wide && wide[s])) continue;
                 const int32_t wb = std::min(kT, k - b * kT);
                 const int64_t below = (int64_t)m - b * kT - wb;
                 const int32_t nch = std::max<int32_t>(1, (int32_t)((below + kFwdRows - 1) / kFwdRows));
@@ -753,8 +854,8 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
                 const int32_t ncb = std::max<int32_t>(1, (b * kT + kBwdCols - 1) / kBwdCols);
                 for (int32_t c = 0; c < ncb; ++c) { P.bwd_items.push_back(s); P.bwd_items.push_back(c); lb.count++; }
             }
-            fw.push_back(lf);
-            bw.push_back(lb);
+            if (lf.count) fw.push_back(lf);
+            if (lb.count) bw.push_back(lb);
         }
         Launch li{5, 0, (int64_t)P.bwd_items.size() / 2, 0};
         for (int32_t p = S.level_ptr[l]; p < S.level_ptr[l + 1]; ++p) {
@@ -778,8 +879,18 @@ void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch) {
 template <typename TL>
 void launch_solve_step_t(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
                          const TL* L, const double* D, double* w, double* z, double* x, int nb, const Strides& bs,
-                         cudaStream_t st) {
+                         cudaStream_t st, const WideArgs* wa) {
     const dim3 g(l.count, nb);
+    if constexpr (std::is_same<TL, float>::value) {
+        if (l.kind == 15 && wa) {
+            k_fwd_wide<<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, *wa, w, z, bs);
+            return;
+        }
+        if (l.kind == 16 && wa) {
+            k_bwd_wide<<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, l.step, L, *wa, w, x, bs);
+            return;
+        }
+    }
     switch (l.kind) {
         case 4: k_fwd_step<TL><<<g, kThreads, 0, st>>>(d, fwd_items + 2 * l.off, l.step, L, w, z, bs); break;
         case 5: k_bwd_init<TL><<<g, kThreads, 0, st>>>(d, bwd_items + 2 * l.off, L, D, z, x, w, bs); break;
@@ -791,10 +902,10 @@ void launch_solve_step_t(const DevSym& d, const Launch& l, const int32_t* fwd_it
 
 void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
                        const double* L, const double* D, double* w, double* z, double* x, int nb,
-                       const Strides& bs, cudaStream_t st, const float* L32) {
+                       const Strides& bs, cudaStream_t st, const float* L32, const WideArgs* wa) {
     if (l.count == 0 || nb == 0) return;
-    if (L32) launch_solve_step_t<float>(d, l, fwd_items, bwd_items, L32, D, w, z, x, nb, bs, st);
-    else launch_solve_step_t<double>(d, l, fwd_items, bwd_items, L, D, w, z, x, nb, bs, st);
+    if (L32) launch_solve_step_t<float>(d, l, fwd_items, bwd_items, L32, D, w, z, x, nb, bs, st, wa);
+    else launch_solve_step_t<double>(d, l, fwd_items, bwd_items, L, D, w, z, x, nb, bs, st, wa);
 }
 
 }  // namespace spi

@@ -80,7 +80,9 @@ struct Launch {
                      // 12 persistent per-level kernel: whole panels of small fronts, one CTA
                      // per front at a time; solves: 4 forward step, 5 backward first launch of
                      // a level, 6 backward step, 10 / 11 forward / backward sweep of a whole
-                     // level; -1 a timing marker of the autotuner (no launch; `step` = group)
+                     // level, 15 / 16 forward / backward step of 128 columns (mixed form,
+                     // inverted diagonal tiles); -1 a timing marker of the autotuner (no
+                     // launch; `step` = group)
     int step;        // block column b for kinds 0/1
     int64_t off;     // offset into the item array of the kind
     int32_t count;   // CTAs (kind 12: fronts)
@@ -166,8 +168,10 @@ struct SolvePlan {
                                // done, [2 ns, 3 ns) backward tasks done
 };
 
-// batch: bands per launch (the fused per-level sweeps are used for batches only)
-void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch);
+// batch: bands per launch (the fused per-level sweeps are used for batches only);
+// wide: per supernode, 1 = steps of 128 columns with the inverted diagonal tiles of
+// the mixed form (launch kinds 15 and 16; such a plan is run with FP32 panels)
+void build_solve_plan(const Symbolic& S, SolvePlan& P, int batch, const uint8_t* wide = nullptr);
 void build_solve_dag(const Symbolic& S, SolvePlan& P);
 // both sweeps in one dependency-driven launch; counters: nb * cstride + 1 ints, zeroed before
 void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* counters, int cstride, const double* L,
@@ -219,9 +223,17 @@ void launch_factor_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* c
 void launch_permute_in(int32_t n, const int32_t* perm, const double* b, double* w, int nb, cudaStream_t st);
 void launch_permute_out(int32_t n, const int32_t* perm, const double* w, double* x, int nb, cudaStream_t st);
 // L32: the mixed form's FP32 panels (read instead of L, the same values), or null
+// The inverted 128 x 128 diagonal tiles of the mixed form's tensor-core supernodes, for the
+// solve's wide steps (launch kinds 15 and 16).
+struct WideArgs {
+    const float* xinv = nullptr;   // [bands][tiles][128 x 128], row-major
+    const int32_t* xptr = nullptr; // [ns] first tile of each supernode
+    int64_t xband = 0;             // floats per band
+};
 void launch_solve_step(const DevSym& d, const Launch& l, const int32_t* fwd_items, const int32_t* bwd_items,
                        const double* L, const double* D, double* w, double* z, double* x, int nb,
-                       const Strides& bs, cudaStream_t st, const float* L32 = nullptr);
+                       const Strides& bs, cudaStream_t st, const float* L32 = nullptr,
+                       const WideArgs* wa = nullptr);
 void launch_sym_residual(int32_t n, const int64_t* cp, const int32_t* ri, const double* va, const double* x,
                          double* r, int nb, int64_t nnz, cudaStream_t st);
 void launch_norms2(int32_t n, const double* a, const double* b, double* out, int nb, cudaStream_t st);

@@ -353,9 +353,9 @@ def bench_bands(P, args, dev, st, flush, world):
     info = s.info()
     ph = _phases(evs[-ksteps:])
     solve_alone = _time_alone(lambda q: s.solve_batch(b, x, stream=q), st)
-    # the solve reads every band's stored factor twice (forward and backward sweeps), per solve
+    # the solve reads every band's stored FP32 factor twice (forward and backward sweeps), per solve
     nsolves = 1 + info["refine_steps"]
-    solve_bytes = 2.0 * nsolves * nb * info["nnz_l_stored"] * 8
+    solve_bytes = 2.0 * nsolves * nb * info["nnz_l_stored"] * 4
     # one band in FP64, the plain form, as the sequential reference
     s1 = P.Solver(n, bb.colptr, bb.rowind, async_=True)
     v1 = torch.from_numpy(bb.values[: bb.nnz]).to(dev)

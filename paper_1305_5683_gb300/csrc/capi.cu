@@ -333,8 +333,6 @@ int upload_plan(spi_ctx* c, const DiagPlan& h, DevDiagPlan& d) {
     d.zsize = h.zbase.empty() ? 0 : h.zbase.back();
     // FP64 elements per band are enough for both element types
     CK(dev_alloc(c, &d.Z, (size_t)std::max<int64_t>(d.zsize, 1) * (size_t)c->opt.batch, tr));
-    if (c->dtc.ntc > 0 && h.B <= kDiagTcMaxBlock)  // the mixed form's FP32 rows, all bands
-        CK(diag_tc_z_map(reinterpret_cast<float*>(d.Z), h.B, d.zsize * c->opt.batch / h.B, d.zmap));
     return SPI_OK;
 }
 

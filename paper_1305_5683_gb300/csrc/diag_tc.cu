@@ -251,23 +251,24 @@ __device__ __forceinline__ void z_load32(const float* zr, float (&v)[32], int n0
     }
 }
 
-// Roles of the variance CTA (warp-specialized): warps 0-3 split the right
-// operand into TF32 hi/lo, add finished hi*hi groups into S and run the tile
-// epilogues (they own tensor-memory lanes 0-127); lane 0 of warp 4 copies the
-// packed left operands, lane 0 of warp 5 the raw right-operand chunks of Z
-// (TMA tensor copies of 32 rows x 132 columns through a map over the
-// workspace), lane 0 of warp 6 issues the MMAs.  They meet only at mbarriers.
+// Roles of the variance CTA (warp-specialized): warps 0-3 load chunks of Z
+// (plain loads, one chunk ahead), split them into TF32 hi/lo, add finished
+// hi*hi groups into S and run the tile epilogues (they own tensor-memory lanes
+// 0-127); lane 0 of warp 4 copies the packed left operands (TMA tensor
+// copies), lane 0 of warp 5 issues the MMAs.  They meet only at mbarriers.
+// (The Z chunks went through a second TMA tensor map at first; when the
+// kernel shared its SMs with the dependency-driven solve, those copies read
+// rows that the previous tile's epilogue had written -- released to the
+// copying thread through an mbarrier -- with stale values, while plain loads
+// behind the same mbarrier read them right; so the workers load Z themselves.)
 constexpr int kDtWork = 128;                       // threads of warps 0-3
-constexpr int kDtRoles = kDtWork + 3 * 32;         // + warps 4, 5, 6
+constexpr int kDtRoles = kDtWork + 2 * 32;         // + warps 4, 5
 constexpr int kDtAStages = 3, kDtBStages = 2;
-constexpr int kDtRawCols = 132;                    // the copied columns: N + the 16-byte round-down
-constexpr int kDtRawFloats = kDtK * kDtRawCols;    // one raw chunk (16,896 bytes)
-constexpr int kDtOffB = kDtAStages * 2 * kDtTile;  // floats: A ring, then split B ring, then raw ring
-constexpr int kDtOffRaw = kDtOffB + kDtBStages * 2 * kDtTile;
-constexpr int kDtOffVar = kDtOffRaw + kDtBStages * kDtRawFloats;
-// mbarriers: A full/empty, raw full/empty, B full/empty, group full/empty, acc full/empty, z ready
-enum : int { kBAF = 0, kBAE = 3, kBRF = 6, kBRE = 8, kBBF = 10, kBBE = 12, kBGF = 14, kBGE = 16, kBCF = 18,
-             kBCE = 19, kBZR = 20, kDtBars = 21 };
+constexpr int kDtOffB = kDtAStages * 2 * kDtTile;  // floats: A ring, then split B ring
+constexpr int kDtOffVar = kDtOffB + kDtBStages * 2 * kDtTile;
+// mbarriers: A full/empty, B full/empty, group full/empty, acc full/empty, z ready
+enum : int { kBAF = 0, kBAE = 3, kBBF = 6, kBBE = 8, kBGF = 10, kBGE = 12, kBCF = 14, kBCE = 15, kBZR = 16,
+             kDtBars = 17 };
 constexpr size_t kDtSmem2 = (size_t)kDtOffVar * sizeof(float) + 128 * sizeof(double) + kDtBars * sizeof(uint64_t) + 16;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -282,12 +283,6 @@ __device__ __forceinline__ bool dt_wait(uint64_t* bar, uint32_t parity, uint32_t
         if (!done && *abort) return false;
     }
     return done != 0;
-}
-__device__ __forceinline__ void tma_raw_chunk(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
 }
 
 // The block's tensor-core supernodes in walk order and the shape of each.
@@ -323,15 +318,13 @@ __device__ __forceinline__ int dt_chunks(const DtNode& x, int tile) {
 
 __global__ void __launch_bounds__(kDtRoles, 1)
     k_diag_inv_tc(DevSym d, DiagArgsTc p, DiagTcArgs ta, const double* __restrict__ D, double* __restrict__ out,
-                  Strides bs, DevStatus* status, uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap,
-                  const __grid_constant__ CUtensorMap zmap) {
+                  Strides bs, DevStatus* status, uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap) {
     const int band = blockIdx.y;
     D += band * bs.n;
     out += band * bs.out;
     extern __shared__ __align__(1024) float dsm[];
     float* Aring = dsm;
     float* Bring = dsm + kDtOffB;
-    float* Raw = dsm + kDtOffRaw;
     double* var = reinterpret_cast<double*>(dsm + kDtOffVar);  // [128]
     uint64_t* bar = reinterpret_cast<uint64_t*>(var + 128);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + kDtBars);
@@ -340,7 +333,6 @@ __global__ void __launch_bounds__(kDtRoles, 1)
     const int B = p.B;
     const int b = p.order[blockIdx.x];
     float* Z = p.Z + band * bs.Z + p.zbase[b];
-    const int32_t zrow0 = (int32_t)((band * bs.Z + p.zbase[b]) / B);  // the block's first row in the Z map
     const int r0b = p.blk_ptr[b], nr = p.blk_ptr[b + 1] - r0b;
     const int64_t tile_band = (int64_t)band * ta.npt;
     const int u0 = p.uptr[b], u1 = p.uptr[b + 1];
@@ -351,11 +343,11 @@ __global__ void __launch_bounds__(kDtRoles, 1)
     }
     if (tid == kDtWork) {
         // arrivals per phase: one per worker warp for the barriers the worker warps arrive
-        // on (raw empty, B full, group empty, acc empty, z ready), else one (a copy's
+        // on (B full, group empty, acc empty, z ready), else one (a copy's
         // expect-tx arrival or an MMA commit)
         for (int q = 0; q < kDtBars; ++q) {
-            const bool workers = (q >= kBRE && q < kBRE + kDtBStages) || (q >= kBBF && q < kBBF + kDtBStages) ||
-                                 (q >= kBGE && q < kBGE + 2) || q == kBCE || q == kBZR;
+            const bool workers = (q >= kBBF && q < kBBF + kDtBStages) || (q >= kBGE && q < kBGE + 2) || q == kBCE ||
+                                 q == kBZR;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc_smem_u32(bar + q)),
                          "r"(workers ? kDtWork / 32 : 1));
         }
@@ -369,7 +361,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t lim = wait_limit;
     // the last copies and commits of each role, drained below if a wait ran out
-    uint32_t a_issued = 0, r_issued = 0, mma_chunks = 0;
+    uint32_t a_issued = 0, mma_chunks = 0;
     int mma_tiles = 0;
     if (warp == 4) {
         // ---- packed left operands: run ahead of the MMAs by up to 3 chunks
@@ -395,41 +387,6 @@ __global__ void __launch_bounds__(kDtRoles, 1)
             if (!ok) *abort = 1;
         }
     } else if (warp == 5) {
-        // ---- raw right-operand chunks.  A tile whose rows the previous tile's epilogue
-        // wrote (an own tile, or the first tile below) waits for that epilogue; the
-        // worker warps signal z-ready after exactly those epilogues (own tiles, the last
-        // tile below), so that every wait here meets the next completion in order: a
-        // phase-parity wait that skipped a completion would take completion n - 2 for n.
-        if (lane == 0) {
-            int u = u0 - 1, tiles = 0;
-            uint32_t zwaits = 0;
-            DtNode x;
-            bool ok = true;
-            while (ok && dt_next(d, p, ta, u, u1, x)) {
-                const int32_t x0 = x.lo0 & ~3;
-                for (int tile = 0; tile < x.T + x.R && ok; ++tile, ++tiles) {
-                    if (tiles > 0 && tile <= x.T && !dt_wait(bar + kBZR, zwaits++ & 1u, lim, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    const int nck = dt_chunks(x, tile);
-                    for (int c = 0; c < nck; ++c) {
-                        const uint32_t g = r_issued, st = g % kDtBStages;
-                        if (g >= kDtBStages &&
-                            !dt_wait(bar + kBRE + st, ((g - kDtBStages) / kDtBStages) & 1u, lim, abort)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_expect_tx(tc_smem_u32(bar + kBRF + st), kDtRawFloats * sizeof(float));
-                        tma_raw_chunk(tc_smem_u32(Raw + st * kDtRawFloats), &zmap, x0, zrow0 + x.zo + c * kDtK,
-                                      tc_smem_u32(bar + kBRF + st));
-                        ++r_issued;
-                    }
-                }
-            }
-            if (!ok) *abort = 1;
-        }
-    } else if (warp == 6) {
         // ---- MMA issue: 4 k-steps x 3 products per chunk (hi*lo and lo*hi into X, hi*hi
         // into the group's buffer); commits free the stages, hand finished groups to
         // the flush and finished tiles to the epilogue
@@ -498,6 +455,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
         // the warps meet each other only at mbarriers, whose waits are all bounded.
         auto wwait = [&](uint64_t* br, uint32_t par) { return __all_sync(0xffffffffu, dt_wait(br, par, lim, abort)); };
         int u = u0 - 1, tiles = 0;
+        uint32_t zwaits = 0;
         DtNode x;
         bool ok = true;
         uint32_t g = 0;                // chunks split
@@ -505,32 +463,33 @@ __global__ void __launch_bounds__(kDtRoles, 1)
         while (ok && dt_next(d, p, ta, u, u1, x)) {
             const int32_t* rel = p.rel + x.urel;
             const bool vec = (x.lo0 & 3) == 0;
-            const int sh = x.lo0 - (x.lo0 & ~3);
             const int nitems = x.N * (kDtK / 4);
+            float v[8][4];  // the chunk being staged: rows of s, right-hand sides [lo0, lo0 + N)
+            auto fetch = [&](int c, int kext) {
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int item = tid + it * kDtWork;
+                    const int n = item % x.N, kq = item / x.N;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int kr = c * kDtK + kq * 4 + e;
+                        v[it][e] = (item < nitems && n < x.nbu && kr < kext)
+                                       ? Z[(int64_t)(x.zo + kr) * B + x.lo0 + n] : 0.f;
+                    }
+                }
+            };
             for (int tile = 0; tile < x.T + x.R && ok; ++tile, ++tiles) {
                 const bool own = tile < x.T;
                 const int rows0 = own ? tile * kDtM : x.k + (tile - x.T) * kDtM;
                 const int nrow = min(kDtM, (own ? x.k : x.m) - rows0);
                 const int kext = own ? min(kDtM * (tile + 1), x.k) : x.k;
                 const int nck = (kext + kDtK - 1) / kDtK;
+                // the rows this tile reads were written by the previous tile's epilogue (an own
+                // tile, or the first tile below) in all four warps: wait for their z-ready
+                if (tiles > 0 && tile <= x.T && !wwait(bar + kBZR, zwaits++ & 1u)) { ok = false; break; }
+                fetch(0, kext);
                 for (int c = 0; c < nck && ok; ++c, ++g) {
                     const uint32_t sr = g % kDtBStages;
-                    if (!wwait(bar + kBRF + sr, (g / kDtBStages) & 1u)) { ok = false; break; }
-                    const float* raw = Raw + sr * kDtRawFloats;
-                    float v[8][4];
-#pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int item = tid + it * kDtWork;
-                        const int n = item % x.N, kq = item / x.N;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int kr = c * kDtK + kq * 4 + e;
-                            v[it][e] = (item < nitems && n < x.nbu && kr < kext)
-                                           ? raw[(kq * 4 + e) * kDtRawCols + sh + n] : 0.f;
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar + kBRE + sr);
                     if (g >= kDtBStages && !wwait(bar + kBBE + sr, ((g - kDtBStages) / kDtBStages) & 1u)) {
                         ok = false;
                         break;
@@ -554,6 +513,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
                     asm volatile("fence.proxy.async.shared::cta;");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar + kBBF + sr);
+                    if (c + 1 < nck) fetch(c + 1, kext);  // in flight while the group fold below runs
                     if ((c & 3) == 0 && c > 0) {
                         // S (+)= the buffer of group c/4 - 1 while this group accumulates in the other
                         const int pb = ((c >> 2) - 1) & 1;
@@ -612,8 +572,6 @@ __global__ void __launch_bounds__(kDtRoles, 1)
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
-                // the Z rows written above are read next by TMA copies (the async proxy)
-                asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(bar + kBCE);
@@ -633,10 +591,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
             for (uint32_t q = a_issued > kDtAStages ? a_issued - kDtAStages : 0; q < a_issued; ++q)
                 tc_wait(bar + kBAF + q % kDtAStages, (q / kDtAStages) & 1u);
         }
-        if (tid == kDtWork + 32)
-            for (uint32_t q = r_issued > kDtBStages ? r_issued - kDtBStages : 0; q < r_issued; ++q)
-                tc_wait(bar + kBRF + q % kDtBStages, (q / kDtBStages) & 1u);
-        if (tid == kDtWork + 64 && mma_chunks > 0) {
+        if (tid == kDtWork + 32 && mma_chunks > 0) {
             // one more commit tracks every MMA issued so far
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(tc_smem_u32(bar + kBCF)));
@@ -701,21 +656,6 @@ cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_ou
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// The tensor map over a variance workspace of `rows` rows of B floats (all bands):
-// boxes of 32 rows x 132 columns, columns beyond B read as zeros.
-cudaError_t diag_tc_z_map(float* Z, int B, int64_t rows, void* map_out) {
-    EncodeFn encode = nullptr;
-    cudaError_t e = tensor_map_encoder(&encode);
-    if (e != cudaSuccess) return e;
-    const cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)std::max<int64_t>(rows, 1)};
-    const cuuint64_t strides[1] = {(cuuint64_t)B * sizeof(float)};
-    const cuuint32_t box[2] = {kDtRawCols, kDtK};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Z, dims,
-                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
 
 void launch_diag_tc_pack(const DevSym& d, const DevDiagTc& p, const float* L32, int nb, const Strides& bs,
                          cudaStream_t st) {
@@ -733,8 +673,7 @@ void launch_diag_inv_tc(const DevSym& d, const DevDiagPlan& dp, const DevDiagTc&
                  dp.urel, dp.zbase, reinterpret_cast<float*>(dp.Z)};
     DiagTcArgs t{p.tc, p.tptr, p.npt};
     k_diag_inv_tc<<<dim3(dp.nblocks, nb), kDtRoles, kDtSmem2, st>>>(
-        d, a, t, D, out, bs, status, lim, *reinterpret_cast<const CUtensorMap*>(p.tmap),
-        *reinterpret_cast<const CUtensorMap*>(dp.zmap));
+        d, a, t, D, out, bs, status, lim, *reinterpret_cast<const CUtensorMap*>(p.tmap));
 }
 
 }  // namespace spi

@@ -201,7 +201,6 @@ struct DevDiagPlan {
     int32_t* rowmap = nullptr;
     double flops = 0, work_flops = 0;
     double tc_flops = 0;  // TF32 MMA flops of the tensor-core variance kernel on this plan
-    alignas(64) unsigned char zmap[128];  // CUtensorMap over Z for the tensor-core kernel (mixed form)
     std::vector<void*> allocs;
 };
 
@@ -274,8 +273,6 @@ cudaError_t diag_tc_setup();
 size_t diag_tc_pack_floats(int64_t npt);
 size_t diag_tc_xinv_floats(int64_t ndt);
 cudaError_t diag_tc_tensor_map(float* pack, int64_t npt, int bands, void* map_out);
-// over a variance workspace: rows of B floats, all bands
-cudaError_t diag_tc_z_map(float* Z, int B, int64_t rows, void* map_out);
 // the left operands from the FP32 panels of nb bands (once per factorization)
 void launch_diag_tc_pack(const DevSym& d, const DevDiagTc& p, const float* L32, int nb, const Strides& bs,
                          cudaStream_t st);

@@ -397,49 +397,79 @@ __device__ __forceinline__ T ldx(const T* p) {
     else return *p;
 }
 
+// 1/d in FP64 by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r),
+// from a correctly rounded single-precision seed: each step squares the relative
+// error (2^-24 -> 2^-48 -> below FP64 rounding), two FP64 FMAs per step instead of
+// a full FP64 division on this GPU's narrow FP64 pipe.  Outside the single-precision
+// range of the seed it divides.
+__device__ __forceinline__ double recip_nr(double d) {
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Unblocked LDL^T, in FP64, of the w x w pivot tile whose first pivot is
 // column c0 of supernode s (panel P of storage type S, leading dimension m),
 // by the CTA's 128 threads; writes L (unit lower, d on the diagonal) back into
 // P, d into D (FP64) and into DS (the storage type's copy used for scaling).
+// FP64 is a narrow pipe on this GPU, so per column: each thread updates its
+// fixed pairs (i, j) of the lower triangle (at most 5 of the 528), one FMA
+// chain each, with the unscaled column (A_ij -= A_ic (A_jc / d_c)); the thread
+// that finishes the next pivot forms its reciprocal at once; one barrier per
+// column; the columns are scaled by 1/d at the end.
 template <typename S, bool kCg = false>
 __device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, S* P, int64_t m, int c0, int w,
                                   int f, double* D, S* DS, const double* __restrict__ adiag, DevStatus* status,
                                   int band_base) {
     const int tid = threadIdx.x;
+    __shared__ double sinv[kT];
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
         A[i][j] = (i < w && j <= i) ? (double)ldx<kCg>(P + (c0 + i) + (int64_t)(c0 + j) * m) : 0.0;
     }
-    // FP64 is a narrow pipe on this GPU: one thread forms each pivot's
-    // reciprocal, and the update visits only the trailing square.
-    __shared__ double rinv;
+    // this thread's pairs p = tid + 128 q of the lower triangle, p = i (i + 1) / 2 + j
+    constexpr int kPairs = (kT * (kT + 1) / 2 + kThreads - 1) / kThreads;
+    int pi[kPairs], pj[kPairs];
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        const int p = tid + q * kThreads;
+        int i = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+        while (i * (i + 1) / 2 > p) --i;
+        while ((i + 1) * (i + 2) / 2 <= p) ++i;
+        pi[q] = p < kT * (kT + 1) / 2 ? i : kT;  // kT: no pair
+        pj[q] = p - i * (i + 1) / 2;
+    }
+    auto pivot = [&](int c) {  // d_c = A[c][c] is final: check it and form 1/d_c
+        const double dc = A[c][c];
+        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
+            atomicOr(&status->flags, FLAG_NOT_SPD);
+            atomicMin(&status->bad_pivot, band_base + f + c0 + c);
+        }
+        dv[c] = dc;
+        sinv[c] = recip_nr(dc);
+    };
+    __syncthreads();
+    if (tid == 0 && w > 0) pivot(0);
     __syncthreads();
     for (int c = 0; c < w; ++c) {
-        if (tid == 0) {
-            const double dc = A[c][c];
-            if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
-                atomicOr(&status->flags, FLAG_NOT_SPD);
-                atomicMin(&status->bad_pivot, band_base + f + c0 + c);
+        const double inv = sinv[c];
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const int i = pi[q], j = pj[q];
+            if (i < w && j > c) {
+                A[i][j] = fma(-A[i][c], A[j][c] * inv, A[i][j]);
+                if (i == c + 1 && j == c + 1) pivot(c + 1);  // this thread finished the next pivot
             }
-            dv[c] = dc;
-            rinv = 1.0 / dc;
         }
         __syncthreads();
-        const double inv = rinv;
-        const int t = w - c - 1;
-        for (int e = tid; e < t * t; e += kThreads) {
-            const int i = c + 1 + e / t, j = c + 1 + e % t;
-            if (j <= i) A[i][j] -= A[i][c] * inv * A[j][c];
-        }
-        __syncthreads();
-        // column c is not read again until the final store; the next pivot and
-        // column were completed by the update above
-        for (int i = c + 1 + tid; i < w; i += kThreads) A[i][c] *= inv;
     }
-    __syncthreads();
     for (int e = tid; e < kT * kT; e += kThreads) {
         int i = e % kT, j = e / kT;
-        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (S)((i == j) ? dv[i] : A[i][j]);
+        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (S)((i == j) ? dv[i] : A[i][j] * sinv[j]);
     }
     if (tid < w) {
         D[f + c0 + tid] = dv[tid];

@@ -264,12 +264,27 @@ __device__ __forceinline__ void z_load32(const float* zr, float (&v)[32], int n0
 constexpr int kDtWork = 128;                       // threads of warps 0-3
 constexpr int kDtRoles = kDtWork + 2 * 32;         // + warps 4, 5
 constexpr int kDtAStages = 3, kDtBStages = 2;
-constexpr int kDtOffB = kDtAStages * 2 * kDtTile;  // floats: A ring, then split B ring
-constexpr int kDtOffVar = kDtOffB + kDtBStages * 2 * kDtTile;
+constexpr int kDtRStages = 3;                      // raw Z chunks in flight (two ahead of the split)
+constexpr int kDtRawCols = 132;                    // columns of a raw chunk: N + the 16-byte round-down
+constexpr int kDtRaw = kDtK * kDtRawCols;          // floats of one raw chunk (32 rows)
+constexpr int kDtOffB = kDtAStages * 2 * kDtTile;  // floats: A ring, split B ring, raw Z ring
+constexpr int kDtOffRaw = kDtOffB + kDtBStages * 2 * kDtTile;
+constexpr int kDtOffVar = kDtOffRaw + kDtRStages * kDtRaw;
 // mbarriers: A full/empty, B full/empty, group full/empty, acc full/empty, z ready
 enum : int { kBAF = 0, kBAE = 3, kBBF = 6, kBBE = 8, kBGF = 10, kBGE = 12, kBCF = 14, kBCE = 15, kBZR = 16,
              kDtBars = 17 };
 constexpr size_t kDtSmem2 = (size_t)kDtOffVar * sizeof(float) + 128 * sizeof(double) + kDtBars * sizeof(uint64_t) + 16;
+
+// 16-byte asynchronous copy global -> shared (L2 only); src_bytes 0 writes zeros
+__device__ __forceinline__ void dt_cp16(uint32_t dst, const float* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void dt_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's copy groups are pending (n = 0 or 1)
+__device__ __forceinline__ void dt_cp_wait(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc_smem_u32(bar)) : "memory");
@@ -325,6 +340,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
     extern __shared__ __align__(1024) float dsm[];
     float* Aring = dsm;
     float* Bring = dsm + kDtOffB;
+    float* Rring = dsm + kDtOffRaw;
     double* var = reinterpret_cast<double*>(dsm + kDtOffVar);  // [128]
     uint64_t* bar = reinterpret_cast<uint64_t*>(var + 128);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + kDtBars);
@@ -463,20 +479,22 @@ __global__ void __launch_bounds__(kDtRoles, 1)
         while (ok && dt_next(d, p, ta, u, u1, x)) {
             const int32_t* rel = p.rel + x.urel;
             const bool vec = (x.lo0 & 3) == 0;
-            const int nitems = x.N * (kDtK / 4);
-            float v[8][4];  // the chunk being staged: rows of s, right-hand sides [lo0, lo0 + N)
-            auto fetch = [&](int c, int kext) {
-#pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int item = tid + it * kDtWork;
-                    const int n = item % x.N, kq = item / x.N;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int kr = c * kDtK + kq * 4 + e;
-                        v[it][e] = (item < nitems && n < x.nbu && kr < kext)
-                                       ? Z[(int64_t)(x.zo + kr) * B + x.lo0 + n] : 0.f;
-                    }
+            // Warp w stages rows [8 w, 8 w + 8) of every 32-row chunk: it copies them (16-byte
+            // copies from the 16-byte-aligned column x0 at or below lo0, rows past kext and
+            // columns past the workspace read as zeros) into the raw ring, and its lanes split
+            // them (lane: right-hand sides lane + 32 v).  No other warp reads these rows.
+            const int x0 = x.lo0 & ~3, sh = x.lo0 - x0;
+            const int ngr = (sh + x.N + 3) / 4;  // 16-byte groups per row
+            auto fetch = [&](int c, int kext, int rs) {
+                float* raw = Rring + rs * kDtRaw;
+                for (int e = lane; e < 8 * ngr; e += 32) {
+                    const int r = 8 * warp + e / ngr, gq = e % ngr;
+                    const int kr = c * kDtK + r, col = x0 + 4 * gq;
+                    const bool on = kr < kext && col < B;
+                    dt_cp16(tc_smem_u32(raw + r * kDtRawCols + 4 * gq), on ? Z + (int64_t)(x.zo + kr) * B + col : Z,
+                            on ? 16 : 0);
                 }
+                dt_cp_commit();
             };
             for (int tile = 0; tile < x.T + x.R && ok; ++tile, ++tiles) {
                 const bool own = tile < x.T;
@@ -487,33 +505,42 @@ __global__ void __launch_bounds__(kDtRoles, 1)
                 // the rows this tile reads were written by the previous tile's epilogue (an own
                 // tile, or the first tile below) in all four warps: wait for their z-ready
                 if (tiles > 0 && tile <= x.T && !wwait(bar + kBZR, zwaits++ & 1u)) { ok = false; break; }
-                fetch(0, kext);
+                for (int c = 0; c < kDtRStages - 1 && c < nck; ++c) fetch(c, kext, c);
                 for (int c = 0; c < nck && ok; ++c, ++g) {
                     const uint32_t sr = g % kDtBStages;
                     if (g >= kDtBStages && !wwait(bar + kBBE + sr, ((g - kDtBStages) / kDtBStages) & 1u)) {
                         ok = false;
                         break;
                     }
+                    dt_cp_wait(c + 1 < nck ? 1 : 0);  // this warp's copies of chunk c have landed
+                    __syncwarp();
+                    const float* raw = Rring + (c % kDtRStages) * kDtRaw;
                     float* Bh = Bring + sr * 2 * kDtTile;
 #pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int item = tid + it * kDtWork;
-                        if (item < nitems) {
-                            const int n = item % x.N, kq = item / x.N;
-                            const int o = tc_kmajor_off(n, 4 * kq) >> 2;
-                            float4 h, l;
-                            tc_split2(v[it][0], h.x, l.x);
-                            tc_split2(v[it][1], h.y, l.y);
-                            tc_split2(v[it][2], h.z, l.z);
-                            tc_split2(v[it][3], h.w, l.w);
-                            *reinterpret_cast<float4*>(Bh + o) = h;
-                            *reinterpret_cast<float4*>(Bh + kDtTile + o) = l;
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int kq = 2 * warp + h2;
+#pragma unroll
+                        for (int vq = 0; vq < 4; ++vq) {
+                            const int n = lane + 32 * vq;
+                            if (n < x.N) {
+                                const bool on = n < x.nbu;
+                                float4 h, l;
+                                tc_split2(on ? raw[(4 * kq + 0) * kDtRawCols + sh + n] : 0.f, h.x, l.x);
+                                tc_split2(on ? raw[(4 * kq + 1) * kDtRawCols + sh + n] : 0.f, h.y, l.y);
+                                tc_split2(on ? raw[(4 * kq + 2) * kDtRawCols + sh + n] : 0.f, h.z, l.z);
+                                tc_split2(on ? raw[(4 * kq + 3) * kDtRawCols + sh + n] : 0.f, h.w, l.w);
+                                const int o = tc_kmajor_off(n, 4 * kq) >> 2;
+                                *reinterpret_cast<float4*>(Bh + o) = h;
+                                *reinterpret_cast<float4*>(Bh + kDtTile + o) = l;
+                            }
                         }
                     }
                     asm volatile("fence.proxy.async.shared::cta;");
-                    __syncwarp();
+                    __syncwarp();  // this warp's reads of the raw stage are done before it is refilled
                     if (lane == 0) mbar_arrive(bar + kBBF + sr);
-                    if (c + 1 < nck) fetch(c + 1, kext);  // in flight while the group fold below runs
+                    // the stage just read takes chunk c + 2 (still this tile: the next tile's rows may
+                    // wait for this tile's epilogue)
+                    if (c + kDtRStages - 1 < nck) fetch(c + kDtRStages - 1, kext, (c + kDtRStages - 1) % kDtRStages);
                     if ((c & 3) == 0 && c > 0) {
                         // S (+)= the buffer of group c/4 - 1 while this group accumulates in the other
                         const int pb = ((c >> 2) - 1) & 1;
@@ -579,6 +606,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
                 }
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy of this thread left in flight
         if (!ok) *abort = 1;
     }
     // ---- a wait ran out somewhere: let the copies and products in flight finish (again

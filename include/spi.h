@@ -250,7 +250,10 @@ int spi_factor(spi_ctx* ctx, const double* values, int values_on_device, void* s
 
 /* Solution phase (Sec. 3.2.3): x = N^-1 b by z = L^-1 P b (bottom-up over the
  * tree), w = D^-1 z, x = P^T L^-T w (top-down).  In mixed precision the
- * result is refined in FP64 against the FP64 values of N.
+ * result is refined in FP64 against the FP64 values of N: x += solve(b - N x)
+ * until ||b - N x||_2 <= opt.refine_tol ||b||_2 or opt.refine_max steps.  A
+ * call after a converged one first runs as many steps as that one took, with no
+ * residual check between them, then checks after every further step.
  *   b, x    float64[n]; host when on_device = 0, device otherwise; x may
  *           alias b.
  * Errors: SPI_ERR_STATE, SPI_ERR_ARG, SPI_ERR_CUDA. */

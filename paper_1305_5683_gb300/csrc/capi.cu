@@ -87,6 +87,7 @@ struct spi_ctx {
     int32_t* d_ri = nullptr;
     double *d_b2 = nullptr, *d_x = nullptr, *d_r = nullptr, *d_dx = nullptr, *d_norm = nullptr, *h_norm = nullptr;
     int64_t refine_steps = 0;
+    int64_t refine_planned = -1;  // correction steps the last converged solve took (-1: none yet)
     double solve_relres = 0;
     // CUDA graphs of the launch sequences that touch only context buffers, per band count
     cudaStream_t cap = nullptr;
@@ -1091,11 +1092,22 @@ int solve_impl(spi_ctx* c, int nb, const double* b, double* x, int on_device, cu
     if (!mixed_of(c)) {
         CK(solve_core(c, nb, bd, xd, st));
     } else if (n) {
-        // FP64 iterative refinement against N: x += solve(b - N x), every band until all converge
+        // FP64 iterative refinement against N: x += solve(b - N x), every band until all converge.
+        // The correction steps the last converged solve needed run first without a look at
+        // the residual (no host round trip between them); then the residual is checked after
+        // every step until it is below refine_tol.
         CK(cudaMemcpyAsync(c->d_b2, bd, bytes, cudaMemcpyDeviceToDevice, st));
         CK(solve_core(c, nb, c->d_b2, c->d_x, st));
         std::vector<double> bnorm(nb, -1.0);
         c->refine_steps = 0;
+        const int64_t blind = std::min<int64_t>(std::max<int64_t>(c->refine_planned, 0), c->opt.refine_max);
+        for (int64_t q = 0; q < blind; ++q) {
+            CK(cudaMemcpyAsync(c->d_r, c->d_b2, bytes, cudaMemcpyDeviceToDevice, st));
+            launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, c->d_x, c->d_r, nb, c->S.nnz_a, st);
+            CK(solve_core(c, nb, c->d_r, c->d_dx, st));
+            launch_axpy(n, c->d_dx, c->d_x, nb, st);
+            c->refine_steps++;
+        }
         for (int it = 0;; ++it) {
             CK(cudaMemcpyAsync(c->d_r, c->d_b2, bytes, cudaMemcpyDeviceToDevice, st));
             launch_sym_residual(n, c->d_cp, c->d_ri, c->d_vals, c->d_x, c->d_r, nb, c->S.nnz_a, st);
@@ -1112,7 +1124,8 @@ int solve_impl(spi_ctx* c, int nb, const double* b, double* x, int on_device, cu
                 if (rn > c->opt.refine_tol * bnorm[k]) done = false;
             }
             c->solve_relres = worst;
-            if (done || it >= c->opt.refine_max) break;
+            if (done) c->refine_planned = c->refine_steps;
+            if (done || c->refine_steps >= c->opt.refine_max) break;
             CK(solve_core(c, nb, c->d_r, c->d_dx, st));
             launch_axpy(n, c->d_dx, c->d_x, nb, st);
             c->refine_steps++;

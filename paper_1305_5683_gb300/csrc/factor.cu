@@ -397,83 +397,118 @@ __device__ __forceinline__ T ldx(const T* p) {
     else return *p;
 }
 
-// 1/d in FP64 by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r),
-// from a correctly rounded single-precision seed: each step squares the relative
-// error (2^-24 -> 2^-48 -> below FP64 rounding), two FP64 FMAs per step instead of
-// a full FP64 division on this GPU's narrow FP64 pipe.  Outside the single-precision
-// range of the seed it divides.
-__device__ __forceinline__ double recip_nr(double d) {
-    const double ad = fabs(d);
-    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-    double r = (double)__frcp_rn((float)d);
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+// 1/d in FP64 with three FP64 operations on the dependency chain (a dependent FP64
+// operation costs about 64 cycles on this GPU; a division or a conversion to and from
+// single precision costs several).  d = m 2^(ex - 1023) with m in [1, 2): a single-
+// precision seed r0 ~ 1/m is formed from m's top 23 mantissa bits by bit operations and
+// one __frcp_rn, refined by the cubic correction r0 (1 + e + e^2), e = 1 - m r0
+// (|e| < 2^-22, so the dropped e^3 term is below FP64 rounding: within 2 ulp of 1/m),
+// and the exponent is restored by integer arithmetic.  Zero, subnormal, huge or
+// non-finite d divide.
+__device__ __forceinline__ double recip_fp64(double d) {
+    const long long b = __double_as_longlong(d);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex < 4 || ex > 2042) return 1.0 / d;
+    const double m = __longlong_as_double((b & 0x800FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const float mf = __int_as_float((int)((b >> 29) & 0x7FFFFF) | 0x3F800000 | (int)((b >> 32) & 0x80000000LL));
+    const int rb = __float_as_int(__frcp_rn(mf));  // in (0.5, 1]
+    const double r0 = __longlong_as_double(((long long)(rb & 0x80000000) << 32) |
+                                           ((long long)(((rb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                           ((long long)(rb & 0x7FFFFF) << 29));
+    const double e = fma(-m, r0, 1.0);
+    const double r = fma(r0, fma(e, e, e), r0);
+    return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
 }
+
+// Entries of the lower triangle of order kT - 2, row by row: entry e is (e >> 8, e & 255).
+constexpr int kTri = (kT - 2) * (kT - 1) / 2;
 
 // Unblocked LDL^T, in FP64, of the w x w pivot tile whose first pivot is
 // column c0 of supernode s (panel P of storage type S, leading dimension m),
 // by the CTA's 128 threads; writes L (unit lower, d on the diagonal) back into
 // P, d into D (FP64) and into DS (the storage type's copy used for scaling).
-// FP64 is a narrow pipe on this GPU, so per column: each thread updates its
-// fixed pairs (i, j) of the lower triangle (at most 5 of the 528), one FMA
-// chain each, with the unscaled column (A_ij -= A_ic (A_jc / d_c)); the thread
-// that finishes the next pivot forms its reciprocal at once; one barrier per
-// column; the columns are scaled by 1/d at the end.
+// The tile is bound by its column-to-column dependency chain, not by FP64
+// throughput, so the work is split by that chain.  Per column c, one barrier
+// apart: warp 3 forms column c + 1 -- its last update, the pivot
+// d_{c+1} = a_{c+1,c+1} - a_{c+1,c} l_{c+1,c} and 1/d_{c+1} (every lane
+// computes them: one lane costs as much as 32), then l_{j,c+1} = a_{j,c+1} / d_{c+1}
+// -- while warps 0-2 apply column c to the rest of the triangle,
+// a_ij -= a_ic l_jc for c + 2 <= j <= i (from a table of the triangle's
+// entries).  The scaled columns of L wait in the tile's unused upper triangle
+// until the end; the pivots are checked there, all at once.
 template <typename S, bool kCg = false>
 __device__ void factor_pivot_tile(double (*A)[kT + 1], double* dv, S* P, int64_t m, int c0, int w,
                                   int f, double* D, S* DS, const double* __restrict__ adiag, DevStatus* status,
                                   int band_base) {
-    const int tid = threadIdx.x;
-    __shared__ double sinv[kT];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double lc[2][kT];    // l_{j,c} of the column being applied, alternating
+    __shared__ uint16_t tri[kTri];
+    static_assert(kThreads == 128 && kT == 32, "three update warps and one pivot warp over a 32 x 32 tile");
     for (int e = tid; e < kT * kT; e += kThreads) {
-        int i = e % kT, j = e / kT;
-        A[i][j] = (i < w && j <= i) ? (double)ldx<kCg>(P + (c0 + i) + (int64_t)(c0 + j) * m) : 0.0;
+        const int i = e % kT, j = e / kT;
+        if (i < w && j <= i) A[i][j] = (double)ldx<kCg>(P + (c0 + i) + (int64_t)(c0 + j) * m);
     }
-    // this thread's pairs p = tid + 128 q of the lower triangle, p = i (i + 1) / 2 + j
-    constexpr int kPairs = (kT * (kT + 1) / 2 + kThreads - 1) / kThreads;
-    int pi[kPairs], pj[kPairs];
-#pragma unroll
-    for (int q = 0; q < kPairs; ++q) {
-        const int p = tid + q * kThreads;
-        int i = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
-        while (i * (i + 1) / 2 > p) --i;
-        while ((i + 1) * (i + 2) / 2 <= p) ++i;
-        pi[q] = p < kT * (kT + 1) / 2 ? i : kT;  // kT: no pair
-        pj[q] = p - i * (i + 1) / 2;
+    for (int e = tid; e < kTri; e += kThreads) {
+        int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        if ((i + 1) * (i + 2) / 2 <= e) ++i;
+        if (i * (i + 1) / 2 > e) --i;
+        tri[e] = (uint16_t)((i << 8) | (e - i * (i + 1) / 2));
     }
-    auto pivot = [&](int c) {  // d_c = A[c][c] is final: check it and form 1/d_c
-        const double dc = A[c][c];
-        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + c]) {
-            atomicOr(&status->flags, FLAG_NOT_SPD);
-            atomicMin(&status->bad_pivot, band_base + f + c0 + c);
+    __syncthreads();
+    if (warp == 3) {  // column 0
+        const double d = A[0][0];
+        const double inv = recip_fp64(d);
+        if (lane == 0) dv[0] = d;
+        if (lane > 0 && lane < w) {
+            const double l = A[lane][0] * inv;
+            lc[0][lane] = l;
+            A[0][lane] = l;
         }
-        dv[c] = dc;
-        sinv[c] = recip_nr(dc);
-    };
+    }
     __syncthreads();
-    if (tid == 0 && w > 0) pivot(0);
-    __syncthreads();
-    for (int c = 0; c < w; ++c) {
-        const double inv = sinv[c];
-#pragma unroll
-        for (int q = 0; q < kPairs; ++q) {
-            const int i = pi[q], j = pj[q];
-            if (i < w && j > c) {
-                A[i][j] = fma(-A[i][c], A[j][c] * inv, A[i][j]);
-                if (i == c + 1 && j == c + 1) pivot(c + 1);  // this thread finished the next pivot
+    for (int c = 0; c + 1 < w; ++c) {
+        const double* l = lc[c & 1];
+        if (warp == 3) {
+            const int j = lane;
+            const double lcc = l[c + 1];
+            const double d = fma(-A[c + 1][c], lcc, A[c + 1][c + 1]);
+            double a = 0.0;
+            if (j > c + 1 && j < w) a = fma(-A[j][c], lcc, A[j][c + 1]);
+            const double inv = recip_fp64(d);
+            if (j == c + 1) dv[c + 1] = d;
+            if (j > c + 1 && j < w) {
+                const double lj = a * inv;
+                A[j][c + 1] = a;
+                lc[(c + 1) & 1][j] = lj;
+                A[c + 1][j] = lj;
+            }
+        } else {
+            const int n = w - 2 - c, N = n * (n + 1) / 2;
+            for (int e = tid; e < N; e += 2 * 96) {
+                const int e2 = e + 96;
+                const int t = tri[e], t2 = tri[e2 < N ? e2 : e];
+                const int gi = c + 2 + (t >> 8), gj = c + 2 + (t & 255);
+                const int gi2 = c + 2 + (t2 >> 8), gj2 = c + 2 + (t2 & 255);
+                const double v = fma(-A[gi][c], l[gj], A[gi][gj]);
+                const double v2 = fma(-A[gi2][c], l[gj2], A[gi2][gj2]);
+                A[gi][gj] = v;
+                if (e2 < N) A[gi2][gj2] = v2;
             }
         }
         __syncthreads();
     }
     for (int e = tid; e < kT * kT; e += kThreads) {
-        int i = e % kT, j = e / kT;
-        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (S)((i == j) ? dv[i] : A[i][j] * sinv[j]);
+        const int i = e % kT, j = e / kT;
+        if (i < w && j <= i) P[(c0 + i) + (int64_t)(c0 + j) * m] = (S)(i == j ? dv[i] : A[j][i]);
     }
     if (tid < w) {
-        D[f + c0 + tid] = dv[tid];
-        DS[f + c0 + tid] = (S)dv[tid];
+        const double dc = dv[tid];
+        if (!(dc > 0.0) || dc <= 1e-14 * adiag[f + c0 + tid]) {
+            atomicOr(&status->flags, FLAG_NOT_SPD);
+            atomicMin(&status->bad_pivot, band_base + f + c0 + tid);
+        }
+        D[f + c0 + tid] = dc;
+        DS[f + c0 + tid] = (S)dc;
     }
 }
 

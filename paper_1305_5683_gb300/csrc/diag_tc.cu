@@ -186,23 +186,6 @@ __device__ __forceinline__ void tma_tile_pair(uint32_t dst, const CUtensorMap* m
         : "memory");
 }
 
-// Sum over the warp's 32 lanes of each of the 32 values v[0..31]; lane j returns
-// the sum for index j (a butterfly: at each step a lane keeps half of its values
-// and adds its partner's copy of that half).
-__device__ __forceinline__ float lane_column_sum(float (&v)[32], int lane) {
-#pragma unroll
-    for (int sft = 16; sft >= 1; sft >>= 1) {
-        const bool up = (lane & sft) != 0;
-#pragma unroll
-        for (int i = 0; i < sft; ++i) {
-            const float send = up ? v[i] : v[i + sft];
-            const float keep = up ? v[i + sft] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
-        }
-    }
-    return v[0];
-}
-
 struct DiagArgsTc {
     int32_t B;
     const int32_t *order, *blk_ptr, *uptr, *us, *ulo, *uhi, *uzoff, *rel, *rhs_out;
@@ -589,7 +572,7 @@ __global__ void __launch_bounds__(kDtRoles, 1)
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj)
                             w[jj] = (rv && q * 32 + jj < x.nbu) ? w[jj] * w[jj] * dinv : 0.f;
-                        const float cs = lane_column_sum(w, lane);  // this warp's 32 rows of column q*32+lane
+                        const float cs = lane_sums(w, lane);  // this warp's 32 rows of column q*32+lane
                         if (q * 32 + lane < x.nbu) atomicAdd(&var[x.lo0 + q * 32 + lane], (double)cs);
                     } else if (rv) {
                         z_load32(zrow, w, q * 32, x.nbu, vec);

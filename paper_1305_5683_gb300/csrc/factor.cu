@@ -701,17 +701,22 @@ __global__ void __launch_bounds__(kThreads) k_front_panel(DevSym d, const int32_
 }
 
 // Row tile rt below the diagonal tile of block column b (already updated by
-// the block columns before it): L21 = X L11^-T D^-1, one thread per row.
+// the block columns before it): L21 = X L11^-T D^-1.  Four lanes per row (warp
+// w holds rows 8 w .. 8 w + 7, lane q = lane % 4 of a row's group the columns
+// q, q + 4, ...): column c is final at its owner when the columns before it
+// have been applied; a shuffle hands it to the row's other lanes, which apply
+// it to their later columns.  All four warps work (a narrow FP64 pipe gives
+// one warp a quarter of the SM's rate), and the dependency chain per column is
+// one shuffle and one multiply-add.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t* __restrict__ items, int b,
                                                          C* __restrict__ L, const double* __restrict__ D,
                                                          Strides bs) {
     L += blockIdx.y * bs.L;
     D += blockIdx.y * bs.n;
-    __shared__ C X[kT][kT + 1];
     __shared__ C Bd[kT][kT + 1];
     __shared__ C dv[kT];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, q = lane & 3;
     const int s = items[2 * blockIdx.x], rt = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
@@ -719,25 +724,34 @@ __global__ void __launch_bounds__(kThreads) k_panel_trsm(DevSym d, const int32_t
     const int c0 = b * kT, w = min(kT, k - c0);
     const int64_t r0 = c0 + w + (int64_t)rt * kT;
     const int nr = (int)(m - r0 < kT ? m - r0 : kT);
+    const int r = 8 * (tid >> 5) + (lane >> 2);
+    const bool on = r < nr;
     for (int e = tid; e < kT * kT; e += kThreads) {
-        int i = e % kT, j = e / kT;
-        X[i][j] = (i < nr && j < w) ? P[(r0 + i) + (int64_t)(c0 + j) * m] : C(0);
+        const int i = e % kT, j = e / kT;
         Bd[i][j] = (i < w && j < i) ? P[(c0 + i) + (int64_t)(c0 + j) * m] : C(0);
     }
-    if (tid < kT) dv[tid] = (tid < w) ? (C)(1.0 / D[f + c0 + tid]) : C(0);
-    __syncthreads();
-    if (tid < nr) {
-        const int i = tid;
-        for (int c = 0; c < w; ++c) {
-            C y = X[i][c];
-            for (int cp = 0; cp < c; ++cp) y -= X[i][cp] * Bd[c][cp];
-            X[i][c] = y;
-        }
+    if (tid < kT) dv[tid] = (tid < w) ? (C)recip_fp64(D[f + c0 + tid]) : C(0);
+    C y[kT / 4];  // y[t]: column 4 t + q of row r
+#pragma unroll
+    for (int t = 0; t < kT / 4; ++t) {
+        const int c = 4 * t + q;
+        y[t] = (on && c < w) ? P[(r0 + r) + (int64_t)(c0 + c) * m] : C(0);
     }
     __syncthreads();
-    for (int e = tid; e < kT * kT; e += kThreads) {
-        int i = e % kT, j = e / kT;
-        if (i < nr && j < w) P[(r0 + i) + (int64_t)(c0 + j) * m] = X[i][j] * dv[j];
+#pragma unroll
+    for (int c = 0; c < kT; ++c) {
+        if (c >= w) break;
+        const C xc = __shfl_sync(0xffffffffu, y[c >> 2], (lane & ~3) | (c & 3));
+#pragma unroll
+        for (int t = 0; t < kT / 4; ++t) {
+            const int cc = 4 * t + q;
+            if (4 * t + 3 > c && cc > c && cc < w) y[t] -= xc * Bd[cc][c];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kT / 4; ++t) {
+        const int c = 4 * t + q;
+        if (on && c < w) P[(r0 + r) + (int64_t)(c0 + c) * m] = y[t] * dv[c];
     }
 }
 

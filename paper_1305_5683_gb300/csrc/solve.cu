@@ -48,6 +48,41 @@ __device__ __forceinline__ double dinv_z(const DevSym& d, const double* z, const
     return d.dinv_a[j] * z[j] + (q >= 0 ? d.dinv_b[j] * z[q] : 0.0);
 }
 
+// y[a] -= sum_{r < wb} P[cb + r][a] xb[r] for the columns a in [a0, a1) of a panel P
+// (column-major, leading dimension m; wb <= 32 kRowChunks): the backward sweep's update of
+// a supernode's earlier columns by a solved block.  Warp w takes the groups of 32
+// consecutive columns g = a0 + 32 (w + i nwarps); lane r loads row cb + r (+ 32 t) of each
+// of the group's columns -- coalesced: the rows of a column are contiguous -- and
+// lane_sums leaves column g + j's dot product in lane j.  kCg: y is read through L2
+// (written by other CTAs of the same launch).
+template <int kRowChunks, bool kCg, typename TL>
+__device__ void bwd_update(const TL* P, int64_t m, int cb, int wb, const TL* xb, int a0, int a1, double* y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    TL xr[kRowChunks];
+#pragma unroll
+    for (int t = 0; t < kRowChunks; ++t) xr[t] = 32 * t + lane < wb ? xb[32 * t + lane] : TL(0);
+    for (int g = a0 + 32 * warp; g < a1; g += 32 * nw) {
+        TL v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = TL(0);
+#pragma unroll
+        for (int t = 0; t < kRowChunks; ++t) {
+            const int r = 32 * t + lane;
+            if (r < wb) {
+                const TL* p = P + (cb + r) + (int64_t)g * m;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (g + j < a1) v[j] += p[(int64_t)j * m] * xr[t];
+            }
+        }
+        const TL sum = lane_sums(v, lane);
+        if (g + lane < a1) {
+            double* py = y + g + lane;
+            *py = (kCg ? __ldcg(py) : *py) - (double)sum;
+        }
+    }
+}
+
 // Forward block step b of the supernodes of one level.  Item (s, chunk):
 // every CTA of supernode s solves the 32 x 32 unit-lower diagonal block
 // x_b = L_bb^-1 w_b in registers (lane r owns row r), the chunk-0 CTA stores
@@ -174,13 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
         if (chunk == 0 && lane < wb) x[f + cb + lane] = y;
     }
     __syncthreads();
-    const int a1 = min(cb, (chunk + 1) * kBwdCols);
-    for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
-        const TL* col = P + (int64_t)a * m + cb;
-        TL acc = 0;
-        for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
-        w[f + a] -= acc;
-    }
+    bwd_update<1, false>(P, m, cb, wb, xb, chunk * kBwdCols, min(cb, (chunk + 1) * kBwdCols), w + f);
 }
 
 // Forward sweep of one level in one launch: one CTA per (supernode, band)
@@ -303,12 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
             if (lane < wb) x[f + cb + lane] = y;
         }
         __syncthreads();
-        for (int a = tid; a < cb; a += kThreads) {
-            const TL* col = P + (int64_t)a * m + cb;
-            TL acc = 0;
-            for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
-            w[f + a] -= acc;
-        }
+        bwd_update<1, false>(P, m, cb, wb, xb, 0, cb, w + f);
         __syncthreads();
     }
 }
@@ -489,13 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_wide(DevSym d, const int32_t* 
     }
     __syncthreads();
     if (chunk == 0 && tid < wb) x[f + cb + tid] = xb[tid];
-    const int a1 = min(cb, (chunk + 1) * kBwdColsW);
-    for (int a = chunk * kBwdColsW + tid; a < a1; a += kThreads) {
-        const float* col = P + (int64_t)a * m + cb;
-        float acc = 0.f;
-        for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
-        w[f + a] -= acc;
-    }
+    bwd_update<kW / 32, false>(P, m, cb, wb, xb, chunk * kBwdColsW, min(cb, (chunk + 1) * kBwdColsW), w + f);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,13 +663,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
                 if (chunk == 0 && lane < wb) xv[f + cb + lane] = y;
             }
             __syncthreads();
-            const int a1 = min(cb, (chunk + 1) * kBwdCols);
-            for (int a = chunk * kBwdCols + tid; a < a1; a += kThreads) {
-                const TL* col = P + (int64_t)a * m + cb;
-                TL acc = 0;
-                for (int r = 0; r < wb; ++r) acc += col[r] * xb[r];
-                wb_[f + a] = __ldcg(wb_ + f + a) - acc;
-            }
+            bwd_update<1, true>(P, m, cb, wb, xb, chunk * kBwdCols, min(cb, (chunk + 1) * kBwdCols), wb_ + f);
         }
         __threadfence();
         __syncthreads();

@@ -315,4 +315,23 @@ void launch_bg_sums(bool mle, int64_t nrows, const int64_t* rowptr, const int32_
                     const double* y, const double* w, int32_t npat, double* sums, double* acc, cudaStream_t st);
 void launch_bg_pattern(int32_t npat, const double* sums, double* U, cudaStream_t st);
 
+// Sums over the 32 lanes of a warp of each of v[0..31]: lane j returns the sum of v[j].
+// Recursive halving: at distance h every lane keeps the half of its values whose index
+// has bit h equal to its own, adds its partner's copy of that half and sends the other
+// half (31 shuffles for the 32 sums).  v is overwritten.
+template <typename T>
+__device__ __forceinline__ T lane_sums(T (&v)[32], int lane) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    return v[0];
+}
+
 }  // namespace spi

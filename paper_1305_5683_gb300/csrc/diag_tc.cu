@@ -44,7 +44,7 @@ namespace {
 constexpr int kDtM = kDiagTcRows;       // rows of a tile (the MMA's M)
 constexpr int kDtK = kDiagTcK;          // K columns of a tile
 constexpr int kDtTile = kDtM * kDtK;    // floats of one TF32 plane of a tile (16 KB)
-constexpr size_t kTinvSmem = 2 * kDtM * (kDtM + 1) * sizeof(float);
+constexpr size_t kTinvSmem = (2 * kDtM * (kDtM + 1) + 3 * 32 * 33) * sizeof(float);
 constexpr size_t kPackSmem = (kDtM * (kDtM + 1) + kDtM * (kDtK + 1)) * sizeof(float);
 
 struct DiagTcArgs {
@@ -53,9 +53,26 @@ struct DiagTcArgs {
     int64_t npt;          // packed tiles per band
 };
 
-// Inverse of the unit-lower 128 x 128 diagonal block of own row tile i of s
-// (rows and columns [128 i, 128 i + w), zero beyond w): thread j computes column
-// j by forward substitution, X[r][j] = -sum_{c=j}^{r-1} L[r][c] X[c][j].
+// acc[q] += sum_k A[r][k] B[k][c0 + 4 q] for the 32 x 32 blocks A, B in shared memory
+// (row strides lda, ldb): thread t takes row r = t % 32 and the columns c0 + 4 q,
+// c0 = t / 32 -- a warp reads one B entry at a time (broadcast) and A with lanes on rows.
+__device__ __forceinline__ void mm32_acc(float (&acc)[8], const float* A, int lda, const float* B, int ldb) {
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+        const float a = A[r * lda + k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fmaf(a, B[k * ldb + c0 + 4 * q], acc[q]);
+    }
+}
+
+// Inverse X of the unit-lower 128 x 128 diagonal block of own row tile i of s (rows
+// and columns [128 i, 128 i + w), zero beyond w), in 32 x 32 blocks: warp b inverts
+// diagonal block b by forward substitution (lane j holds column j in registers),
+// then the blocks below the diagonal follow by distance d = i - j,
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj, as products of 32 x 32 blocks by all four
+// warps (the blocks of one distance depend only on shorter distances).
+constexpr int kTinvLd = kDtM + 1;
 __global__ void __launch_bounds__(kDtM) k_diag_tinv(DevSym d, const int32_t* __restrict__ dtiles, int64_t ndt,
                                                      const float* __restrict__ L, float* __restrict__ xinv,
                                                      int64_t bsL) {
@@ -63,36 +80,68 @@ __global__ void __launch_bounds__(kDtM) k_diag_tinv(DevSym d, const int32_t* __r
     L += blockIdx.y * bsL;
     xinv += ((int64_t)blockIdx.y * ndt + t) * (kDtM * kDtM);
     extern __shared__ float tsh[];
-    float* Ls = tsh;                      // [128][129], row r, column c < r
-    float* Xs = tsh + kDtM * (kDtM + 1);  // [128][129], X[r][j]
+    float* Ls = tsh;                     // [128][129], row r, column c < r
+    float* Xs = tsh + kDtM * kTinvLd;    // [128][129], X[r][j]
+    float* Tb = Xs + kDtM * kTinvLd;     // three [32][33] sums of one distance
     const int s = dtiles[2 * t], i = dtiles[2 * t + 1];
     const int k = d.sfirst[s + 1] - d.sfirst[s];
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const float* P = L + d.lptr[s];
     const int r0 = i * kDtM, w = min(kDtM, k - r0);
-    const int j = threadIdx.x;
-    for (int c = 0; c < kDtM; ++c) {
-        Ls[j * (kDtM + 1) + c] = (j < w && c < j) ? P[(r0 + j) + (int64_t)(r0 + c) * m] : 0.f;
-        Xs[c * (kDtM + 1) + j] = (c == j && j < w) ? 1.f : 0.f;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c0 = 0; c0 < kDtM; c0 += 16) {  // thread = row, 16 loads in flight
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            v[q] = (tid < w && c0 + q < tid) ? P[(r0 + tid) + (int64_t)(r0 + c0 + q) * m] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Ls[tid * kTinvLd + c0 + q] = v[q];
     }
+    for (int e = tid; e < kDtM * kTinvLd; e += kDtM) Xs[e] = 0.f;
     __syncthreads();
-    if (j < w) {
-        for (int r = j + 1; r < w; ++r) {
-            const float* lr = Ls + r * (kDtM + 1);
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            int c = j;
-            for (; c + 3 < r; c += 4) {
-                a0 = fmaf(lr[c], Xs[c * (kDtM + 1) + j], a0);
-                a1 = fmaf(lr[c + 1], Xs[(c + 1) * (kDtM + 1) + j], a1);
-                a2 = fmaf(lr[c + 2], Xs[(c + 2) * (kDtM + 1) + j], a2);
-                a3 = fmaf(lr[c + 3], Xs[(c + 3) * (kDtM + 1) + j], a3);
-            }
-            for (; c < r; ++c) a0 = fmaf(lr[c], Xs[c * (kDtM + 1) + j], a0);
-            Xs[r * (kDtM + 1) + j] = -((a0 + a1) + (a2 + a3));
+    {
+        const int b = warp, gj = 32 * b + lane;
+        const float* Lb = Ls + 32 * b * kTinvLd + 32 * b;
+        float x[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < r; ++c) acc = fmaf(Lb[r * kTinvLd + c], x[c], acc);
+            x[r] = r < lane ? 0.f : (r == lane ? 1.f : -acc);
+        }
+        if (gj < w) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) Xs[(32 * b + r) * kTinvLd + gj] = x[r];
         }
     }
     __syncthreads();
-    for (int r = 0; r < kDtM; ++r) xinv[r * kDtM + j] = Xs[r * (kDtM + 1) + j];
+    const int tr = tid & 31, tc = tid >> 5;
+    for (int dd = 1; dd < 4; ++dd) {
+        for (int ib = dd; ib < 4; ++ib) {
+            const int jb = ib - dd;
+            float acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+            for (int kb = jb; kb < ib; ++kb)
+                mm32_acc(acc, Ls + 32 * ib * kTinvLd + 32 * kb, kTinvLd, Xs + 32 * kb * kTinvLd + 32 * jb, kTinvLd);
+            float* T = Tb + jb * 32 * 33;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) T[tr * 33 + tc + 4 * q] = acc[q];
+        }
+        __syncthreads();
+        for (int ib = dd; ib < 4; ++ib) {
+            const int jb = ib - dd;
+            float acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+            mm32_acc(acc, Xs + 32 * ib * kTinvLd + 32 * ib, kTinvLd, Tb + jb * 32 * 33, 33);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Xs[(32 * ib + tr) * kTinvLd + 32 * jb + tc + 4 * q] = -acc[q];
+        }
+        __syncthreads();
+    }
+    for (int r = 0; r < kDtM; ++r) xinv[r * kDtM + tid] = Xs[r * kTinvLd + tid];
 }
 
 // a = hi + lo with two TF32 values
@@ -136,16 +185,28 @@ __global__ void __launch_bounds__(kDtM) k_diag_pack(DevSym d, const int32_t* __r
         float* Lc = psh + kDtM * (kDtM + 1);   // [128][33]
         if (c >= 4 * rt) {
             const int c0 = (c - 4 * rt) * kDtK;
-            for (int r = 0; r < kDtM; ++r)
-                if (tid < kDtK) Xs[r * (kDtM + 1) + tid] = X[r * kDtM + c0 + tid];
+#pragma unroll 8
+            for (int e = tid; e < kDtM * kDtK; e += kDtM) {
+                const int r = e / kDtK, q = e % kDtK;
+                Xs[r * (kDtM + 1) + q] = X[r * kDtM + c0 + q];
+            }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < kDtK; ++q) v[q] = Xs[tid * (kDtM + 1) + q];
         } else {
             const int r0 = rt * kDtM, w = min(kDtM, k - r0);
-            for (int r = 0; r < kDtM; ++r) Xs[r * (kDtM + 1) + tid] = X[r * kDtM + tid];
-            for (int q = 0; q < kDtK; ++q)
-                Lc[tid * (kDtK + 1) + q] = tid < w ? P[(r0 + tid) + (int64_t)(c * kDtK + q) * m] : 0.f;
+            for (int r0x = 0; r0x < kDtM; r0x += 16) {  // 16 loads in flight per thread
+                float xv[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) xv[q] = X[(r0x + q) * kDtM + tid];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) Xs[(r0x + q) * (kDtM + 1) + tid] = xv[q];
+            }
+            float lv[kDtK];
+#pragma unroll
+            for (int q = 0; q < kDtK; ++q) lv[q] = tid < w ? P[(r0 + tid) + (int64_t)(c * kDtK + q) * m] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kDtK; ++q) Lc[tid * (kDtK + 1) + q] = lv[q];
             __syncthreads();
             float acc[kDtK];
 #pragma unroll

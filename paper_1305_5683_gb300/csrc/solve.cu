@@ -48,6 +48,32 @@ __device__ __forceinline__ double dinv_z(const DevSym& d, const double* z, const
     return d.dinv_a[j] * z[j] + (q >= 0 ? d.dinv_b[j] * z[q] : 0.0);
 }
 
+// Rows of x gathered per pass of the backward first pass (x[rows[t]] for a chunk of
+// rows t below the supernode): staged in shared memory by independent loads of the
+// whole CTA, so that the column dot products read them from there instead of
+// waiting on a dependent rows[t] -> x[rows[t]] pair of global loads per row.
+constexpr int kXs = 2048;
+
+template <bool kCg, typename TL>
+__device__ __forceinline__ void gather_x(TL* xs, const double* x, const int32_t* rows, int64_t t0, int64_t t1) {
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+        xs[t - t0] = (TL)(kCg ? __ldcg(x + rows[t]) : x[rows[t]]);
+}
+
+// Backward diagonal block of a 32-column step: lane c (of warp 0) receives column c of
+// L_bb below the diagonal (row r in lcol[r], r > c; rows past wb zero), staged through
+// shared memory so that the panel is read a column at a time (lanes = rows).
+template <typename TL>
+__device__ __forceinline__ void bwd_block_cols(const TL* P, int64_t m, int cb, int wb, TL (*Lbb)[kT + 1],
+                                               TL (&lcol)[kT], int lane) {
+#pragma unroll 8
+    for (int c = 0; c < kT; ++c)
+        Lbb[lane][c] = (lane > c && lane < wb) ? P[(cb + lane) + (int64_t)(cb + c) * m] : TL(0);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kT; ++r) lcol[r] = Lbb[r][lane];
+}
+
 // y[a] -= sum_{r < wb} P[cb + r][a] xb[r] for the columns a in [a0, a1) of a panel P
 // (column-major, leading dimension m; wb <= 32 kRowChunks): the backward sweep's update of
 // a supernode's earlier columns by a solved block.  Warp w takes the groups of 32
@@ -58,9 +84,7 @@ __device__ __forceinline__ double dinv_z(const DevSym& d, const double* z, const
 template <int kRowChunks, bool kCg, typename TL>
 __device__ void bwd_update(const TL* P, int64_t m, int cb, int wb, const TL* xb, int a0, int a1, double* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    TL xr[kRowChunks];
-#pragma unroll
-    for (int t = 0; t < kRowChunks; ++t) xr[t] = 32 * t + lane < wb ? xb[32 * t + lane] : TL(0);
+
     for (int g = a0 + 32 * warp; g < a1; g += 32 * nw) {
         TL v[32];
 #pragma unroll
@@ -69,10 +93,11 @@ __device__ void bwd_update(const TL* P, int64_t m, int cb, int wb, const TL* xb,
         for (int t = 0; t < kRowChunks; ++t) {
             const int r = 32 * t + lane;
             if (r < wb) {
+                const TL xr = xb[r];
                 const TL* p = P + (cb + r) + (int64_t)g * m;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    if (g + j < a1) v[j] += p[(int64_t)j * m] * xr[t];
+                    if (g + j < a1) v[j] += p[(int64_t)j * m] * xr;
             }
         }
         const TL sum = lane_sums(v, lane);
@@ -156,15 +181,22 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
     const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
     const int c0 = chunk * kT, nc = min(kT, k - c0);
+    __shared__ TL xs[kXs];
     TL acc[kPer];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
-    for (int64_t t = k + lane; t < m; t += 32) {
-        const TL xv = (TL)x[rows[t]];
+    for (int64_t t0 = k; t0 < m; t0 += kXs) {
+        const int64_t t1 = m < t0 + kXs ? m : t0 + kXs;
+        __syncthreads();
+        gather_x<false>(xs, x, rows, t0, t1);
+        __syncthreads();
+        for (int64_t t = t0 + lane; t < t1; t += 32) {
+            const TL xv = xs[t - t0];
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int c = warp + kWarps * q;
-            if (c < nc) acc[q] += P[t + (int64_t)(c0 + c) * m] * xv;
+            for (int q = 0; q < kPer; ++q) {
+                const int c = warp + kWarps * q;
+                if (c < nc) acc[q] += P[t + (int64_t)(c0 + c) * m] * xv;
+            }
         }
     }
 #pragma unroll
@@ -187,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     w += blockIdx.y * bs.n;
     x += blockIdx.y * bs.n;
     __shared__ TL xb[kT];
+    __shared__ TL Lbb[kT][kT + 1];
     const int tid = threadIdx.x, lane = tid & 31;
     const int s = items[2 * blockIdx.x], chunk = items[2 * blockIdx.x + 1];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
@@ -196,9 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_step(DevSym d, const int32_t* 
     if (tid < 32) {
         // lane c holds column c of the diagonal block (L_bb^T row c)
         TL lcol[kT];
-#pragma unroll
-        for (int r = 0; r < kT; ++r)
-            lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
+        bwd_block_cols(P, m, cb, wb, Lbb, lcol, lane);
         TL y = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
         for (int r = kT - 1; r > 0; --r) {
@@ -302,26 +333,36 @@ __global__ void __launch_bounds__(kThreads) k_bwd_level(DevSym d, const int32_t*
     w += blockIdx.y * bs.n;
     constexpr int kWarps = kThreads / 32;
     __shared__ TL xb[kT];
+    __shared__ TL xs[kXs];
+    __shared__ TL Lbb[kT][kT + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = items[2 * blockIdx.x];
     const int f = d.sfirst[s], k = d.sfirst[s + 1] - f;
     const int64_t m = d.srowptr[s + 1] - d.srowptr[s];
     const TL* P = L + d.lptr[s];
     const int32_t* rows = d.srows + d.srowptr[s];
-    for (int c = warp; c < k; c += kWarps) {
-        TL acc = 0;
-        for (int64_t t = k + lane; t < m; t += 32) acc += P[t + (int64_t)c * m] * x[rows[t]];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) w[f + c] = dinv_z(d, z, D, f + c) - acc;
+    // y_c = z_c / d_c - sum_{t >= k} L[t][c] x[rows[t]], a warp per column, the rows
+    // below in passes of kXs whose x are gathered into shared memory first
+    if (m == k)
+        for (int c = tid; c < k; c += kThreads) w[f + c] = dinv_z(d, z, D, f + c);
+    for (int64_t t0 = k; t0 < m; t0 += kXs) {
+        const int64_t t1 = m < t0 + kXs ? m : t0 + kXs;
+        __syncthreads();
+        gather_x<false>(xs, x, rows, t0, t1);
+        __syncthreads();
+        for (int c = warp; c < k; c += kWarps) {
+            TL acc = 0;
+            for (int64_t t = t0 + lane; t < t1; t += 32) acc += P[t + (int64_t)c * m] * xs[t - t0];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) w[f + c] = (t0 == k ? dinv_z(d, z, D, f + c) : w[f + c]) - acc;
+        }
     }
     __syncthreads();
     for (int cb = ((k - 1) / kT) * kT; cb >= 0; cb -= kT) {
         const int wb = min(kT, k - cb);
         if (tid < 32) {
             TL lcol[kT];
-#pragma unroll
-            for (int r = 0; r < kT; ++r)
-                lcol[r] = (r > lane && r < wb) ? P[(cb + r) + (int64_t)(cb + lane) * m] : 0.0;
+            bwd_block_cols(P, m, cb, wb, Lbb, lcol, lane);
             TL y = lane < wb ? (TL)w[f + cb + lane] : TL(0);
 #pragma unroll
             for (int r = kT - 1; r > 0; --r) {
@@ -488,7 +529,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_wide(DevSym d, const int32_t* 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_bwd_wide(DevSym d, const int32_t* __restrict__ items, int b,
+// (at most 128 registers: its CTAs must fit beside a variance kernel's on one SM, since
+// the two run concurrently on two streams)
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_wide(DevSym d, const int32_t* __restrict__ items, int b,
                                                        const float* __restrict__ L, WideArgs wa,
                                                        double* __restrict__ w, double* __restrict__ x, Strides bs) {
     const int band = blockIdx.y;
@@ -562,7 +605,10 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
                                                         int nb, int* cnt, int cstride, const TL* __restrict__ L,
                                                         const double* __restrict__ D, double* w, double* z, double* x,
                                                         DevStatus* status, Strides bs, uint32_t wait_limit) {
+    // small shared memory: many CTAs of this kernel share an SM, each running short tasks
+    constexpr int kXsDag = 512;
     __shared__ TL xb[kT];
+    __shared__ TL xs[kXsDag];
     __shared__ int64_t s_t;
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -631,12 +677,18 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             TL acc[kPer];
 #pragma unroll
             for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
-            for (int64_t r = k + lane; r < m; r += 32) {
-                const TL xr = (TL)__ldcg(xv + rows[r]);
+            for (int64_t t0 = k; t0 < m; t0 += kXsDag) {
+                const int64_t t1 = m < t0 + kXsDag ? m : t0 + kXsDag;
+                __syncthreads();
+                gather_x<true>(xs, xv, rows, t0, t1);
+                __syncthreads();
+                for (int64_t r = t0 + lane; r < t1; r += 32) {
+                    const TL xr = xs[r - t0];
 #pragma unroll
-                for (int q = 0; q < kPer; ++q) {
-                    const int c = warp + kWarps * q;
-                    if (c < nc) acc[q] += P[r + (int64_t)(c0 + c) * m] * xr;
+                    for (int q = 0; q < kPer; ++q) {
+                        const int c = warp + kWarps * q;
+                        if (c < nc) acc[q] += P[r + (int64_t)(c0 + c) * m] * xr;
+                    }
                 }
             }
 #pragma unroll

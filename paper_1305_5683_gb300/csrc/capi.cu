@@ -278,6 +278,7 @@ int ensure_device(spi_ctx* c) {
     }
     CK(diag_kernel_setup(512, c->diag_smem_pad));
     CK(factor_kernel_setup());
+    CK(solve_kernel_setup());
     if (mixed_of(c) && !c->opt.pivoting && c->opt.diag_tc_min_pivots >= 0) {
         build_diag_tc(S, c->opt.diag_tc_min_pivots > 0 ? c->opt.diag_tc_min_pivots : kDiagTcMinPivots, c->dtc_h);
         DevDiagTc& t = c->dtc;

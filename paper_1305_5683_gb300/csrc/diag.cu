@@ -515,8 +515,13 @@ cudaError_t diag_kernel_setup(int B, size_t smem_min) {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max(diag_smem_bytes<double>(B), smem_min));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_diag_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)std::max(diag_f32_smem_bytes((B + 7) & ~7), smem_min));
+    e = cudaFuncSetAttribute(k_diag_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)std::max(diag_f32_smem_bytes((B + 7) & ~7), smem_min));
+    // the largest shared-memory carveout, as the solve kernels that run beside them
+    const int pref = (int)cudaSharedmemCarveoutMaxShared;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_diag_inv_f32, cudaFuncAttributePreferredSharedMemoryCarveout, pref);
+    return e;
 }
 
 void launch_diag_inverse(const DevSym& d, const DevDiagPlan& p, const double* L, const double* D, double* out,

@@ -682,6 +682,9 @@ __global__ void __launch_bounds__(kDtRoles, 1)
 cudaError_t diag_tc_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_diag_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDtSmem2);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_diag_inv_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_diag_tinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTinvSmem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_diag_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPackSmem);

@@ -805,6 +805,29 @@ void launch_solve_dag(const DevSym& d, const DagTask* tasks, int ntasks, int* co
                                                     lim);
 }
 
+// The solve runs on one stream while the variance kernels of the same factor run on
+// another, and a variance CTA takes most of an SM's shared memory.  The solve kernels
+// state the same (largest) shared-memory carveout preference as the variance kernels,
+// so that an SM configured for a variance CTA can take theirs beside it (their shared
+// memory and registers fit in what a variance CTA leaves).
+cudaError_t solve_kernel_setup() {
+    const int pref = (int)cudaSharedmemCarveoutMaxShared;
+    const cudaFuncAttribute a = cudaFuncAttributePreferredSharedMemoryCarveout;
+    const void* fns[] = {
+        (const void*)k_fwd_step<float>,  (const void*)k_fwd_step<double>,  (const void*)k_bwd_init<float>,
+        (const void*)k_bwd_init<double>, (const void*)k_bwd_step<float>,  (const void*)k_bwd_step<double>,
+        (const void*)k_fwd_level<float>, (const void*)k_fwd_level<double>, (const void*)k_bwd_level<float>,
+        (const void*)k_bwd_level<double>, (const void*)k_fwd_wide,       (const void*)k_bwd_wide,
+        (const void*)k_solve_dag<float>, (const void*)k_solve_dag<double>, (const void*)k_sym_residual,
+        (const void*)k_norms2,           (const void*)k_axpy,             (const void*)k_permute_in,
+        (const void*)k_permute_out};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, a, pref);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t solve_dag_grid(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);

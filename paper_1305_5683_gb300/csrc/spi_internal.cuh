@@ -156,6 +156,7 @@ bool fused_legal(int64_t m, int64_t k);
 // group launched on its own (the autotuner's plans)
 void build_factor_plan(const Symbolic& S, FactorPlan& F, bool tensor_cores, const FactorChoice& ch, bool markers);
 cudaError_t factor_kernel_setup();
+cudaError_t solve_kernel_setup();
 
 struct SolvePlan {
     std::vector<int32_t> fwd_items;  // pairs (supernode, row chunk)

@@ -508,14 +508,23 @@ __global__ void __launch_bounds__(kThreads) k_fwd_wide(DevSym d, const int32_t* 
     const int cb = b * kW, wb = min(kW, k - cb);
     const float* X = wa.xinv + band * wa.xband + (int64_t)(wa.xptr[s] + b) * (kW * kW);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kRowsPerWarp = kW / (kThreads / 32);
+    // x_b[r] = sum_c X[r][c] w[c]: a warp per row (rows warp + 8 q), 16-byte loads of the
+    // row, all of the warp's rows loaded before the reductions
+    float4 xr[kRowsPerWarp];
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q)
+        xr[q] = *reinterpret_cast<const float4*>(X + (warp + (kThreads / 32) * q) * kW + 4 * lane);
     if (tid < kW) wv[tid] = tid < wb ? (float)w[f + cb + tid] : 0.f;
     __syncthreads();
-    // x_b[r] = sum_c X[r][c] w[c]: a warp per row, 16-byte loads of the row
-    for (int r = warp; r < kW; r += kThreads / 32) {
-        const float4 xr = *reinterpret_cast<const float4*>(X + r * kW + 4 * lane);
-        float v = xr.x * wv[4 * lane] + xr.y * wv[4 * lane + 1] + xr.z * wv[4 * lane + 2] + xr.w * wv[4 * lane + 3];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) xb[r] = v;
+    {
+        const float w0 = wv[4 * lane], w1 = wv[4 * lane + 1], w2 = wv[4 * lane + 2], w3 = wv[4 * lane + 3];
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            float v = xr[q].x * w0 + xr[q].y * w1 + xr[q].z * w2 + xr[q].w * w3;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) xb[warp + (kThreads / 32) * q] = v;
+        }
     }
     __syncthreads();
     if (chunk == 0 && tid < wb) z[f + cb + tid] = xb[tid];
@@ -523,6 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_wide(DevSym d, const int32_t* 
     const int64_t r1 = m < r0 + kFwdRowsW ? m : r0 + kFwdRowsW;
     for (int64_t r = r0 + tid; r < r1; r += kThreads) {
         float acc = 0.f;
+#pragma unroll 16
         for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
         if (r < k) w[f + r] -= acc;
         else atomicAdd(w + rows[r], -(double)acc);
@@ -546,13 +556,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_wide(DevSym d, const int32_
     const int cb = b * kW, wb = min(kW, k - cb);
     const float* X = wa.xinv + band * wa.xband + (int64_t)(wa.xptr[s] + b) * (kW * kW);
     const int tid = threadIdx.x;
+    __shared__ float part[kW];
     if (tid < kW) yv[tid] = tid < wb ? (float)w[f + cb + tid] : 0.f;
     __syncthreads();
-    // x_b[c] = sum_{r >= c} X[r][c] y[r]: thread c takes column c (coalesced over c)
-    if (tid < kW) {
+    // x_b[c] = sum_r X[r][c] y[r] (X is zero above its diagonal): column c by threads c
+    // (rows [0, 64)) and c + 128 (rows [64, 128)), coalesced over c, 16 loads in flight
+    static_assert(kThreads == 2 * kW, "two threads per column of the diagonal tile");
+    {
+        const int c = tid % kW, h = tid / kW;
         float v = 0.f;
-        for (int r = tid; r < kW; ++r) v += X[r * kW + tid] * yv[r];
-        xb[tid] = v;
+#pragma unroll 16
+        for (int r = 64 * h; r < 64 * h + 64; ++r) v += X[r * kW + c] * yv[r];
+        if (h == 1) part[c] = v;
+        __syncthreads();
+        if (h == 0) xb[c] = v + part[c];
     }
     __syncthreads();
     if (chunk == 0 && tid < wb) x[f + cb + tid] = xb[tid];

@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_step(DevSym d, const int32_t* 
     const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
     for (int64_t r = r0 + tid; r < r1; r += kThreads) {
         TL acc = 0;
+#pragma unroll 8
         for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
         if (r < k) w[f + r] -= acc;
         else atomicAdd(w + rows[r], -(double)acc);
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_init(DevSym d, const int32_t* 
         __syncthreads();
         gather_x<false>(xs, x, rows, t0, t1);
         __syncthreads();
+#pragma unroll 4
         for (int64_t t = t0 + lane; t < t1; t += 32) {
             const TL xv = xs[t - t0];
 #pragma unroll
@@ -684,6 +686,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
             const int64_t r1 = (m < r0 + kFwdRows) ? m : r0 + kFwdRows;
             for (int64_t r = r0 + tid; r < r1; r += kThreads) {
                 TL acc = 0;
+#pragma unroll 8
                 for (int c = 0; c < wb; ++c) acc += P[r + (int64_t)(cb + c) * m] * xb[c];
                 if (r < k) wb_[f + r] = __ldcg(wb_ + f + r) - acc;
                 else atomicAdd(wb_ + rows[r], -(double)acc);
@@ -699,6 +702,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_dag(DevSym d, const DagTask*
                 __syncthreads();
                 gather_x<true>(xs, xv, rows, t0, t1);
                 __syncthreads();
+#pragma unroll 4
                 for (int64_t r = t0 + lane; r < t1; r += 32) {
                     const TL xr = xs[r - t0];
 #pragma unroll
